@@ -1,0 +1,161 @@
+"""Pins of the FP64 oracle's loss, gradient, spectral method and GD (Sec. II-B, IV).
+
+The gradient is pinned by central finite differences, the spectral method by
+the leading eigenvector of the explicitly formed covariance matrix (a library
+eigensolver on a matrix the oracle never forms), GD by exact recovery on
+noiseless tiny problems, and the metrics by brute force over the global phase.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_claims.json")
+
+
+def _problem(seed, n, alpha, L, signal="gaussian"):
+    m = int(round(alpha * n))
+    theta = S.phases(seed, L, m)
+    x = S.signal_gaussian(seed, 1, n) if signal == "gaussian" else S.signal_amplitude_phase(seed, 1, n)
+    fwd, adj = O.structured_ops(theta, n, m)
+    y = np.abs(fwd(x)) ** 2
+    return theta, x, y, fwd, adj, m
+
+
+def test_gradient_matches_central_differences():
+    """dL/dRe x_k = 2 Re g_k and dL/dIm x_k = 2 Im g_k, g = 2 A^H((|Ax|^2 - y) Ax)."""
+    n, m = 8, 32
+    theta = S.phases(1, 2, m)
+    fwd, adj = O.structured_ops(theta, n, m)
+    x_true = S.signal_gaussian(1, 1, n)
+    y = np.abs(fwd(x_true)) ** 2
+    x = S.signal_gaussian(2, 1, n)
+    _, g = O.loss_and_grad(x, y, fwd, adj)
+    h = 1e-6
+    for k in range(n):
+        for direction, part in ((1.0, np.real), (1j, np.imag)):
+            xp = x.copy()
+            xm = x.copy()
+            xp[0, k] += h * direction
+            xm[0, k] -= h * direction
+            fd = (O.intensity_loss(fwd(xp), y)[0] - O.intensity_loss(fwd(xm), y)[0]) / (2 * h)
+            assert np.isclose(fd, 2 * part(g[0, k]), rtol=1e-6, atol=1e-7)
+
+
+def test_loss_is_brute_force_sum():
+    n, m = 6, 24
+    theta = S.phases(4, 2, m)
+    A = O.dense_structured_matrix(theta, n, m)
+    x = S.signal_gaussian(4, 1, n)[0]
+    y = np.linspace(0.0, 1.0, m)
+    expect = 0.0
+    for i in range(m):
+        zi = sum(A[i, j] * x[j] for j in range(n))
+        expect += (abs(zi) ** 2 - y[i]) ** 2
+    assert np.isclose(O.intensity_loss(O.forward(x, theta, m), y), expect, rtol=1e-12)
+
+
+def test_gradient_vanishes_at_truth_and_loss_is_phase_blind():
+    theta, x, y, fwd, adj, m = _problem(3, 16, 4, 2)
+    loss, g = O.loss_and_grad(x, y, fwd, adj)
+    assert loss[0] < 1e-25 and np.max(np.abs(g)) < 1e-12
+    x2 = S.signal_gaussian(9, 1, 16)
+    l1 = O.intensity_loss(fwd(x2), y)
+    l2 = O.intensity_loss(fwd(np.exp(0.7j) * x2), y)
+    assert np.allclose(l1, l2, rtol=1e-12)
+
+
+def test_spectral_weights_closed_form():
+    y = np.array([[0.0, 0.5, 1.0, 2.0, 4.5]])  # sum 8, m 5 -> y_hat = 5y/8
+    yhat = 5 * y / 8
+    assert np.allclose(O.spectral_weights(y, "identity"), yhat)
+    t = O.spectral_weights(y, "optimal", lam=-1.0)
+    # y_hat = [0, 0.3125, 0.625, 1.25, 2.8125]: 1 - 1/y_hat = [-inf, -2.2, -0.6, 0.2, 0.6444]
+    assert np.allclose(t, [[-1.0, -1.0, -0.6, 0.2, 1 - 1 / 2.8125]])
+    assert np.isclose(O.spectral_weights(y, "identity").mean(), 1.0)
+    with pytest.raises(ValueError):
+        O.spectral_weights(y, "nope")
+
+
+@pytest.mark.parametrize("mode,lam", [("identity", -1.0), ("optimal", -1.0), ("optimal", -0.3)])
+def test_power_iteration_reaches_top_eigenvector(mode, lam):
+    """The iterate approaches the leading eigenvector of the explicit n x n matrix
+    M = A^H diag(T) A (Eq. 3) within the power-iteration error bound
+    tan(angle_T) <= tan(angle_0) * rho^T, rho = max_{i>=2}|mu_i + s| / (mu_1 + s)."""
+    n, m, L = 24, 96, 2
+    theta, x, y, fwd, adj, _ = _problem(5, n, 4, L)
+    A = O.dense_structured_matrix(theta, n, m)
+    w = O.spectral_weights(y, mode, lam)[0]
+    M = A.conj().T @ (w[:, None] * A)
+    mu, V = np.linalg.eigh(M)
+    u1 = V[:, -1]
+    s = 0.0 if mode == "identity" else -2.0 * lam
+    rho = np.max(np.abs(mu[:-1] + s)) / (mu[-1] + s)
+    assert rho < 1
+    v0 = S.start_vector(5, 1, n)
+    c0 = abs(np.vdot(u1, v0[0])) / np.linalg.norm(v0)
+    tan0 = np.sqrt(1 - c0 ** 2) / c0
+    for T in (5, 40, 200):
+        xs = O.spectral_init(y, v0, fwd, adj, T, mode=mode, lam=lam)[0]
+        assert np.isclose(np.linalg.norm(xs), np.sqrt(y.sum()), rtol=1e-12)
+        v = xs / np.linalg.norm(xs)
+        c = abs(np.vdot(u1, v))
+        sinT = np.linalg.norm(v - u1 * np.vdot(u1, v))  # accurate for tiny angles
+        assert sinT / c <= tan0 * rho ** T * (1 + 1e-6) + 1e-12
+
+
+def test_gd_recovers_noiseless_tiny_problem():
+    """GD from the spectral start recovers x up to a global phase at alpha = 4,
+    L = 2 (full recovery by alpha ~ 3 per Sec. IV-A), with a decreasing loss."""
+    errs = []
+    for seed in range(6):
+        theta, x, y, fwd, adj, m = _problem(seed, 32, 4, 2)
+        x0 = O.spectral_init(y, S.start_vector(seed, 1, 32), fwd, adj, 50, mode="optimal")
+        xT, hist = O.gradient_descent(x0, y, fwd, adj, 3000, mu0=0.1)
+        errs.append(O.relative_error_global_phase(xT, x)[0])
+        assert hist[-1, 0] < 1e-12 * hist[0, 0]
+        assert np.all(np.diff(hist[:, 0]) <= 1e-12 * hist[0, 0])
+    assert np.max(errs) < 1e-8
+
+
+def test_metrics_brute_force_over_phase():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(20) + 1j * rng.standard_normal(20)
+    xh = x + 0.3 * (rng.standard_normal(20) + 1j * rng.standard_normal(20))
+    xh = np.exp(1.1j) * xh
+    phis = np.linspace(0, 2 * np.pi, 200001)
+    brute = min(np.linalg.norm(np.exp(1j * p) * xh - x) for p in phis[::100])
+    fine = np.min(np.linalg.norm(np.exp(1j * phis[:, None]) * xh[None] - x[None], axis=1))
+    r = O.relative_error_global_phase(xh[None], x[None])[0]
+    assert r <= brute / np.linalg.norm(x) + 1e-12
+    assert np.isclose(r, fine / np.linalg.norm(x), rtol=1e-6)
+    assert np.isclose(O.cosine_similarity(np.exp(2.0j) * 3 * x[None], x[None])[0], 1.0)
+    assert np.isclose(O.relative_error_global_phase(np.exp(2.0j) * x[None], x[None])[0], 0.0, atol=1e-7)
+    # orthogonal estimate: cosine 0
+    e1 = np.zeros(4, complex); e1[0] = 1
+    e2 = np.zeros(4, complex); e2[1] = 1j
+    assert O.cosine_similarity(e1[None], e2[None])[0] == 0.0
+
+
+def test_paper_claims_layers_and_alpha():
+    """Qualitative claims of Sec. IV (recorded in tests/golden/paper_claims.json):
+    two layers beat one by a wide margin, three layers are close to two, and
+    accuracy grows with alpha. Spectral method only, as in Fig. 3."""
+    claims = json.load(open(GOLDEN))
+    assert "two_layers_beat_one" in claims and "monotone_in_alpha" in claims
+
+    def cos(n, alpha, L, seed):
+        theta, x, y, fwd, adj, _ = _problem(seed, n, alpha, L)
+        xs = O.spectral_init(y, S.start_vector(seed, 1, n), fwd, adj, 300, mode="optimal")
+        return O.cosine_similarity(xs, x)[0]
+
+    seeds = range(6)
+    c = {(a, L): np.mean([cos(64, a, L, s) for s in seeds]) for a in (2, 3, 4) for L in (1, 2, 3)}
+    for a in (3, 4):
+        assert c[(a, 2)] > c[(a, 1)] + 0.25
+        assert abs(c[(a, 3)] - c[(a, 2)]) < 0.1
+    assert c[(2, 2)] < c[(3, 2)] < c[(4, 2)]
