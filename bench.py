@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the structured random phase-retrieval hot path on GB300.
+
+One step = one whole solve of the paper's pipeline (Sec. IV-A) for a batch of
+B independent problems: spectral initialisation by power iteration (Eq. 3-4)
+followed by gradient descent (Eq. 2), every iteration one application of A and
+one of A^H through the CUDA library. Workload: B = 64 signals, n = 2^14
+(128 x 128 image-like signals, amplitude U[0, 1] times a random phase),
+alpha = 4 (m = 2^16), L = 2, noiseless y, 100 power iterations + 500 GD steps.
+
+Prints ONE JSON line (rank 0). `value` counts problem-iterations per second
+(one iteration = one forward + adjoint pair on one problem), summed over all
+ranks; each rank solves its own batch (weak scaling, no collective on the
+data path).
+
+--impl reference times the FP64 CPU oracle instead (the reference arm of this
+comparison), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GD iters/sec (fwd+adj) & HBM GB/s vs peak; speedup over dense i.i.d. at equal error"
+UNIT = "problem-iters/s"
+WORKLOAD = dict(name="structured-L2-n16384-m65536-B64-sp100-gd500", n=2 ** 14, m=2 ** 16, L=2, B=64,
+                spectral_iters=100, gd_iters=500, weight="optimal", lam=-1.0, mu0=0.1, seed=20240905)
+FLUSH_BYTES = 512 << 20  # > 129 MB L2: written between timed steps
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- oracle leg
+def oracle_sample(W, power_iters: int, gd_iters: int, seed: int):
+    """Times the FP64 oracle on one problem of the workload's shape; returns
+    (problem-iterations per second, seconds)."""
+    import oracle as O
+    import synthetic as S
+    n, m, L = W["n"], W["m"], W["L"]
+    theta = S.phases(seed, L, m)
+    fwd, adj = O.structured_ops(theta, n, m)
+    x = S.signal_amplitude_phase(seed, 1, n)
+    y = np.abs(fwd(x)) ** 2
+    v0 = S.start_vector(seed, 1, n)
+    t0 = time.perf_counter()
+    x0 = O.spectral_init(y, v0, fwd, adj, power_iters, mode=W["weight"], lam=W["lam"])
+    O.gradient_descent(x0, y, fwd, adj, gd_iters, mu0=W["mu0"])
+    dt = time.perf_counter() - t0
+    return (power_iters + gd_iters) / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    W = WORKLOAD
+    sp, gd = 2, 20  # bounded sample per step: one problem, 22 iterations
+    for _ in range(args.warmup):
+        oracle_sample(W, sp, gd, W["seed"])
+    total = 0.0
+    for k in range(args.steps):
+        _, dt = oracle_sample(W, sp, gd, W["seed"] + k)
+        total += dt
+    value = args.steps * (sp + gd) / total
+    sample = f"one problem (n={W['n']}, m={W['m']}, L={W['L']}) x {sp} power + {gd} GD iterations per step, numpy FP64"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(W, world),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(W, world):
+    return {"workload": W["name"], "n": W["n"], "m": W["m"], "alpha": W["m"] / W["n"], "L": W["L"],
+            "batch_per_gpu": W["B"], "global_batch": W["B"] * world, "spectral_iters": W["spectral_iters"],
+            "gd_iters": W["gd_iters"], "spectral_weight": f"{W['weight']}(lambda={W['lam']})", "mu0": W["mu0"],
+            "signal": "amplitude U[0,1] x random phase, seeded Philox", "y": "noiseless |Ax|^2",
+            "l2": "flushed between timed steps (512 MiB write)",
+            "parallelism": f"replicas x{world} (independent batches per GPU)"}
+
+
+# ------------------------------------------------------------------ our leg
+def algorithmic_mid_bytes(W):
+    """Compulsory HBM bytes of one middle pass, averaged over the 2L-1 middle
+    passes of one iteration: each reads and writes the batch's exchange buffer
+    (8 B per complex element each way); the diagonal passes read one shared
+    D table (8 m B); the epilogue pass reads y (4 B per element)."""
+    m, B, L = W["m"], W["B"], W["L"]
+    n_mid = 2 * L - 1
+    diag = n_mid - 1
+    total = n_mid * 16 * m * B + diag * 8 * m + 4 * m * B
+    return total / n_mid
+
+
+def iteration_bytes(W):
+    """Compulsory bytes of one iteration (all 2L+1 passes) for the batch."""
+    m, n, B, L = W["m"], W["n"], W["B"], W["L"]
+    first = 8 * n * B + 8 * m + 8 * m * B          # read x, D_1, write exchange
+    mids = algorithmic_mid_bytes(W) * (2 * L - 1)
+    last = 8 * m * B + 8 * m + 16 * n * B           # read exchange, D_1, read+write x
+    return first + mids + last
+
+
+def traffic_from_profile(name: str):
+    """dram bytes per launch recorded by an ncu summary under profiles/, if the
+    kernel source has not changed since (hash recorded in the summary)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", name)
+    src = os.path.join(ROOT, "paper_2409_05734_gb300", "csrc", "fourstep.cu")
+    if not os.path.exists(path):
+        return None
+    want = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("fourstep.cu sha256[:16]") != want:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (the product path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    from paper_2409_05734_gb300 import Plan, buildlib, _lib
+    import synthetic as S
+    buildlib.build()
+    lib = _lib.load()
+    W = WORKLOAD
+    n, m, L, B = W["n"], W["m"], W["L"], W["B"]
+    seed = W["seed"] + 1000 * rank
+    plan = Plan(n, m, L, seed)
+    plan.reserve(B)
+    dev = torch.device("cuda", local)
+    x_true = torch.from_numpy(S.signal_amplitude_phase(seed, B, n)).to(torch.complex64).to(dev)
+    y = (plan.forward(x_true).abs() ** 2).contiguous()
+    v0 = torch.from_numpy(S.start_vector(seed, B, n)).to(torch.complex64).to(dev)
+    x = torch.empty_like(v0)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(y_in, v_in, x_out):
+        plan.spectral_init(y_in, v_in, W["spectral_iters"], weight=W["weight"], lam=W["lam"], out=x_out)
+        plan.gd_solve(y_in, x_out, W["gd_iters"], mu0=W["mu0"])
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(y, v0, x)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = lib.sr_kernel_launches()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(y, v0, x)
+        e1.record(stream)
+        evs.append((e0, e1))
+    barrier()
+    launches = lib.sr_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms_local = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    ms_step = max_over_ranks(ms_local)
+    iters = W["spectral_iters"] + W["gd_iters"]
+    value = world * B * iters / (ms_step / 1e3)
+
+    # accuracy of the solve (relative error up to a global phase, cosine similarity)
+    inner = torch.sum(torch.conj(x) * x_true, dim=1, keepdim=True)
+    phase = inner / inner.abs().clamp_min(1e-30)
+    rel_err = (torch.linalg.vector_norm(phase * x - x_true, dim=1) / torch.linalg.vector_norm(x_true, dim=1))
+    cos = inner.abs()[:, 0] / (torch.linalg.vector_norm(x, dim=1) * torch.linalg.vector_norm(x_true, dim=1))
+
+    # end to end through the public API with host buffers: pinned H2D of y and v0,
+    # the solve, D2H of the estimate, every step
+    y_h = y.cpu().pin_memory()
+    v0_h = v0.cpu().pin_memory()
+    x_h = torch.empty(x.shape, dtype=x.dtype).pin_memory()
+    y_d = torch.empty_like(y)
+    v0_d = torch.empty_like(v0)
+    x_d = torch.empty_like(x)
+    for _ in range(args.warmup):
+        y_d.copy_(y_h, non_blocking=True)
+        v0_d.copy_(v0_h, non_blocking=True)
+        step(y_d, v0_d, x_d)
+        x_h.copy_(x_d, non_blocking=True)
+    barrier()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        y_d.copy_(y_h, non_blocking=True)
+        v0_d.copy_(v0_h, non_blocking=True)
+        step(y_d, v0_d, x_d)
+        x_h.copy_(x_d, non_blocking=True)
+        e1.record(stream)
+        evs.append((e0, e1))
+    barrier()
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / args.steps)
+    e2e = {"value": world * B * iters / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": y.numel() * 4 + v0.numel() * 8, "d2h_bytes_per_step": x.numel() * 8}
+
+    # roofline of the dominant kernel: one extra step with per-pass event timing
+    flush.zero_()
+    torch.cuda.synchronize()
+    _lib.check(lib.sr_plan_set_timing(plan._h, 1), "sr_plan_set_timing")
+    step(y, v0, x)
+    import ctypes as C
+    ms3 = (C.c_double * 3)()
+    cnt3 = (C.c_int64 * 3)()
+    _lib.check(lib.sr_plan_get_timing(plan._h, ms3, cnt3), "sr_plan_get_timing")
+    lib.sr_plan_set_timing(plan._h, 0)
+    pass_ms = {k: (ms3[i] / cnt3[i] if cnt3[i] else None) for i, k in enumerate(("first", "mid", "last"))}
+    share_mid = ms3[1] / max(1e-9, ms3[0] + ms3[1] + ms3[2])
+    peak, peak_kind = measured_peaks()
+    mid_bytes = algorithmic_mid_bytes(W)
+    achieved = mid_bytes / (pass_ms["mid"] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_mid (middle four-step pass, lines of 256)", "achieved": achieved,
+                "peak": peak, "peak_kind": peak_kind + " hbm_gbs (copy, burst)", "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_from_profile("k_mid_256_structured_B64_m65536.md"),
+                "algorithmic_bytes_per_launch": mid_bytes, "avg_launch_ms": pass_ms["mid"],
+                "share_of_pass_time": share_mid, "pass_avg_ms": pass_ms,
+                "iteration_gbs": iteration_bytes(W) / (ms_step / 1e3 / iters) / 1e9}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Philox signals; y = |Ax|^2 on device)",
+            "config": config_dict(W, world), "roofline": roofline, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk,
+            "accuracy": {"median_rel_err_global_phase": float(rel_err.median()),
+                         "median_cosine_similarity": float(cos.median())}}
+    if rank == 0 and not args.no_cpu_baseline:
+        sp, gd = 20, 200
+        v, dt = oracle_sample(W, sp, gd, W["seed"])
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"one problem of the workload, {sp} power + {gd} GD iterations, "
+                                          f"numpy FP64 (pocketfft, single thread), {dt:.1f} s"}
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,159 @@
+/*
+ * sr.h -- C ABI of the GB300 library for the structured random phase-retrieval
+ * model of Hu, Tachella, Unser and Dong, "Structured Random Model for Fast and
+ * Robust Phase Retrieval" (arXiv 2409.05734).
+ *
+ * The sensing operator (Sec. III, Eq. 5, oversampling branch alpha = m/n >= 1) is
+ *
+ *     A = F D_L ... F D_1 U,      A in C^{m x n},
+ *
+ * where U zero-pads x in C^n to C^m (x occupies entries 0..n-1), F is the
+ * unitary length-m DFT, F[k, j] = m^{-1/2} exp(-2 pi i j k / m), and
+ * D_l = diag(exp(i theta_l)) with theta_l[k] ~ U[0, 2 pi) (D_1 acts first).
+ * The measurements are y = |A x|^2 (Sec. II-A, Eq. 1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Complex data is interleaved single precision (re, im) = 8 bytes per
+ *   element ("c64"); a batch of B problems is stored problem-major:
+ *   x is c64[B][n], z is c64[B][m], y is float[B][m].
+ * - All array arguments of the compute calls are DEVICE pointers on the
+ *   current CUDA device, owned by the caller, aligned to at least 8 bytes.
+ *   Outputs must not overlap inputs unless a call says so.
+ * - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls
+ *   enqueue their kernels on it and return without synchronising; errors of
+ *   the launches themselves are reported through the return value.
+ * - The plan owns its device tables (diagonals, twiddles) and a workspace for
+ *   up to B_cap problems (2 exchange buffers of B_cap*m c64, a permuted copy
+ *   of y, per-block partial sums). A call with B > B_cap grows the workspace
+ *   (cudaMalloc) first; call sr_plan_reserve() beforehand to keep later calls
+ *   free of allocation. Concurrent calls on one plan must not overlap in time
+ *   (they share the workspace); use one plan per stream.
+ * - Supported sizes: m a power of two with 4 <= m <= 2^24, 1 <= n <= m,
+ *   1 <= L <= 8, 1 <= B <= 65535. Other sizes return SR_ERR_UNSUPPORTED.
+ * - Every call returns SR_OK or an error code; sr_last_error() gives a
+ *   thread-local message for the last failing call on the calling thread.
+ */
+#ifndef SR_H
+#define SR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sr_plan sr_plan; /* opaque, owned by the library */
+
+typedef enum sr_status {
+  SR_OK = 0,
+  SR_ERR_INVALID_ARG = 1,  /* null pointer, B < 1, iters < 0, bad option value */
+  SR_ERR_UNSUPPORTED = 2,  /* size outside the supported set */
+  SR_ERR_OOM = 3,          /* device or host allocation failed */
+  SR_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
+  SR_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+  SR_ERR_NUMERIC = 6       /* non-finite or invalid numeric input */
+} sr_status;
+
+/* Spectral weights T applied to y_hat = m * y / sum(y) (Sec. II-B-2, Eq. 3). */
+typedef enum sr_weight_mode {
+  SR_WEIGHT_IDENTITY = 0, /* T(y_hat) = y_hat: M = A^H diag(y_hat) A, no shift */
+  SR_WEIGHT_OPTIMAL = 1   /* T(y_hat) = max(1 - 1/y_hat, lambda), T = lambda where
+                             y_hat <= 0; shift -2*lambda (Eq. 4) */
+} sr_weight_mode;
+
+typedef struct sr_spectral_opts {
+  int weight_mode; /* sr_weight_mode */
+  float lambda;    /* lower threshold, < 0, used by SR_WEIGHT_OPTIMAL */
+} sr_spectral_opts;
+
+typedef struct sr_gd_opts {
+  float mu0; /* step size is mu = mu0 * m / sum(y) per problem; > 0 */
+} sr_gd_opts;
+
+/* ---- phases (host only; no GPU needed) ------------------------------------
+ * sr_phases: the diffuser phases a plan created with `seed` uses (Sec. III:
+ * theta ~ U[0, 2 pi)). theta[l*m + k] = 2*pi*u with u = (w >> 8) * 2^-24 and
+ * w the first word of Philox4x32-10 (Salmon et al., SC'11) at counter
+ * (k mod 2^32, k div 2^32, l, 1) under key (seed mod 2^32, seed div 2^32).
+ * theta: host double[L*m], caller-owned. Needs L >= 1, m >= 1. */
+sr_status sr_phases(uint64_t seed, int L, int64_t m, double* theta);
+
+/* ---- plan ------------------------------------------------------------------
+ * sr_plan_create: operator A of Sec. III, Eq. 5 for sizes (n, m, L) with the
+ * phases of sr_phases(seed, L, m), on the current CUDA device. Builds the
+ * device tables (D_l = exp(i theta_l)/sqrt(m) rounded to float, twiddles
+ * computed in double and rounded). *out receives the plan; release it with
+ * sr_plan_destroy. */
+sr_status sr_plan_create(int64_t n, int64_t m, int L, uint64_t seed, sr_plan** out);
+sr_status sr_plan_destroy(sr_plan* plan); /* NULL is accepted (no-op) */
+
+/* Copies the plan's phases (double[L*m], host) out / replaces them from host
+ * memory (the diagonal tables are rebuilt synchronously). */
+sr_status sr_plan_get_phases(const sr_plan* plan, double* theta);
+sr_status sr_plan_set_phases(sr_plan* plan, const double* theta);
+
+/* Reports the plan's sizes (any output pointer may be NULL). */
+sr_status sr_plan_info(const sr_plan* plan, int64_t* n, int64_t* m, int* L);
+
+/* Grows the workspace to hold B problems (synchronous cudaMalloc). */
+sr_status sr_plan_reserve(sr_plan* plan, int B);
+
+/* ---- operator applications (Sec. III, Eq. 5) --------------------------------
+ * sr_forward: z = A x.    x: c64[B][n] (input), z: c64[B][m] (output).
+ * sr_adjoint: x = A^H z = U^H D_1^H F^H ... D_L^H F^H z.
+ *             z: c64[B][m] (input), x: c64[B][n] (output). */
+sr_status sr_forward(sr_plan* plan, const void* x, void* z, int B, void* stream);
+sr_status sr_adjoint(sr_plan* plan, const void* z, void* x, int B, void* stream);
+
+/* ---- loss and gradient (Sec. II-B-1, Eq. 2) ----------------------------------
+ * With z = A x and r = |z|^2 - y:
+ *   loss[b] = sum_k r_k^2                   (float[B], device)
+ *   grad    = 2 A^H (r * z)                 (c64[B][n], device)
+ * Eq. 2 prints diag(x); it is read as diag(A x), which makes grad the
+ * Wirtinger derivative dL/d conj(x). x: c64[B][n], y: float[B][m].
+ * loss may be NULL. */
+sr_status sr_loss_grad(sr_plan* plan, const void* x, const float* y, float* loss,
+                       void* grad, int B, void* stream);
+
+/* ---- spectral initialisation (Sec. II-B-2, Eq. 3-4) --------------------------
+ * Power iteration on M = A^H diag(T(y_hat)) A with shift s (0 for the identity
+ * weight, -2*lambda for the optimal weight): v <- v0/||v0||, then `iters`
+ * times u = M v + s v, v = u/||u||; finally x_out = sqrt(sum(y)) * v.
+ * y: float[B][m]; v0: c64[B][n] start vectors (random draws are inputs);
+ * x_out: c64[B][n]; x_out may equal v0. opts may be NULL (identity weight). */
+sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int iters,
+                           const sr_spectral_opts* opts, void* x_out, int B, void* stream);
+
+/* ---- gradient descent (Sec. II-B-1, Sec. IV-A) ------------------------------
+ * `iters` steps x <- x - mu * 2 A^H((|Ax|^2 - y) * Ax), mu = mu0 * m / sum(y),
+ * updating x (c64[B][n], device) in place. loss_hist (float[iters][B],
+ * device) receives the loss at each iterate before its update, or is NULL.
+ * opts may be NULL (mu0 = 0.1). */
+sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters,
+                      const sr_gd_opts* opts, float* loss_hist, int B, void* stream);
+
+/* ---- profiling ------------------------------------------------------------
+ * sr_kernel_launches: number of CUDA kernels this library has launched in the
+ * process so far (all plans, all devices).
+ * sr_plan_set_timing: when enable != 0, every pass kernel the plan launches
+ * afterwards is bracketed by two CUDA events on its stream (a small extra
+ * cost per launch); enable == 0 stops recording.
+ * sr_plan_get_timing: waits for the recorded events, returns the summed
+ * device time (ms) and launch count of each pass class -- index 0 the first
+ * pass of a chain, 1 the middle passes, 2 the last pass -- and clears the
+ * record. ms and count are host arrays of 3 elements (either may be NULL). */
+uint64_t sr_kernel_launches(void);
+sr_status sr_plan_set_timing(sr_plan* plan, int enable);
+sr_status sr_plan_get_timing(sr_plan* plan, double* ms, int64_t* count);
+
+/* ---- errors --------------------------------------------------------------- */
+const char* sr_status_string(sr_status status);
+const char* sr_last_error(void); /* thread-local; "" when none */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SR_H */

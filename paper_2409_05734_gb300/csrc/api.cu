@@ -1,0 +1,631 @@
+// C ABI of the structured random phase-retrieval library (include/sr.h):
+// argument validation, plan construction (host Philox phases, diagonal and
+// twiddle tables computed in double and rounded to float), workspace, and the
+// orchestration of the pass kernels into the operator applications and solver
+// loops of the paper (Sec. II-B, Sec. III).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sr_internal.h"
+
+using sr::Plan;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sr_status fail(sr_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+sr_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(SR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SR_CUDA(call, where)                       \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
+// multiplications with the published round constants and Weyl key increments.
+void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+constexpr uint32_t kStreamTheta = 1;
+
+void gen_phases(uint64_t seed, int L, int64_t m, double* theta) {
+  const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+  for (int l = 0; l < L; ++l) {
+    for (int64_t k = 0; k < m; ++k) {
+      uint32_t c[4] = {(uint32_t)((uint64_t)k & 0xFFFFFFFFu), (uint32_t)((uint64_t)k >> 32), (uint32_t)l,
+                       kStreamTheta};
+      philox4x32_10(c, k0, k1);
+      const double u = (double)(c[0] >> 8) * 0x1p-24;
+      theta[(size_t)l * m + k] = 2.0 * M_PI * u;
+    }
+  }
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int64_t v) {
+  int r = 0;
+  while ((int64_t(1) << r) < v) ++r;
+  return r;
+}
+
+sr_status check_sizes(int64_t n, int64_t m, int L) {
+  if (L < 1 || L > 8) return fail(SR_ERR_UNSUPPORTED, "L must be in [1, 8]");
+  if (!is_pow2(m) || m < 4 || m > (int64_t(1) << 24))
+    return fail(SR_ERR_UNSUPPORTED, "m must be a power of two in [4, 2^24]");
+  if (n < 1 || n > m) return fail(SR_ERR_UNSUPPORTED, "n must satisfy 1 <= n <= m");
+  return SR_OK;
+}
+
+sr_status check_device(const Plan* p) {
+  int dev = -1;
+  SR_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev != p->device) return fail(SR_ERR_INVALID_ARG, "current CUDA device differs from the plan's device");
+  return SR_OK;
+}
+
+template <typename T>
+sr_status dalloc(T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) return SR_OK;
+  cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(SR_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return SR_OK;
+}
+
+void free_workspace(Plan* p) {
+  cudaFree(p->d_e0);
+  cudaFree(p->d_e1);
+  cudaFree(p->d_yp);
+  cudaFree(p->d_part);
+  cudaFree(p->d_scal);
+  p->d_e0 = p->d_e1 = nullptr;
+  p->d_yp = nullptr;
+  p->d_part = p->d_scal = nullptr;
+  p->B_cap = 0;
+}
+
+// Size of one bank of per-CTA partial sums per problem.
+int part_stride(const Plan& p) {
+  const sr::LineGeom gx = sr::geom_for(p, sr::kLayoutX), gy = sr::geom_for(p, sr::kLayoutY);
+  return std::max(std::max(gx.cpp, gy.cpp), 64);
+}
+constexpr int kPartBanks = 4;  // 0,1: power-iteration norms (ping-pong), 2: loss, 3: sums
+
+sr_status ensure_workspace(Plan* p, int B) {
+  if (B <= p->B_cap) return SR_OK;
+  free_workspace(p);
+  const size_t bm = (size_t)B * (size_t)p->m;
+  sr_status st;
+  if ((st = dalloc(&p->d_e0, bm)) != SR_OK || (st = dalloc(&p->d_e1, bm)) != SR_OK ||
+      (st = dalloc(&p->d_yp, bm)) != SR_OK ||
+      (st = dalloc(&p->d_part, (size_t)kPartBanks * B * part_stride(*p))) != SR_OK ||
+      (st = dalloc(&p->d_scal, (size_t)4 * B)) != SR_OK) {
+    free_workspace(p);
+    return st;
+  }
+  p->B_cap = B;
+  return SR_OK;
+}
+
+float* part_bank(const Plan& p, int bank, int B) { return p.d_part + (size_t)bank * B * part_stride(p); }
+
+// Rebuilds the device diagonal tables from p->theta: D_l = exp(i theta_l)/sqrt(m)
+// (the 1/sqrt(m) of each unitary F folded in), permuted into the line layout of
+// the pass that applies D_l.
+sr_status upload_diagonals(Plan* p) {
+  const int64_t m = p->m;
+  const double scale = 1.0 / std::sqrt((double)m);
+  std::vector<float2> host((size_t)p->L * m);
+  for (int d = 0; d < p->L; ++d) {
+    const sr::LineGeom g = sr::geom_for(*p, sr::diag_layout(d));
+    const double* th = p->theta.data() + (size_t)d * m;
+    float2* out = host.data() + (size_t)d * m;
+    for (int gl = 0; gl < g.nl; ++gl)
+      for (int f = 0; f < g.ell; ++f) {
+        const double t = th[(size_t)f * g.nl + gl];
+        out[(size_t)gl * g.ell + f] = make_float2((float)(std::cos(t) * scale), (float)(std::sin(t) * scale));
+      }
+  }
+  SR_CUDA(cudaMemcpy(p->d_dp, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice),
+          "cudaMemcpy(diagonals)");
+  return SR_OK;
+}
+
+float2 root_of_unity(int64_t j, int64_t N) {
+  // exp(-2 pi i j / N) in double, rounded to float
+  const double a = -kTwoPi * (double)j / (double)N;
+  return make_float2((float)std::cos(a), (float)std::sin(a));
+}
+
+sr_status upload_twiddles(Plan* p) {
+  std::vector<float2> twl(p->lmax);
+  for (int j = 0; j < p->lmax; ++j) twl[j] = root_of_unity(j, p->lmax);
+  const int64_t nlo = int64_t(1) << p->tw_shift, nhi = (p->m + nlo - 1) / nlo;
+  std::vector<float2> lo(nlo), hi(nhi);
+  for (int64_t j = 0; j < nlo; ++j) lo[j] = root_of_unity(j, p->m);
+  for (int64_t j = 0; j < nhi; ++j) hi[j] = root_of_unity(j * nlo, p->m);
+  sr_status st;
+  if ((st = dalloc(&p->d_twl, twl.size())) != SR_OK || (st = dalloc(&p->d_tw_lo, lo.size())) != SR_OK ||
+      (st = dalloc(&p->d_tw_hi, hi.size())) != SR_OK)
+    return st;
+  SR_CUDA(cudaMemcpy(p->d_twl, twl.data(), twl.size() * sizeof(float2), cudaMemcpyHostToDevice), "cudaMemcpy");
+  SR_CUDA(cudaMemcpy(p->d_tw_lo, lo.data(), lo.size() * sizeof(float2), cudaMemcpyHostToDevice), "cudaMemcpy");
+  SR_CUDA(cudaMemcpy(p->d_tw_hi, hi.data(), hi.size() * sizeof(float2), cudaMemcpyHostToDevice), "cudaMemcpy");
+  return SR_OK;
+}
+
+// ------------------------------------------------------------ chains of DFTs
+
+struct MidOp {
+  int op = sr::kOpNone;
+  int d = 0;  // diagonal index for the diagonal operations
+};
+
+struct Chain {
+  int nfft = 0;
+  int s0 = 0;                 // decomposition parity of DFT 0
+  int dir[16] = {0};
+  int first_op = sr::kOpNone; // kOpNone or kOpDiag (D_1)
+  MidOp mid[16];              // mid[k], k = 1..nfft-1
+  int last_op = sr::kOpNone;  // kOpNone or kOpDiagConj (D_1^H)
+  // input of the first pass
+  const float2* xin = nullptr;
+  int n_in = 0;
+  const float* norm_in = nullptr;
+  int norm_in_count = 0;
+  // output of the last pass
+  float2* xout = nullptr;
+  int n_out = 0;
+  int out_mode = sr::kOutStore;
+  const float* mu = nullptr;
+  float shift = 0.f;
+  float* spec_part_out = nullptr;
+  float* loss_out = nullptr;
+  // epilogue data
+  const float* yp = nullptr;
+  const float* sumy = nullptr;
+  float lam = 0.f;
+  int weight_mode = SR_WEIGHT_IDENTITY;
+  float* loss_part = nullptr;
+};
+
+sr::PassArgs base_args(const Plan& p) {
+  sr::PassArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.m = (int)p.m;
+  a.twl = p.d_twl;
+  a.tw_hi = p.d_tw_hi;
+  a.tw_lo = p.d_tw_lo;
+  a.tw_shift = p.tw_shift;
+  return a;
+}
+
+// Event pair around one pass launch when the plan records timing.
+struct PassTimer {
+  Plan* p;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t end = nullptr;
+  PassTimer(const Plan& plan, int k, cudaStream_t st) : p(const_cast<Plan*>(&plan)), cls(k), s(st) {
+    if (!p->timing) return;
+    std::vector<cudaEvent_t>& v = p->ev[cls];
+    const size_t i = p->ev_used[cls];
+    while (v.size() < i + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      v.push_back(e);
+    }
+    cudaEventRecord(v[i], s);
+    end = v[i + 1];
+    p->ev_used[cls] = i + 2;
+  }
+  ~PassTimer() {
+    if (end) cudaEventRecord(end, s);
+  }
+};
+
+sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
+  const sr::PassArgs base = base_args(p);
+  float2* cur = p.d_e0;
+  float2* nxt = p.d_e1;
+  int loss_cpp = 0;
+  // FIRST
+  {
+    sr::PassArgs a = base;
+    a.out_dir = c.dir[0];
+    a.xin = c.xin;
+    a.n_in = c.n_in;
+    a.norm_in = c.norm_in;
+    a.norm_in_count = c.norm_in_count;
+    a.op = c.first_op;
+    a.dp = p.d_dp;
+    a.eout = cur;
+    PassTimer tm(p, 0, s);
+    SR_CUDA(sr::launch_first(p, sr::s1_layout(c.s0), a, B, s), "launch(first pass)");
+  }
+  for (int k = 1; k < c.nfft; ++k) {
+    const sr::Layout lay = sr::s2_layout((c.s0 + k - 1) % 2);
+    sr::PassArgs a = base;
+    a.in_dir = c.dir[k - 1];
+    a.out_dir = c.dir[k];
+    a.ein = cur;
+    a.eout = nxt;
+    a.op = c.mid[k].op;
+    a.dp = p.d_dp + (size_t)c.mid[k].d * p.m;
+    if (a.op == sr::kOpGdEpilogue) {
+      a.yp = c.yp;
+      a.part_out = c.loss_part;
+      loss_cpp = sr::geom_for(p, lay).cpp;
+    } else if (a.op == sr::kOpSpecEpilogue) {
+      a.yp = c.yp;
+      a.sumy = c.sumy;
+      a.lam = c.lam;
+      a.weight_mode = c.weight_mode;
+    }
+    {
+      PassTimer tm(p, 1, s);
+      SR_CUDA(sr::launch_mid(p, lay, a, B, s), "launch(mid pass)");
+    }
+    std::swap(cur, nxt);
+  }
+  // LAST
+  {
+    sr::PassArgs a = base;
+    a.in_dir = c.dir[c.nfft - 1];
+    a.ein = cur;
+    a.op = c.last_op;
+    a.dp = p.d_dp;
+    a.xout = c.xout;
+    a.n_out = c.n_out;
+    a.out_mode = c.out_mode;
+    a.mu = c.mu;
+    a.shift = c.shift;
+    a.norm_in = c.norm_in;
+    a.norm_in_count = c.norm_in_count;
+    a.part_out = c.spec_part_out;
+    a.loss_part = c.loss_part;
+    a.loss_cpp = loss_cpp;
+    a.loss_out = c.loss_out;
+    PassTimer tm(p, 2, s);
+    SR_CUDA(sr::launch_last(p, sr::s2_layout((c.s0 + c.nfft - 1) % 2), a, B, s), "launch(last pass)");
+  }
+  return SR_OK;
+}
+
+// The 2L DFTs of one gradient or power-iteration step: A (D_1 first), then A^H.
+Chain round_trip_chain(const Plan& p, int epilogue_op) {
+  Chain c;
+  const int L = p.L;
+  c.nfft = 2 * L;
+  c.s0 = 0;
+  for (int k = 0; k < L; ++k) c.dir[k] = -1;
+  for (int k = L; k < 2 * L; ++k) c.dir[k] = +1;
+  c.first_op = sr::kOpDiag;  // D_1
+  for (int k = 1; k < L; ++k) c.mid[k] = MidOp{sr::kOpDiag, k};  // D_{k+1}
+  c.mid[L] = MidOp{epilogue_op, 0};
+  for (int k = L + 1; k < 2 * L; ++k) c.mid[k] = MidOp{sr::kOpDiagConj, 2 * L - k};  // D_{2L-k+1}^H
+  c.last_op = sr::kOpDiagConj;  // D_1^H
+  return c;
+}
+
+// Layout of the epilogue pass (step 2 of DFT L-1), used for the permuted y.
+sr::LineGeom epilogue_geom(const Plan& p) { return sr::geom_for(p, sr::s2_layout((p.L - 1) % 2)); }
+
+sr_status prepare_y(Plan* p, const float* y, int B, float mu0, cudaStream_t s) {
+  const sr::LineGeom ge = epilogue_geom(*p);
+  SR_CUDA(sr::launch_permute_real(y, p->d_yp, B, (int)p->m, ge.nl, ge.ell, s), "launch(permute y)");
+  const int chunks = (int)std::min<int64_t>(64, (p->m + 4095) / 4096);
+  float* part = part_bank(*p, 3, B);
+  SR_CUDA(sr::launch_sum_rows(y, B, (int)p->m, part, chunks, s), "launch(sum y)");
+  SR_CUDA(sr::launch_finish_scalars(part, chunks, B, mu0, (int)p->m, p->d_scal, p->d_scal + B, s),
+          "launch(step size)");
+  return SR_OK;
+}
+
+sr_status check_plan_call(sr_plan* plan, int B) {
+  if (!plan) return fail(SR_ERR_INVALID_ARG, "plan is NULL");
+  if (B < 1) return fail(SR_ERR_INVALID_ARG, "B must be >= 1");
+  if (B > 65535) return fail(SR_ERR_UNSUPPORTED, "B must be <= 65535");
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  sr_status st = check_device(p);
+  if (st != SR_OK) return st;
+  if ((double)B * (double)p->m > 4.0e9) return fail(SR_ERR_UNSUPPORTED, "B*m too large");
+  return ensure_workspace(p, B);
+}
+
+}  // namespace
+
+struct sr_plan : public Plan {};
+
+extern "C" {
+
+sr_status sr_phases(uint64_t seed, int L, int64_t m, double* theta) {
+  if (!theta) return fail(SR_ERR_INVALID_ARG, "theta is NULL");
+  if (L < 1 || m < 1) return fail(SR_ERR_INVALID_ARG, "need L >= 1 and m >= 1");
+  gen_phases(seed, L, m, theta);
+  return SR_OK;
+}
+
+sr_status sr_plan_create(int64_t n, int64_t m, int L, uint64_t seed, sr_plan** out) {
+  if (!out) return fail(SR_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  sr_status st = check_sizes(n, m, L);
+  if (st != SR_OK) return st;
+  sr_plan* p = new (std::nothrow) sr_plan();
+  if (!p) return fail(SR_ERR_OOM, "host allocation failed");
+  p->n = n;
+  p->m = m;
+  p->L = L;
+  p->seed = seed;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  const int a = ilog2(m);
+  p->m1 = 1 << ((a + 1) / 2);
+  p->m2 = (int)(m / p->m1);
+  p->lmax = p->m1;
+  p->tw_shift = (a + 1) / 2;
+  p->theta.resize((size_t)L * m);
+  gen_phases(seed, L, m, p->theta.data());
+  if ((st = dalloc(&p->d_dp, (size_t)L * m)) != SR_OK || (st = upload_diagonals(p)) != SR_OK ||
+      (st = upload_twiddles(p)) != SR_OK) {
+    sr_plan_destroy(p);
+    return st;
+  }
+  *out = p;
+  return SR_OK;
+}
+
+sr_status sr_plan_destroy(sr_plan* plan) {
+  if (!plan) return SR_OK;
+  for (auto& v : plan->ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
+  free_workspace(plan);
+  cudaFree(plan->d_dp);
+  cudaFree(plan->d_twl);
+  cudaFree(plan->d_tw_hi);
+  cudaFree(plan->d_tw_lo);
+  delete plan;
+  return SR_OK;
+}
+
+sr_status sr_plan_get_phases(const sr_plan* plan, double* theta) {
+  if (!plan || !theta) return fail(SR_ERR_INVALID_ARG, "NULL argument");
+  std::memcpy(theta, plan->theta.data(), plan->theta.size() * sizeof(double));
+  return SR_OK;
+}
+
+sr_status sr_plan_set_phases(sr_plan* plan, const double* theta) {
+  if (!plan || !theta) return fail(SR_ERR_INVALID_ARG, "NULL argument");
+  sr_status st = check_device(plan);
+  if (st != SR_OK) return st;
+  for (size_t i = 0; i < plan->theta.size(); ++i)
+    if (!std::isfinite(theta[i])) return fail(SR_ERR_NUMERIC, "non-finite phase");
+  std::memcpy(plan->theta.data(), theta, plan->theta.size() * sizeof(double));
+  SR_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  return upload_diagonals(plan);
+}
+
+sr_status sr_plan_info(const sr_plan* plan, int64_t* n, int64_t* m, int* L) {
+  if (!plan) return fail(SR_ERR_INVALID_ARG, "plan is NULL");
+  if (n) *n = plan->n;
+  if (m) *m = plan->m;
+  if (L) *L = plan->L;
+  return SR_OK;
+}
+
+sr_status sr_plan_reserve(sr_plan* plan, int B) { return check_plan_call(plan, B); }
+
+sr_status sr_forward(sr_plan* plan, const void* x, void* z, int B, void* stream) {
+  sr_status st = check_plan_call(plan, B);
+  if (st != SR_OK) return st;
+  if (!x || !z) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
+  Plan& p = *plan;
+  Chain c;
+  c.nfft = p.L;
+  c.s0 = 0;
+  for (int k = 0; k < p.L; ++k) c.dir[k] = -1;
+  c.first_op = sr::kOpDiag;
+  for (int k = 1; k < p.L; ++k) c.mid[k] = MidOp{sr::kOpDiag, k};
+  c.last_op = sr::kOpNone;
+  c.xin = (const float2*)x;
+  c.n_in = (int)p.n;
+  c.xout = (float2*)z;
+  c.n_out = (int)p.m;
+  c.out_mode = sr::kOutStore;
+  return run_chain(p, c, B, (cudaStream_t)stream);
+}
+
+sr_status sr_adjoint(sr_plan* plan, const void* z, void* x, int B, void* stream) {
+  sr_status st = check_plan_call(plan, B);
+  if (st != SR_OK) return st;
+  if (!x || !z) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
+  Plan& p = *plan;
+  Chain c;
+  c.nfft = p.L;
+  c.s0 = p.L % 2;  // keeps every D_l in the layout it was stored in
+  for (int k = 0; k < p.L; ++k) c.dir[k] = +1;
+  c.first_op = sr::kOpNone;
+  for (int k = 1; k < p.L; ++k) c.mid[k] = MidOp{sr::kOpDiagConj, p.L - k};
+  c.last_op = sr::kOpDiagConj;
+  c.xin = (const float2*)z;
+  c.n_in = (int)p.m;
+  c.xout = (float2*)x;
+  c.n_out = (int)p.n;
+  c.out_mode = sr::kOutStore;
+  return run_chain(p, c, B, (cudaStream_t)stream);
+}
+
+sr_status sr_loss_grad(sr_plan* plan, const void* x, const float* y, float* loss, void* grad, int B,
+                       void* stream) {
+  sr_status st = check_plan_call(plan, B);
+  if (st != SR_OK) return st;
+  if (!x || !y || !grad) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
+  Plan& p = *plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = prepare_y(&p, y, B, 0.f, s)) != SR_OK) return st;
+  Chain c = round_trip_chain(p, sr::kOpGdEpilogue);
+  c.xin = (const float2*)x;
+  c.n_in = (int)p.n;
+  c.xout = (float2*)grad;
+  c.n_out = (int)p.n;
+  c.out_mode = sr::kOutGrad;
+  c.yp = p.d_yp;
+  c.loss_part = part_bank(p, 2, B);
+  c.loss_out = loss;
+  return run_chain(p, c, B, s);
+}
+
+sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int iters, const sr_spectral_opts* opts,
+                           void* x_out, int B, void* stream) {
+  sr_status st = check_plan_call(plan, B);
+  if (st != SR_OK) return st;
+  if (!y || !v0 || !x_out) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
+  if (iters < 0) return fail(SR_ERR_INVALID_ARG, "iters must be >= 0");
+  sr_spectral_opts o{SR_WEIGHT_IDENTITY, -1.0f};
+  if (opts) o = *opts;
+  if (o.weight_mode != SR_WEIGHT_IDENTITY && o.weight_mode != SR_WEIGHT_OPTIMAL)
+    return fail(SR_ERR_INVALID_ARG, "unknown weight_mode");
+  if (o.weight_mode == SR_WEIGHT_OPTIMAL && !(o.lambda < 0.f && std::isfinite(o.lambda)))
+    return fail(SR_ERR_INVALID_ARG, "lambda must be finite and < 0");
+  Plan& p = *plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = (int)p.n;
+  if (x_out != v0)
+    SR_CUDA(cudaMemcpyAsync(x_out, v0, (size_t)B * n * sizeof(float2), cudaMemcpyDeviceToDevice, s),
+            "cudaMemcpyAsync(v0)");
+  if ((st = prepare_y(&p, y, B, 0.f, s)) != SR_OK) return st;
+  float2* v = (float2*)x_out;
+  const int init_chunks = std::min(64, (n + 4095) / 4096);
+  float* bank[2] = {part_bank(p, 0, B), part_bank(p, 1, B)};
+  SR_CUDA(sr::launch_norm_rows(v, B, n, bank[1], init_chunks, s), "launch(norm v0)");
+  const int last_cpp = sr::geom_for(p, sr::s2_layout((2 * p.L - 1) % 2)).cpp;
+  Chain c = round_trip_chain(p, sr::kOpSpecEpilogue);
+  c.xin = v;
+  c.n_in = n;
+  c.xout = v;
+  c.n_out = n;
+  c.out_mode = sr::kOutSpec;
+  c.shift = o.weight_mode == SR_WEIGHT_IDENTITY ? 0.f : -2.0f * o.lambda;
+  c.yp = p.d_yp;
+  c.sumy = p.d_scal;
+  c.lam = o.lambda;
+  c.weight_mode = o.weight_mode;
+  int prev = 1, prev_count = init_chunks;
+  for (int it = 0; it < iters; ++it) {
+    const int cur = it % 2;
+    c.norm_in = bank[prev];
+    c.norm_in_count = prev_count;
+    c.spec_part_out = bank[cur];
+    if ((st = run_chain(p, c, B, s)) != SR_OK) return st;
+    prev = cur;
+    prev_count = last_cpp;
+  }
+  SR_CUDA(sr::launch_scale_rows(v, B, n, bank[prev], prev_count, p.d_scal, s), "launch(scale)");
+  return SR_OK;
+}
+
+sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters, const sr_gd_opts* opts, float* loss_hist,
+                      int B, void* stream) {
+  sr_status st = check_plan_call(plan, B);
+  if (st != SR_OK) return st;
+  if (!y || !x) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
+  if (iters < 0) return fail(SR_ERR_INVALID_ARG, "iters must be >= 0");
+  const float mu0 = opts ? opts->mu0 : 0.1f;
+  if (!(mu0 > 0.f && std::isfinite(mu0))) return fail(SR_ERR_INVALID_ARG, "mu0 must be finite and > 0");
+  Plan& p = *plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = prepare_y(&p, y, B, mu0, s)) != SR_OK) return st;
+  Chain c = round_trip_chain(p, sr::kOpGdEpilogue);
+  c.xin = (const float2*)x;
+  c.n_in = (int)p.n;
+  c.xout = (float2*)x;
+  c.n_out = (int)p.n;
+  c.out_mode = sr::kOutGd;
+  c.mu = p.d_scal + B;
+  c.yp = p.d_yp;
+  c.loss_part = part_bank(p, 2, B);
+  for (int it = 0; it < iters; ++it) {
+    c.loss_out = loss_hist ? loss_hist + (size_t)it * B : nullptr;
+    if ((st = run_chain(p, c, B, s)) != SR_OK) return st;
+  }
+  return SR_OK;
+}
+
+uint64_t sr_kernel_launches(void) {
+  return sr::launches_so_far();
+}
+
+sr_status sr_plan_set_timing(sr_plan* plan, int enable) {
+  if (!plan) return fail(SR_ERR_INVALID_ARG, "plan is NULL");
+  plan->timing = enable != 0;
+  return SR_OK;
+}
+
+sr_status sr_plan_get_timing(sr_plan* plan, double* ms, int64_t* count) {
+  if (!plan) return fail(SR_ERR_INVALID_ARG, "plan is NULL");
+  for (int k = 0; k < 3; ++k) {
+    double total = 0.0;
+    const size_t used = plan->ev_used[k];
+    if (used) SR_CUDA(cudaEventSynchronize(plan->ev[k][used - 1]), "cudaEventSynchronize");
+    for (size_t i = 0; i + 1 < used; i += 2) {
+      float t = 0.f;
+      SR_CUDA(cudaEventElapsedTime(&t, plan->ev[k][i], plan->ev[k][i + 1]), "cudaEventElapsedTime");
+      total += t;
+    }
+    if (ms) ms[k] = total;
+    if (count) count[k] = (int64_t)(used / 2);
+    plan->ev_used[k] = 0;
+  }
+  return SR_OK;
+}
+
+const char* sr_status_string(sr_status status) {
+  switch (status) {
+    case SR_OK: return "ok";
+    case SR_ERR_INVALID_ARG: return "invalid argument";
+    case SR_ERR_UNSUPPORTED: return "unsupported size";
+    case SR_ERR_OOM: return "out of memory";
+    case SR_ERR_CUDA: return "CUDA error";
+    case SR_ERR_TIMEOUT: return "device wait timed out";
+    case SR_ERR_NUMERIC: return "numeric error";
+  }
+  return "unknown status";
+}
+
+const char* sr_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,283 @@
+// Device building blocks of the structured-operator kernels: complex helpers,
+// radix-2/4/8/16 DFT butterflies, the per-line Stockham FFT held in registers
+// and shared memory, and compensated (two-sum) float reductions.
+//
+// All FFTs here are unnormalised and use the forward sign exp(-2*pi*i*jk/N);
+// the inverse transform is obtained as conj(FFT(conj(v))), and the unitary
+// 1/sqrt(m) of F (Sec. III, Eq. 5) is folded into the diagonal tables.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sr {
+
+// ------------------------------------------------------------ complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+// a * (-i)
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }
+
+// --------------------------------------------------------- small DFTs (sign -)
+// Constants of the 8th and 16th roots of unity: cos(pi/4), cos(pi/8), sin(pi/8).
+constexpr float kC4 = 0.70710678118654752440f;
+constexpr float kC8 = 0.92387953251128675613f;
+constexpr float kS8 = 0.38268343236508977173f;
+
+__device__ __forceinline__ void dft2(float2& a0, float2& a1) {
+  float2 t = a0;
+  a0 = cadd(t, a1);
+  a1 = csub(t, a1);
+}
+
+// X_k = sum_j a_j exp(-2 pi i jk/4), in place, natural order in and out.
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+  float2 t2 = cadd(a1, a3), t3 = mul_mi(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+// Radix-2 split into two length-4 DFTs (even / odd inputs), w8 = exp(-i pi/4).
+__device__ __forceinline__ void dft8(float2* a) {
+  float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+  float2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+  dft4(e0, e1, e2, e3);
+  dft4(o0, o1, o2, o3);
+  o1 = make_float2(kC4 * (o1.x + o1.y), kC4 * (o1.y - o1.x));   // * (1 - i)/sqrt2
+  o2 = mul_mi(o2);                                               // * -i
+  o3 = make_float2(kC4 * (o3.y - o3.x), -kC4 * (o3.x + o3.y));  // * (-1 - i)/sqrt2
+  a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
+  a[1] = cadd(e1, o1); a[5] = csub(e1, o1);
+  a[2] = cadd(e2, o2); a[6] = csub(e2, o2);
+  a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
+}
+
+// 16 = 4 x 4: length-4 DFTs over the stride-4 groups, twiddles w16^(j2*k1),
+// length-4 DFTs across groups; input index j2 + 4*j1, output index k1 + 4*k2.
+__device__ __forceinline__ void dft16(float2* a) {
+#pragma unroll
+  for (int j2 = 0; j2 < 4; ++j2) dft4(a[j2], a[j2 + 4], a[j2 + 8], a[j2 + 12]);
+  // now a[j2 + 4*k1] = B[k1][j2]; multiply by w16^(j2*k1), w16 = exp(-i pi/8)
+  const float2 w1 = make_float2(kC8, -kS8), w2 = make_float2(kC4, -kC4), w3 = make_float2(kS8, -kC8);
+  a[5] = cmul(a[5], w1);            // j2=1,k1=1
+  a[6] = cmul(a[6], w2);            // j2=2,k1=1
+  a[7] = cmul(a[7], w3);            // j2=3,k1=1
+  a[9] = cmul(a[9], w2);            // j2=1,k1=2
+  a[10] = mul_mi(a[10]);            // j2=2,k1=2: w^4 = -i
+  a[11] = cmul(a[11], make_float2(-kC4, -kC4));  // j2=3,k1=2: w^6
+  a[13] = cmul(a[13], w3);          // j2=1,k1=3: w^3
+  a[14] = cmul(a[14], make_float2(-kC4, -kC4));  // j2=2,k1=3: w^6
+  a[15] = cmul(a[15], make_float2(-kC8, kS8));   // j2=3,k1=3: w^9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+  // a[4*k1 + k2] = X[k1 + 4*k2]: transpose the 4x4 index grid
+  float2 t[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) t[i] = a[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
+template <int R>
+__device__ __forceinline__ void dft_small(float2* a) {
+  if constexpr (R == 2) dft2(a[0], a[1]);
+  else if constexpr (R == 4) dft4(a[0], a[1], a[2], a[3]);
+  else if constexpr (R == 8) dft8(a);
+  else if constexpr (R == 16) dft16(a);
+  else static_assert(R == 1, "radix must be 1, 2, 4, 8 or 16");
+}
+
+// ------------------------------------------------------------ line FFT shape
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+// A line of N points is held by P = N/E threads with E elements each; thread p
+// holds "slot" j = position p + j*P. Stages: radix 16 while >= 16 remains, then
+// one stage of the remaining radix (N < 16: a single stage of radix N).
+template <int N>
+struct LineShape {
+  static constexpr int E = N < 16 ? N : 16;
+  static constexpr int P = N / E;
+  static constexpr int LOGN = ilog2c(N);
+  static constexpr int NSTAGE = N < 16 ? 1 : (LOGN + 3) / 4;
+  static constexpr int LS = N + N / 16;  // padded shared-memory stride of a line
+  __host__ __device__ static constexpr int radix(int s) { return N < 16 ? N : (s < LOGN / 4 ? 16 : (1 << (LOGN % 4))); }
+  __host__ __device__ static constexpr int span(int s) { return s == 0 ? 1 : 16 * span(s - 1); }  // Ns of stage s (radix-16 prefix)
+};
+
+// Padded shared-memory index: one spare slot after every 16 (bank-conflict relief
+// for the stride-16 writes of the first stage).
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+// Synchronise the threads of the lines (a warp when a line fits in one and the
+// block is made of whole warps, else the block).
+template <int P>
+__device__ __forceinline__ void line_sync(bool warp_ok) {
+  if constexpr (P <= 32) {
+    if (warp_ok) {
+      __syncwarp();
+      return;
+    }
+  }
+  __syncthreads();
+}
+
+// One Stockham radix-R stage (Govindaraju et al., SC'08 formulation): butterfly b
+// reads positions b + r*N/R, applies twiddles W_{Ns R}^{r (b mod Ns)}, a radix-R
+// DFT, and writes position (b/Ns)*Ns*R + (b mod Ns) + r*Ns. Butterflies of this
+// thread: b = p + q*P, q < E/R; their inputs are slots q + r*E/R.
+template <int N, int S>
+__device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* sm, int p,
+                                          const float2* __restrict__ twl, int tws, bool warp_ok) {
+  using LS_ = LineShape<N>;
+  constexpr int E = LS_::E, P = LS_::P;
+  constexpr int R = LS_::radix(S);
+  constexpr int Q = E / R;
+  constexpr int Ns = LS_::span(S);
+  constexpr bool LAST = (S == LS_::NSTAGE - 1);
+  if constexpr (S > 0) {
+    // inputs of this stage: the previous stage's outputs, slot pattern
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[j] = sm[pad16(p + j * P)];
+    if constexpr (!LAST) line_sync<P>(warp_ok);  // everyone read before anyone overwrites
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int b = p + q * P;
+    float2 a[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[r] = v[q + r * Q];
+    if constexpr (S > 0) {
+      const int k = b % Ns;
+      // W_{Ns R}^{r k} = W_N^{r k N/(Ns R)}; table holds W_Lmax^j, stride tws = Lmax/N
+      constexpr int step = N / (Ns * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) a[r] = cmul(a[r], __ldg(&twl[(r * k * step) * tws]));
+    }
+    dft_small<R>(a);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q + r * Q] = a[r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[pad16((b / Ns) * Ns * R + (b % Ns) + r * Ns)] = a[r];
+    }
+  }
+  if constexpr (!LAST) line_sync<P>(warp_ok);
+}
+
+template <int N, int S>
+__device__ __forceinline__ void fft_stages(float2 (&v)[LineShape<N>::E], float2* sm, int p,
+                                           const float2* __restrict__ twl, int tws, bool warp_ok) {
+  if constexpr (S < LineShape<N>::NSTAGE) {
+    fft_stage<N, S>(v, sm, p, twl, tws, warp_ok);
+    fft_stages<N, S + 1>(v, sm, p, twl, tws, warp_ok);
+  }
+}
+
+// Unnormalised length-N DFT of one line, sign -1 (dir < 0) or +1 (dir > 0).
+// In: slot j = position p + j*P; out: slot j = frequency p + j*P (natural order).
+// sm: this line's scratch (LineShape<N>::LS float2). The caller synchronises
+// before the call if the scratch was in use by other threads.
+template <int N>
+__device__ __forceinline__ void line_fft(float2 (&v)[LineShape<N>::E], float2* sm, int p, int dir,
+                                         const float2* __restrict__ twl, int tws, bool warp_ok) {
+  constexpr int E = LineShape<N>::E;
+  if (dir > 0) {
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[j].y = -v[j].y;
+  }
+  fft_stages<N, 0>(v, sm, p, twl, tws, warp_ok);
+  if (dir > 0) {
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[j].y = -v[j].y;
+  }
+}
+
+// ---------------------------------------------------- compensated summation
+// Value = s + c, accumulated with Knuth's error-free two-sum so that the
+// rounding error of each addition is carried in c.
+struct fsum2 {
+  float s, c;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void acc_add(fsum2& A, float x) {
+  float s, e;
+  two_sum(A.s, x, s, e);
+  A.s = s;
+  A.c += e;
+}
+
+__device__ __forceinline__ fsum2 acc_merge(fsum2 A, fsum2 B) {
+  float s, e;
+  two_sum(A.s, B.s, s, e);
+  return fsum2{s, A.c + B.c + e};
+}
+
+// Block-wide compensated sum; result valid in thread 0. `red` holds >= 64 floats.
+// Blocks that are not whole warps (tiny sizes, < 32 threads) reduce serially.
+__device__ __forceinline__ float block_sum(fsum2 A, float* red) {
+  if (blockDim.x % 32 != 0) {
+    __syncthreads();
+    red[2 * threadIdx.x] = A.s;
+    red[2 * threadIdx.x + 1] = A.c;
+    __syncthreads();
+    float out = 0.f;
+    if (threadIdx.x == 0) {
+      fsum2 T{red[0], red[1]};
+      for (unsigned w = 1; w < blockDim.x; ++w) T = acc_merge(T, fsum2{red[2 * w], red[2 * w + 1]});
+      out = T.s + T.c;
+    }
+    __syncthreads();
+    return out;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    fsum2 B{__shfl_down_sync(0xffffffffu, A.s, off), __shfl_down_sync(0xffffffffu, A.c, off)};
+    if ((threadIdx.x & 31) + off < 32) A = acc_merge(A, B);
+  }
+  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    red[2 * warp] = A.s;
+    red[2 * warp + 1] = A.c;
+  }
+  __syncthreads();
+  float out = 0.f;
+  if (threadIdx.x == 0) {
+    fsum2 T{red[0], red[1]};
+    for (int w = 1; w < nwarp; ++w) T = acc_merge(T, fsum2{red[2 * w], red[2 * w + 1]});
+    out = T.s + T.c;
+  }
+  __syncthreads();
+  return out;
+}
+
+// Deterministic compensated sum of `count` partials (serial, fixed order).
+__device__ __forceinline__ float sum_partials(const float* __restrict__ part, int count) {
+  fsum2 A{0.f, 0.f};
+  for (int i = 0; i < count; ++i) acc_add(A, part[i]);
+  return A.s + A.c;
+}
+
+}  // namespace sr

@@ -1,0 +1,170 @@
+"""Python binding of the C ABI: torch tensors in, torch tensors out.
+
+Argument marshalling only -- every step of the operator and of the solvers
+runs in the CUDA kernels of libsr.so. Complex arrays are torch.complex64
+(interleaved re/im, the ABI's c64), real arrays torch.float32, all on the
+plan's CUDA device and C-contiguous. Calls are enqueued on the current torch
+stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _stream_handle(stream=None) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _p(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+class Plan:
+    """Structured random operator A = F D_L ... F D_1 U (Sec. III, Eq. 5) on one GPU."""
+
+    def __init__(self, n: int, m: int, L: int = 2, seed: int = 0, device=None):
+        self._lib = _lib.load()
+        self.n, self.m, self.L, self.seed = int(n), int(m), int(L), int(seed)
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if dev.type != "cuda":
+            raise ValueError("a plan lives on a CUDA device")
+        self.device = torch.device("cuda", dev.index if dev.index is not None else torch.cuda.current_device())
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_plan_create(self.n, self.m, self.L, self.seed, C.byref(h)), "sr_plan_create")
+        self._h = h
+
+    # -------------------------------------------------------------- lifecycle
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.sr_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ----------------------------------------------------------------- phases
+    @property
+    def phases(self) -> np.ndarray:
+        out = np.empty((self.L, self.m), dtype=np.float64)
+        _lib.check(self._lib.sr_plan_get_phases(self._h, out.ctypes.data_as(C.POINTER(C.c_double))),
+                   "sr_plan_get_phases")
+        return out
+
+    def set_phases(self, theta) -> None:
+        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(self.L, self.m)
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_plan_set_phases(self._h, th.ctypes.data_as(C.POINTER(C.c_double))),
+                       "sr_plan_set_phases")
+
+    def reserve(self, B: int) -> None:
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_plan_reserve(self._h, int(B)), "sr_plan_reserve")
+
+    # ---------------------------------------------------------------- helpers
+    def _c64(self, t, last: int, name: str):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.complex64:
+            raise TypeError(f"{name} must be a torch.complex64 tensor")
+        if t.device != self.device:
+            raise ValueError(f"{name} must live on {self.device}")
+        if t.shape[-1] != last or t.dim() not in (1, 2):
+            raise ValueError(f"{name} must have shape [B, {last}] or [{last}]")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return t
+
+    def _f32(self, t, last: int, name: str):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32:
+            raise TypeError(f"{name} must be a torch.float32 tensor")
+        if t.device != self.device or t.shape[-1] != last or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous [B, {last}] tensor on {self.device}")
+        return t
+
+    @staticmethod
+    def _batch(t) -> int:
+        return 1 if t.dim() == 1 else t.shape[0]
+
+    # ------------------------------------------------------------- operators
+    def forward(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """z = A x; x: complex64 [B, n] -> z: complex64 [B, m]."""
+        x = self._c64(x, self.n, "x")
+        B = self._batch(x)
+        z = out if out is not None else torch.empty(x.shape[:-1] + (self.m,), dtype=torch.complex64, device=self.device)
+        self._c64(z, self.m, "out")
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_forward(self._h, _p(x), _p(z), B, _stream_handle()), "sr_forward")
+        return z
+
+    def adjoint(self, z: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """x = A^H z; z: complex64 [B, m] -> x: complex64 [B, n]."""
+        z = self._c64(z, self.m, "z")
+        B = self._batch(z)
+        x = out if out is not None else torch.empty(z.shape[:-1] + (self.n,), dtype=torch.complex64, device=self.device)
+        self._c64(x, self.n, "out")
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_adjoint(self._h, _p(z), _p(x), B, _stream_handle()), "sr_adjoint")
+        return x
+
+    def loss_grad(self, x: torch.Tensor, y: torch.Tensor):
+        """(loss [B], grad [B, n]) of L = || |Ax|^2 - y ||^2, grad = 2 A^H((|Ax|^2 - y) Ax) (Eq. 2)."""
+        x = self._c64(x, self.n, "x")
+        y = self._f32(y, self.m, "y")
+        B = self._batch(x)
+        loss = torch.empty(B, dtype=torch.float32, device=self.device)
+        grad = torch.empty_like(x)
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_loss_grad(self._h, _p(x), _p(y), _p(loss), _p(grad), B, _stream_handle()),
+                       "sr_loss_grad")
+        return loss, grad
+
+    def spectral_init(self, y: torch.Tensor, v0: torch.Tensor, iters: int, weight: str = "identity",
+                      lam: float = -1.0, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Power iteration on M = A^H diag(T(y_hat)) A from v0 (Eq. 3-4); returns sqrt(sum y) v."""
+        y = self._f32(y, self.m, "y")
+        v0 = self._c64(v0, self.n, "v0")
+        B = self._batch(v0)
+        mode = {"identity": _lib.SR_WEIGHT_IDENTITY, "optimal": _lib.SR_WEIGHT_OPTIMAL}[weight]
+        opts = _lib.SpectralOpts(mode, float(lam))
+        x = out if out is not None else torch.empty_like(v0)
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_spectral_init(self._h, _p(y), _p(v0), int(iters), C.byref(opts), _p(x), B,
+                                                  _stream_handle()), "sr_spectral_init")
+        return x
+
+    def gd_solve(self, y: torch.Tensor, x: torch.Tensor, iters: int, mu0: float = 0.1,
+                 record_loss: bool = False, loss_hist: torch.Tensor | None = None):
+        """In-place GD on x (Sec. II-B-1); returns (x, loss history [iters, B] or None)."""
+        y = self._f32(y, self.m, "y")
+        x = self._c64(x, self.n, "x")
+        B = self._batch(x)
+        hist = loss_hist
+        if hist is None and record_loss:
+            hist = torch.empty((int(iters), B), dtype=torch.float32, device=self.device)
+        opts = _lib.GdOpts(float(mu0))
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_gd_solve(self._h, _p(y), _p(x), int(iters), C.byref(opts), _p(hist), B,
+                                             _stream_handle()), "sr_gd_solve")
+        return x, hist
+
+
+def phases(seed: int, L: int, m: int) -> np.ndarray:
+    """Host-side phases a plan with this seed uses (sr_phases): float64 [L, m]."""
+    lib = _lib.load()
+    out = np.empty((L, m), dtype=np.float64)
+    _lib.check(lib.sr_phases(int(seed), int(L), int(m), out.ctypes.data_as(C.POINTER(C.c_double))), "sr_phases")
+    return out

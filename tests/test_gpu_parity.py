@@ -1,0 +1,187 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP32 arithmetic against FP64):
+* one application of A or A^H: relative error <= 1e-5 in norm, and every
+  element within 2e-5 of the RMS of the reference. An FP32 radix-16 FFT of
+  length m carries a relative error of about eps32 * c * log2(m) with
+  eps32 = 6e-8 (twiddles rounded from double add ~1 ulp each); L <= 4 chained
+  transforms keep this near 1e-6, and 1e-5 is the per-application target;
+* loss and gradient at a point away from the solution: relative 1e-5;
+* power iteration after T steps from the same start: relative 1e-4;
+* gradient descent: final reconstruction error (up to a global phase) within
+  1e-4 of the oracle's.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Plan():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2409_05734_gb300 import buildlib
+    buildlib.build()
+    from paper_2409_05734_gb300 import Plan as P
+    return P
+
+
+def dev(a, dtype=torch.complex64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.complex128 if t.is_complex() else np.float64)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def assert_close_elementwise(got, ref, tol_norm=1e-5, tol_elem=2e-5):
+    assert rel(got, ref) <= tol_norm, rel(got, ref)
+    rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    worst = np.max(np.abs(got - ref)) / rms
+    assert worst <= tol_elem, worst
+
+
+OPERATOR_CASES = [
+    # (n, m, L, B): tiny, ragged n, several tiles per pass, odd log2(m), alpha = 1, L up to 4
+    (4, 4, 2, 1),
+    (1, 8, 1, 2),
+    (8, 32, 1, 3),
+    (5, 32, 3, 2),
+    (64, 256, 2, 1),
+    (100, 512, 2, 4),
+    (256, 256, 2, 2),
+    (1000, 8192, 3, 2),
+    (3001, 4096, 2, 3),
+    (20000, 2 ** 16, 2, 2),
+    (2 ** 14, 2 ** 16, 4, 1),
+    (2 ** 17 - 5, 2 ** 19, 2, 1),
+    (7, 16, 2, 1000),
+]
+
+
+@pytest.mark.parametrize("n,m,L,B", OPERATOR_CASES)
+def test_forward_adjoint_match_oracle(Plan, n, m, L, B):
+    seed = 1000 + n + m + L
+    plan = Plan(n, m, L, seed)
+    theta = S.phases(seed, L, m)
+    assert np.array_equal(plan.phases, theta)
+    x = S.signal_gaussian(seed, B, n)
+    z = host(plan.forward(dev(x)))
+    assert_close_elementwise(z, O.forward(x, theta, m))
+    w = S.complex_gaussian(seed + 1, (B, m), S.STREAM_NOISE)
+    xa = host(plan.adjoint(dev(w)))
+    assert_close_elementwise(xa, O.adjoint(w, theta, n))
+
+
+@pytest.mark.parametrize("n,m,L,B", [(64, 256, 2, 1), (37, 128, 3, 5), (3000, 16384, 2, 2), (5, 32, 1, 2)])
+def test_loss_grad_match_oracle(Plan, n, m, L, B):
+    seed = 7 + n
+    plan = Plan(n, m, L, seed)
+    theta = S.phases(seed, L, m)
+    fwd, adj = O.structured_ops(theta, n, m)
+    y = np.abs(fwd(S.signal_gaussian(seed, B, n))) ** 2
+    x = S.signal_gaussian(seed + 1, B, n)
+    loss_o, g_o = O.loss_and_grad(x, y, fwd, adj)
+    loss, g = plan.loss_grad(dev(x), dev(y, torch.float32))
+    assert np.max(np.abs(host(loss) - loss_o) / loss_o) <= 1e-5
+    assert_close_elementwise(host(g), g_o)
+
+
+@pytest.mark.parametrize("weight", ["identity", "optimal"])
+def test_spectral_init_matches_oracle(Plan, weight):
+    n, m, L, B, T = 64, 256, 2, 3, 50
+    seed = 20240905
+    plan = Plan(n, m, L, seed)
+    theta = S.phases(seed, L, m)
+    fwd, adj = O.structured_ops(theta, n, m)
+    x = S.signal_gaussian(seed, B, n)
+    y = np.abs(fwd(x)) ** 2
+    v0 = S.start_vector(seed, B, n)
+    ref = O.spectral_init(y, v0, fwd, adj, T, mode=weight, lam=-1.0)
+    got = host(plan.spectral_init(dev(y, torch.float32), dev(v0), T, weight=weight, lam=-1.0))
+    for b in range(B):
+        assert rel(got[b], ref[b]) <= 1e-4
+    # zero iterations: the normalised start scaled by sqrt(sum y)
+    got0 = host(plan.spectral_init(dev(y, torch.float32), dev(v0), 0))
+    ref0 = O.spectral_init(y, v0, fwd, adj, 0)
+    assert rel(got0, ref0) <= 1e-6
+
+
+def test_gradient_descent_matches_oracle_small_config(Plan):
+    """n = 64, alpha = 4 (m = 256), L = 2: 50 power iterations, then 300 GD steps."""
+    n, m, L = 64, 256, 2
+    seed = 20240905
+    plan = Plan(n, m, L, seed)
+    theta = S.phases(seed, L, m)
+    fwd, adj = O.structured_ops(theta, n, m)
+    x_true = S.signal_gaussian(seed, 1, n)
+    y = np.abs(fwd(x_true)) ** 2
+    v0 = S.start_vector(seed, 1, n)
+    x0_o = O.spectral_init(y, v0, fwd, adj, 50, mode="optimal")
+    xT_o, hist_o = O.gradient_descent(x0_o, y, fwd, adj, 300, mu0=0.1)
+    x0 = plan.spectral_init(dev(y, torch.float32), dev(v0), 50, weight="optimal")
+    assert rel(host(x0), x0_o) <= 1e-4
+    x = dev(x0_o)
+    _, hist = plan.gd_solve(dev(y, torch.float32), x, 300, mu0=0.1, record_loss=True)
+    e_gpu = O.relative_error_global_phase(host(x), x_true)[0]
+    e_or = O.relative_error_global_phase(xT_o, x_true)[0]
+    assert abs(e_gpu - e_or) <= 1e-4, (e_gpu, e_or)
+    h = host(hist)[:, 0]
+    assert np.max(np.abs(h[:50] - hist_o[:50, 0]) / hist_o[:50, 0]) <= 1e-3
+
+
+def test_full_size_batch_sampled(Plan):
+    """The benchmark shape: B = 64 signals, n = 2^14, alpha = 4 (m = 2^16), L = 2.
+    All 64 forward outputs against the oracle; the solver checked on sampled
+    problems of the batch (oracle run one problem at a time)."""
+    n, m, L, B = 2 ** 14, 2 ** 16, 2, 64
+    seed = 20240905
+    plan = Plan(n, m, L, seed)
+    theta = S.phases(seed, L, m)
+    fwd, adj = O.structured_ops(theta, n, m)
+    x_true = S.signal_amplitude_phase(seed, B, n)
+    y_o = np.abs(fwd(x_true)) ** 2
+    z = host(plan.forward(dev(x_true)))
+    assert_close_elementwise(z, fwd(x_true))
+    y = dev(y_o, torch.float32)
+    v0 = S.start_vector(seed, B, n)
+    x = plan.spectral_init(y, dev(v0), 10, weight="optimal")
+    _, hist = plan.gd_solve(y, x, 20, mu0=0.1, record_loss=True)
+    xg = host(x)
+    hg = host(hist)
+    for b in (0, 37, 63):
+        fb, ab = O.structured_ops(theta, n, m)
+        x0b = O.spectral_init(y_o[b:b + 1], v0[b:b + 1], fb, ab, 10, mode="optimal")
+        xTb, hb = O.gradient_descent(x0b, y_o[b:b + 1], fb, ab, 20, mu0=0.1)
+        assert rel(xg[b], xTb[0]) <= 1e-3
+        assert np.max(np.abs(hg[:, b] - hb[:, 0]) / hb[:, 0]) <= 1e-3
+
+
+def test_results_are_deterministic(Plan):
+    plan = Plan(3000, 16384, 2, 5)
+    x = dev(S.signal_gaussian(5, 4, 3000))
+    y = torch.abs(plan.forward(x)) ** 2
+    g1 = plan.loss_grad(x * 0.5, y.contiguous())[1].clone()
+    g2 = plan.loss_grad(x * 0.5, y.contiguous())[1].clone()
+    assert torch.equal(g1, g2)
+
+
+def test_binding_rejects_bad_arguments(Plan):
+    plan = Plan(16, 64, 2, 0)
+    with pytest.raises(TypeError):
+        plan.forward(torch.zeros(1, 16, dtype=torch.complex128, device="cuda"))
+    with pytest.raises(ValueError):
+        plan.forward(torch.zeros(1, 15, dtype=torch.complex64, device="cuda"))
+    from paper_2409_05734_gb300._lib import SrError
+    with pytest.raises(SrError):
+        plan.gd_solve(torch.zeros(1, 64, device="cuda"), torch.zeros(1, 16, dtype=torch.complex64, device="cuda"),
+                      1, mu0=-1.0)
