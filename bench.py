@@ -36,7 +36,8 @@ if ROOT not in sys.path:
 METRIC = "GD iters/sec (fwd+adj) & HBM GB/s vs peak; speedup over dense i.i.d. at equal error"
 UNIT = "problem-iters/s"
 WORKLOAD = dict(name="structured-L2-n16384-m65536-B64-sp100-gd500", n=2 ** 14, m=2 ** 16, L=2, B=64,
-                spectral_iters=100, gd_iters=500, weight="optimal", lam=-1.0, mu0=0.1, seed=20240905)
+                spectral_iters=100, gd_iters=500, weight="optimal", lam=-1.0, mu0=0.15, tau0=100.0,
+                seed=20240905)
 FLUSH_BYTES = 512 << 20  # > 129 MB L2: written between timed steps
 
 
@@ -129,7 +130,7 @@ def oracle_sample(W, power_iters: int, gd_iters: int, seed: int):
     v0 = S.start_vector(seed, 1, n)
     t0 = time.perf_counter()
     x0 = O.spectral_init(y, v0, fwd, adj, power_iters, mode=W["weight"], lam=W["lam"])
-    O.gradient_descent(x0, y, fwd, adj, gd_iters, mu0=W["mu0"])
+    O.gradient_descent(x0, y, fwd, adj, gd_iters, mu0=W["mu0"], tau0=W["tau0"])
     dt = time.perf_counter() - t0
     return (power_iters + gd_iters) / dt, dt
 
@@ -161,7 +162,7 @@ def run_reference(args):
 def config_dict(W, world):
     return {"workload": W["name"], "n": W["n"], "m": W["m"], "alpha": W["m"] / W["n"], "L": W["L"],
             "batch_per_gpu": W["B"], "global_batch": W["B"] * world, "spectral_iters": W["spectral_iters"],
-            "gd_iters": W["gd_iters"], "spectral_weight": f"{W['weight']}(lambda={W['lam']})", "mu0": W["mu0"],
+            "gd_iters": W["gd_iters"], "spectral_weight": f"{W['weight']}(lambda={W['lam']})", "mu0": W["mu0"], "tau0": W["tau0"],
             "signal": "amplitude U[0,1] x random phase, seeded Philox", "y": "noiseless |Ax|^2",
             "l2": "flushed between timed steps (512 MiB write)",
             "parallelism": f"replicas x{world} (independent batches per GPU)"}
@@ -239,7 +240,7 @@ def run_ours(args):
 
     def step(y_in, v_in, x_out):
         plan.spectral_init(y_in, v_in, W["spectral_iters"], weight=W["weight"], lam=W["lam"], out=x_out)
-        plan.gd_solve(y_in, x_out, W["gd_iters"], mu0=W["mu0"])
+        plan.gd_solve(y_in, x_out, W["gd_iters"], mu0=W["mu0"], tau0=W["tau0"])
 
     def barrier():
         torch.cuda.synchronize()

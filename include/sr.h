@@ -69,7 +69,8 @@ typedef struct sr_spectral_opts {
 } sr_spectral_opts;
 
 typedef struct sr_gd_opts {
-  float mu0; /* step size is mu = mu0 * m / sum(y) per problem; > 0 */
+  float mu0;  /* step scale, > 0 */
+  float tau0; /* warm-up length, >= 0 (0: constant step) */
 } sr_gd_opts;
 
 /* ---- phases (host only; no GPU needed) ------------------------------------
@@ -127,12 +128,24 @@ sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int it
                            const sr_spectral_opts* opts, void* x_out, int B, void* stream);
 
 /* ---- gradient descent (Sec. II-B-1, Sec. IV-A) ------------------------------
- * `iters` steps x <- x - mu * 2 A^H((|Ax|^2 - y) * Ax), mu = mu0 * m / sum(y),
- * updating x (c64[B][n], device) in place. loss_hist (float[iters][B],
- * device) receives the loss at each iterate before its update, or is NULL.
- * opts may be NULL (mu0 = 0.1). */
+ * `iters` steps x <- x - mu_t * 2 A^H((|Ax|^2 - y) * Ax) with
+ *   mu_t = mu0 * (1 - exp(-(t+1)/tau0)) * m / sum(y)   (tau0 > 0), or
+ *   mu_t = mu0 * m / sum(y)                             (tau0 == 0),
+ * t = 0..iters-1 counted from this call (the paper gives no step size; the
+ * warm-up follows the Wirtinger-flow schedule of Candes et al. 2015), updating
+ * x (c64[B][n], device) in place. loss_hist (float[iters][B], device)
+ * receives the loss at each iterate before its update, or is NULL.
+ * opts may be NULL (mu0 = 0.1, tau0 = 0). */
 sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters,
                       const sr_gd_opts* opts, float* loss_hist, int B, void* stream);
+
+/* ---- device status -----------------------------------------------------------
+ * sr_plan_check: waits for the device (cudaDeviceSynchronize) and reports the
+ * status the plan's kernels recorded since the last check: SR_ERR_TIMEOUT if
+ * a pass kernel's bounded wait for its input tile gave up (the kernel then
+ * stops early and its outputs are invalid), SR_OK otherwise. Clears the
+ * recorded status. */
+sr_status sr_plan_check(sr_plan* plan);
 
 /* ---- profiling ------------------------------------------------------------
  * sr_kernel_launches: number of CUDA kernels this library has launched in the

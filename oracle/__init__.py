@@ -42,6 +42,7 @@ from .recovery import (
     spectral_weights,
     spectral_init,
     gradient_descent,
+    step_ramp,
     cosine_similarity,
     relative_error_global_phase,
     structured_ops,
@@ -51,7 +52,7 @@ from .dense_iid import dense_forward, dense_adjoint, dense_ops
 __all__ = [
     "dft_matrix", "dft_naive", "unitary_fft", "unitary_ifft", "zero_pad", "forward",
     "adjoint", "dense_structured_matrix", "intensity_loss", "loss_and_grad",
-    "spectral_weights", "spectral_init", "gradient_descent", "cosine_similarity",
+    "spectral_weights", "spectral_init", "gradient_descent", "step_ramp", "cosine_similarity",
     "relative_error_global_phase", "structured_ops", "dense_forward", "dense_adjoint",
     "dense_ops",
 ]

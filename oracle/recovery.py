@@ -13,8 +13,11 @@ Readings of the paper used here:
   the Wirtinger derivative dL/d conj(x). The derivative with respect to the
   real and imaginary parts is twice its real and imaginary parts.
 * The loss is the sum (not the mean) of squared intensity residuals.
-* Step size mu = mu0 * m / sum(y), mu0 = 0.1 by default (the paper gives no
-  step size; sum(y) = ||x||^2 for the unitary model sets the scale).
+* Step size (the paper gives none): mu_t = mu0 * ramp_t * m / sum(y), with
+  sum(y) = ||x||^2 for the unitary model setting the scale and
+  ramp_t = 1 - exp(-(t+1)/tau0) a warm-up in the manner of the Wirtinger-flow
+  schedule (Candes, Li and Soltanolkotabi, 2015); tau0 = 0 means a constant
+  step (ramp_t = 1). A constant mu0 = 0.1 diverges from poor spectral starts.
 * Spectral weights: y_hat = m * y / sum(y) (mean one). The default weight is
   the identity, T(y_hat) = y_hat, i.e. M = A^H diag(y_hat) A; the optional
   weight is the preprocessing T(y_hat) = max(1 - 1/y_hat, lambda) of Sec. II-B-2
@@ -55,9 +58,14 @@ def loss_and_grad(x: np.ndarray, y: np.ndarray, fwd, adj):
     return loss, grad
 
 
+def step_ramp(t: int, tau0: float) -> float:
+    """Warm-up factor of step t: 1 - exp(-(t+1)/tau0), or 1 when tau0 == 0."""
+    return 1.0 if tau0 == 0 else 1.0 - np.exp(-(t + 1) / tau0)
+
+
 def gradient_descent(x0: np.ndarray, y: np.ndarray, fwd, adj, iters: int,
-                     mu0: float = MU0_DEFAULT):
-    """x_{t+1} = x_t - mu * grad(x_t), mu = mu0 * m / sum(y) (Sec. II-B-1, Sec. IV-A).
+                     mu0: float = MU0_DEFAULT, tau0: float = 0.0):
+    """x_{t+1} = x_t - mu_t * grad(x_t), mu_t = mu0 * ramp_t * m / sum(y) (Sec. II-B-1, Sec. IV-A).
 
     Returns (x_T, loss history [iters, ...]); entry t is the loss at x_t.
     """
@@ -66,10 +74,10 @@ def gradient_descent(x0: np.ndarray, y: np.ndarray, fwd, adj, iters: int,
     m = y.shape[-1]
     mu = (mu0 * m / np.sum(y, axis=-1))[..., None]
     hist = []
-    for _ in range(iters):
+    for t in range(iters):
         loss, g = loss_and_grad(x, y, fwd, adj)
         hist.append(loss)
-        x = x - mu * g
+        x = x - (step_ramp(t, tau0) * mu) * g
     return x, np.array(hist)
 
 

@@ -106,19 +106,50 @@ sr_status dalloc(T** ptr, size_t count) {
 void free_workspace(Plan* p) {
   cudaFree(p->d_e0);
   cudaFree(p->d_e1);
-  cudaFree(p->d_yp);
   cudaFree(p->d_part);
   cudaFree(p->d_scal);
   p->d_e0 = p->d_e1 = nullptr;
-  p->d_yp = nullptr;
   p->d_part = p->d_scal = nullptr;
   p->B_cap = 0;
 }
 
-// Size of one bank of per-CTA partial sums per problem.
-int part_stride(const Plan& p) {
-  const sr::LineGeom gx = sr::geom_for(p, sr::kLayoutX), gy = sr::geom_for(p, sr::kLayoutY);
-  return std::max(std::max(gx.cpp, gy.cpp), 64);
+// Size of one bank of per-tile partial sums per problem.
+int part_stride(const Plan& p) { return std::max(std::max(p.geom[0].cpp, p.geom[1].cpp), 64); }
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+sr_status get_encoder(EncodeTiledFn* fn) {
+  static EncodeTiledFn cached = nullptr;
+  if (!cached) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f)
+      return fail(SR_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cached = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  *fn = cached;
+  return SR_OK;
+}
+
+// Rows of an exchange buffer as a 2D tensor for the TMA loads of the passes
+// that read it: `rows` rows of `ell` complex values (2*ell floats), loaded in
+// boxes of 16 complex values (128 bytes) x T rows with 128-byte swizzle.
+sr_status encode_rows(CUtensorMap* map, float2* base, int ell, int64_t rows, int T) {
+  EncodeTiledFn enc;
+  sr_status st = get_encoder(&enc);
+  if (st != SR_OK) return st;
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * ell), (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ell * 8};
+  const cuuint32_t box[2] = {32, (cuuint32_t)T};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(SR_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return SR_OK;
 }
 constexpr int kPartBanks = 4;  // 0,1: power-iteration norms (ping-pong), 2: loss, 3: sums
 
@@ -128,11 +159,21 @@ sr_status ensure_workspace(Plan* p, int B) {
   const size_t bm = (size_t)B * (size_t)p->m;
   sr_status st;
   if ((st = dalloc(&p->d_e0, bm)) != SR_OK || (st = dalloc(&p->d_e1, bm)) != SR_OK ||
-      (st = dalloc(&p->d_yp, bm)) != SR_OK ||
       (st = dalloc(&p->d_part, (size_t)kPartBanks * B * part_stride(*p))) != SR_OK ||
       (st = dalloc(&p->d_scal, (size_t)4 * B)) != SR_OK) {
     free_workspace(p);
     return st;
+  }
+  for (int lay = 0; lay < 2; ++lay) {
+    const sr::LineGeom& g = p->geom[lay];
+    if (g.ell < 16) continue;  // short lines are read without TMA
+    for (int buf = 0; buf < 2; ++buf) {
+      st = encode_rows(&p->tmap[buf][lay], buf ? p->d_e1 : p->d_e0, g.ell, (int64_t)B * g.nl, g.T);
+      if (st != SR_OK) {
+        free_workspace(p);
+        return st;
+      }
+    }
   }
   p->B_cap = B;
   return SR_OK;
@@ -141,21 +182,15 @@ sr_status ensure_workspace(Plan* p, int B) {
 float* part_bank(const Plan& p, int bank, int B) { return p.d_part + (size_t)bank * B * part_stride(p); }
 
 // Rebuilds the device diagonal tables from p->theta: D_l = exp(i theta_l)/sqrt(m)
-// (the 1/sqrt(m) of each unitary F folded in), permuted into the line layout of
-// the pass that applies D_l.
+// (the 1/sqrt(m) of each unitary F folded in), natural order, computed in
+// double and rounded to float.
 sr_status upload_diagonals(Plan* p) {
   const int64_t m = p->m;
   const double scale = 1.0 / std::sqrt((double)m);
   std::vector<float2> host((size_t)p->L * m);
-  for (int d = 0; d < p->L; ++d) {
-    const sr::LineGeom g = sr::geom_for(*p, sr::diag_layout(d));
-    const double* th = p->theta.data() + (size_t)d * m;
-    float2* out = host.data() + (size_t)d * m;
-    for (int gl = 0; gl < g.nl; ++gl)
-      for (int f = 0; f < g.ell; ++f) {
-        const double t = th[(size_t)f * g.nl + gl];
-        out[(size_t)gl * g.ell + f] = make_float2((float)(std::cos(t) * scale), (float)(std::sin(t) * scale));
-      }
+  for (size_t i = 0; i < host.size(); ++i) {
+    const double t = p->theta[i];
+    host[i] = make_float2((float)(std::cos(t) * scale), (float)(std::sin(t) * scale));
   }
   SR_CUDA(cudaMemcpy(p->d_dp, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice),
           "cudaMemcpy(diagonals)");
@@ -209,11 +244,12 @@ struct Chain {
   int n_out = 0;
   int out_mode = sr::kOutStore;
   const float* mu = nullptr;
+  float mu_scale = 1.f;
   float shift = 0.f;
   float* spec_part_out = nullptr;
   float* loss_out = nullptr;
   // epilogue data
-  const float* yp = nullptr;
+  const float* y = nullptr;
   const float* sumy = nullptr;
   float lam = 0.f;
   int weight_mode = SR_WEIGHT_IDENTITY;
@@ -228,6 +264,7 @@ sr::PassArgs base_args(const Plan& p) {
   a.tw_hi = p.d_tw_hi;
   a.tw_lo = p.d_tw_lo;
   a.tw_shift = p.tw_shift;
+  a.err = p.d_err;
   return a;
 }
 
@@ -259,6 +296,7 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
   const sr::PassArgs base = base_args(p);
   float2* cur = p.d_e0;
   float2* nxt = p.d_e1;
+  int cur_idx = 0;  // which exchange buffer `cur` is (selects its tensor maps)
   int loss_cpp = 0;
   // FIRST
   {
@@ -281,14 +319,15 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     a.out_dir = c.dir[k];
     a.ein = cur;
     a.eout = nxt;
+    a.tmap = p.tmap[cur_idx][lay];
     a.op = c.mid[k].op;
     a.dp = p.d_dp + (size_t)c.mid[k].d * p.m;
     if (a.op == sr::kOpGdEpilogue) {
-      a.yp = c.yp;
+      a.y = c.y;
       a.part_out = c.loss_part;
-      loss_cpp = sr::geom_for(p, lay).cpp;
+      loss_cpp = p.geom[lay].cpp;
     } else if (a.op == sr::kOpSpecEpilogue) {
-      a.yp = c.yp;
+      a.y = c.y;
       a.sumy = c.sumy;
       a.lam = c.lam;
       a.weight_mode = c.weight_mode;
@@ -298,18 +337,22 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
       SR_CUDA(sr::launch_mid(p, lay, a, B, s), "launch(mid pass)");
     }
     std::swap(cur, nxt);
+    cur_idx ^= 1;
   }
   // LAST
   {
+    const sr::Layout lay = sr::s2_layout((c.s0 + c.nfft - 1) % 2);
     sr::PassArgs a = base;
     a.in_dir = c.dir[c.nfft - 1];
     a.ein = cur;
+    a.tmap = p.tmap[cur_idx][lay];
     a.op = c.last_op;
     a.dp = p.d_dp;
     a.xout = c.xout;
     a.n_out = c.n_out;
     a.out_mode = c.out_mode;
     a.mu = c.mu;
+    a.mu_scale = c.mu_scale;
     a.shift = c.shift;
     a.norm_in = c.norm_in;
     a.norm_in_count = c.norm_in_count;
@@ -318,7 +361,7 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     a.loss_cpp = loss_cpp;
     a.loss_out = c.loss_out;
     PassTimer tm(p, 2, s);
-    SR_CUDA(sr::launch_last(p, sr::s2_layout((c.s0 + c.nfft - 1) % 2), a, B, s), "launch(last pass)");
+    SR_CUDA(sr::launch_last(p, lay, a, B, s), "launch(last pass)");
   }
   return SR_OK;
 }
@@ -339,12 +382,8 @@ Chain round_trip_chain(const Plan& p, int epilogue_op) {
   return c;
 }
 
-// Layout of the epilogue pass (step 2 of DFT L-1), used for the permuted y.
-sr::LineGeom epilogue_geom(const Plan& p) { return sr::geom_for(p, sr::s2_layout((p.L - 1) % 2)); }
-
+// sum(y) per problem (and the GD step mu0 * m / sum(y)) into the scalar workspace.
 sr_status prepare_y(Plan* p, const float* y, int B, float mu0, cudaStream_t s) {
-  const sr::LineGeom ge = epilogue_geom(*p);
-  SR_CUDA(sr::launch_permute_real(y, p->d_yp, B, (int)p->m, ge.nl, ge.ell, s), "launch(permute y)");
   const int chunks = (int)std::min<int64_t>(64, (p->m + 4095) / 4096);
   float* part = part_bank(*p, 3, B);
   SR_CUDA(sr::launch_sum_rows(y, B, (int)p->m, part, chunks, s), "launch(sum y)");
@@ -398,12 +437,26 @@ sr_status sr_plan_create(int64_t n, int64_t m, int L, uint64_t seed, sr_plan** o
   p->m2 = (int)(m / p->m1);
   p->lmax = p->m1;
   p->tw_shift = (a + 1) / 2;
+  p->geom[sr::kLayoutX] = sr::make_geom(m, p->m1);
+  p->geom[sr::kLayoutY] = sr::make_geom(m, p->m2);
+  e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+  for (int lay = 0; lay < 2 && e == cudaSuccess; ++lay)
+    e = sr::pass_occupancy(p->geom[lay], &p->per_sm_mid[lay], &p->per_sm_last[lay]);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "plan geometry");
+  }
   p->theta.resize((size_t)L * m);
   gen_phases(seed, L, m, p->theta.data());
   if ((st = dalloc(&p->d_dp, (size_t)L * m)) != SR_OK || (st = upload_diagonals(p)) != SR_OK ||
-      (st = upload_twiddles(p)) != SR_OK) {
+      (st = upload_twiddles(p)) != SR_OK || (st = dalloc(&p->d_err, 1)) != SR_OK) {
     sr_plan_destroy(p);
     return st;
+  }
+  e = cudaMemset(p->d_err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    sr_plan_destroy(p);
+    return cuda_fail(e, "cudaMemset");
   }
   *out = p;
   return SR_OK;
@@ -414,6 +467,7 @@ sr_status sr_plan_destroy(sr_plan* plan) {
   for (auto& v : plan->ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
   free_workspace(plan);
+  cudaFree(plan->d_err);
   cudaFree(plan->d_dp);
   cudaFree(plan->d_twl);
   cudaFree(plan->d_tw_hi);
@@ -503,7 +557,7 @@ sr_status sr_loss_grad(sr_plan* plan, const void* x, const float* y, float* loss
   c.xout = (float2*)grad;
   c.n_out = (int)p.n;
   c.out_mode = sr::kOutGrad;
-  c.yp = p.d_yp;
+  c.y = y;
   c.loss_part = part_bank(p, 2, B);
   c.loss_out = loss;
   return run_chain(p, c, B, s);
@@ -532,7 +586,7 @@ sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int it
   const int init_chunks = std::min(64, (n + 4095) / 4096);
   float* bank[2] = {part_bank(p, 0, B), part_bank(p, 1, B)};
   SR_CUDA(sr::launch_norm_rows(v, B, n, bank[1], init_chunks, s), "launch(norm v0)");
-  const int last_cpp = sr::geom_for(p, sr::s2_layout((2 * p.L - 1) % 2)).cpp;
+  const int last_cpp = p.geom[sr::s2_layout((2 * p.L - 1) % 2)].cpp;
   Chain c = round_trip_chain(p, sr::kOpSpecEpilogue);
   c.xin = v;
   c.n_in = n;
@@ -540,7 +594,7 @@ sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int it
   c.n_out = n;
   c.out_mode = sr::kOutSpec;
   c.shift = o.weight_mode == SR_WEIGHT_IDENTITY ? 0.f : -2.0f * o.lambda;
-  c.yp = p.d_yp;
+  c.y = y;
   c.sumy = p.d_scal;
   c.lam = o.lambda;
   c.weight_mode = o.weight_mode;
@@ -565,7 +619,9 @@ sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters, const s
   if (!y || !x) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
   if (iters < 0) return fail(SR_ERR_INVALID_ARG, "iters must be >= 0");
   const float mu0 = opts ? opts->mu0 : 0.1f;
+  const float tau0 = opts ? opts->tau0 : 0.f;
   if (!(mu0 > 0.f && std::isfinite(mu0))) return fail(SR_ERR_INVALID_ARG, "mu0 must be finite and > 0");
+  if (!(tau0 >= 0.f && std::isfinite(tau0))) return fail(SR_ERR_INVALID_ARG, "tau0 must be finite and >= 0");
   Plan& p = *plan;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = prepare_y(&p, y, B, mu0, s)) != SR_OK) return st;
@@ -576,11 +632,26 @@ sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters, const s
   c.n_out = (int)p.n;
   c.out_mode = sr::kOutGd;
   c.mu = p.d_scal + B;
-  c.yp = p.d_yp;
+  c.y = y;
   c.loss_part = part_bank(p, 2, B);
   for (int it = 0; it < iters; ++it) {
     c.loss_out = loss_hist ? loss_hist + (size_t)it * B : nullptr;
+    c.mu_scale = tau0 > 0.f ? (float)(1.0 - std::exp(-(double)(it + 1) / (double)tau0)) : 1.0f;
     if ((st = run_chain(p, c, B, s)) != SR_OK) return st;
+  }
+  return SR_OK;
+}
+
+sr_status sr_plan_check(sr_plan* plan) {
+  if (!plan) return fail(SR_ERR_INVALID_ARG, "plan is NULL");
+  sr_status st = check_device(plan);
+  if (st != SR_OK) return st;
+  SR_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  int code = 0;
+  SR_CUDA(cudaMemcpy(&code, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy(status)");
+  if (code != 0) {
+    SR_CUDA(cudaMemset(plan->d_err, 0, sizeof(int)), "cudaMemset(status)");
+    return fail((sr_status)code, "a device-side wait of a pass kernel gave up");
   }
   return SR_OK;
 }

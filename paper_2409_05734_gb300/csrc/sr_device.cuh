@@ -105,44 +105,39 @@ __device__ __forceinline__ void dft_small(float2* a) {
 // ------------------------------------------------------------ line FFT shape
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 
-// A line of N points is held by P = N/E threads with E elements each; thread p
-// holds "slot" j = position p + j*P. Stages: radix 16 while >= 16 remains, then
-// one stage of the remaining radix (N < 16: a single stage of radix N).
+// A line of N points is held by P = N/E threads with E elements each. Threads
+// are numbered tid = t + T*p (line index t fastest, T lines per CTA): thread
+// (t, p) holds "slot" j = position p + j*P of line t. Stages: radix 16 while
+// >= 16 remains, then one stage of the remaining radix (N < 16: a single stage
+// of radix N).
 template <int N>
 struct LineShape {
   static constexpr int E = N < 16 ? N : 16;
   static constexpr int P = N / E;
   static constexpr int LOGN = ilog2c(N);
   static constexpr int NSTAGE = N < 16 ? 1 : (LOGN + 3) / 4;
-  static constexpr int LS = N + N / 16;  // padded shared-memory stride of a line
+  static constexpr int LS = N + N / 16;  // padded positions per line in the scratch
   __host__ __device__ static constexpr int radix(int s) { return N < 16 ? N : (s < LOGN / 4 ? 16 : (1 << (LOGN % 4))); }
-  __host__ __device__ static constexpr int span(int s) { return s == 0 ? 1 : 16 * span(s - 1); }  // Ns of stage s (radix-16 prefix)
+  __host__ __device__ static constexpr int span(int s) { return s == 0 ? 1 : 16 * span(s - 1); }  // Ns of stage s
 };
 
-// Padded shared-memory index: one spare slot after every 16 (bank-conflict relief
-// for the stride-16 writes of the first stage).
+// Padded position: one spare row after every 16 (bank-conflict relief for the
+// stride-16 writes of the first stage when T < 16).
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
-// Synchronise the threads of the lines (a warp when a line fits in one and the
-// block is made of whole warps, else the block).
-template <int P>
-__device__ __forceinline__ void line_sync(bool warp_ok) {
-  if constexpr (P <= 32) {
-    if (warp_ok) {
-      __syncwarp();
-      return;
-    }
-  }
-  __syncthreads();
-}
+// Scratch layout: position-major, line-minor -- element (pos, t) at
+// (pad16(pos) << lgT) + t, so the T lines of one position are contiguous and
+// the line-fastest threads of a warp touch consecutive words.
+__device__ __forceinline__ int sidx(int pos, int t, int lgT) { return (pad16(pos) << lgT) + t; }
 
 // One Stockham radix-R stage (Govindaraju et al., SC'08 formulation): butterfly b
 // reads positions b + r*N/R, applies twiddles W_{Ns R}^{r (b mod Ns)}, a radix-R
 // DFT, and writes position (b/Ns)*Ns*R + (b mod Ns) + r*Ns. Butterflies of this
 // thread: b = p + q*P, q < E/R; their inputs are slots q + r*E/R.
+// tw: shared-memory table W_N^k, k < N.
 template <int N, int S>
-__device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* sm, int p,
-                                          const float2* __restrict__ twl, int tws, bool warp_ok) {
+__device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, int lgT,
+                                          const float2* tw) {
   using LS_ = LineShape<N>;
   constexpr int E = LS_::E, P = LS_::P;
   constexpr int R = LS_::radix(S);
@@ -150,10 +145,9 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* 
   constexpr int Ns = LS_::span(S);
   constexpr bool LAST = (S == LS_::NSTAGE - 1);
   if constexpr (S > 0) {
-    // inputs of this stage: the previous stage's outputs, slot pattern
 #pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = sm[pad16(p + j * P)];
-    if constexpr (!LAST) line_sync<P>(warp_ok);  // everyone read before anyone overwrites
+    for (int j = 0; j < E; ++j) v[j] = sm[sidx(p + j * P, t, lgT)];
+    if constexpr (!LAST) __syncthreads();  // everyone read before anyone overwrites
   }
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
@@ -163,10 +157,9 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* 
     for (int r = 0; r < R; ++r) a[r] = v[q + r * Q];
     if constexpr (S > 0) {
       const int k = b % Ns;
-      // W_{Ns R}^{r k} = W_N^{r k N/(Ns R)}; table holds W_Lmax^j, stride tws = Lmax/N
-      constexpr int step = N / (Ns * R);
+      constexpr int step = N / (Ns * R);  // W_{Ns R}^{r k} = W_N^{r k step}
 #pragma unroll
-      for (int r = 1; r < R; ++r) a[r] = cmul(a[r], __ldg(&twl[(r * k * step) * tws]));
+      for (int r = 1; r < R; ++r) a[r] = cmul(a[r], tw[r * k * step]);
     }
     dft_small<R>(a);
     if constexpr (LAST) {
@@ -174,34 +167,35 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* 
       for (int r = 0; r < R; ++r) v[q + r * Q] = a[r];
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[pad16((b / Ns) * Ns * R + (b % Ns) + r * Ns)] = a[r];
+      for (int r = 0; r < R; ++r) sm[sidx((b / Ns) * Ns * R + (b % Ns) + r * Ns, t, lgT)] = a[r];
     }
   }
-  if constexpr (!LAST) line_sync<P>(warp_ok);
+  if constexpr (!LAST) __syncthreads();
 }
 
 template <int N, int S>
-__device__ __forceinline__ void fft_stages(float2 (&v)[LineShape<N>::E], float2* sm, int p,
-                                           const float2* __restrict__ twl, int tws, bool warp_ok) {
+__device__ __forceinline__ void fft_stages(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, int lgT,
+                                           const float2* tw) {
   if constexpr (S < LineShape<N>::NSTAGE) {
-    fft_stage<N, S>(v, sm, p, twl, tws, warp_ok);
-    fft_stages<N, S + 1>(v, sm, p, twl, tws, warp_ok);
+    fft_stage<N, S>(v, sm, p, t, lgT, tw);
+    fft_stages<N, S + 1>(v, sm, p, t, lgT, tw);
   }
 }
 
-// Unnormalised length-N DFT of one line, sign -1 (dir < 0) or +1 (dir > 0).
+// Unnormalised length-N DFT of line t, sign -1 (dir < 0) or +1 (dir > 0).
 // In: slot j = position p + j*P; out: slot j = frequency p + j*P (natural order).
-// sm: this line's scratch (LineShape<N>::LS float2). The caller synchronises
-// before the call if the scratch was in use by other threads.
+// The scratch is shared by the CTA's lines: every thread of the block must
+// call this together, and the caller synchronises before the call if the
+// scratch was in use.
 template <int N>
-__device__ __forceinline__ void line_fft(float2 (&v)[LineShape<N>::E], float2* sm, int p, int dir,
-                                         const float2* __restrict__ twl, int tws, bool warp_ok) {
+__device__ __forceinline__ void line_fft(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, int lgT, int dir,
+                                         const float2* tw) {
   constexpr int E = LineShape<N>::E;
   if (dir > 0) {
 #pragma unroll
     for (int j = 0; j < E; ++j) v[j].y = -v[j].y;
   }
-  fft_stages<N, 0>(v, sm, p, twl, tws, warp_ok);
+  fft_stages<N, 0>(v, sm, p, t, lgT, tw);
   if (dir > 0) {
 #pragma unroll
     for (int j = 0; j < E; ++j) v[j].y = -v[j].y;

@@ -72,6 +72,11 @@ class Plan:
             _lib.check(self._lib.sr_plan_set_phases(self._h, th.ctypes.data_as(C.POINTER(C.c_double))),
                        "sr_plan_set_phases")
 
+    def check(self) -> None:
+        """Synchronise and raise if a kernel of this plan recorded a device-side error."""
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_plan_check(self._h), "sr_plan_check")
+
     def reserve(self, B: int) -> None:
         with torch.cuda.device(self.device):
             _lib.check(self._lib.sr_plan_reserve(self._h, int(B)), "sr_plan_reserve")
@@ -146,16 +151,17 @@ class Plan:
                                                   _stream_handle()), "sr_spectral_init")
         return x
 
-    def gd_solve(self, y: torch.Tensor, x: torch.Tensor, iters: int, mu0: float = 0.1,
+    def gd_solve(self, y: torch.Tensor, x: torch.Tensor, iters: int, mu0: float = 0.1, tau0: float = 0.0,
                  record_loss: bool = False, loss_hist: torch.Tensor | None = None):
-        """In-place GD on x (Sec. II-B-1); returns (x, loss history [iters, B] or None)."""
+        """In-place GD on x (Sec. II-B-1), step mu0 (1 - exp(-(t+1)/tau0)) m / sum(y)
+        (constant when tau0 == 0); returns (x, loss history [iters, B] or None)."""
         y = self._f32(y, self.m, "y")
         x = self._c64(x, self.n, "x")
         B = self._batch(x)
         hist = loss_hist
         if hist is None and record_loss:
             hist = torch.empty((int(iters), B), dtype=torch.float32, device=self.device)
-        opts = _lib.GdOpts(float(mu0))
+        opts = _lib.GdOpts(float(mu0), float(tau0))
         with torch.cuda.device(self.device):
             _lib.check(self._lib.sr_gd_solve(self._h, _p(y), _p(x), int(iters), C.byref(opts), _p(hist), B,
                                              _stream_handle()), "sr_gd_solve")

@@ -76,9 +76,11 @@ def test_forward_adjoint_match_oracle(Plan, n, m, L, B):
     assert np.array_equal(plan.phases, theta)
     x = S.signal_gaussian(seed, B, n)
     z = host(plan.forward(dev(x)))
+    plan.check()
     assert_close_elementwise(z, O.forward(x, theta, m))
     w = S.complex_gaussian(seed + 1, (B, m), S.STREAM_NOISE)
     xa = host(plan.adjoint(dev(w)))
+    plan.check()
     assert_close_elementwise(xa, O.adjoint(w, theta, n))
 
 
@@ -92,6 +94,7 @@ def test_loss_grad_match_oracle(Plan, n, m, L, B):
     x = S.signal_gaussian(seed + 1, B, n)
     loss_o, g_o = O.loss_and_grad(x, y, fwd, adj)
     loss, g = plan.loss_grad(dev(x), dev(y, torch.float32))
+    plan.check()
     assert np.max(np.abs(host(loss) - loss_o) / loss_o) <= 1e-5
     assert_close_elementwise(host(g), g_o)
 
@@ -139,6 +142,23 @@ def test_gradient_descent_matches_oracle_small_config(Plan):
     assert np.max(np.abs(h[:50] - hist_o[:50, 0]) / hist_o[:50, 0]) <= 1e-3
 
 
+def test_gradient_descent_warmup_schedule_matches_oracle(Plan):
+    n, m, L, B = 64, 256, 2, 4
+    seed = 11
+    plan = Plan(n, m, L, seed)
+    theta = S.phases(seed, L, m)
+    fwd, adj = O.structured_ops(theta, n, m)
+    x_true = S.signal_gaussian(seed, B, n)
+    y = np.abs(fwd(x_true)) ** 2
+    x0 = O.spectral_init(y, S.start_vector(seed, B, n), fwd, adj, 50, mode="optimal")
+    xT_o, _ = O.gradient_descent(x0, y, fwd, adj, 200, mu0=0.15, tau0=30.0)
+    x = dev(x0)
+    plan.gd_solve(dev(y, torch.float32), x, 200, mu0=0.15, tau0=30.0)
+    e_gpu = O.relative_error_global_phase(host(x), x_true)
+    e_or = O.relative_error_global_phase(xT_o, x_true)
+    assert np.max(np.abs(e_gpu - e_or)) <= 1e-4, (e_gpu, e_or)
+
+
 def test_full_size_batch_sampled(Plan):
     """The benchmark shape: B = 64 signals, n = 2^14, alpha = 4 (m = 2^16), L = 2.
     All 64 forward outputs against the oracle; the solver checked on sampled
@@ -156,6 +176,7 @@ def test_full_size_batch_sampled(Plan):
     v0 = S.start_vector(seed, B, n)
     x = plan.spectral_init(y, dev(v0), 10, weight="optimal")
     _, hist = plan.gd_solve(y, x, 20, mu0=0.1, record_loss=True)
+    plan.check()
     xg = host(x)
     hg = host(hist)
     for b in (0, 37, 63):

@@ -159,3 +159,20 @@ def test_paper_claims_layers_and_alpha():
         assert c[(a, 2)] > c[(a, 1)] + 0.25
         assert abs(c[(a, 3)] - c[(a, 2)]) < 0.1
     assert c[(2, 2)] < c[(3, 2)] < c[(4, 2)]
+
+
+def test_step_ramp_and_gd_with_warmup():
+    """ramp_t = 1 - exp(-(t+1)/tau0): closed form at chosen t; constant when tau0 = 0;
+    GD with the warm-up still recovers the tiny noiseless problem."""
+    assert O.step_ramp(0, 0.0) == 1.0 and O.step_ramp(123, 0.0) == 1.0
+    assert np.isclose(O.step_ramp(99, 100.0), 1 - np.exp(-1.0))
+    assert np.isclose(O.step_ramp(0, 1.0), 1 - np.exp(-1.0))
+    assert O.step_ramp(5, 10.0) < O.step_ramp(6, 10.0) < 1.0
+    theta, x, y, fwd, adj, m = _problem(2, 32, 4, 2)
+    x0 = O.spectral_init(y, S.start_vector(2, 1, 32), fwd, adj, 50, mode="optimal")
+    # one step by hand: x1 = x0 - (1 - e^{-1/tau0}) * mu0 * m / sum(y) * g(x0)
+    _, g0 = O.loss_and_grad(x0, y, fwd, adj)
+    x1, _ = O.gradient_descent(x0, y, fwd, adj, 1, mu0=0.15, tau0=20.0)
+    assert np.allclose(x1, x0 - (1 - np.exp(-1 / 20.0)) * 0.15 * m / y.sum() * g0, atol=1e-12)
+    xT, hist = O.gradient_descent(x0, y, fwd, adj, 3000, mu0=0.15, tau0=100.0)
+    assert O.relative_error_global_phase(xT, x)[0] < 1e-8
