@@ -14,7 +14,9 @@
 // per warp instruction straight from registers. The exchange rows a MID/LAST
 // pass reads are brought into shared memory by 2D TMA loads with 128-byte
 // swizzle, double-buffered across the tiles of a persistent grid so that the
-// next tile's load overlaps the current tile's FFTs.
+// next tile's load overlaps the current tile's FFTs. Kernels are instantiated
+// per tile shape (line length ELL, lines per CTA T) so that all index
+// arithmetic folds at compile time.
 #include <algorithm>
 #include <atomic>
 
@@ -28,6 +30,24 @@ std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
+// Threads per CTA allowed for lines of length ELL: 256 up to ELL = 512, 512 beyond.
+__host__ __device__ constexpr int pass_threads(int ell) { return ell <= 512 ? 256 : 512; }
+
+// Input tiles are staged by TMA when a box row is a whole 128-byte line and the
+// box (T rows) fills a 1024-byte swizzle period.
+__host__ __device__ constexpr bool uses_tma(int ell, int T) { return ell >= 16 && T >= 8; }
+
+template <int ELL, int T_>
+struct Tile {
+  static constexpr int T = T_;
+  static constexpr int E = LineShape<ELL>::E, P = LineShape<ELL>::P;
+  static constexpr int THREADS = T * P;
+  static constexpr bool TMA = uses_tma(ELL, T);
+  static constexpr int BOX = T * 128;  // bytes of one box: 16 complex values x T rows
+  static constexpr int MIN_CTAS = THREADS <= 256 ? 2 : 1;
+  static_assert(THREADS <= 512, "tile too large");
+};
+
 // ------------------------------------------------------ shared-memory layout
 struct PipeSmem {
   size_t in0, in1, scratch, tw, rowtw, bar, total;
@@ -35,15 +55,12 @@ struct PipeSmem {
 
 __host__ __device__ inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Bytes one TMA box (16 complex values x T rows) occupies in shared memory:
-// every box starts on a 1024-byte boundary (the period of the 128-byte swizzle).
-__host__ __device__ inline int box_bytes(int T) { return (int)round_up((size_t)T * 128, 1024); }
-
-// Layout relative to a 1024-byte-aligned base. tma: the pass stages its input
-// tiles (T rows of ell complex values, ell/16 boxes) in `nbuf` swizzled buffers.
-__host__ __device__ inline PipeSmem pipe_layout(int ell, int T, int nbuf, bool tma) {
+// Layout relative to a 1024-byte-aligned base; input tiles (T rows of ell
+// complex values as ell/16 boxes) in `nbuf` swizzled buffers when staged.
+__host__ __device__ inline PipeSmem pipe_layout(int ell, int T, int nbuf, bool stage_input) {
   PipeSmem L;
-  const size_t tile = tma ? (size_t)(ell / 16) * box_bytes(T) : 0;
+  const bool tma = stage_input && uses_tma(ell, T);
+  const size_t tile = tma ? (size_t)(ell / 16) * T * 128 : 0;
   const int E = ell < 16 ? ell : 16;
   L.in0 = 0;
   L.in1 = tile;
@@ -66,9 +83,11 @@ __device__ __forceinline__ unsigned char* aligned_smem(unsigned char* raw) {
 
 // ------------------------------------------------------------------ tables
 
-// W_m^e = W_m^(hi part) * W_m^(lo part), both tables rounded from double.
-__device__ __forceinline__ float2 tw_m(const PassArgs& a, int e) {
-  return cmul(__ldg(&a.tw_hi[e >> a.tw_shift]), __ldg(&a.tw_lo[e & ((1 << a.tw_shift) - 1)]));
+// W_m^e = W_m^(hi part) * W_m^(lo part), both tables rounded from double;
+// conjugated when dir > 0.
+__device__ __forceinline__ float2 tw_m(const PassArgs& a, int e, int dir) {
+  const float2 w = cmul(__ldg(&a.tw_hi[e >> a.tw_shift]), __ldg(&a.tw_lo[e & ((1 << a.tw_shift) - 1)]));
+  return dir > 0 ? conjf2(w) : w;
 }
 
 // Line twiddles W_ELL^k, k < ELL, into shared memory.
@@ -77,60 +96,86 @@ __device__ __forceinline__ void load_line_twiddles(const PassArgs& a, float2* tw
   for (int i = threadIdx.x; i < ELL; i += blockDim.x) tw[i] = __ldg(&a.twl[i * a.tws]);
 }
 
-// Four-step twiddle of (line g, frequency f = p + j*P) is W_m^(g p) * W_m^(g P j);
-// the second factor is tabulated per tile: rowtw[j*T + t] = W_m^((g0 + t) P j).
-template <int ELL>
-__device__ __forceinline__ void fill_row_twiddles(const PassArgs& a, int g0, float2* rowtw) {
-  constexpr int E = LineShape<ELL>::E, P = LineShape<ELL>::P;
-  for (int i = threadIdx.x; i < E * a.T; i += blockDim.x) {
-    const int t = i & (a.T - 1), j = i >> a.lgT;
-    rowtw[i] = tw_m(a, (g0 + t) * P * j);
+// The four-step twiddle of (line g, frequency f = p + j*P) is
+// W_m^(g p) * W_m^(g P j); the second factor is tabulated per tile,
+// rowtw[j*T + t] = W_m^((g0 + t) P j). RowTw holds this thread's entries of
+// the table between their (early) load and their (late) store to shared memory.
+template <class TL>
+struct RowTw {
+  static constexpr int N = (TL::E * TL::T + TL::THREADS - 1) / TL::THREADS;
+  float2 w[N];
+  __device__ __forceinline__ void load(const PassArgs& a, int g0, int dir) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int i = threadIdx.x + k * TL::THREADS;
+      if (i < TL::E * TL::T) w[k] = tw_m(a, (g0 + i % TL::T) * TL::P * (i / TL::T), dir);
+    }
   }
-}
+  __device__ __forceinline__ void store(float2* rowtw) const {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int i = threadIdx.x + k * TL::THREADS;
+      if (i < TL::E * TL::T) rowtw[i] = w[k];
+    }
+  }
+};
 
-// Step-1 outputs of line g times W_m^(dir g f), stored to the exchange buffer
-// at f*NL + g (T consecutive elements per frequency across the warp).
-template <int ELL>
-__device__ __forceinline__ void twiddle_store(float2 (&v)[LineShape<ELL>::E], const PassArgs& a, int b, int g,
-                                              int t, int p, const float2* rowtw) {
-  constexpr int E = LineShape<ELL>::E, P = LineShape<ELL>::P;
-  const float2 A = tw_m(a, g * p);
+// Step-1 outputs of line g times the four-step twiddles (already conjugated
+// for an inverse transform), stored to the exchange buffer at f*NL + g
+// (T consecutive elements per frequency across the warp).
+template <class TL>
+__device__ __forceinline__ void twiddle_store(float2 (&v)[TL::E], const PassArgs& a, int b, int g, int t, int p,
+                                              float2 A, const float2* rowtw) {
   float2* eb = a.eout + (size_t)b * a.m + g;
 #pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const float2 w = cmul(A, rowtw[j * a.T + t]);
-    const float2 o = a.out_dir > 0 ? cmulc(v[j], w) : cmul(v[j], w);
-    eb[(size_t)(p + j * P) * a.nl] = o;
+  for (int j = 0; j < TL::E; ++j) {
+    const float2 w = cmul(A, rowtw[j * TL::T + t]);
+    eb[(size_t)(p + j * TL::P) * a.nl] = cmul(v[j], w);
   }
 }
 
-// Elementwise operation at (line g, frequency f): natural index f*NL + g.
-template <int ELL>
-__device__ __forceinline__ void mid_op(float2 (&v)[LineShape<ELL>::E], const PassArgs& a, int b, int g, int p,
-                                       fsum2& acc) {
-  constexpr int E = LineShape<ELL>::E, P = LineShape<ELL>::P;
+// Values an elementwise operation needs at (line g, frequency f), natural
+// index f*NL + g: the diagonal entries, or the measurements. Loaded before the
+// pass's first FFT so that their latency overlaps it.
+template <class TL>
+struct OpData {
+  float2 d[TL::E];
+  float y[TL::E];
+  __device__ __forceinline__ void load(const PassArgs& a, int op, int b, int g, int p) {
+    if (op == kOpDiag || op == kOpDiagConj) {
+#pragma unroll
+      for (int j = 0; j < TL::E; ++j) d[j] = __ldg(&a.dp[(p + j * TL::P) * a.nl + g]);
+    } else if (op == kOpGdEpilogue || op == kOpSpecEpilogue) {
+      const float* yb = a.y + (size_t)b * a.m + g;
+#pragma unroll
+      for (int j = 0; j < TL::E; ++j) y[j] = __ldg(&yb[(p + j * TL::P) * a.nl]);
+    }
+  }
+};
+
+template <class TL>
+__device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, const OpData<TL>& od, int b,
+                                         fsum2& acc) {
   if (a.op == kOpDiag) {
 #pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = cmul(v[j], __ldg(&a.dp[(p + j * P) * a.nl + g]));
+    for (int j = 0; j < TL::E; ++j) v[j] = cmul(v[j], od.d[j]);
   } else if (a.op == kOpDiagConj) {
 #pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&a.dp[(p + j * P) * a.nl + g]));
+    for (int j = 0; j < TL::E; ++j) v[j] = cmulc(v[j], od.d[j]);
   } else if (a.op == kOpGdEpilogue) {
     // z -> r = |z|^2 - y, w = r z (Eq. 2); loss partial sum of r^2
-    const float* y = a.y + (size_t)b * a.m + g;
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const float r = cabs2(v[j]) - __ldg(&y[(p + j * P) * a.nl]);
+    for (int j = 0; j < TL::E; ++j) {
+      const float r = cabs2(v[j]) - od.y[j];
       acc_add(acc, r * r);
       v[j] = cscale(v[j], r);
     }
   } else if (a.op == kOpSpecEpilogue) {
     // z -> T(y_hat) z, y_hat = m y / sum(y) (Eq. 3)
-    const float* y = a.y + (size_t)b * a.m + g;
     const float scale = (float)a.m / __ldg(&a.sumy[b]);
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const float yh = __ldg(&y[(p + j * P) * a.nl]) * scale;
+    for (int j = 0; j < TL::E; ++j) {
+      const float yh = od.y[j] * scale;
       float w;
       if (a.weight_mode == SR_WEIGHT_IDENTITY) w = yh;
       else w = yh > 0.f ? fmaxf(1.0f - 1.0f / yh, a.lam) : a.lam;
@@ -141,27 +186,25 @@ __device__ __forceinline__ void mid_op(float2 (&v)[LineShape<ELL>::E], const Pas
 
 // ------------------------------------------------------------ FIRST pass
 
-// Threads per CTA of the passes over lines of length ELL (make_geom keeps
-// T * P within this bound): 256 up to ELL = 512, 512 beyond; at least two
-// CTAs per SM for the shorter lines.
-__host__ __device__ constexpr int pass_threads(int ell) { return ell <= 512 ? 256 : 512; }
-__host__ __device__ constexpr int pass_min_ctas(int ell) { return ell <= 512 ? 2 : 1; }
-
-template <int ELL>
-__global__ void __launch_bounds__(pass_threads(ELL), pass_min_ctas(ELL)) k_first(const __grid_constant__ PassArgs a) {
-  using S = LineShape<ELL>;
-  constexpr int E = S::E, P = S::P;
+template <int ELL, int T>
+__global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
+    k_first(const __grid_constant__ PassArgs a) {
+  using TL = Tile<ELL, T>;
+  constexpr int E = TL::E, P = TL::P;
   extern __shared__ unsigned char smem_raw[];
   __shared__ float s_scale;
   unsigned char* smem = aligned_smem(smem_raw);
-  const PipeSmem L = pipe_layout(ELL, a.T, 1, false);
+  const PipeSmem L = pipe_layout(ELL, T, 1, false);
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
   float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
-  const int tid = threadIdx.x, lgT = a.lgT, t = tid & (a.T - 1), p = tid >> lgT;
-  const int b = blockIdx.x / a.cpp, g0 = (blockIdx.x - b * a.cpp) << lgT, g = g0 + t;
+  const int tid = threadIdx.x, t = tid % T, p = tid / T;
+  const int b = blockIdx.x / a.cpp, g0 = (blockIdx.x - b * a.cpp) * T, g = g0 + t;
   load_line_twiddles<ELL>(a, tw);
-  fill_row_twiddles<ELL>(a, g0, rowtw);
+  RowTw<TL> rw;
+  rw.load(a, g0, a.out_dir);
+  rw.store(rowtw);
+  const float2 A = tw_m(a, g * p, a.out_dir);
   if (tid == 0)
     s_scale = a.norm_in ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count))
                         : 1.0f;
@@ -174,67 +217,66 @@ __global__ void __launch_bounds__(pass_threads(ELL), pass_min_ctas(ELL)) k_first
     const int nat = (p + j * P) * a.nl + g;
     v[j] = nat < a.n_in ? xb[nat] : make_float2(0.f, 0.f);
   }
-  __syncthreads();
-  const float sc = s_scale;
-#pragma unroll
-  for (int j = 0; j < E; ++j) v[j] = cscale(v[j], sc);
   if (a.op == kOpDiag) {
 #pragma unroll
     for (int j = 0; j < E; ++j) v[j] = cmul(v[j], __ldg(&a.dp[(p + j * P) * a.nl + g]));
   }
-  line_fft<ELL>(v, scratch, p, t, lgT, a.out_dir, tw);
-  twiddle_store<ELL>(v, a, b, g, t, p, rowtw);
+  __syncthreads();
+  const float sc = s_scale;
+#pragma unroll
+  for (int j = 0; j < E; ++j) v[j] = cscale(v[j], sc);
+  line_fft<ELL, T>(v, scratch, p, t, a.out_dir, tw);
+  twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
 }
 
 // ------------------------------------------------------ MID and LAST passes
 
 // Issues the TMA loads of tile `tile` (T rows of ELL complex values, boxes of
 // 16 values x T rows) into `buf`, completing on barrier `bar`.
-template <int ELL>
+template <class TL, int ELL>
 __device__ __forceinline__ void issue_tile(const PassArgs& a, int tile, uint32_t buf, uint32_t bar) {
-  const int b = tile / a.cpp, g0 = (tile - b * a.cpp) << a.lgT;
+  const int b = tile / a.cpp, g0 = (tile - b * a.cpp) * TL::T;
   const int row = b * a.nl + g0;
-  mbar_arrive_expect_tx(bar, (uint32_t)(a.T * ELL * 8));
+  mbar_arrive_expect_tx(bar, (uint32_t)(TL::T * ELL * 8));
 #pragma unroll 1
-  const int bb = box_bytes(a.T);
-  for (int kb = 0; kb < ELL / 16; ++kb) tma_load_2d(buf + (uint32_t)(kb * bb), &a.tmap, kb * 32, row, bar);
+  for (int kb = 0; kb < ELL / 16; ++kb) tma_load_2d(buf + (uint32_t)(kb * TL::BOX), &a.tmap, kb * 32, row, bar);
 }
 
 // Shared pipeline of the persistent MID / LAST passes: for every tile of this
 // CTA, loads the T input lines (rows of the exchange buffer) into registers
 // (slot j = position p + j*P) and calls body(v, b, g0).
-template <int ELL, class Body>
+template <int ELL, int T, class Body>
 __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned char* smem, const PipeSmem& L,
                                            Body&& body) {
-  constexpr int E = LineShape<ELL>::E, P = LineShape<ELL>::P;
-  constexpr bool kTma = ELL >= 16;
-  const int tid = threadIdx.x, lgT = a.lgT, t = tid & (a.T - 1), p = tid >> lgT;
+  using TL = Tile<ELL, T>;
+  constexpr int E = TL::E, P = TL::P;
+  const int tid = threadIdx.x, t = tid % T, p = tid / T;
   // an earlier pass gave up (see mbar_wait_bounded): do nothing
   if (__syncthreads_or(tid == 0 && *(volatile int*)a.err != 0)) return;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar);
   const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
   const uint32_t in0 = smem_addr(smem + L.in0), in1 = smem_addr(smem + L.in1);
   int tile = blockIdx.x;
-  if constexpr (kTma) {
+  if constexpr (TL::TMA) {
     if (tid == 0) {
       mbar_init(bar0, 1);
       mbar_init(bar1, 1);
       mbar_init_fence();
     }
     __syncthreads();
-    if (tid == 0 && tile < a.ntiles) issue_tile<ELL>(a, tile, in0, bar0);
+    if (tid == 0 && tile < a.ntiles) issue_tile<TL, ELL>(a, tile, in0, bar0);
   }
   for (int k = 0; tile < a.ntiles; ++k, tile += gridDim.x) {
-    const int b = tile / a.cpp, g0 = (tile - b * a.cpp) << lgT, g = g0 + t;
+    const int b = tile / a.cpp, g0 = (tile - b * a.cpp) * T, g = g0 + t;
     const int next = tile + (int)gridDim.x;
     float2 v[E];
-    if constexpr (kTma) {
+    if constexpr (TL::TMA) {
       const int buf = nbuf == 2 ? (k & 1) : 0;
       const uint32_t parity = nbuf == 2 ? (uint32_t)((k >> 1) & 1) : (uint32_t)(k & 1);
       const uint32_t bar = buf ? bar1 : bar0;
       if (nbuf == 2 && tid == 0 && next < a.ntiles) {
         fence_proxy_async_smem();
-        issue_tile<ELL>(a, next, buf ? in0 : in1, buf ? bar0 : bar1);
+        issue_tile<TL, ELL>(a, next, buf ? in0 : in1, buf ? bar0 : bar1);
       }
       const bool ok = mbar_wait_bounded(bar, parity);
       if (!__syncthreads_and(ok)) {
@@ -246,14 +288,13 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
         return;
       }
       const unsigned char* src = smem + (buf ? L.in1 : L.in0);
-      const int bb = box_bytes(a.T);
 #pragma unroll
-      for (int j = 0; j < E; ++j) v[j] = *reinterpret_cast<const float2*>(src + swz128_offset(bb, t, p + j * P));
+      for (int j = 0; j < E; ++j) v[j] = *reinterpret_cast<const float2*>(src + swz128_offset(TL::BOX, t, p + j * P));
       if (nbuf == 1) {
         __syncthreads();  // every thread has its slots before the buffer is refilled
         if (tid == 0 && next < a.ntiles) {
           fence_proxy_async_smem();
-          issue_tile<ELL>(a, next, in0, bar0);
+          issue_tile<TL, ELL>(a, next, in0, bar0);
         }
       }
     } else {
@@ -266,51 +307,58 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
   }
 }
 
-template <int ELL>
-__global__ void __launch_bounds__(pass_threads(ELL), pass_min_ctas(ELL)) k_mid(const __grid_constant__ PassArgs a, int nbuf) {
-  using S = LineShape<ELL>;
-  constexpr int E = S::E;
+template <int ELL, int T>
+__global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
+    k_mid(const __grid_constant__ PassArgs a, int nbuf) {
+  using TL = Tile<ELL, T>;
+  constexpr int E = TL::E;
   extern __shared__ unsigned char smem_raw[];
   __shared__ float red[64];
   unsigned char* smem = aligned_smem(smem_raw);
-  const PipeSmem L = pipe_layout(ELL, a.T, nbuf, ELL >= 16);
+  const PipeSmem L = pipe_layout(ELL, T, nbuf, true);
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
   float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
-  const int tid = threadIdx.x, lgT = a.lgT, t = tid & (a.T - 1), p = tid >> lgT;
+  const int tid = threadIdx.x, t = tid % T, p = tid / T;
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
-  pipe_tiles<ELL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
+  pipe_tiles<ELL, T>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
     const int g = g0 + t;
-    fill_row_twiddles<ELL>(a, g0, rowtw);
-    line_fft<ELL>(v, scratch, p, t, lgT, a.in_dir, tw);
+    OpData<TL> od;
+    od.load(a, a.op, b, g, p);
+    RowTw<TL> rw;
+    rw.load(a, g0, a.out_dir);
+    const float2 A = tw_m(a, g * p, a.out_dir);
+    line_fft<ELL, T>(v, scratch, p, t, a.in_dir, tw);
     fsum2 acc{0.f, 0.f};
-    mid_op<ELL>(v, a, b, g, p, acc);
+    apply_op<TL>(v, a, od, b, acc);
     if (a.op == kOpGdEpilogue) {
       const float s = block_sum(acc, red);
-      if (tid == 0) a.part_out[(size_t)b * a.cpp + (g0 >> lgT)] = s;
+      if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = s;
     }
+    rw.store(rowtw);
     __syncthreads();  // first FFT's scratch reads done; row twiddles visible
-    line_fft<ELL>(v, scratch, p, t, lgT, a.out_dir, tw);
-    twiddle_store<ELL>(v, a, b, g, t, p, rowtw);
+    line_fft<ELL, T>(v, scratch, p, t, a.out_dir, tw);
+    twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
   });
 }
 
-template <int ELL>
-__global__ void __launch_bounds__(pass_threads(ELL), pass_min_ctas(ELL)) k_last(const __grid_constant__ PassArgs a, int nbuf) {
-  using S = LineShape<ELL>;
-  constexpr int E = S::E, P = S::P;
+template <int ELL, int T>
+__global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
+    k_last(const __grid_constant__ PassArgs a, int nbuf) {
+  using TL = Tile<ELL, T>;
+  constexpr int E = TL::E, P = TL::P;
   extern __shared__ unsigned char smem_raw[];
   __shared__ float red[64];
   __shared__ float s_inv_old, s_mu;
   unsigned char* smem = aligned_smem(smem_raw);
-  const PipeSmem L = pipe_layout(ELL, a.T, nbuf, ELL >= 16);
+  const PipeSmem L = pipe_layout(ELL, T, nbuf, true);
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
-  const int tid = threadIdx.x, lgT = a.lgT, t = tid & (a.T - 1), p = tid >> lgT;
+  const int tid = threadIdx.x, t = tid % T, p = tid / T;
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
-  pipe_tiles<ELL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
+  pipe_tiles<ELL, T>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
     const int g = g0 + t;
     if (tid == 0) {
       s_inv_old = (a.out_mode == kOutSpec && a.norm_in)
@@ -318,11 +366,13 @@ __global__ void __launch_bounds__(pass_threads(ELL), pass_min_ctas(ELL)) k_last(
                       : 1.0f;
       s_mu = a.mu ? a.mu[b] : 0.f;
     }
-    line_fft<ELL>(v, scratch, p, t, lgT, a.in_dir, tw);
+    OpData<TL> od;
+    od.load(a, a.op, b, g, p);
+    line_fft<ELL, T>(v, scratch, p, t, a.in_dir, tw);
     __syncthreads();  // tile scalars visible
     if (a.op == kOpDiagConj) {
 #pragma unroll
-      for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&a.dp[(p + j * P) * a.nl + g]));
+      for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], od.d[j]);
     }
     // natural index of (line g, frequency f) is f*NL + g; keep those < n_out (U^H)
     float2* xb = a.xout + (size_t)b * a.n_out;
@@ -351,7 +401,7 @@ __global__ void __launch_bounds__(pass_threads(ELL), pass_min_ctas(ELL)) k_last(
     }
     if (a.out_mode == kOutSpec) {
       const float s = block_sum(acc, red);
-      if (tid == 0) a.part_out[(size_t)b * a.cpp + (g0 >> lgT)] = s;
+      if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = s;
     }
     if (a.loss_out && g0 == 0 && tid == 0)
       a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
@@ -419,15 +469,14 @@ LineGeom make_geom(int64_t m, int ell) {
   int T = std::max(8, 256 / g.P);
   T = std::min(T, pass_threads(ell) / g.P);
   T = std::min(T, g.nl);
-  const bool tma = ell >= 16;
-  while (T > 1 && pipe_layout(ell, T, 1, tma).total + 1024 > kSmemBudget) T >>= 1;
+  while (T > 1 && pipe_layout(ell, T, 1, true).total + 1024 > kSmemBudget) T >>= 1;
   g.T = T;
   g.lgT = 0;
   while ((1 << g.lgT) < T) ++g.lgT;
   g.cpp = g.nl / T;
   g.threads = T * g.P;
-  g.nbuf = (tma && pipe_layout(ell, T, 2, tma).total + 1024 <= kSmemBudget) ? 2 : 1;
-  g.smem_pipe = pipe_layout(ell, T, g.nbuf, tma).total + 1024;
+  g.nbuf = (uses_tma(ell, T) && pipe_layout(ell, T, 2, true).total + 1024 <= kSmemBudget) ? 2 : 1;
+  g.smem_pipe = pipe_layout(ell, T, g.nbuf, true).total + 1024;
   g.smem_first = pipe_layout(ell, T, 1, false).total + 1024;
   return g;
 }
@@ -437,22 +486,32 @@ LineGeom make_geom(int64_t m, int ell) {
 Layout s1_layout(int parity) { return parity == 0 ? kLayoutX : kLayoutY; }
 Layout s2_layout(int parity) { return parity == 0 ? kLayoutY : kLayoutX; }
 
-#define SR_ELL_SWITCH(ell, KERNEL, fn)     \
-  switch (ell) {                           \
-    case 2: fn = KERNEL<2>; break;         \
-    case 4: fn = KERNEL<4>; break;         \
-    case 8: fn = KERNEL<8>; break;         \
-    case 16: fn = KERNEL<16>; break;       \
-    case 32: fn = KERNEL<32>; break;       \
-    case 64: fn = KERNEL<64>; break;       \
-    case 128: fn = KERNEL<128>; break;     \
-    case 256: fn = KERNEL<256>; break;     \
-    case 512: fn = KERNEL<512>; break;     \
-    case 1024: fn = KERNEL<1024>; break;   \
-    case 2048: fn = KERNEL<2048>; break;   \
-    case 4096: fn = KERNEL<4096>; break;   \
-    default: return cudaErrorInvalidValue; \
-  }
+// Every (line length, lines per CTA) pair make_geom produces for m = 4 .. 2^24.
+#define SR_TILE_SHAPES(X)                                                                                      \
+  X(2, 2) X(2, 4) X(4, 2) X(4, 4) X(4, 8) X(8, 4) X(8, 8) X(8, 16) X(16, 8) X(16, 16) X(16, 32) X(32, 16)    \
+  X(32, 32) X(32, 64) X(64, 32) X(64, 64) X(128, 32) X(256, 16) X(512, 8) X(1024, 8) X(2048, 4) X(4096, 2)
+
+#define SR_PICK(ELL_, T_) \
+  if (ell == ELL_ && T == T_) return reinterpret_cast<const void*>(&KERNEL<ELL_, T_>);
+
+static const void* pick_first(int ell, int T) {
+#define KERNEL k_first
+  SR_TILE_SHAPES(SR_PICK)
+#undef KERNEL
+  return nullptr;
+}
+static const void* pick_mid(int ell, int T) {
+#define KERNEL k_mid
+  SR_TILE_SHAPES(SR_PICK)
+#undef KERNEL
+  return nullptr;
+}
+static const void* pick_last(int ell, int T) {
+#define KERNEL k_last
+  SR_TILE_SHAPES(SR_PICK)
+#undef KERNEL
+  return nullptr;
+}
 
 static cudaError_t allow_smem(const void* fn, size_t smem) {
   if (smem <= 48 * 1024) return cudaSuccess;
@@ -474,8 +533,8 @@ static PassArgs with_geom(const PassArgs& a0, const Plan& p, const LineGeom& g, 
 
 cudaError_t launch_first(const Plan& p, Layout lay, const PassArgs& a0, int B, cudaStream_t s) {
   const LineGeom& g = p.geom[lay];
-  void (*fn)(PassArgs) = nullptr;
-  SR_ELL_SWITCH(g.ell, k_first, fn);
+  auto fn = reinterpret_cast<void (*)(PassArgs)>(const_cast<void*>(pick_first(g.ell, g.T)));
+  if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = allow_smem((const void*)fn, g.smem_first);
   if (e != cudaSuccess) return e;
   const PassArgs a = with_geom(a0, p, g, B);
@@ -486,12 +545,9 @@ cudaError_t launch_first(const Plan& p, Layout lay, const PassArgs& a0, int B, c
 
 static cudaError_t launch_pipe(bool last, const Plan& p, Layout lay, const PassArgs& a0, int B, cudaStream_t s) {
   const LineGeom& g = p.geom[lay];
-  void (*fn)(PassArgs, int) = nullptr;
-  if (last) {
-    SR_ELL_SWITCH(g.ell, k_last, fn);
-  } else {
-    SR_ELL_SWITCH(g.ell, k_mid, fn);
-  }
+  auto fn = reinterpret_cast<void (*)(PassArgs, int)>(
+      const_cast<void*>(last ? pick_last(g.ell, g.T) : pick_mid(g.ell, g.T)));
+  if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = allow_smem((const void*)fn, g.smem_pipe);
   if (e != cudaSuccess) return e;
   const PassArgs a = with_geom(a0, p, g, B);
@@ -510,13 +566,12 @@ cudaError_t launch_last(const Plan& p, Layout lay, const PassArgs& a, int B, cud
 }
 
 cudaError_t pass_occupancy(const LineGeom& g, int* per_sm_mid, int* per_sm_last) {
-  void (*fm)(PassArgs, int) = nullptr;
-  void (*fl)(PassArgs, int) = nullptr;
-  SR_ELL_SWITCH(g.ell, k_mid, fm);
-  SR_ELL_SWITCH(g.ell, k_last, fl);
+  const void* fm = pick_mid(g.ell, g.T);
+  const void* fl = pick_last(g.ell, g.T);
+  if (!fm || !fl) return cudaErrorInvalidValue;
   cudaError_t e;
-  if ((e = allow_smem((const void*)fm, g.smem_pipe)) != cudaSuccess) return e;
-  if ((e = allow_smem((const void*)fl, g.smem_pipe)) != cudaSuccess) return e;
+  if ((e = allow_smem(fm, g.smem_pipe)) != cudaSuccess) return e;
+  if ((e = allow_smem(fl, g.smem_pipe)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_mid, fm, g.threads, g.smem_pipe)) != cudaSuccess)
     return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_last, fl, g.threads, g.smem_pipe)) != cudaSuccess)

@@ -122,22 +122,22 @@ struct LineShape {
 };
 
 // Padded position: one spare row after every 16 (bank-conflict relief for the
-// stride-16 writes of the first stage when T < 16).
-__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+// stride-16 writes of the first stage when fewer than 16 lines share a row).
+__host__ __device__ constexpr int pad16(int i) { return i + (i >> 4); }
 
 // Scratch layout: position-major, line-minor -- element (pos, t) at
-// (pad16(pos) << lgT) + t, so the T lines of one position are contiguous and
-// the line-fastest threads of a warp touch consecutive words.
-__device__ __forceinline__ int sidx(int pos, int t, int lgT) { return (pad16(pos) << lgT) + t; }
+// pad16(pos) * T + t, so the T lines of one position are contiguous and the
+// line-fastest threads of a warp touch consecutive words.
+template <int T>
+__device__ __forceinline__ int sidx(int pos, int t) { return pad16(pos) * T + t; }
 
 // One Stockham radix-R stage (Govindaraju et al., SC'08 formulation): butterfly b
 // reads positions b + r*N/R, applies twiddles W_{Ns R}^{r (b mod Ns)}, a radix-R
 // DFT, and writes position (b/Ns)*Ns*R + (b mod Ns) + r*Ns. Butterflies of this
 // thread: b = p + q*P, q < E/R; their inputs are slots q + r*E/R.
 // tw: shared-memory table W_N^k, k < N.
-template <int N, int S>
-__device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, int lgT,
-                                          const float2* tw) {
+template <int N, int T, int S>
+__device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, const float2* tw) {
   using LS_ = LineShape<N>;
   constexpr int E = LS_::E, P = LS_::P;
   constexpr int R = LS_::radix(S);
@@ -146,7 +146,7 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* 
   constexpr bool LAST = (S == LS_::NSTAGE - 1);
   if constexpr (S > 0) {
 #pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = sm[sidx(p + j * P, t, lgT)];
+    for (int j = 0; j < E; ++j) v[j] = sm[sidx<T>(p + j * P, t)];
     if constexpr (!LAST) __syncthreads();  // everyone read before anyone overwrites
   }
 #pragma unroll
@@ -167,38 +167,41 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* 
       for (int r = 0; r < R; ++r) v[q + r * Q] = a[r];
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[sidx((b / Ns) * Ns * R + (b % Ns) + r * Ns, t, lgT)] = a[r];
+      for (int r = 0; r < R; ++r) sm[sidx<T>((b / Ns) * Ns * R + (b % Ns) + r * Ns, t)] = a[r];
     }
   }
   if constexpr (!LAST) __syncthreads();
 }
 
-template <int N, int S>
-__device__ __forceinline__ void fft_stages(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, int lgT,
-                                           const float2* tw) {
+template <int N, int T, int S>
+__device__ __forceinline__ void fft_stages(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, const float2* tw) {
   if constexpr (S < LineShape<N>::NSTAGE) {
-    fft_stage<N, S>(v, sm, p, t, lgT, tw);
-    fft_stages<N, S + 1>(v, sm, p, t, lgT, tw);
+    fft_stage<N, T, S>(v, sm, p, t, tw);
+    fft_stages<N, T, S + 1>(v, sm, p, t, tw);
   }
 }
 
+__device__ __forceinline__ float2 swap_ri(float2 a) { return make_float2(a.y, a.x); }
+
 // Unnormalised length-N DFT of line t, sign -1 (dir < 0) or +1 (dir > 0).
 // In: slot j = position p + j*P; out: slot j = frequency p + j*P (natural order).
-// The scratch is shared by the CTA's lines: every thread of the block must
-// call this together, and the caller synchronises before the call if the
-// scratch was in use.
-template <int N>
-__device__ __forceinline__ void line_fft(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, int lgT, int dir,
+// The inverse sign is the forward transform between two exchanges of the real
+// and imaginary parts (swap(z) = i conj(z), so swap(F(swap(x))) = conj(F(conj(x)))),
+// which costs no arithmetic. The scratch is shared by the CTA's lines: every
+// thread of the block calls this together, and the caller synchronises before
+// the call if the scratch was in use.
+template <int N, int T>
+__device__ __forceinline__ void line_fft(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, int dir,
                                          const float2* tw) {
   constexpr int E = LineShape<N>::E;
   if (dir > 0) {
 #pragma unroll
-    for (int j = 0; j < E; ++j) v[j].y = -v[j].y;
+    for (int j = 0; j < E; ++j) v[j] = swap_ri(v[j]);
   }
-  fft_stages<N, 0>(v, sm, p, t, lgT, tw);
+  fft_stages<N, T, 0>(v, sm, p, t, tw);
   if (dir > 0) {
 #pragma unroll
-    for (int j = 0; j < E; ++j) v[j].y = -v[j].y;
+    for (int j = 0; j < E; ++j) v[j] = swap_ri(v[j]);
   }
 }
 
