@@ -48,6 +48,19 @@ struct Tile {
   static_assert(THREADS <= 512, "tile too large");
 };
 
+// Thread coordinates (line t, butterfly column p) with their ranges stated to
+// the compiler, which lets it fold the per-slot index arithmetic (padding,
+// swizzle, Stockham positions) into immediate offsets.
+template <class TL>
+__device__ __forceinline__ void thread_coords(int& t, int& p) {
+  const int tid = threadIdx.x;
+  __builtin_assume(tid >= 0 && tid < TL::THREADS);
+  t = tid % TL::T;
+  p = tid / TL::T;
+  __builtin_assume(t >= 0 && t < TL::T);
+  __builtin_assume(p >= 0 && p < TL::P);
+}
+
 // ------------------------------------------------------ shared-memory layout
 struct PipeSmem {
   size_t in0, in1, scratch, tw, rowtw, bar, total;
@@ -134,18 +147,15 @@ __device__ __forceinline__ void twiddle_store(float2 (&v)[TL::E], const PassArgs
   }
 }
 
-// Values an elementwise operation needs at (line g, frequency f), natural
-// index f*NL + g: the diagonal entries, or the measurements. Loaded before the
-// pass's first FFT so that their latency overlaps it.
+// Measurements an epilogue needs at (line g, frequency f), natural index
+// f*NL + g, loaded before the pass's first FFT so that their latency overlaps
+// it. (Diagonal entries are read where they are applied: they are shared by
+// all problems and stay in L2.)
 template <class TL>
 struct OpData {
-  float2 d[TL::E];
   float y[TL::E];
-  __device__ __forceinline__ void load(const PassArgs& a, int op, int b, int g, int p) {
-    if (op == kOpDiag || op == kOpDiagConj) {
-#pragma unroll
-      for (int j = 0; j < TL::E; ++j) d[j] = __ldg(&a.dp[(p + j * TL::P) * a.nl + g]);
-    } else if (op == kOpGdEpilogue || op == kOpSpecEpilogue) {
+  __device__ __forceinline__ void load_y(const PassArgs& a, int op, int b, int g, int p) {
+    if (op == kOpGdEpilogue || op == kOpSpecEpilogue) {
       const float* yb = a.y + (size_t)b * a.m + g;
 #pragma unroll
       for (int j = 0; j < TL::E; ++j) y[j] = __ldg(&yb[(p + j * TL::P) * a.nl]);
@@ -154,14 +164,14 @@ struct OpData {
 };
 
 template <class TL>
-__device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, const OpData<TL>& od, int b,
-                                         fsum2& acc) {
+__device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, const OpData<TL>& od, int b, int g,
+                                         int p, fsum2& acc) {
   if (a.op == kOpDiag) {
 #pragma unroll
-    for (int j = 0; j < TL::E; ++j) v[j] = cmul(v[j], od.d[j]);
+    for (int j = 0; j < TL::E; ++j) v[j] = cmul(v[j], __ldg(&a.dp[(p + j * TL::P) * a.nl + g]));
   } else if (a.op == kOpDiagConj) {
 #pragma unroll
-    for (int j = 0; j < TL::E; ++j) v[j] = cmulc(v[j], od.d[j]);
+    for (int j = 0; j < TL::E; ++j) v[j] = cmulc(v[j], __ldg(&a.dp[(p + j * TL::P) * a.nl + g]));
   } else if (a.op == kOpGdEpilogue) {
     // z -> r = |z|^2 - y, w = r z (Eq. 2); loss partial sum of r^2
 #pragma unroll
@@ -198,7 +208,9 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
   float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
-  const int tid = threadIdx.x, t = tid % T, p = tid / T;
+  const int tid = threadIdx.x;
+  int t, p;
+  thread_coords<TL>(t, p);
   const int b = blockIdx.x / a.cpp, g0 = (blockIdx.x - b * a.cpp) * T, g = g0 + t;
   load_line_twiddles<ELL>(a, tw);
   RowTw<TL> rw;
@@ -250,7 +262,9 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
                                            Body&& body) {
   using TL = Tile<ELL, T>;
   constexpr int E = TL::E, P = TL::P;
-  const int tid = threadIdx.x, t = tid % T, p = tid / T;
+  const int tid = threadIdx.x;
+  int t, p;
+  thread_coords<TL>(t, p);
   // an earlier pass gave up (see mbar_wait_bounded): do nothing
   if (__syncthreads_or(tid == 0 && *(volatile int*)a.err != 0)) return;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar);
@@ -319,19 +333,21 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
   float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
-  const int tid = threadIdx.x, t = tid % T, p = tid / T;
+  const int tid = threadIdx.x;
+  int t, p;
+  thread_coords<TL>(t, p);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
   pipe_tiles<ELL, T>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
     const int g = g0 + t;
     OpData<TL> od;
-    od.load(a, a.op, b, g, p);
+    od.load_y(a, a.op, b, g, p);
     RowTw<TL> rw;
     rw.load(a, g0, a.out_dir);
     const float2 A = tw_m(a, g * p, a.out_dir);
     line_fft<ELL, T>(v, scratch, p, t, a.in_dir, tw);
     fsum2 acc{0.f, 0.f};
-    apply_op<TL>(v, a, od, b, acc);
+    apply_op<TL>(v, a, od, b, g, p, acc);
     if (a.op == kOpGdEpilogue) {
       const float s = block_sum(acc, red);
       if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = s;
@@ -355,7 +371,9 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   const PipeSmem L = pipe_layout(ELL, T, nbuf, true);
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
-  const int tid = threadIdx.x, t = tid % T, p = tid / T;
+  const int tid = threadIdx.x;
+  int t, p;
+  thread_coords<TL>(t, p);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
   pipe_tiles<ELL, T>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
@@ -366,13 +384,11 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
                       : 1.0f;
       s_mu = a.mu ? a.mu[b] : 0.f;
     }
-    OpData<TL> od;
-    od.load(a, a.op, b, g, p);
     line_fft<ELL, T>(v, scratch, p, t, a.in_dir, tw);
     __syncthreads();  // tile scalars visible
     if (a.op == kOpDiagConj) {
 #pragma unroll
-      for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], od.d[j]);
+      for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&a.dp[(p + j * P) * a.nl + g]));
     }
     // natural index of (line g, frequency f) is f*NL + g; keep those < n_out (U^H)
     float2* xb = a.xout + (size_t)b * a.n_out;
