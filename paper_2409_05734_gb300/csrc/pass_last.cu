@@ -1,0 +1,18 @@
+// Instantiations of the LAST pass kernel for every tile shape and
+// transform direction (see passes.cuh).
+#include "passes.cuh"
+
+namespace sr {
+
+const void* pick_last(int ell, int T, int da) {
+#define SR_PICK_LAST(E_, T_)                                                  \
+  if (ell == E_ && T == T_) {                                                 \
+    if (da < 0) return reinterpret_cast<const void*>(&k_last<E_, T_, -1>);    \
+    return reinterpret_cast<const void*>(&k_last<E_, T_, 1>);                 \
+  }
+  SR_TILE_SHAPES(SR_PICK_LAST)
+#undef SR_PICK_LAST
+  return nullptr;
+}
+
+}  // namespace sr

@@ -1,0 +1,435 @@
+// Device templates of the four-step pass kernels (FIRST, MID, LAST) of the
+// structured operator A = F D_L ... F D_1 U (Sec. III, Eq. 5).
+//
+// A chain of DFTs (the L transforms of A, then the L of A^H for a gradient or
+// power-iteration step) runs as: one FIRST pass (natural-order input, fused
+// zero-padding U / input scaling / D_1, step 1 of DFT 0), one MID pass per
+// interior boundary (step 2 of DFT k-1, fused elementwise operation, step 1 of
+// DFT k), and one LAST pass (step 2 of the final DFT, fused D_1^H and the
+// natural-order output or solver update). Between passes the data crosses HBM
+// (or L2) once, through an exchange buffer.
+//
+// Threads are numbered line-fastest (tid = t + T*p), so every natural-order
+// access (x, y, D_l) and every exchange-buffer write is T consecutive elements
+// per warp instruction straight from registers. The exchange rows a MID/LAST
+// pass reads are brought into shared memory by 2D TMA loads with 128-byte
+// swizzle; in the persistent grid the next tile's load is issued as soon as
+// the current tile's slots are in registers, so it overlaps the current
+// tile's FFTs. Kernels are instantiated per tile shape (line length ELL, lines
+// per CTA T) and per transform direction, so that index arithmetic folds and
+// the inverse-transform exchanges resolve at compile time.
+#pragma once
+
+#include "sr_device.cuh"
+#include "sr_internal.h"
+#include "sr_tma.cuh"
+
+namespace sr {
+
+// Threads per CTA allowed for lines of length ELL: 256 up to ELL = 512, 512 beyond.
+__host__ __device__ constexpr int pass_threads(int ell) { return ell <= 512 ? 256 : 512; }
+
+// Input tiles are staged by TMA when a box row is a whole 128-byte line and the
+// box (T rows) fills a 1024-byte swizzle period.
+__host__ __device__ constexpr bool uses_tma(int ell, int T) { return ell >= 16 && T >= 8; }
+
+template <int ELL, int T_>
+struct Tile {
+  static constexpr int T = T_;
+  static constexpr int E = LineShape<ELL>::E, P = LineShape<ELL>::P;
+  static constexpr int THREADS = T * P;
+  static constexpr bool TMA = uses_tma(ELL, T);
+  static constexpr int BOX = T * 128;  // bytes of one box: 16 complex values x T rows
+  static constexpr int MIN_CTAS = THREADS <= 256 ? 3 : 1;
+  static_assert(THREADS <= 512, "tile too large");
+};
+
+// Thread coordinates (line t, butterfly column p) with their ranges stated to
+// the compiler, which lets it fold the per-slot index arithmetic (padding,
+// swizzle, Stockham positions) into immediate offsets.
+template <class TL>
+__device__ __forceinline__ void thread_coords(int& t, int& p) {
+  const int tid = threadIdx.x;
+  __builtin_assume(tid >= 0 && tid < TL::THREADS);
+  t = tid % TL::T;
+  p = tid / TL::T;
+  __builtin_assume(t >= 0 && t < TL::T);
+  __builtin_assume(p >= 0 && p < TL::P);
+}
+
+// ------------------------------------------------------ shared-memory layout
+struct PipeSmem {
+  size_t in0, in1, scratch, tw, rowtw, bar, total;
+};
+
+__host__ __device__ inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Layout relative to a 1024-byte-aligned base; input tiles (T rows of ell
+// complex values as ell/16 boxes) in `nbuf` swizzled buffers when staged.
+__host__ __device__ inline PipeSmem pipe_layout(int ell, int T, int nbuf, bool stage_input) {
+  PipeSmem L;
+  const bool tma = stage_input && uses_tma(ell, T);
+  const size_t tile = tma ? (size_t)(ell / 16) * T * 128 : 0;
+  const int E = ell < 16 ? ell : 16;
+  L.in0 = 0;
+  L.in1 = tile;
+  size_t off = tile * (tma ? nbuf : 0);
+  L.scratch = off;
+  off += (size_t)T * (ell + ell / 16) * 8;
+  L.tw = off;
+  off += (size_t)ell * 8;
+  L.rowtw = off;
+  off += (size_t)E * T * 8;
+  L.bar = round_up(off, 8);
+  L.total = L.bar + 16;
+  return L;
+}
+
+__device__ __forceinline__ unsigned char* aligned_smem(unsigned char* raw) {
+  const uint32_t a = smem_addr(raw);
+  return raw + (((a + 1023u) & ~1023u) - a);
+}
+
+// ------------------------------------------------------------------ tables
+
+// W_m^e = W_m^(hi part) * W_m^(lo part), both tables rounded from double;
+// conjugated when dir > 0.
+__device__ __forceinline__ float2 tw_m(const PassArgs& a, int e, int dir) {
+  const float2 w = cmul(__ldg(&a.tw_hi[e >> a.tw_shift]), __ldg(&a.tw_lo[e & ((1 << a.tw_shift) - 1)]));
+  return dir > 0 ? conjf2(w) : w;
+}
+
+// Line twiddles W_ELL^k, k < ELL, into shared memory.
+template <int ELL>
+__device__ __forceinline__ void load_line_twiddles(const PassArgs& a, float2* tw) {
+  for (int i = threadIdx.x; i < ELL; i += blockDim.x) tw[i] = __ldg(&a.twl[i * a.tws]);
+}
+
+// The four-step twiddle of (line g, frequency f = p + j*P) is
+// W_m^(g p) * W_m^(g P j); the second factor is tabulated per tile,
+// rowtw[j*T + t] = W_m^((g0 + t) P j). RowTw holds this thread's entries of
+// the table between their (early) load and their (late) store to shared memory.
+template <class TL>
+struct RowTw {
+  static constexpr int N = (TL::E * TL::T + TL::THREADS - 1) / TL::THREADS;
+  float2 w[N];
+  __device__ __forceinline__ void load(const PassArgs& a, int g0, int dir) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int i = threadIdx.x + k * TL::THREADS;
+      if (i < TL::E * TL::T) w[k] = tw_m(a, (g0 + i % TL::T) * TL::P * (i / TL::T), dir);
+    }
+  }
+  __device__ __forceinline__ void store(float2* rowtw) const {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int i = threadIdx.x + k * TL::THREADS;
+      if (i < TL::E * TL::T) rowtw[i] = w[k];
+    }
+  }
+};
+
+// Step-1 outputs of line g times the four-step twiddles (already conjugated
+// for an inverse transform), stored to the exchange buffer at f*NL + g
+// (T consecutive elements per frequency across the warp).
+template <class TL>
+__device__ __forceinline__ void twiddle_store(float2 (&v)[TL::E], const PassArgs& a, int b, int g, int t, int p,
+                                              float2 A, const float2* rowtw) {
+  float2* eb = a.eout + (size_t)b * a.m + g;
+#pragma unroll
+  for (int j = 0; j < TL::E; ++j) {
+    const float2 w = cmul(A, rowtw[j * TL::T + t]);
+    eb[(size_t)(p + j * TL::P) * a.nl] = cmul(v[j], w);
+  }
+}
+
+// Measurements an epilogue needs at (line g, frequency f), natural index
+// f*NL + g, loaded before the pass's first FFT so that their latency overlaps
+// it. (Diagonal entries are read where they are applied: they are shared by
+// all problems and stay in L2.)
+template <class TL>
+struct OpData {
+  float y[TL::E];
+  __device__ __forceinline__ void load_y(const PassArgs& a, int op, int b, int g, int p) {
+    if (op == kOpGdEpilogue || op == kOpSpecEpilogue) {
+      const float* yb = a.y + (size_t)b * a.m + g;
+#pragma unroll
+      for (int j = 0; j < TL::E; ++j) y[j] = __ldg(&yb[(p + j * TL::P) * a.nl]);
+    }
+  }
+};
+
+template <class TL>
+__device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, const OpData<TL>& od, int b, int g,
+                                         int p, fsum2& acc) {
+  if (a.op == kOpDiag) {
+#pragma unroll
+    for (int j = 0; j < TL::E; ++j) v[j] = cmul(v[j], __ldg(&a.dp[(p + j * TL::P) * a.nl + g]));
+  } else if (a.op == kOpDiagConj) {
+#pragma unroll
+    for (int j = 0; j < TL::E; ++j) v[j] = cmulc(v[j], __ldg(&a.dp[(p + j * TL::P) * a.nl + g]));
+  } else if (a.op == kOpGdEpilogue) {
+    // z -> r = |z|^2 - y, w = r z (Eq. 2); loss partial sum of r^2
+#pragma unroll
+    for (int j = 0; j < TL::E; ++j) {
+      const float r = cabs2(v[j]) - od.y[j];
+      acc_add(acc, r * r);
+      v[j] = cscale(v[j], r);
+    }
+  } else if (a.op == kOpSpecEpilogue) {
+    // z -> T(y_hat) z, y_hat = m y / sum(y) (Eq. 3)
+    const float scale = (float)a.m / __ldg(&a.sumy[b]);
+#pragma unroll
+    for (int j = 0; j < TL::E; ++j) {
+      const float yh = od.y[j] * scale;
+      float w;
+      if (a.weight_mode == SR_WEIGHT_IDENTITY) w = yh;
+      else w = yh > 0.f ? fmaxf(1.0f - 1.0f / yh, a.lam) : a.lam;
+      v[j] = cscale(v[j], w);
+    }
+  }
+}
+
+// ------------------------------------------------------------ FIRST pass
+
+template <int ELL, int T, int DB>
+__global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
+    k_first(const __grid_constant__ PassArgs a) {
+  using TL = Tile<ELL, T>;
+  constexpr int E = TL::E, P = TL::P;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ float s_scale;
+  unsigned char* smem = aligned_smem(smem_raw);
+  const PipeSmem L = pipe_layout(ELL, T, 1, false);
+  float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
+  float2* tw = reinterpret_cast<float2*>(smem + L.tw);
+  float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
+  const int tid = threadIdx.x;
+  int t, p;
+  thread_coords<TL>(t, p);
+  const int b = blockIdx.x / a.cpp, g0 = (blockIdx.x - b * a.cpp) * T, g = g0 + t;
+  load_line_twiddles<ELL>(a, tw);
+  RowTw<TL> rw;
+  rw.load(a, g0, DB);
+  rw.store(rowtw);
+  const float2 A = tw_m(a, g * p, DB);
+  if (tid == 0)
+    s_scale = a.norm_in ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count))
+                        : 1.0f;
+  // Natural-order input, zero beyond n_in (the padding U): element (line g,
+  // position q) is x[q*NL + g]; the warp reads T consecutive elements.
+  const float2* xb = a.xin + (size_t)b * a.n_in;
+  float2 v[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int nat = (p + j * P) * a.nl + g;
+    v[j] = nat < a.n_in ? xb[nat] : make_float2(0.f, 0.f);
+  }
+  if (a.op == kOpDiag) {
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[j] = cmul(v[j], __ldg(&a.dp[(p + j * P) * a.nl + g]));
+  }
+  __syncthreads();
+  const float sc = s_scale;
+#pragma unroll
+  for (int j = 0; j < E; ++j) v[j] = cscale(v[j], sc);
+  line_fft<ELL, T, DB>(v, scratch, p, t, tw);
+  twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+}
+
+// ------------------------------------------------------ MID and LAST passes
+
+// Issues the TMA loads of tile `tile` (T rows of ELL complex values, boxes of
+// 16 values x T rows) into `buf`, completing on barrier `bar`.
+template <class TL, int ELL>
+__device__ __forceinline__ void issue_tile(const PassArgs& a, int tile, uint32_t buf, uint32_t bar) {
+  const int b = tile / a.cpp, g0 = (tile - b * a.cpp) * TL::T;
+  const int row = b * a.nl + g0;
+  mbar_arrive_expect_tx(bar, (uint32_t)(TL::T * ELL * 8));
+#pragma unroll 1
+  for (int kb = 0; kb < ELL / 16; ++kb) tma_load_2d(buf + (uint32_t)(kb * TL::BOX), &a.tmap, kb * 32, row, bar);
+}
+
+// Shared pipeline of the persistent MID / LAST passes: for every tile of this
+// CTA, loads the T input lines (rows of the exchange buffer) into registers
+// (slot j = position p + j*P) and calls body(v, b, g0).
+template <int ELL, int T, class Body>
+__device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned char* smem, const PipeSmem& L,
+                                           Body&& body) {
+  using TL = Tile<ELL, T>;
+  constexpr int E = TL::E, P = TL::P;
+  const int tid = threadIdx.x;
+  int t, p;
+  thread_coords<TL>(t, p);
+  // an earlier pass gave up (see mbar_wait_bounded): do nothing
+  if (__syncthreads_or(tid == 0 && *(volatile int*)a.err != 0)) return;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar);
+  const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
+  const uint32_t in0 = smem_addr(smem + L.in0), in1 = smem_addr(smem + L.in1);
+  int tile = blockIdx.x;
+  if constexpr (TL::TMA) {
+    if (tid == 0) {
+      mbar_init(bar0, 1);
+      mbar_init(bar1, 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0 && tile < a.ntiles) issue_tile<TL, ELL>(a, tile, in0, bar0);
+  }
+  for (int k = 0; tile < a.ntiles; ++k, tile += gridDim.x) {
+    const int b = tile / a.cpp, g0 = (tile - b * a.cpp) * T, g = g0 + t;
+    const int next = tile + (int)gridDim.x;
+    float2 v[E];
+    if constexpr (TL::TMA) {
+      const int buf = nbuf == 2 ? (k & 1) : 0;
+      const uint32_t parity = nbuf == 2 ? (uint32_t)((k >> 1) & 1) : (uint32_t)(k & 1);
+      const uint32_t bar = buf ? bar1 : bar0;
+      if (nbuf == 2 && tid == 0 && next < a.ntiles) {
+        fence_proxy_async_smem();
+        issue_tile<TL, ELL>(a, next, buf ? in0 : in1, buf ? bar0 : bar1);
+      }
+      const bool ok = mbar_wait_bounded(bar, parity);
+      if (!__syncthreads_and(ok)) {
+        // a load never completed: record it, let a pending prefetch land, stop
+        if (tid == 0) {
+          atomicExch(a.err, (int)SR_ERR_TIMEOUT);
+          if (nbuf == 2 && next < a.ntiles) mbar_wait_bounded(buf ? bar0 : bar1, (uint32_t)(((k + 1) >> 1) & 1));
+        }
+        return;
+      }
+      const unsigned char* src = smem + (buf ? L.in1 : L.in0);
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[j] = *reinterpret_cast<const float2*>(src + swz128_offset(TL::BOX, t, p + j * P));
+      if (nbuf == 1) {
+        __syncthreads();  // every thread has its slots before the buffer is refilled
+        if (tid == 0 && next < a.ntiles) {
+          fence_proxy_async_smem();
+          issue_tile<TL, ELL>(a, next, in0, bar0);
+        }
+      }
+    } else {
+      const float2* src = a.ein + (size_t)b * a.m + (size_t)g * ELL;
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[j] = src[p + j * P];
+    }
+    body(v, b, g0);
+    __syncthreads();  // scratch, tables and input buffer free for the next tile
+  }
+}
+
+template <int ELL, int T, int DA, int DB>
+__global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
+    k_mid(const __grid_constant__ PassArgs a, int nbuf) {
+  using TL = Tile<ELL, T>;
+  constexpr int E = TL::E;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ float red[64];
+  unsigned char* smem = aligned_smem(smem_raw);
+  const PipeSmem L = pipe_layout(ELL, T, nbuf, true);
+  float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
+  float2* tw = reinterpret_cast<float2*>(smem + L.tw);
+  float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
+  const int tid = threadIdx.x;
+  int t, p;
+  thread_coords<TL>(t, p);
+  load_line_twiddles<ELL>(a, tw);
+  __syncthreads();
+  pipe_tiles<ELL, T>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
+    const int g = g0 + t;
+    OpData<TL> od;
+    od.load_y(a, a.op, b, g, p);
+    RowTw<TL> rw;
+    rw.load(a, g0, DB);
+    const float2 A = tw_m(a, g * p, DB);
+    line_fft<ELL, T, DA>(v, scratch, p, t, tw);
+    fsum2 acc{0.f, 0.f};
+    apply_op<TL>(v, a, od, b, g, p, acc);
+    if (a.op == kOpGdEpilogue) {
+      const float s = block_sum(acc, red);
+      if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = s;
+    }
+    rw.store(rowtw);
+    __syncthreads();  // first FFT's scratch reads done; row twiddles visible
+    line_fft<ELL, T, DB>(v, scratch, p, t, tw);
+    twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+  });
+}
+
+template <int ELL, int T, int DA>
+__global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
+    k_last(const __grid_constant__ PassArgs a, int nbuf) {
+  using TL = Tile<ELL, T>;
+  constexpr int E = TL::E, P = TL::P;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ float red[64];
+  __shared__ float s_inv_old, s_mu;
+  unsigned char* smem = aligned_smem(smem_raw);
+  const PipeSmem L = pipe_layout(ELL, T, nbuf, true);
+  float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
+  float2* tw = reinterpret_cast<float2*>(smem + L.tw);
+  const int tid = threadIdx.x;
+  int t, p;
+  thread_coords<TL>(t, p);
+  load_line_twiddles<ELL>(a, tw);
+  __syncthreads();
+  pipe_tiles<ELL, T>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
+    const int g = g0 + t;
+    if (tid == 0) {
+      s_inv_old = (a.out_mode == kOutSpec && a.norm_in)
+                      ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count))
+                      : 1.0f;
+      s_mu = a.mu ? a.mu[b] : 0.f;
+    }
+    line_fft<ELL, T, DA>(v, scratch, p, t, tw);
+    __syncthreads();  // tile scalars visible
+    if (a.op == kOpDiagConj) {
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&a.dp[(p + j * P) * a.nl + g]));
+    }
+    // natural index of (line g, frequency f) is f*NL + g; keep those < n_out (U^H)
+    float2* xb = a.xout + (size_t)b * a.n_out;
+    const float inv_old = s_inv_old, mu2 = 2.0f * s_mu * a.mu_scale, sh = a.shift * inv_old;
+    fsum2 acc{0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int nat = (p + j * P) * a.nl + g;
+      if (nat >= a.n_out) continue;
+      const float2 val = v[j];
+      if (a.out_mode == kOutStore) {
+        xb[nat] = val;
+      } else if (a.out_mode == kOutGrad) {
+        xb[nat] = cscale(val, 2.0f);
+      } else if (a.out_mode == kOutGd) {
+        float2 x = xb[nat];
+        x.x = fmaf(-mu2, val.x, x.x);
+        x.y = fmaf(-mu2, val.y, x.y);
+        xb[nat] = x;
+      } else {  // kOutSpec
+        const float2 old = xb[nat];
+        const float2 u = make_float2(fmaf(sh, old.x, val.x), fmaf(sh, old.y, val.y));
+        xb[nat] = u;
+        acc_add(acc, cabs2(u));
+      }
+    }
+    if (a.out_mode == kOutSpec) {
+      const float s = block_sum(acc, red);
+      if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = s;
+    }
+    if (a.loss_out && g0 == 0 && tid == 0)
+      a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
+  });
+}
+
+
+// Every (line length, lines per CTA) pair make_geom produces for m = 4 .. 2^24.
+#define SR_TILE_SHAPES(X)                                                                                      \
+  X(2, 2) X(2, 4) X(4, 2) X(4, 4) X(4, 8) X(8, 4) X(8, 8) X(8, 16) X(16, 8) X(16, 16) X(16, 32) X(32, 16)    \
+  X(32, 32) X(32, 64) X(64, 32) X(64, 64) X(128, 32) X(256, 16) X(512, 8) X(1024, 8) X(2048, 4) X(4096, 2)
+
+// Kernel entry points by tile shape and transform direction (nullptr when the
+// combination is not instantiated). Defined in pass_first.cu / pass_mid.cu / pass_last.cu.
+const void* pick_first(int ell, int T, int db);
+const void* pick_mid(int ell, int T, int da, int db);
+const void* pick_last(int ell, int T, int da);
+
+}  // namespace sr

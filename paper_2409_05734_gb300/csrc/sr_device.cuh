@@ -183,23 +183,22 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[LineShape<N>::E], float2*
 
 __device__ __forceinline__ float2 swap_ri(float2 a) { return make_float2(a.y, a.x); }
 
-// Unnormalised length-N DFT of line t, sign -1 (dir < 0) or +1 (dir > 0).
+// Unnormalised length-N DFT of line t, sign -1 (DIR < 0) or +1 (DIR > 0).
 // In: slot j = position p + j*P; out: slot j = frequency p + j*P (natural order).
 // The inverse sign is the forward transform between two exchanges of the real
 // and imaginary parts (swap(z) = i conj(z), so swap(F(swap(x))) = conj(F(conj(x)))),
 // which costs no arithmetic. The scratch is shared by the CTA's lines: every
 // thread of the block calls this together, and the caller synchronises before
 // the call if the scratch was in use.
-template <int N, int T>
-__device__ __forceinline__ void line_fft(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, int dir,
-                                         const float2* tw) {
+template <int N, int T, int DIR>
+__device__ __forceinline__ void line_fft(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, const float2* tw) {
   constexpr int E = LineShape<N>::E;
-  if (dir > 0) {
+  if constexpr (DIR > 0) {
 #pragma unroll
     for (int j = 0; j < E; ++j) v[j] = swap_ri(v[j]);
   }
   fft_stages<N, T, 0>(v, sm, p, t, tw);
-  if (dir > 0) {
+  if constexpr (DIR > 0) {
 #pragma unroll
     for (int j = 0; j < E; ++j) v[j] = swap_ri(v[j]);
   }

@@ -113,7 +113,8 @@ struct Plan {
   float2* d_tw_lo = nullptr;
   int* d_err = nullptr;          // device status word
   LineGeom geom[2];              // per layout
-  int per_sm_mid[2] = {1, 1}, per_sm_last[2] = {1, 1};  // co-resident CTAs per SM per layout
+  int per_sm_mid[2][3] = {{1, 1, 1}, {1, 1, 1}};  // co-resident CTAs per SM: [layout][direction pair]
+  int per_sm_last[2][2] = {{1, 1}, {1, 1}};       // [layout][inverse]
   // workspace
   int B_cap = 0;
   float2* d_e0 = nullptr;
@@ -140,7 +141,8 @@ Layout s2_layout(int parity);
 cudaError_t launch_first(const Plan& p, Layout lay, const PassArgs& a, int B, cudaStream_t s);
 cudaError_t launch_mid(const Plan& p, Layout lay, const PassArgs& a, int B, cudaStream_t s);
 cudaError_t launch_last(const Plan& p, Layout lay, const PassArgs& a, int B, cudaStream_t s);
-// Max co-resident CTAs per SM of the middle / last pass kernels for a geometry.
+// Max co-resident CTAs per SM of the middle pass kernels (3 direction pairs)
+// and of the last pass kernels (2 directions) of a geometry.
 cudaError_t pass_occupancy(const LineGeom& g, int* per_sm_mid, int* per_sm_last);
 // Helpers (fourstep.cu)
 cudaError_t launch_sum_rows(const float* y, int B, int m, float* part, int chunks, cudaStream_t s);
