@@ -298,8 +298,20 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
         return;
       }
       const unsigned char* src = smem + (buf ? L.in1 : L.in0);
+      // swz128_offset(BOX, t, p + j*P) as a per-thread base plus a per-slot
+      // constant: for P >= 16 the slot only moves the box; for P < 16 it adds
+      // (j*P) & 15 to the 16-byte chunk index, whose bits are disjoint from p's.
+      const int t7 = t & 7;
+      if constexpr (P >= 16) {
+        const unsigned char* base = src + (p >> 4) * TL::BOX + t * 128 + (((p & 15) << 3) ^ (t7 << 4));
 #pragma unroll
-      for (int j = 0; j < E; ++j) v[j] = *reinterpret_cast<const float2*>(src + swz128_offset(TL::BOX, t, p + j * P));
+        for (int j = 0; j < E; ++j) v[j] = *reinterpret_cast<const float2*>(base + j * (P / 16) * TL::BOX);
+      } else {
+        const int base = t * 128 + ((p << 3) ^ (t7 << 4));
+#pragma unroll
+        for (int j = 0; j < E; ++j)
+          v[j] = *reinterpret_cast<const float2*>(src + ((j * P) >> 4) * TL::BOX + (base ^ (((j * P) & 15) << 3)));
+      }
       if (nbuf == 1) {
         __syncthreads();  // every thread has its slots before the buffer is refilled
         if (tid == 0 && next < a.ntiles) {

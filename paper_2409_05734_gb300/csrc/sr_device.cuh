@@ -136,6 +136,13 @@ __device__ __forceinline__ int sidx(int pos, int t) { return pad16(pos) * T + t;
 // DFT, and writes position (b/Ns)*Ns*R + (b mod Ns) + r*Ns. Butterflies of this
 // thread: b = p + q*P, q < E/R; their inputs are slots q + r*E/R.
 // tw: shared-memory table W_N^k, k < N.
+//
+// Addressing is written as a per-thread base plus compile-time offsets. With
+// P and 16 powers of two and p < P: pad16(p + j*P) = pad16(p) + pad16(j*P);
+// the only stages that write back are stage 0 (radix 16, Ns = 1: position
+// 16(p + qP) + r, padded 17(p + qP) + r) and stage 1 (radix 16, Ns = 16, one
+// butterfly b = p per thread: position 256(p>>4) + (p&15) + 16r, padded
+// 272(p>>4) + (p&15) + 17r); and b mod Ns = (p mod Ns) + (qP mod Ns).
 template <int N, int T, int S>
 __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, const float2* tw) {
   using LS_ = LineShape<N>;
@@ -144,30 +151,42 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* 
   constexpr int Q = E / R;
   constexpr int Ns = LS_::span(S);
   constexpr bool LAST = (S == LS_::NSTAGE - 1);
+  static_assert(LAST || S <= 1, "only stages 0 and 1 write back");
   if constexpr (S > 0) {
+    const float2* rb = sm + pad16(p) * T + t;
 #pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = sm[sidx<T>(p + j * P, t)];
+    for (int j = 0; j < E; ++j) v[j] = rb[pad16(j * P) * T];
     if constexpr (!LAST) __syncthreads();  // everyone read before anyone overwrites
   }
+  float2* wb = sm + t;
+  if constexpr (!LAST) {
+    static_assert(R == 16, "write-back stages are radix 16");
+    if constexpr (S == 0) wb += 17 * p * T;
+    else wb += (272 * (p >> 4) + (p & 15)) * T;
+  }
+  const int kp = (P >= Ns) ? (p & (Ns - 1)) : p;  // runtime part of b mod Ns
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const int b = p + q * P;
     float2 a[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) a[r] = v[q + r * Q];
     if constexpr (S > 0) {
-      const int k = b % Ns;
+      const int kq = (P >= Ns) ? 0 : ((q * P) & (Ns - 1));
       constexpr int step = N / (Ns * R);  // W_{Ns R}^{r k} = W_N^{r k step}
+      const int k = kp + kq;
 #pragma unroll
-      for (int r = 1; r < R; ++r) a[r] = cmul(a[r], tw[r * k * step]);
+      for (int r = 1; r < R; ++r) a[r] = cmul(a[r], tw[r * step * k]);
     }
     dft_small<R>(a);
     if constexpr (LAST) {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q + r * Q] = a[r];
+    } else if constexpr (S == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) wb[(17 * q * P + r) * T] = a[r];
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[sidx<T>((b / Ns) * Ns * R + (b % Ns) + r * Ns, t)] = a[r];
+      for (int r = 0; r < R; ++r) wb[17 * r * T] = a[r];
     }
   }
   if constexpr (!LAST) __syncthreads();
