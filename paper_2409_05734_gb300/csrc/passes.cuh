@@ -394,11 +394,8 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     }
     line_fft<ELL, T, DA>(v, scratch, p, t, tw);
     __syncthreads();  // tile scalars visible
-    if (a.op == kOpDiagConj) {
-#pragma unroll
-      for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&a.dp[(p + j * P) * a.nl + g]));
-    }
-    // natural index of (line g, frequency f) is f*NL + g; keep those < n_out (U^H)
+    // natural index of (line g, frequency f) is f*NL + g; keep those < n_out
+    // (U^H), and apply D_1^H only to the kept entries
     float2* xb = a.xout + (size_t)b * a.n_out;
     const float inv_old = s_inv_old, mu2 = 2.0f * s_mu * a.mu_scale, sh = a.shift * inv_old;
     fsum2 acc{0.f, 0.f};
@@ -406,7 +403,8 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     for (int j = 0; j < E; ++j) {
       const int nat = (p + j * P) * a.nl + g;
       if (nat >= a.n_out) continue;
-      const float2 val = v[j];
+      float2 val = v[j];
+      if (a.op == kOpDiagConj) val = cmulc(val, __ldg(&a.dp[nat]));
       if (a.out_mode == kOutStore) {
         xb[nat] = val;
       } else if (a.out_mode == kOutGrad) {
