@@ -139,6 +139,28 @@ sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int it
 sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters,
                       const sr_gd_opts* opts, float* loss_hist, int B, void* stream);
 
+/* ---- forward without allocation (the paper has no counterpart) ---------------
+ * sr_forward_noalloc: z = A x exactly like sr_forward, for callers that cannot
+ * allocate device memory when they make the call -- code running while a CUDA
+ * graph is being captured on its stream (cudaMalloc is not allowed there), or
+ * hosts whose device memory is owned by their own allocator. It never calls
+ * cudaMalloc/cudaFree and never touches the plan's workspace: its two exchange
+ * buffers live in a fixed scratch array compiled into the library (2 x
+ * SR_FORWARD_NOALLOC_MAX_ELEMENTS complex values, 8 MiB, held by every GPU
+ * that loads the library until the process exits). The plan must already
+ * exist (sr_plan_create allocates its tables once).
+ * - B * m must not exceed SR_FORWARD_NOALLOC_MAX_ELEMENTS; larger calls
+ *   return SR_ERR_UNSUPPORTED and launch nothing.
+ * - The first call on a device looks up the scratch array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ * - All calls share the one scratch array, which keeps the last call's
+ *   contents (every element is rewritten before it is read, so nothing needs
+ *   clearing). Calls that overlap on the GPU -- concurrent streams, or several
+ *   host threads -- race on it; serialise them.
+ * x: c64[B][n], z: c64[B][m], device pointers as for sr_forward. */
+#define SR_FORWARD_NOALLOC_MAX_ELEMENTS ((size_t)1 << 19)
+sr_status sr_forward_noalloc(const sr_plan* plan, const void* x, void* z, int B, void* stream);
+
 /* ---- device status -----------------------------------------------------------
  * sr_plan_check: waits for the device (cudaDeviceSynchronize) and reports the
  * status the plan's kernels recorded since the last check: SR_ERR_TIMEOUT if

@@ -47,6 +47,7 @@ SIGNATURES = [
     ("sr_loss_grad", C.c_int, [_VP, _VP, _VP, _VP, _VP, C.c_int, _VP]),
     ("sr_spectral_init", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(SpectralOpts), _VP, C.c_int, _VP]),
     ("sr_gd_solve", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(GdOpts), _VP, C.c_int, _VP]),
+    ("sr_forward_noalloc", C.c_int, [_VP, _VP, _VP, C.c_int, _VP]),
     ("sr_plan_check", C.c_int, [_VP]),
     ("sr_kernel_launches", C.c_uint64, []),
     ("sr_plan_set_timing", C.c_int, [_VP, C.c_int]),

@@ -407,6 +407,10 @@ sr_status check_plan_call(sr_plan* plan, int B) {
 
 struct sr_plan : public Plan {};
 
+namespace sr {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace sr
+
 extern "C" {
 
 sr_status sr_phases(uint64_t seed, int L, int64_t m, double* theta) {

@@ -128,6 +128,9 @@ struct Plan {
   size_t ev_used[3] = {0, 0, 0};
 };
 
+// Sets the thread-local message sr_last_error() returns.
+void set_last_error(const std::string& msg);
+
 // Counts every kernel launch of the library (sr_kernel_launches).
 void count_launch();
 uint64_t launches_so_far();
