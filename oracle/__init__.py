@@ -19,6 +19,8 @@ What it computes, in float64 / complex128, following the paper step by step:
   phase).
 * ``dense_iid`` -- the i.i.d. random comparison model (Sec. II-A) as plain
   matrix products.
+* ``autodiff`` -- the backward pass of z = A x with respect to x and the
+  diffuser phases theta_l, by the chain rule written out layer by layer.
 
 Pins: every function here is checked by ``tests/test_oracle_*.py`` against
 closed forms, invariants, brute-force sums and library special cases (not
@@ -48,11 +50,12 @@ from .recovery import (
     structured_ops,
 )
 from .dense_iid import dense_forward, dense_adjoint, dense_ops
+from . import autodiff
 
 __all__ = [
     "dft_matrix", "dft_naive", "unitary_fft", "unitary_ifft", "zero_pad", "forward",
     "adjoint", "dense_structured_matrix", "intensity_loss", "loss_and_grad",
     "spectral_weights", "spectral_init", "gradient_descent", "step_ramp", "cosine_similarity",
     "relative_error_global_phase", "structured_ops", "dense_forward", "dense_adjoint",
-    "dense_ops",
+    "dense_ops", "autodiff",
 ]
