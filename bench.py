@@ -192,19 +192,22 @@ def iteration_bytes(W):
 
 def traffic_from_profile(name: str):
     """dram bytes per launch recorded by an ncu summary under profiles/, if the
-    kernel source has not changed since (hash recorded in the summary)."""
+    pass kernels' sources have not changed since (hash recorded in the summary)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", name)
-    src = os.path.join(ROOT, "paper_2409_05734_gb300", "csrc", "fourstep.cu")
+    csrc = os.path.join(ROOT, "paper_2409_05734_gb300", "csrc")
     if not os.path.exists(path):
         return None
-    want = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("passes.cuh", "sr_device.cuh", "sr_tma.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    want = h.hexdigest()[:16]
     vals = {}
     for line in open(path):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("fourstep.cu sha256[:16]") != want:
+    if vals.get("kernel sources sha256[:16]") != want:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
