@@ -95,6 +95,12 @@ sr_status sr_plan_destroy(sr_plan* plan); /* NULL is accepted (no-op) */
 sr_status sr_plan_get_phases(const sr_plan* plan, double* theta);
 sr_status sr_plan_set_phases(sr_plan* plan, const double* theta);
 
+/* Replaces the phases from DEVICE memory (float[L*m], e.g. a trainable
+ * tensor): the diagonal tables are rebuilt on `stream` (D = exp(i theta)/sqrt(m)
+ * in float). The host copy returned by sr_plan_get_phases is refreshed from
+ * them on its next call (which then synchronises the device). */
+sr_status sr_plan_set_phases_device(sr_plan* plan, const float* theta, void* stream);
+
 /* Reports the plan's sizes (any output pointer may be NULL). */
 sr_status sr_plan_info(const sr_plan* plan, int64_t* n, int64_t* m, int* L);
 
@@ -107,6 +113,19 @@ sr_status sr_plan_reserve(sr_plan* plan, int B);
  *             z: c64[B][m] (input), x: c64[B][n] (output). */
 sr_status sr_forward(sr_plan* plan, const void* x, void* z, int B, void* stream);
 sr_status sr_adjoint(sr_plan* plan, const void* z, void* x, int B, void* stream);
+
+/* ---- backward of the operator (phases theta_l are the model's parameters) ----
+ * For z = A x (Sec. III, Eq. 5) and the gradient G_z of a real loss with
+ * respect to z (convention G_w = dL/dRe w + i dL/dIm w, as in PyTorch):
+ *   grad_x     = A^H G_z                                  (c64[B][n], or NULL)
+ *   grad_theta = sum over b of Im(conj(p_l) * h_l)         (float[L][m], or NULL)
+ * where p_l = D_l q_l is layer l's value right after D_l (q_1 = U x,
+ * q_{l+1} = F p_l) and h_l = F^H D_{l+1}^H ... D_L^H F^H G_z is the gradient
+ * arriving at p_l (dp_l/dtheta_l = i p_l). The q_l are recomputed from x, not
+ * stored: L(L+1)/2 DFT applications in all (3 for L = 2). x: c64[B][n],
+ * G_z: c64[B][m]. Uses two extra B*m workspace vectors (grown on first use). */
+sr_status sr_backward(sr_plan* plan, const void* x, const void* gz, void* grad_x, float* grad_theta, int B,
+                      void* stream);
 
 /* ---- loss and gradient (Sec. II-B-1, Eq. 2) ----------------------------------
  * With z = A x and r = |z|^2 - y:
@@ -160,6 +179,29 @@ sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters,
  * x: c64[B][n], z: c64[B][m], device pointers as for sr_forward. */
 #define SR_FORWARD_NOALLOC_MAX_ELEMENTS ((size_t)1 << 19)
 sr_status sr_forward_noalloc(const sr_plan* plan, const void* x, void* z, int B, void* stream);
+
+/* ---- dense i.i.d. comparison model (Sec. II-A) -----------------------------
+ * The random model the paper compares against: a dense A in C^{m x n} with
+ * i.i.d. entries, here supplied by the caller (host float[m][n][2], interleaved
+ * re/im) and rounded once to BF16: the rounded matrix IS the model's A. The
+ * products run on the tensor cores (tcgen05, BF16 inputs, FP32 accumulation);
+ * the vector operand is split into BF16 high and low parts, so a product carries
+ * about 2^-16 relative error beyond the FP32 accumulation.
+ * Sizes: n a multiple of 64, m a multiple of 128, 64 <= n <= m <= 2^22,
+ * B a multiple of 8 in [8, 128]. The model owns two copies of A (A and its
+ * transpose, 2 * 4 * m * n bytes) and a workspace for B problems. */
+typedef struct sr_dense sr_dense;
+sr_status sr_dense_create(int64_t n, int64_t m, const float* a_host, sr_dense** out);
+sr_status sr_dense_destroy(sr_dense* model); /* NULL accepted */
+/* z = A x (x: c64[B][n], z: c64[B][m], device) and x = A^H w (w: c64[B][m]). */
+sr_status sr_dense_forward(sr_dense* model, const void* x, void* z, int B, void* stream);
+sr_status sr_dense_adjoint(sr_dense* model, const void* w, void* x, int B, void* stream);
+/* Gradient descent as sr_gd_solve (same loss, gradient, step rule and loss
+ * history), with the dense A. */
+sr_status sr_dense_gd_solve(sr_dense* model, const float* y, void* x, int iters, const sr_gd_opts* opts,
+                            float* loss_hist, int B, void* stream);
+/* As sr_plan_check, for the dense model's kernels. */
+sr_status sr_dense_check(sr_dense* model);
 
 /* ---- device status -----------------------------------------------------------
  * sr_plan_check: waits for the device (cudaDeviceSynchronize) and reports the

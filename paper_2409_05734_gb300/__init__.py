@@ -7,5 +7,8 @@ descent run in hand-written CUDA kernels for sm_103a behind a C ABI
 """
 from .buildlib import build, library_path
 from .plan import Plan, phases
+from .autograd import StructuredRandomOp, structured_random
+from .dense import DenseModel
 
-__all__ = ["Plan", "phases", "build", "library_path"]
+__all__ = ["Plan", "phases", "build", "library_path", "StructuredRandomOp", "structured_random",
+           "DenseModel"]

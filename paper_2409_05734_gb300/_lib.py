@@ -47,7 +47,15 @@ SIGNATURES = [
     ("sr_loss_grad", C.c_int, [_VP, _VP, _VP, _VP, _VP, C.c_int, _VP]),
     ("sr_spectral_init", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(SpectralOpts), _VP, C.c_int, _VP]),
     ("sr_gd_solve", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(GdOpts), _VP, C.c_int, _VP]),
+    ("sr_plan_set_phases_device", C.c_int, [_VP, _VP, _VP]),
+    ("sr_backward", C.c_int, [_VP, _VP, _VP, _VP, _VP, C.c_int, _VP]),
     ("sr_forward_noalloc", C.c_int, [_VP, _VP, _VP, C.c_int, _VP]),
+    ("sr_dense_create", C.c_int, [C.c_int64, C.c_int64, _VP, C.POINTER(_VP)]),
+    ("sr_dense_destroy", C.c_int, [_VP]),
+    ("sr_dense_forward", C.c_int, [_VP, _VP, _VP, C.c_int, _VP]),
+    ("sr_dense_adjoint", C.c_int, [_VP, _VP, _VP, C.c_int, _VP]),
+    ("sr_dense_gd_solve", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(GdOpts), _VP, C.c_int, _VP]),
+    ("sr_dense_check", C.c_int, [_VP]),
     ("sr_plan_check", C.c_int, [_VP]),
     ("sr_kernel_launches", C.c_uint64, []),
     ("sr_plan_set_timing", C.c_int, [_VP, C.c_int]),

@@ -179,6 +179,23 @@ sr_status ensure_workspace(Plan* p, int B) {
   return SR_OK;
 }
 
+sr_status ensure_backward_buffers(Plan* p, int B) {
+  if (B <= p->W_cap) return SR_OK;
+  cudaFree(p->d_w0);
+  cudaFree(p->d_w1);
+  p->d_w0 = p->d_w1 = nullptr;
+  p->W_cap = 0;
+  const size_t bm = (size_t)B * (size_t)p->m;
+  sr_status st;
+  if ((st = dalloc(&p->d_w0, bm)) != SR_OK || (st = dalloc(&p->d_w1, bm)) != SR_OK) {
+    cudaFree(p->d_w0);
+    p->d_w0 = nullptr;
+    return st;
+  }
+  p->W_cap = B;
+  return SR_OK;
+}
+
 float* part_bank(const Plan& p, int bank, int B) { return p.d_part + (size_t)bank * B * part_stride(p); }
 
 // Rebuilds the device diagonal tables from p->theta: D_l = exp(i theta_l)/sqrt(m)
@@ -231,7 +248,8 @@ struct Chain {
   int nfft = 0;
   int s0 = 0;                 // decomposition parity of DFT 0
   int dir[16] = {0};
-  int first_op = sr::kOpNone; // kOpNone or kOpDiag (D_1)
+  int first_op = sr::kOpNone; // kOpNone, kOpDiag or kOpDiagConj
+  int first_d = 0;            // index of the diagonal the first pass applies
   MidOp mid[16];              // mid[k], k = 1..nfft-1
   int last_op = sr::kOpNone;  // kOpNone or kOpDiagConj (D_1^H)
   // input of the first pass
@@ -307,7 +325,7 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     a.norm_in = c.norm_in;
     a.norm_in_count = c.norm_in_count;
     a.op = c.first_op;
-    a.dp = p.d_dp;
+    a.dp = p.d_dp + (size_t)c.first_d * p.m;
     a.eout = cur;
     PassTimer tm(p, 0, s);
     SR_CUDA(sr::launch_first(p, sr::s1_layout(c.s0), a, B, s), "launch(first pass)");
@@ -471,6 +489,9 @@ sr_status sr_plan_destroy(sr_plan* plan) {
   for (auto& v : plan->ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
   free_workspace(plan);
+  cudaFree(plan->d_w0);
+  cudaFree(plan->d_w1);
+  cudaFree(plan->d_theta_f);
   cudaFree(plan->d_err);
   cudaFree(plan->d_dp);
   cudaFree(plan->d_twl);
@@ -480,9 +501,33 @@ sr_status sr_plan_destroy(sr_plan* plan) {
   return SR_OK;
 }
 
-sr_status sr_plan_get_phases(const sr_plan* plan, double* theta) {
-  if (!plan || !theta) return fail(SR_ERR_INVALID_ARG, "NULL argument");
+sr_status sr_plan_get_phases(const sr_plan* plan_c, double* theta) {
+  if (!plan_c || !theta) return fail(SR_ERR_INVALID_ARG, "NULL argument");
+  sr_plan* plan = const_cast<sr_plan*>(plan_c);
+  if (plan->host_theta_stale) {
+    // phases were last set from the device: refresh the host copy
+    std::vector<float> f(plan->theta.size());
+    SR_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    SR_CUDA(cudaMemcpy(f.data(), plan->d_theta_f, f.size() * sizeof(float), cudaMemcpyDeviceToHost), "cudaMemcpy");
+    for (size_t i = 0; i < f.size(); ++i) plan->theta[i] = f[i];
+    plan->host_theta_stale = false;
+  }
   std::memcpy(theta, plan->theta.data(), plan->theta.size() * sizeof(double));
+  return SR_OK;
+}
+
+sr_status sr_plan_set_phases_device(sr_plan* plan, const float* theta, void* stream) {
+  if (!plan || !theta) return fail(SR_ERR_INVALID_ARG, "NULL argument");
+  sr_status st = check_device(plan);
+  if (st != SR_OK) return st;
+  const size_t count = (size_t)plan->L * plan->m;
+  if (!plan->d_theta_f && (st = dalloc(&plan->d_theta_f, count)) != SR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  SR_CUDA(cudaMemcpyAsync(plan->d_theta_f, theta, count * sizeof(float), cudaMemcpyDeviceToDevice, s),
+          "cudaMemcpyAsync(theta)");
+  SR_CUDA(sr::launch_set_diag(plan->d_theta_f, plan->d_dp, count, (float)(1.0 / std::sqrt((double)plan->m)), s),
+          "launch(diagonals)");
+  plan->host_theta_stale = true;
   return SR_OK;
 }
 
@@ -493,6 +538,7 @@ sr_status sr_plan_set_phases(sr_plan* plan, const double* theta) {
   for (size_t i = 0; i < plan->theta.size(); ++i)
     if (!std::isfinite(theta[i])) return fail(SR_ERR_NUMERIC, "non-finite phase");
   std::memcpy(plan->theta.data(), theta, plan->theta.size() * sizeof(double));
+  plan->host_theta_stale = false;
   SR_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
   return upload_diagonals(plan);
 }
@@ -685,6 +731,70 @@ sr_status sr_plan_get_timing(sr_plan* plan, double* ms, int64_t* count) {
     if (count) count[k] = (int64_t)(used / 2);
     plan->ev_used[k] = 0;
   }
+  return SR_OK;
+}
+
+sr_status sr_backward(sr_plan* plan, const void* x, const void* gz, void* grad_x, float* grad_theta, int B,
+                      void* stream) {
+  sr_status st = check_plan_call(plan, B);
+  if (st != SR_OK) return st;
+  if (!x || !gz) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
+  if (!grad_x && !grad_theta) return SR_OK;
+  if ((st = ensure_backward_buffers(plan, B)) != SR_OK) return st;
+  Plan& p = *plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int L = p.L, n = (int)p.n, m = (int)p.m;
+  float2* h = p.d_w0;  // gradient at p_l, carried with a factor sqrt(m)
+  float2* q = p.d_w1;  // recomputed layer input q_l
+  // h_L = F^H G_z (one inverse DFT, unnormalised: sqrt(m) F^H)
+  {
+    Chain c;
+    c.nfft = 1;
+    c.dir[0] = +1;
+    c.xin = (const float2*)gz;
+    c.n_in = m;
+    c.xout = h;
+    c.n_out = m;
+    if ((st = run_chain(p, c, B, s)) != SR_OK) return st;
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    if (grad_theta) {
+      const float2* ql = (const float2*)x;  // q_1 = U x
+      int nq = n;
+      if (l > 0) {
+        // recompute q_l = F D_{l-1} ... F D_1 U x instead of storing it
+        Chain c;
+        c.nfft = l;
+        for (int k = 0; k < l; ++k) c.dir[k] = -1;
+        c.first_op = sr::kOpDiag;
+        for (int k = 1; k < l; ++k) c.mid[k] = MidOp{sr::kOpDiag, k};
+        c.xin = (const float2*)x;
+        c.n_in = n;
+        c.xout = q;
+        c.n_out = m;
+        if ((st = run_chain(p, c, B, s)) != SR_OK) return st;
+        ql = q;
+        nq = m;
+      }
+      SR_CUDA(sr::launch_theta_grad(ql, nq, p.d_dp + (size_t)l * m, h, m, B, grad_theta + (size_t)l * m, s),
+              "launch(theta grad)");
+    }
+    if (l > 0) {
+      // h_{l-1} = F^H D_l^H h_l (the input is consumed by the first pass before
+      // the last pass overwrites it)
+      Chain c;
+      c.nfft = 1;
+      c.dir[0] = +1;
+      c.first_op = sr::kOpDiagConj;
+      c.first_d = l;
+      c.xin = h;
+      c.n_in = m;
+      c.xout = h;
+      c.n_out = m;
+      if ((st = run_chain(p, c, B, s)) != SR_OK) return st;
+    }
+  }
+  if (grad_x) SR_CUDA(sr::launch_conj_diag_prune(h, p.d_dp, m, n, B, (float2*)grad_x, s), "launch(grad x)");
   return SR_OK;
 }
 

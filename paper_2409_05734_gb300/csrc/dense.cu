@@ -1,0 +1,577 @@
+// Dense i.i.d. comparison model (Sec. II-A): z = A x and A^H w for a dense
+// complex A in C^{m x n}, as real GEMMs on the fifth-generation tensor cores.
+//
+// Number formats. A is stored in BF16 and is, by definition, the model's
+// matrix: the caller's entries are rounded to BF16 once when the model is
+// created, so the product involves no further error from A. The vector
+// operand (x, or the residual-weighted w) is split into a BF16 high part and a
+// BF16 low part (v = hi + lo to about 2^-17 relative); each A tile staged in
+// shared memory is multiplied with both parts, accumulating in FP32 in tensor
+// memory, so the split costs no extra HBM traffic.
+//
+// Complex products as one real GEMM with interleaved layouts:
+//   forward  Z'[i][c] = sum_k Af[i][k] X'[c][k],  Af[i][2j] = Re A_ij, Af[i][2j+1] = Im A_ij,
+//            X'[b][(2j,2j+1)] = (Re x_j, -Im x_j), X'[B+b][(2j,2j+1)] = (Im x_j, Re x_j)
+//            -> Z'[i][b] = Re z_i, Z'[i][B+b] = Im z_i;
+//   adjoint  G'[r][c] = sum_i Aa[r][i] W'[c][i],  Aa[2j][i] = Re A_ij, Aa[2j+1][i] = Im A_ij,
+//            W'[b][i] = Re w_i, W'[B+b][i] = Im w_i
+//            -> Re (A^H w)_j = G'[2j][b] + G'[2j+1][B+b], Im = G'[2j][B+b] - G'[2j+1][b].
+// Both operands of both GEMMs are K-major (A is stored twice, Af and its
+// transpose Aa), so one kernel serves both.
+//
+// Kernel: one CTA per 128-row tile of the output, 4 warps. Warp 0 lane 0 issues
+// the TMA loads of a multi-stage ring (A tile 128 x 64, X'/W' hi and lo tiles
+// 2B x 64, all 128-byte swizzled); warp 1 lane 0 issues tcgen05.mma (M = 128,
+// N = 2B, K = 16 per instruction) into a TMEM accumulator and frees each stage
+// with tcgen05.commit; then all four warps read their 32 TMEM lanes and run the
+// fused epilogue. All waits are bounded by the global timer.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "sr_device.cuh"
+#include "sr_internal.h"
+#include "sr_tcgen05.cuh"
+
+namespace sr {
+namespace {
+
+constexpr int kBM = 128;      // output rows per CTA (TMEM lanes)
+constexpr int kBK = 64;       // BF16 values per 128-byte row of a stage
+constexpr int kThreads = 128;
+constexpr int kMaxStages = 6;
+
+enum DenseMode {
+  kDenseStoreZ = 0,  // forward: z = A x
+  kDenseGdFwd = 1,   // forward: r = |z|^2 - y, w = r z as the adjoint's operand, loss partials
+  kDenseStoreX = 2,  // adjoint: x = A^H w
+  kDenseGdAdj = 3    // adjoint: x -= mu_t 2 A^H w, next forward operand, loss history
+};
+
+struct GemmArgs {
+  CUtensorMap ta;   // A operand: rows = output rows, inner = K (BF16)
+  CUtensorMap tbh;  // vector operand, high part: rows = 2B, inner = K
+  CUtensorMap tbl;  // vector operand, low part
+  int M, K, B;      // output rows, reduction length, problems (N = 2B)
+  int mode;
+  int n, m;         // model sizes
+  float2* z;                 // kDenseStoreZ: [B][m]
+  const float* y;            // kDenseGdFwd: [B][m]
+  __nv_bfloat16* w_hi;       // kDenseGdFwd: W' [2B][m]
+  __nv_bfloat16* w_lo;
+  float* loss_part;          // kDenseGdFwd writes [tiles][B]; kDenseGdAdj reads
+  int loss_tiles;
+  float* loss_out;           // kDenseGdAdj: [B] or nullptr
+  float2* x;                 // kDenseStoreX / kDenseGdAdj: [B][n]
+  const float* mu;           // kDenseGdAdj: [B]
+  float mu_scale;
+  __nv_bfloat16* xo_hi;      // kDenseGdAdj: next X' [2B][2n]
+  __nv_bfloat16* xo_lo;
+  int* err;
+};
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constant__ GemmArgs a, int stages) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  __shared__ float red[4][128];
+  const uint32_t base_a = smem_addr(smem_raw);
+  const uint32_t base = (base_a + 1023u) & ~1023u;
+  const int N = 2 * a.B;
+  const uint32_t a_bytes = kBM * 128, b_bytes = (uint32_t)N * 128;
+  const uint32_t stage_bytes = a_bytes + 2 * b_bytes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM;
+  // TMEM columns of one accumulator: N, and every column the epilogue reads
+  // (32-column loads at c0 and B + c0 for c0 < B). Successive K-stages rotate
+  // over `nacc` accumulators (as many as the 512 columns hold, up to 4) that the
+  // epilogue adds in FP32: shorter accumulation chains inside the tensor core.
+  const int need = max(N, a.B + ((a.B - 1) / 32) * 32 + 32);
+  uint32_t acc_cols = 32;
+  while ((int)acc_cols < need) acc_cols <<= 1;
+  const int nacc = (int)min(4u, 512u / acc_cols);
+  const uint32_t ncols = acc_cols * (uint32_t)nacc;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(smem_addr(&full_bar[s]), 1);
+      mbar_init(smem_addr(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_addr(&done_bar), 1);
+    mbar_init_fence();
+    s_fail = 0;
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const int KT = a.K / kBK;
+
+  if (warp == 0 && lane == 0) {
+    // producer: TMA loads into the stage ring
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % stages, round = kt / stages;
+      if (!mbar_wait_bounded(smem_addr(&empty_bar[s]), (uint32_t)((round & 1) ^ 1))) {
+        s_fail = 1;
+        break;
+      }
+      const uint32_t st = base + (uint32_t)s * stage_bytes;
+      const uint32_t fb = smem_addr(&full_bar[s]);
+      mbar_arrive_expect_tx(fb, stage_bytes);
+      tma_load_2d(st, &a.ta, kt * kBK, m0, fb);
+      tma_load_2d(st + a_bytes, &a.tbh, kt * kBK, 0, fb);
+      tma_load_2d(st + a_bytes + b_bytes, &a.tbl, kt * kBK, 0, fb);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: 4 K-steps of 16 per stage, high and low parts
+    const uint32_t idesc = idesc_bf16_f32(kBM, N);
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % stages, round = kt / stages;
+      if (!mbar_wait_bounded(smem_addr(&full_bar[s]), (uint32_t)(round & 1))) {
+        s_fail = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = base + (uint32_t)s * stage_bytes;
+      const uint32_t dacc = tmem + (uint32_t)(kt % nacc) * acc_cols;
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        const uint64_t da = sw128_desc(st + kk * 32);
+        tc_mma_bf16(dacc, da, sw128_desc(st + a_bytes + kk * 32), idesc, (kt >= nacc || kk != 0) ? 1u : 0u);
+        tc_mma_bf16(dacc, da, sw128_desc(st + a_bytes + b_bytes + kk * 32), idesc, 1u);
+      }
+      tc_commit(smem_addr(&empty_bar[s]));
+    }
+    tc_commit(smem_addr(&done_bar));
+  }
+
+  // epilogue: each warp reads its 32 TMEM lanes = 32 output rows
+  bool ok = mbar_wait_bounded(smem_addr(&done_bar), 0);
+  tc_fence_after();
+  ok = __syncthreads_and(ok) && !s_fail;
+  const int row = m0 + warp * 32 + lane;  // output row of this thread
+  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+  if (ok) {
+    for (int c0 = 0; c0 < a.B; c0 += 32) {
+      float re[32], im[32];
+      tmem_ld32(tl + (uint32_t)c0, re);
+      tmem_ld32(tl + (uint32_t)(a.B + c0), im);
+      for (int q = 1; q < nacc && q < KT; ++q) {
+        float r2[32], i2[32];
+        tmem_ld32(tl + (uint32_t)q * acc_cols + (uint32_t)c0, r2);
+        tmem_ld32(tl + (uint32_t)q * acc_cols + (uint32_t)(a.B + c0), i2);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          re[i] += r2[i];
+          im[i] += i2[i];
+        }
+      }
+      const int nb = min(32, a.B - c0);
+      if (a.mode == kDenseStoreZ) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (q < nb) a.z[(size_t)(c0 + q) * a.m + row] = make_float2(re[q], im[q]);
+      } else if (a.mode == kDenseGdFwd) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          if (q >= nb) continue;
+          const int b = c0 + q;
+          const float r = fmaf(re[q], re[q], im[q] * im[q]) - a.y[(size_t)b * a.m + row];
+          __nv_bfloat16 h, l;
+          split_bf16(r * re[q], h, l);
+          a.w_hi[(size_t)b * a.m + row] = h;
+          a.w_lo[(size_t)b * a.m + row] = l;
+          split_bf16(r * im[q], h, l);
+          a.w_hi[(size_t)(a.B + b) * a.m + row] = h;
+          a.w_lo[(size_t)(a.B + b) * a.m + row] = l;
+          float s = r * r;
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+          if (lane == 0) red[warp][q] = s;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < nb)
+          a.loss_part[(size_t)blockIdx.x * a.B + c0 + threadIdx.x] =
+              ((red[0][threadIdx.x] + red[1][threadIdx.x]) + red[2][threadIdx.x]) + red[3][threadIdx.x];
+        __syncthreads();
+      } else {
+        // adjoint: rows 2j (Re A^T) and 2j+1 (Im A^T) sit in neighbouring lanes
+        const int j = row >> 1;
+        const bool even = (row & 1) == 0;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          if (q >= nb) continue;
+          const float o_re = __shfl_xor_sync(0xffffffffu, re[q], 1);
+          const float o_im = __shfl_xor_sync(0xffffffffu, im[q], 1);
+          if (!even) continue;
+          const int b = c0 + q;
+          const float gr = re[q] + o_im;  // G[2j][b] + G[2j+1][B+b]
+          const float gi = im[q] - o_re;  // G[2j][B+b] - G[2j+1][b]
+          float2* xp = &a.x[(size_t)b * a.n + j];
+          if (a.mode == kDenseStoreX) {
+            *xp = make_float2(gr, gi);
+          } else {
+            const float s = 2.0f * a.mu[b] * a.mu_scale;
+            float2 xv = *xp;
+            xv.x = fmaf(-s, gr, xv.x);
+            xv.y = fmaf(-s, gi, xv.y);
+            *xp = xv;
+            // next forward operand: X'[b] = (Re x, -Im x), X'[B+b] = (Im x, Re x)
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf16(xv.x, h0, l0);
+            split_bf16(xv.y, h1, l1);
+            const size_t kb = (size_t)b * (2 * a.n) + 2 * j, kc = (size_t)(a.B + b) * (2 * a.n) + 2 * j;
+            a.xo_hi[kb] = h0;
+            a.xo_lo[kb] = l0;
+            a.xo_hi[kb + 1] = __hneg(h1);
+            a.xo_lo[kb + 1] = __hneg(l1);
+            a.xo_hi[kc] = h1;
+            a.xo_lo[kc] = l1;
+            a.xo_hi[kc + 1] = h0;
+            a.xo_lo[kc + 1] = l0;
+          }
+        }
+      }
+    }
+    if (a.mode == kDenseGdAdj && a.loss_out && blockIdx.x == 0) {
+      for (int b = threadIdx.x; b < a.B; b += blockDim.x) {
+        fsum2 acc{0.f, 0.f};
+        for (int t = 0; t < a.loss_tiles; ++t) acc_add(acc, a.loss_part[(size_t)t * a.B + b]);
+        a.loss_out[b] = acc.s + acc.c;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+  if (!ok && threadIdx.x == 0) atomicExch(a.err, (int)SR_ERR_TIMEOUT);
+}
+
+// X' (high and low) from x: rows b = (Re x, -Im x), rows B+b = (Im x, Re x).
+__global__ void k_dense_prep_x(const float2* __restrict__ x, int n, int B, __nv_bfloat16* __restrict__ hi,
+                               __nv_bfloat16* __restrict__ lo) {
+  const size_t total = (size_t)B * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = i / n, j = i - b * n;
+    const float2 v = x[i];
+    __nv_bfloat16 h0, l0, h1, l1;
+    split_bf16(v.x, h0, l0);
+    split_bf16(v.y, h1, l1);
+    const size_t kb = b * (2 * (size_t)n) + 2 * j, kc = ((size_t)B + b) * (2 * (size_t)n) + 2 * j;
+    hi[kb] = h0;
+    lo[kb] = l0;
+    hi[kb + 1] = __hneg(h1);
+    lo[kb + 1] = __hneg(l1);
+    hi[kc] = h1;
+    lo[kc] = l1;
+    hi[kc + 1] = h0;
+    lo[kc + 1] = l0;
+  }
+}
+
+// W' (high and low) from a complex vector w: rows b = Re w, rows B+b = Im w.
+__global__ void k_dense_prep_w(const float2* __restrict__ w, int m, int B, __nv_bfloat16* __restrict__ hi,
+                               __nv_bfloat16* __restrict__ lo) {
+  const size_t total = (size_t)B * m;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = i / m, k = i - b * m;
+    const float2 v = w[i];
+    __nv_bfloat16 h, l;
+    split_bf16(v.x, h, l);
+    hi[i] = h;
+    lo[i] = l;
+    split_bf16(v.y, h, l);
+    hi[((size_t)B + b) * m + k] = h;
+    lo[((size_t)B + b) * m + k] = l;
+  }
+}
+
+}  // namespace
+}  // namespace sr
+
+// ---------------------------------------------------------------- host side
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+  static EncodeTiledFn enc = nullptr;
+  if (!enc) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      enc = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return enc;
+}
+
+// BF16 matrix [rows][inner] as TMA boxes of 64 values x box_rows rows, 128-byte swizzle.
+bool encode_bf16(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, int box_rows) {
+  EncodeTiledFn enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+struct sr_dense {
+  int64_t n = 0, m = 0;
+  int device = 0;
+  __nv_bfloat16* d_af = nullptr;  // [m][2n]
+  __nv_bfloat16* d_aa = nullptr;  // [2n][m]
+  int* d_err = nullptr;
+  // workspace for B problems
+  int B_cap = 0;
+  __nv_bfloat16 *d_xh = nullptr, *d_xl = nullptr;  // [2B][2n]
+  __nv_bfloat16 *d_wh = nullptr, *d_wl = nullptr;  // [2B][m]
+  float* d_part = nullptr;                          // [m/128][B]
+  float* d_scal = nullptr;                          // [2][B]: sum(y), mu
+};
+
+namespace {
+
+sr_status dfail(sr_status st, const std::string& msg) {
+  sr::set_last_error(msg);
+  return st;
+}
+
+#define SR_DCUDA(call, where)                                                                     \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return dfail(SR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void dense_free_ws(sr_dense* d) {
+  cudaFree(d->d_xh);
+  cudaFree(d->d_xl);
+  cudaFree(d->d_wh);
+  cudaFree(d->d_wl);
+  cudaFree(d->d_part);
+  cudaFree(d->d_scal);
+  d->d_xh = d->d_xl = d->d_wh = d->d_wl = nullptr;
+  d->d_part = d->d_scal = nullptr;
+  d->B_cap = 0;
+}
+
+sr_status dense_ws(sr_dense* d, int B) {
+  if (B <= d->B_cap) return SR_OK;
+  dense_free_ws(d);
+  const size_t xs = (size_t)2 * B * 2 * d->n, ws = (size_t)2 * B * d->m;
+  cudaError_t e;
+  if ((e = cudaMalloc(&d->d_xh, xs * 2)) != cudaSuccess || (e = cudaMalloc(&d->d_xl, xs * 2)) != cudaSuccess ||
+      (e = cudaMalloc(&d->d_wh, ws * 2)) != cudaSuccess || (e = cudaMalloc(&d->d_wl, ws * 2)) != cudaSuccess ||
+      (e = cudaMalloc(&d->d_part, sizeof(float) * (size_t)(d->m / 128) * B)) != cudaSuccess ||
+      (e = cudaMalloc(&d->d_scal, sizeof(float) * 2 * (size_t)B)) != cudaSuccess) {
+    cudaGetLastError();
+    dense_free_ws(d);
+    return dfail(SR_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  d->B_cap = B;
+  return SR_OK;
+}
+
+size_t gemm_smem(int B, int* stages) {
+  const size_t stage = (size_t)sr::kBM * 128 + 2 * (size_t)(2 * B) * 128;
+  int s = (int)std::min<size_t>(sr::kMaxStages, (200 * 1024) / stage);
+  *stages = std::max(2, s);
+  return (size_t)(*stages) * stage + 1024;
+}
+
+sr_status check_call(sr_dense* d, int B) {
+  if (!d) return dfail(SR_ERR_INVALID_ARG, "model is NULL");
+  if (B < 1 || B > 128 || B % 8 != 0) return dfail(SR_ERR_UNSUPPORTED, "dense model: B must be a multiple of 8 in [8, 128]");
+  int dev = -1;
+  SR_DCUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev != d->device) return dfail(SR_ERR_INVALID_ARG, "current CUDA device differs from the model's device");
+  return dense_ws(d, B);
+}
+
+// One GEMM launch: output rows M (multiple of 128), reduction K (multiple of 64).
+sr_status run_gemm(sr_dense* d, sr::GemmArgs& g, const void* a_op, int64_t M, int64_t K, const __nv_bfloat16* bh,
+                   const __nv_bfloat16* bl, int B, cudaStream_t s) {
+  if (!encode_bf16(&g.ta, a_op, K, M, sr::kBM) || !encode_bf16(&g.tbh, bh, K, 2 * B, 2 * B) ||
+      !encode_bf16(&g.tbl, bl, K, 2 * B, 2 * B))
+    return dfail(SR_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  g.M = (int)M;
+  g.K = (int)K;
+  g.B = B;
+  g.n = (int)d->n;
+  g.m = (int)d->m;
+  g.err = d->d_err;
+  int stages = 2;
+  const size_t smem = gemm_smem(B, &stages);
+  SR_DCUDA(cudaFuncSetAttribute(sr::k_dense_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+           "cudaFuncSetAttribute");
+  sr::k_dense_gemm<<<(unsigned)(M / sr::kBM), sr::kThreads, smem, s>>>(g, stages);
+  sr::count_launch();
+  SR_DCUDA(cudaGetLastError(), "launch(dense gemm)");
+  return SR_OK;
+}
+
+sr_status prep_x(sr_dense* d, const float2* x, int B, cudaStream_t s) {
+  const size_t total = (size_t)B * d->n;
+  sr::k_dense_prep_x<<<(unsigned)std::min<size_t>(4096, (total + 255) / 256), 256, 0, s>>>(x, (int)d->n, B, d->d_xh,
+                                                                                        d->d_xl);
+  sr::count_launch();
+  SR_DCUDA(cudaGetLastError(), "launch(dense prep x)");
+  return SR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sr_status sr_dense_create(int64_t n, int64_t m, const float* a_host, sr_dense** out) {
+  if (!out || !a_host) return dfail(SR_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (n < 64 || m < 128 || n % 64 != 0 || m % 128 != 0 || n > (1 << 20) || m > (1 << 22) || n > m)
+    return dfail(SR_ERR_UNSUPPORTED, "dense model: n a multiple of 64, m a multiple of 128, 64 <= n <= m");
+  sr_dense* d = new (std::nothrow) sr_dense();
+  if (!d) return dfail(SR_ERR_OOM, "host allocation failed");
+  d->n = n;
+  d->m = m;
+  cudaError_t e = cudaGetDevice(&d->device);
+  const size_t cnt = (size_t)m * n * 2;
+  std::vector<__nv_bfloat16> af(cnt), aa(cnt);
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      const __nv_bfloat16 re = __float2bfloat16_rn(a_host[(i * n + j) * 2]);
+      const __nv_bfloat16 im = __float2bfloat16_rn(a_host[(i * n + j) * 2 + 1]);
+      af[(size_t)i * 2 * n + 2 * j] = re;
+      af[(size_t)i * 2 * n + 2 * j + 1] = im;
+      aa[(size_t)(2 * j) * m + i] = re;
+      aa[(size_t)(2 * j + 1) * m + i] = im;
+    }
+  if (e == cudaSuccess) e = cudaMalloc(&d->d_af, cnt * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&d->d_aa, cnt * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&d->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(d->d_af, af.data(), cnt * 2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d->d_aa, aa.data(), cnt * 2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(d->d_err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    sr_dense_destroy(d);
+    return dfail(e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA,
+                 std::string("dense model setup: ") + cudaGetErrorString(e));
+  }
+  *out = d;
+  return SR_OK;
+}
+
+sr_status sr_dense_destroy(sr_dense* d) {
+  if (!d) return SR_OK;
+  dense_free_ws(d);
+  cudaFree(d->d_af);
+  cudaFree(d->d_aa);
+  cudaFree(d->d_err);
+  delete d;
+  return SR_OK;
+}
+
+sr_status sr_dense_forward(sr_dense* d, const void* x, void* z, int B, void* stream) {
+  sr_status st = check_call(d, B);
+  if (st != SR_OK) return st;
+  if (!x || !z) return dfail(SR_ERR_INVALID_ARG, "NULL array argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = prep_x(d, (const float2*)x, B, s)) != SR_OK) return st;
+  sr::GemmArgs g;
+  memset(&g, 0, sizeof(g));
+  g.mode = sr::kDenseStoreZ;
+  g.z = (float2*)z;
+  return run_gemm(d, g, d->d_af, d->m, 2 * d->n, d->d_xh, d->d_xl, B, s);
+}
+
+sr_status sr_dense_adjoint(sr_dense* d, const void* w, void* x, int B, void* stream) {
+  sr_status st = check_call(d, B);
+  if (st != SR_OK) return st;
+  if (!x || !w) return dfail(SR_ERR_INVALID_ARG, "NULL array argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t total = (size_t)B * d->m;
+  sr::k_dense_prep_w<<<(unsigned)std::min<size_t>(4096, (total + 255) / 256), 256, 0, s>>>(
+      (const float2*)w, (int)d->m, B, d->d_wh, d->d_wl);
+  sr::count_launch();
+  SR_DCUDA(cudaGetLastError(), "launch(dense prep w)");
+  sr::GemmArgs g;
+  memset(&g, 0, sizeof(g));
+  g.mode = sr::kDenseStoreX;
+  g.x = (float2*)x;
+  return run_gemm(d, g, d->d_aa, 2 * d->n, d->m, d->d_wh, d->d_wl, B, s);
+}
+
+sr_status sr_dense_gd_solve(sr_dense* d, const float* y, void* x, int iters, const sr_gd_opts* opts,
+                            float* loss_hist, int B, void* stream) {
+  sr_status st = check_call(d, B);
+  if (st != SR_OK) return st;
+  if (!y || !x) return dfail(SR_ERR_INVALID_ARG, "NULL array argument");
+  if (iters < 0) return dfail(SR_ERR_INVALID_ARG, "iters must be >= 0");
+  const float mu0 = opts ? opts->mu0 : 0.1f;
+  const float tau0 = opts ? opts->tau0 : 0.f;
+  if (!(mu0 > 0.f && std::isfinite(mu0)) || !(tau0 >= 0.f && std::isfinite(tau0)))
+    return dfail(SR_ERR_INVALID_ARG, "mu0 must be > 0 and tau0 >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  // step mu = mu0 * m / sum(y): the structured model's helpers compute sum(y)
+  const int chunks = (int)std::min<int64_t>(64, (d->m + 4095) / 4096);
+  SR_DCUDA(sr::launch_sum_rows(y, B, (int)d->m, d->d_part, chunks, s), "launch(sum y)");
+  SR_DCUDA(sr::launch_finish_scalars(d->d_part, chunks, B, mu0, (int)d->m, d->d_scal, d->d_scal + B, s),
+           "launch(step size)");
+  if ((st = prep_x(d, (const float2*)x, B, s)) != SR_OK) return st;
+  for (int it = 0; it < iters; ++it) {
+    sr::GemmArgs f;
+    memset(&f, 0, sizeof(f));
+    f.mode = sr::kDenseGdFwd;
+    f.y = y;
+    f.w_hi = d->d_wh;
+    f.w_lo = d->d_wl;
+    f.loss_part = d->d_part;
+    if ((st = run_gemm(d, f, d->d_af, d->m, 2 * d->n, d->d_xh, d->d_xl, B, s)) != SR_OK) return st;
+    sr::GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.mode = sr::kDenseGdAdj;
+    g.x = (float2*)x;
+    g.mu = d->d_scal + B;
+    g.mu_scale = tau0 > 0.f ? (float)(1.0 - std::exp(-(double)(it + 1) / (double)tau0)) : 1.0f;
+    g.xo_hi = d->d_xh;
+    g.xo_lo = d->d_xl;
+    g.loss_part = d->d_part;
+    g.loss_tiles = (int)(d->m / sr::kBM);
+    g.loss_out = loss_hist ? loss_hist + (size_t)it * B : nullptr;
+    if ((st = run_gemm(d, g, d->d_aa, 2 * d->n, d->m, d->d_wh, d->d_wl, B, s)) != SR_OK) return st;
+  }
+  return SR_OK;
+}
+
+sr_status sr_dense_check(sr_dense* d) {
+  if (!d) return dfail(SR_ERR_INVALID_ARG, "model is NULL");
+  SR_DCUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  int code = 0;
+  SR_DCUDA(cudaMemcpy(&code, d->d_err, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy(status)");
+  if (code != 0) {
+    SR_DCUDA(cudaMemset(d->d_err, 0, sizeof(int)), "cudaMemset(status)");
+    return dfail((sr_status)code, "a device-side wait of the dense model gave up");
+  }
+  return SR_OK;
+}
+
+}  // extern "C"

@@ -59,6 +59,47 @@ __global__ void k_scale_rows(float2* __restrict__ v, int n, const float* __restr
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) vb[i] = cscale(vb[i], f);
 }
 
+// D_l[k] = exp(i theta_l[k]) / sqrt(m) from device phases (float), all layers.
+__global__ void k_set_diag(const float* __restrict__ theta, float2* __restrict__ d, size_t count, float scale) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    float sn, cs;
+    sincosf(theta[i], &sn, &cs);
+    d[i] = make_float2(cs * scale, sn * scale);
+  }
+}
+
+// Phase gradient of one layer, summed over the batch (compensated):
+// out[k] = sum_b Im(conj(D[k] q[b][k]) h[b][k]), with q[b][k] = 0 for k >= nq.
+// D carries 1/sqrt(m) and h carries the matching sqrt(m) (unnormalised inverse
+// DFTs), so the product is the unscaled gradient.
+__global__ void k_theta_grad(const float2* __restrict__ q, int nq, const float2* __restrict__ d,
+                             const float2* __restrict__ h, int m, int B, float* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  if (k >= nq) {
+    out[k] = 0.f;
+    return;
+  }
+  const float2 dk = __ldg(&d[k]);
+  fsum2 acc{0.f, 0.f};
+  for (int b = 0; b < B; ++b) {
+    const float2 pk = cmul(dk, q[(size_t)b * nq + k]);
+    const float2 hk = h[(size_t)b * m + k];
+    acc_add(acc, pk.x * hk.y - pk.y * hk.x);  // Im(conj(p) h)
+  }
+  out[k] = acc.s + acc.c;
+}
+
+// out[b][k] = conj(D[k]) h[b][k] for k < n (the last step of the backward: U^H D_1^H).
+__global__ void k_conj_diag_prune(const float2* __restrict__ h, const float2* __restrict__ d, int m, int n, int B,
+                                  float2* __restrict__ out) {
+  const size_t total = (size_t)B * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = i / n, k = i - b * n;
+    out[i] = cmulc(h[b * m + k], __ldg(&d[k]));
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 
 constexpr size_t kSmemBudget = 220 * 1024;
@@ -181,6 +222,27 @@ cudaError_t launch_scale_rows(float2* v, int B, int n, const float* part, int ch
                               cudaStream_t s) {
   const int blocks = std::min(64, (n + 255) / 256);
   k_scale_rows<<<dim3(blocks, B), 256, 0, s>>>(v, n, part, chunks, sumy);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_diag(const float* theta, float2* d, size_t count, float scale, cudaStream_t s) {
+  const int blocks = (int)std::min<size_t>(4096, (count + 255) / 256);
+  k_set_diag<<<blocks, 256, 0, s>>>(theta, d, count, scale);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_theta_grad(const float2* q, int nq, const float2* d, const float2* h, int m, int B, float* out,
+                              cudaStream_t s) {
+  k_theta_grad<<<(m + 255) / 256, 256, 0, s>>>(q, nq, d, h, m, B, out);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_conj_diag_prune(const float2* h, const float2* d, int m, int n, int B, float2* out,
+                                   cudaStream_t s) {
+  const size_t total = (size_t)B * n;
+  const int blocks = (int)std::min<size_t>(4096, (total + 255) / 256);
+  k_conj_diag_prune<<<blocks, 256, 0, s>>>(h, d, m, n, B, out);
   count_launch();
   return cudaGetLastError();
 }

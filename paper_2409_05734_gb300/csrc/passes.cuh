@@ -228,6 +228,9 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   if (a.op == kOpDiag) {
 #pragma unroll
     for (int j = 0; j < E; ++j) v[j] = cmul(v[j], __ldg(&a.dp[(p + j * P) * a.nl + g]));
+  } else if (a.op == kOpDiagConj) {
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&a.dp[(p + j * P) * a.nl + g]));
   }
   __syncthreads();
   const float sc = s_scale;

@@ -121,6 +121,14 @@ struct Plan {
   float2* d_e1 = nullptr;
   float* d_part = nullptr;       // partial sums, 4 banks
   float* d_scal = nullptr;       // [4][B]: sum(y), mu, spare
+  // backward pass: two natural-order vectors per problem (grown on first use)
+  int W_cap = 0;
+  float2* d_w0 = nullptr;
+  float2* d_w1 = nullptr;
+  // phases set from the device (sr_plan_set_phases_device): float copy; the
+  // host copy `theta` is refreshed from it on demand
+  float* d_theta_f = nullptr;
+  bool host_theta_stale = false;
   CUtensorMap tmap[2][2];  // [buffer e0/e1][layout]: rows of the exchange buffer
   // optional per-pass event timing (sr_plan_set_timing)
   bool timing = false;
@@ -154,5 +162,10 @@ cudaError_t launch_finish_scalars(const float* part, int chunks, int B, float mu
                                   float* sumy, float* mu, cudaStream_t s);
 cudaError_t launch_scale_rows(float2* v, int B, int n, const float* part, int chunks,
                               const float* sumy, cudaStream_t s);
+cudaError_t launch_set_diag(const float* theta, float2* d, size_t count, float scale, cudaStream_t s);
+cudaError_t launch_theta_grad(const float2* q, int nq, const float2* d, const float2* h, int m, int B, float* out,
+                              cudaStream_t s);
+cudaError_t launch_conj_diag_prune(const float2* h, const float2* d, int m, int n, int B, float2* out,
+                                   cudaStream_t s);
 
 }  // namespace sr

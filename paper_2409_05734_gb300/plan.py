@@ -77,6 +77,28 @@ class Plan:
         with torch.cuda.device(self.device):
             _lib.check(self._lib.sr_plan_check(self._h), "sr_plan_check")
 
+    def set_phases_device(self, theta: torch.Tensor) -> None:
+        """Phases from a device float32 tensor [L, m]; tables rebuilt on the current stream."""
+        if theta.dtype != torch.float32 or theta.device != self.device or tuple(theta.shape) != (self.L, self.m):
+            raise ValueError(f"theta must be a float32 [{self.L}, {self.m}] tensor on {self.device}")
+        theta = theta.contiguous()
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_plan_set_phases_device(self._h, _p(theta), _stream_handle()),
+                       "sr_plan_set_phases_device")
+
+    def backward(self, x: torch.Tensor, gz: torch.Tensor, need_x: bool = True, need_theta: bool = True):
+        """(grad_x [B, n] or None, grad_theta [L, m] or None) of z = A x for the
+        gradient gz of a real loss with respect to z (PyTorch's complex convention)."""
+        x = self._c64(x, self.n, "x")
+        gz = self._c64(gz, self.m, "gz")
+        B = self._batch(x)
+        gx = torch.empty_like(x) if need_x else None
+        gth = torch.empty((self.L, self.m), dtype=torch.float32, device=self.device) if need_theta else None
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_backward(self._h, _p(x), _p(gz), _p(gx), _p(gth), B, _stream_handle()),
+                       "sr_backward")
+        return gx, gth
+
     def reserve(self, B: int) -> None:
         with torch.cuda.device(self.device):
             _lib.check(self._lib.sr_plan_reserve(self._h, int(B)), "sr_plan_reserve")

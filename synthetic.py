@@ -129,6 +129,23 @@ def dense_iid_matrix(seed: int, m: int, n: int) -> np.ndarray:
     return complex_gaussian(seed, (m, n), STREAM_DENSE, var=1.0 / m)
 
 
+def round_to_bf16(a: np.ndarray) -> np.ndarray:
+    """Nearest-even rounding of float values to the BF16 grid (8-bit significand),
+    returned as float64. Used to define a dense matrix whose entries are exactly
+    representable in BF16 (the stored form of the dense comparison model)."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    bias = ((u >> np.uint32(16)) & np.uint32(1)) + np.uint32(0x7FFF)
+    with np.errstate(over="ignore"):
+        r = (u + bias) & np.uint32(0xFFFF0000)
+    return r.view(np.float32).astype(np.float64)
+
+
+def dense_iid_matrix_bf16(seed: int, m: int, n: int) -> np.ndarray:
+    """CN(0, 1/m) dense matrix with real and imaginary parts on the BF16 grid: [m, n]."""
+    A = dense_iid_matrix(seed, m, n)
+    return round_to_bf16(A.real) + 1j * round_to_bf16(A.imag)
+
+
 def gaussian_noise(seed: int, shape, sigma) -> np.ndarray:
     """Real N(0, sigma^2) noise via Box-Muller (real part of a CN(0, 2) draw)."""
     g = complex_gaussian(seed, shape, STREAM_NOISE, var=2.0)

@@ -1,0 +1,86 @@
+"""GPU parity of the dense i.i.d. comparison model (tcgen05 GEMM) against the
+FP64 oracle's matrix products, with the same BF16-exact matrix on both sides.
+
+Tolerance: the vector operand is split into BF16 high and low parts (about
+2^-17 relative each entry) and products accumulate in FP32, so one product is
+within 2e-5 relative of the FP64 result."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def DenseModel():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2409_05734_gb300 import buildlib
+    buildlib.build()
+    from paper_2409_05734_gb300 import DenseModel as D
+    return D
+
+
+def dev(a, dtype=torch.complex64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("n,m,B", [(64, 128, 8), (128, 512, 16), (256, 1024, 40), (512, 2048, 64)])
+def test_dense_forward_adjoint(DenseModel, n, m, B):
+    A = S.dense_iid_matrix_bf16(n + m, m, n)
+    model = DenseModel(A)
+    x = S.signal_gaussian(1, B, n)
+    z = model.forward(dev(x)).cpu().numpy()
+    model.check()
+    zo = O.dense_forward(A, x)
+    assert rel(z, zo) <= 2e-5
+    assert np.max(np.abs(z - zo)) <= 1e-4 * np.sqrt(np.mean(np.abs(zo) ** 2))
+    w = S.complex_gaussian(2, (B, m), S.STREAM_NOISE)
+    xa = model.adjoint(dev(w)).cpu().numpy()
+    model.check()
+    assert rel(xa, O.dense_adjoint(A, w)) <= 2e-5
+
+
+def test_dense_gradient_descent(DenseModel):
+    n, m, B = 128, 512, 8
+    A = S.dense_iid_matrix_bf16(7, m, n)
+    model = DenseModel(A)
+    fwd, adj = O.dense_ops(A)
+    xt = S.signal_gaussian(3, B, n)
+    y = np.abs(fwd(xt)) ** 2
+    x0 = O.spectral_init(y, S.start_vector(3, B, n), fwd, adj, 30, mode="optimal")
+    xT, hist = O.gradient_descent(x0, y, fwd, adj, 40, mu0=0.1, tau0=10.0)
+    x = dev(x0)
+    _, h = model.gd_solve(dev(y, torch.float32), x, 40, mu0=0.1, tau0=10.0, record_loss=True)
+    model.check()
+    assert rel(x.cpu().numpy(), xT) <= 1e-4
+    hh = h.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(hh - hist) / hist) <= 1e-3
+
+
+def test_dense_comparison_size_sampled(DenseModel):
+    """The comparison shape: n = 4096, m = 16384, B = 64; sampled output rows."""
+    n, m, B = 4096, 16384, 64
+    rng = np.random.default_rng(5)
+    A = S.round_to_bf16(rng.standard_normal((m, n)) / np.sqrt(2 * m)) + \
+        1j * S.round_to_bf16(rng.standard_normal((m, n)) / np.sqrt(2 * m))
+    model = DenseModel(A)
+    x = S.signal_amplitude_phase(2, B, n)
+    z = model.forward(dev(x)).cpu().numpy()
+    model.check()
+    rows = rng.integers(0, m, 256)
+    zo = x @ A[rows].T
+    assert rel(z[:, rows], zo) <= 2e-5
+    w = S.complex_gaussian(4, (B, m), S.STREAM_NOISE)
+    xa = model.adjoint(dev(w)).cpu().numpy()
+    model.check()
+    cols = rng.integers(0, n, 128)
+    xo = w @ np.conj(A[:, cols])
+    assert rel(xa[:, cols], xo) <= 2e-5

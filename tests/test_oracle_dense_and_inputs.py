@@ -71,3 +71,17 @@ def test_signal_generators_shapes_and_moments():
     lam = np.full(4000, 100.0)
     k = S.poisson_counts(2, lam)
     assert abs(k.mean() - 100) < 1.0 and abs(k.var() - 100) < 10
+
+
+def test_round_to_bf16_grid():
+    # exactly representable values are kept; others go to the nearest 8-bit significand, ties to even
+    vals = np.array([1.0, -2.5, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -9, 3.0e-3], dtype=np.float64)
+    r = S.round_to_bf16(vals)
+    assert r[0] == 1.0 and r[1] == -2.5
+    assert r[2] == 1.0          # halfway between 1 and 1 + 2^-7: ties to even (1.0)
+    assert r[3] == 1.0 + 2 ** -6  # halfway between 1 + 2^-7 and 1 + 2^-6: to even (1 + 2^-6)
+    assert r[4] == 1.0
+    m, e = np.frexp(r[5])
+    assert np.isclose(r[5], 3.0e-3, rtol=2 ** -8) and (m * 2 ** 8) == np.round(m * 2 ** 8)
+    A = S.dense_iid_matrix_bf16(1, 64, 32)
+    assert np.array_equal(S.round_to_bf16(A.real), A.real)
