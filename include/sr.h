@@ -200,6 +200,13 @@ sr_status sr_dense_adjoint(sr_dense* model, const void* w, void* x, int B, void*
  * history), with the dense A. */
 sr_status sr_dense_gd_solve(sr_dense* model, const float* y, void* x, int iters, const sr_gd_opts* opts,
                             float* loss_hist, int B, void* stream);
+/* Spectral initialisation as sr_spectral_init (same weights T(y_hat), shift,
+ * normalisation and output sqrt(sum y) v), with the dense A: per iteration one
+ * forward GEMM whose epilogue forms T(y_hat) (A u) / ||u|| and one adjoint GEMM
+ * whose epilogue forms u + shift u / ||u|| and the partial sums of ||u||^2
+ * (Eq. 3-4). y: f32[B][m], v0 and x_out: c64[B][n] (x_out may equal v0). */
+sr_status sr_dense_spectral_init(sr_dense* model, const float* y, const void* v0, int iters,
+                                 const sr_spectral_opts* opts, void* x_out, int B, void* stream);
 /* As sr_plan_check, for the dense model's kernels. */
 sr_status sr_dense_check(sr_dense* model);
 

@@ -55,6 +55,7 @@ SIGNATURES = [
     ("sr_dense_forward", C.c_int, [_VP, _VP, _VP, C.c_int, _VP]),
     ("sr_dense_adjoint", C.c_int, [_VP, _VP, _VP, C.c_int, _VP]),
     ("sr_dense_gd_solve", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(GdOpts), _VP, C.c_int, _VP]),
+    ("sr_dense_spectral_init", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(SpectralOpts), _VP, C.c_int, _VP]),
     ("sr_dense_check", C.c_int, [_VP]),
     ("sr_plan_check", C.c_int, [_VP]),
     ("sr_kernel_launches", C.c_uint64, []),

@@ -19,12 +19,25 @@
 // Both operands of both GEMMs are K-major (A is stored twice, Af and its
 // transpose Aa), so one kernel serves both.
 //
+// Both operands live in HBM pre-tiled: A as tiles of 128 rows x 64 values and
+// the vector operand X'/W' as blocks of 64 columns (high part, then low part),
+// each stored as the exact 128-byte-swizzled shared-memory image the MMA reads.
+// A stage of the main loop is then two contiguous bulk copies (16 KB of A and
+// 2 x 2B x 128 bytes of the vector operand), with no tensor maps. The kernels
+// that produce X' and W' (the operand preparation and the fused epilogues)
+// write the tiled form directly.
+//
+// Throughput: the main loop is bound by the latency of the stage ring (about
+// 2 us from issuing a stage's copies to the MMAs releasing it), with four
+// 48 KB stages in flight per SM; the vector operand takes two thirds of each
+// stage. Pairing SMs on one 256-row tile (cta_group::2, each SM holding half
+// of the vector operand) would raise the matrix bytes in flight per SM.
+//
 // Kernel: one CTA per 128-row tile of the output, 4 warps. Warp 0 lane 0 issues
-// the TMA loads of a multi-stage ring (A tile 128 x 64, X'/W' hi and lo tiles
-// 2B x 64, all 128-byte swizzled); warp 1 lane 0 issues tcgen05.mma (M = 128,
-// N = 2B, K = 16 per instruction) into a TMEM accumulator and frees each stage
-// with tcgen05.commit; then all four warps read their 32 TMEM lanes and run the
-// fused epilogue. All waits are bounded by the global timer.
+// the loads of a multi-stage ring; warp 1 lane 0 issues tcgen05.mma (M = 128,
+// N = 2B, K = 16 per instruction, high and low parts) into TMEM accumulators and
+// frees each stage with tcgen05.commit; then all four warps read their 32 TMEM
+// lanes and run the fused epilogue. All waits are bounded by the global timer.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -49,34 +62,66 @@ enum DenseMode {
   kDenseStoreZ = 0,  // forward: z = A x
   kDenseGdFwd = 1,   // forward: r = |z|^2 - y, w = r z as the adjoint's operand, loss partials
   kDenseStoreX = 2,  // adjoint: x = A^H w
-  kDenseGdAdj = 3    // adjoint: x -= mu_t 2 A^H w, next forward operand, loss history
+  kDenseGdAdj = 3,   // adjoint: x -= mu_t 2 A^H w, next forward operand, loss history
+  kDenseSpecFwd = 4, // forward: w = T(y_hat) z / ||u|| as the adjoint's operand (Eq. 3)
+  kDenseSpecAdj = 5  // adjoint: u = A^H w + s u / ||u||, norm partials, next forward operand (Eq. 4)
 };
 
 struct GemmArgs {
-  CUtensorMap ta;   // A operand: rows = output rows, inner = K (BF16)
-  CUtensorMap tbh;  // vector operand, high part: rows = 2B, inner = K
-  CUtensorMap tbl;  // vector operand, low part
+  const __nv_bfloat16* a_tiles;  // A operand, tiled: [M/128][K/64] images of 128 x 64 (16 KB, swizzled)
+  const __nv_bfloat16* b_tiles;  // vector operand, tiled (vtile_index): [K/64][high, low][2B][64]
   int M, K, B;      // output rows, reduction length, problems (N = 2B)
   int mode;
   int n, m;         // model sizes
   float2* z;                 // kDenseStoreZ: [B][m]
   const float* y;            // kDenseGdFwd: [B][m]
-  __nv_bfloat16* w_hi;       // kDenseGdFwd: W' [2B][m]
-  __nv_bfloat16* w_lo;
+  __nv_bfloat16* w_out;      // kDenseGdFwd / kDenseSpecFwd: W' [2B][m], tiled
   float* loss_part;          // kDenseGdFwd writes [tiles][B]; kDenseGdAdj reads
   int loss_tiles;
   float* loss_out;           // kDenseGdAdj: [B] or nullptr
   float2* x;                 // kDenseStoreX / kDenseGdAdj: [B][n]
   const float* mu;           // kDenseGdAdj: [B]
   float mu_scale;
-  __nv_bfloat16* xo_hi;      // kDenseGdAdj: next X' [2B][2n]
-  __nv_bfloat16* xo_lo;
+  __nv_bfloat16* xo_out;     // kDenseGdAdj / kDenseSpecAdj: next X' [2B][2n], tiled
+  // spectral initialisation
+  const float* inv_norm;     // [B]: 1/||u|| of the current iterate
+  const float* sumy;         // [B]
+  float lam, shift;
+  int weight_mode;
+  float* norm_part;          // kDenseSpecAdj: [tiles][B] partial sums of |u_new|^2
   int* err;
 };
+
+// Contiguous global -> shared copy of `bytes` (multiple of 16, both addresses
+// 16-byte aligned) completing on barrier `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
 
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
   hi = __float2bfloat16_rn(v);
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// Position of element (c, k) of a [2B][K] vector operand (X' or W') in its
+// tiled form: per block of 64 columns, the high part's shared-memory image (2B
+// rows of 128 bytes, 128-byte swizzle) followed by the low part's; the low
+// part of an element sits 2B * 64 values after its high part. One stage of the
+// GEMM is then one contiguous copy of 2 * 2B * 128 bytes.
+__host__ __device__ __forceinline__ size_t vtile_index(int c, int64_t k, int twoB) {
+  return (size_t)(k / 64) * (size_t)(2 * twoB * 64) + (size_t)c * 64 + (size_t)((((k % 64) / 8) ^ (c % 8)) * 8) +
+         (size_t)(k % 8);
+}
+
+// Splits v into BF16 high and low parts and stores both at (c, k) of a tiled operand.
+__device__ __forceinline__ void store_split(__nv_bfloat16* t, int twoB, int c, int64_t k, float v) {
+  __nv_bfloat16 h, l;
+  split_bf16(v, h, l);
+  const size_t i = vtile_index(c, k, twoB);
+  t[i] = h;
+  t[i + (size_t)twoB * 64] = l;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constant__ GemmArgs a, int stages) {
@@ -117,47 +162,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   const int KT = a.K / kBK;
+  // CTAs start their K sweep at staggered offsets so that the vector operand's
+  // tiles are not requested by every CTA at the same moment (K order only
+  // changes the FP32 summation order, which stays fixed per output row).
+  const int kt0 = (int)(((long long)blockIdx.x * KT) / gridDim.x);
 
-  if (warp == 0 && lane == 0) {
-    // producer: TMA loads into the stage ring
-    for (int kt = 0; kt < KT; ++kt) {
-      const int s = kt % stages, round = kt / stages;
-      if (!mbar_wait_bounded(smem_addr(&empty_bar[s]), (uint32_t)((round & 1) ^ 1))) {
-        s_fail = 1;
-        break;
+  // Lanes 1-31 of the producer and MMA warps park at __syncwarp (not in a spin
+  // on the done barrier, which would steal the warp's issue slots from lane 0).
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: TMA loads into the stage ring
+      for (int kt = 0; kt < KT; ++kt) {
+        const int s = kt % stages, round = kt / stages;
+        if (!mbar_wait_bounded(smem_addr(&empty_bar[s]), (uint32_t)((round & 1) ^ 1))) {
+          s_fail = 1;
+          break;
+        }
+        const uint32_t st = base + (uint32_t)s * stage_bytes;
+        const uint32_t fb = smem_addr(&full_bar[s]);
+        mbar_arrive_expect_tx(fb, stage_bytes);
+        const int kx = ((kt + kt0) % KT) * kBK;
+        bulk_load(st, a.a_tiles + ((size_t)blockIdx.x * KT + (kx / kBK)) * (kBM * kBK), a_bytes, fb);
+        bulk_load(st + a_bytes, a.b_tiles + (size_t)(kx / kBK) * (2 * N * kBK), 2 * b_bytes, fb);
       }
-      const uint32_t st = base + (uint32_t)s * stage_bytes;
-      const uint32_t fb = smem_addr(&full_bar[s]);
-      mbar_arrive_expect_tx(fb, stage_bytes);
-      tma_load_2d(st, &a.ta, kt * kBK, m0, fb);
-      tma_load_2d(st + a_bytes, &a.tbh, kt * kBK, 0, fb);
-      tma_load_2d(st + a_bytes + b_bytes, &a.tbl, kt * kBK, 0, fb);
     }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer: 4 K-steps of 16 per stage, high and low parts
-    const uint32_t idesc = idesc_bf16_f32(kBM, N);
-    for (int kt = 0; kt < KT; ++kt) {
-      const int s = kt % stages, round = kt / stages;
-      if (!mbar_wait_bounded(smem_addr(&full_bar[s]), (uint32_t)(round & 1))) {
-        s_fail = 1;
-        break;
-      }
-      tc_fence_after();
-      const uint32_t st = base + (uint32_t)s * stage_bytes;
-      const uint32_t dacc = tmem + (uint32_t)(kt % nacc) * acc_cols;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: 4 K-steps of 16 per stage, high and low parts
+      const uint32_t idesc = idesc_bf16_f32(kBM, N);
+      for (int kt = 0; kt < KT; ++kt) {
+        const int s = kt % stages, round = kt / stages;
+        if (!mbar_wait_bounded(smem_addr(&full_bar[s]), (uint32_t)(round & 1))) {
+          s_fail = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = base + (uint32_t)s * stage_bytes;
+        const uint32_t dacc = tmem + (uint32_t)(kt % nacc) * acc_cols;
 #pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk) {
-        const uint64_t da = sw128_desc(st + kk * 32);
-        tc_mma_bf16(dacc, da, sw128_desc(st + a_bytes + kk * 32), idesc, (kt >= nacc || kk != 0) ? 1u : 0u);
-        tc_mma_bf16(dacc, da, sw128_desc(st + a_bytes + b_bytes + kk * 32), idesc, 1u);
+        for (int kk = 0; kk < kBK / 16; ++kk) {
+          const uint64_t da = sw128_desc(st + kk * 32);
+          tc_mma_bf16(dacc, da, sw128_desc(st + a_bytes + kk * 32), idesc, (kt >= nacc || kk != 0) ? 1u : 0u);
+          tc_mma_bf16(dacc, da, sw128_desc(st + a_bytes + b_bytes + kk * 32), idesc, 1u);
+        }
+        tc_commit(smem_addr(&empty_bar[s]));
       }
-      tc_commit(smem_addr(&empty_bar[s]));
+      tc_commit(smem_addr(&done_bar));
     }
-    tc_commit(smem_addr(&done_bar));
+    __syncwarp();
   }
 
   // epilogue: each warp reads its 32 TMEM lanes = 32 output rows
-  bool ok = mbar_wait_bounded(smem_addr(&done_bar), 0);
+  bool ok = mbar_wait_bounded_sleep(smem_addr(&done_bar), 0, 256);
   tc_fence_after();
   ok = __syncthreads_and(ok) && !s_fail;
   const int row = m0 + warp * 32 + lane;  // output row of this thread
@@ -188,13 +245,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
           if (q >= nb) continue;
           const int b = c0 + q;
           const float r = fmaf(re[q], re[q], im[q] * im[q]) - a.y[(size_t)b * a.m + row];
-          __nv_bfloat16 h, l;
-          split_bf16(r * re[q], h, l);
-          a.w_hi[(size_t)b * a.m + row] = h;
-          a.w_lo[(size_t)b * a.m + row] = l;
-          split_bf16(r * im[q], h, l);
-          a.w_hi[(size_t)(a.B + b) * a.m + row] = h;
-          a.w_lo[(size_t)(a.B + b) * a.m + row] = l;
+          store_split(a.w_out, N, b, row, r * re[q]);
+          store_split(a.w_out, N, a.B + b, row, r * im[q]);
           float s = r * r;
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -205,6 +257,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
           a.loss_part[(size_t)blockIdx.x * a.B + c0 + threadIdx.x] =
               ((red[0][threadIdx.x] + red[1][threadIdx.x]) + red[2][threadIdx.x]) + red[3][threadIdx.x];
         __syncthreads();
+      } else if (a.mode == kDenseSpecFwd) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          if (q >= nb) continue;
+          const int b = c0 + q;
+          const float yh = a.y[(size_t)b * a.m + row] * ((float)a.m / a.sumy[b]);
+          float t;
+          if (a.weight_mode == SR_WEIGHT_IDENTITY) t = yh;
+          else t = yh > 0.f ? fmaxf(1.0f - 1.0f / yh, a.lam) : a.lam;
+          t *= a.inv_norm[b];
+          store_split(a.w_out, N, b, row, t * re[q]);
+          store_split(a.w_out, N, a.B + b, row, t * im[q]);
+        }
       } else {
         // adjoint: rows 2j (Re A^T) and 2j+1 (Im A^T) sit in neighbouring lanes
         const int j = row >> 1;
@@ -222,25 +287,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
           if (a.mode == kDenseStoreX) {
             *xp = make_float2(gr, gi);
           } else {
-            const float s = 2.0f * a.mu[b] * a.mu_scale;
             float2 xv = *xp;
-            xv.x = fmaf(-s, gr, xv.x);
-            xv.y = fmaf(-s, gi, xv.y);
+            if (a.mode == kDenseGdAdj) {
+              const float s = 2.0f * a.mu[b] * a.mu_scale;
+              xv.x = fmaf(-s, gr, xv.x);
+              xv.y = fmaf(-s, gi, xv.y);
+            } else {  // kDenseSpecAdj: u = M v + s v with v = u_old / ||u_old||
+              const float s = a.shift * a.inv_norm[b];
+              xv.x = fmaf(s, xv.x, gr);
+              xv.y = fmaf(s, xv.y, gi);
+            }
             *xp = xv;
             // next forward operand: X'[b] = (Re x, -Im x), X'[B+b] = (Im x, Re x)
-            __nv_bfloat16 h0, l0, h1, l1;
-            split_bf16(xv.x, h0, l0);
-            split_bf16(xv.y, h1, l1);
-            const size_t kb = (size_t)b * (2 * a.n) + 2 * j, kc = (size_t)(a.B + b) * (2 * a.n) + 2 * j;
-            a.xo_hi[kb] = h0;
-            a.xo_lo[kb] = l0;
-            a.xo_hi[kb + 1] = __hneg(h1);
-            a.xo_lo[kb + 1] = __hneg(l1);
-            a.xo_hi[kc] = h1;
-            a.xo_lo[kc] = l1;
-            a.xo_hi[kc + 1] = h0;
-            a.xo_lo[kc + 1] = l0;
+            store_split(a.xo_out, N, b, 2 * j, xv.x);
+            store_split(a.xo_out, N, b, 2 * j + 1, -xv.y);
+            store_split(a.xo_out, N, a.B + b, 2 * j, xv.y);
+            store_split(a.xo_out, N, a.B + b, 2 * j + 1, xv.x);
           }
+        }
+        if (a.mode == kDenseSpecAdj) {
+          // partial sums of |u_new|^2 over this tile, per problem (even lanes hold u)
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            if (q >= nb) continue;
+            float v2 = 0.f;
+            if ((row & 1) == 0) {
+              const float2 u = a.x[(size_t)(c0 + q) * a.n + (row >> 1)];
+              v2 = fmaf(u.x, u.x, u.y * u.y);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+            if (lane == 0) red[warp][q] = v2;
+          }
+          __syncthreads();
+          if ((int)threadIdx.x < nb)
+            a.norm_part[(size_t)blockIdx.x * a.B + c0 + threadIdx.x] =
+                ((red[0][threadIdx.x] + red[1][threadIdx.x]) + red[2][threadIdx.x]) + red[3][threadIdx.x];
+          __syncthreads();
         }
       }
     }
@@ -258,42 +342,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
   if (!ok && threadIdx.x == 0) atomicExch(a.err, (int)SR_ERR_TIMEOUT);
 }
 
-// X' (high and low) from x: rows b = (Re x, -Im x), rows B+b = (Im x, Re x).
-__global__ void k_dense_prep_x(const float2* __restrict__ x, int n, int B, __nv_bfloat16* __restrict__ hi,
-                               __nv_bfloat16* __restrict__ lo) {
+// inv[b] = 1 / sqrt(sum of `count` partials of problem b), partials laid out [count][B].
+__global__ void k_dense_inv_norm(const float* __restrict__ part, int count, int B, float* __restrict__ inv) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  fsum2 acc{0.f, 0.f};
+  for (int t = 0; t < count; ++t) acc_add(acc, part[(size_t)t * B + b]);
+  inv[b] = 1.0f / sqrtf(acc.s + acc.c);
+}
+
+// X' (tiled, high and low) from x: rows b = (Re x, -Im x), rows B+b = (Im x, Re x).
+__global__ void k_dense_prep_x(const float2* __restrict__ x, int n, int B, __nv_bfloat16* __restrict__ xt) {
   const size_t total = (size_t)B * n;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t b = i / n, j = i - b * n;
+    const int b = (int)(i / n);
+    const int64_t j = (int64_t)(i - (size_t)b * n);
     const float2 v = x[i];
-    __nv_bfloat16 h0, l0, h1, l1;
-    split_bf16(v.x, h0, l0);
-    split_bf16(v.y, h1, l1);
-    const size_t kb = b * (2 * (size_t)n) + 2 * j, kc = ((size_t)B + b) * (2 * (size_t)n) + 2 * j;
-    hi[kb] = h0;
-    lo[kb] = l0;
-    hi[kb + 1] = __hneg(h1);
-    lo[kb + 1] = __hneg(l1);
-    hi[kc] = h1;
-    lo[kc] = l1;
-    hi[kc + 1] = h0;
-    lo[kc + 1] = l0;
+    store_split(xt, 2 * B, b, 2 * j, v.x);
+    store_split(xt, 2 * B, b, 2 * j + 1, -v.y);
+    store_split(xt, 2 * B, B + b, 2 * j, v.y);
+    store_split(xt, 2 * B, B + b, 2 * j + 1, v.x);
   }
 }
 
-// W' (high and low) from a complex vector w: rows b = Re w, rows B+b = Im w.
-__global__ void k_dense_prep_w(const float2* __restrict__ w, int m, int B, __nv_bfloat16* __restrict__ hi,
-                               __nv_bfloat16* __restrict__ lo) {
+// W' (tiled, high and low) from a complex vector w: rows b = Re w, rows B+b = Im w.
+__global__ void k_dense_prep_w(const float2* __restrict__ w, int m, int B, __nv_bfloat16* __restrict__ wt) {
   const size_t total = (size_t)B * m;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t b = i / m, k = i - b * m;
+    const int b = (int)(i / m);
+    const int64_t k = (int64_t)(i - (size_t)b * m);
     const float2 v = w[i];
-    __nv_bfloat16 h, l;
-    split_bf16(v.x, h, l);
-    hi[i] = h;
-    lo[i] = l;
-    split_bf16(v.y, h, l);
-    hi[((size_t)B + b) * m + k] = h;
-    lo[((size_t)B + b) * m + k] = l;
+    store_split(wt, 2 * B, b, k, v.x);
+    store_split(wt, 2 * B, B + b, k, v.y);
   }
 }
 
@@ -304,50 +384,21 @@ __global__ void k_dense_prep_w(const float2* __restrict__ w, int m, int B, __nv_
 
 namespace {
 
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encoder() {
-  static EncodeTiledFn enc = nullptr;
-  if (!enc) {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      enc = reinterpret_cast<EncodeTiledFn>(f);
-  }
-  return enc;
-}
-
-// BF16 matrix [rows][inner] as TMA boxes of 64 values x box_rows rows, 128-byte swizzle.
-bool encode_bf16(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, int box_rows) {
-  EncodeTiledFn enc = encoder();
-  if (!enc) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
-  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 }  // namespace
 
 struct sr_dense {
   int64_t n = 0, m = 0;
   int device = 0;
-  __nv_bfloat16* d_af = nullptr;  // [m][2n]
-  __nv_bfloat16* d_aa = nullptr;  // [2n][m]
+  __nv_bfloat16* d_af = nullptr;  // Af [m][2n] as tiles [m/128][2n/64][128][64] (swizzled images)
+  __nv_bfloat16* d_aa = nullptr;  // Aa [2n][m] as tiles [2n/128][m/64][128][64]
   int* d_err = nullptr;
   // workspace for B problems
   int B_cap = 0;
-  __nv_bfloat16 *d_xh = nullptr, *d_xl = nullptr;  // [2B][2n]
-  __nv_bfloat16 *d_wh = nullptr, *d_wl = nullptr;  // [2B][m]
+  __nv_bfloat16* d_xt = nullptr;  // X' [2B][2n], tiled high + low (2 * 2B * 2n values)
+  __nv_bfloat16* d_wt = nullptr;  // W' [2B][m], tiled high + low
   float* d_part = nullptr;                          // [m/128][B]
-  float* d_scal = nullptr;                          // [2][B]: sum(y), mu
+  float* d_npart = nullptr;                         // [max(2n/128, 64)][B]: norm partials
+  float* d_scal = nullptr;                          // [3][B]: sum(y), mu, 1/||u||
 };
 
 namespace {
@@ -364,14 +415,13 @@ sr_status dfail(sr_status st, const std::string& msg) {
   } while (0)
 
 void dense_free_ws(sr_dense* d) {
-  cudaFree(d->d_xh);
-  cudaFree(d->d_xl);
-  cudaFree(d->d_wh);
-  cudaFree(d->d_wl);
+  cudaFree(d->d_xt);
+  cudaFree(d->d_wt);
   cudaFree(d->d_part);
+  cudaFree(d->d_npart);
   cudaFree(d->d_scal);
-  d->d_xh = d->d_xl = d->d_wh = d->d_wl = nullptr;
-  d->d_part = d->d_scal = nullptr;
+  d->d_xt = d->d_wt = nullptr;
+  d->d_part = d->d_npart = d->d_scal = nullptr;
   d->B_cap = 0;
 }
 
@@ -380,10 +430,11 @@ sr_status dense_ws(sr_dense* d, int B) {
   dense_free_ws(d);
   const size_t xs = (size_t)2 * B * 2 * d->n, ws = (size_t)2 * B * d->m;
   cudaError_t e;
-  if ((e = cudaMalloc(&d->d_xh, xs * 2)) != cudaSuccess || (e = cudaMalloc(&d->d_xl, xs * 2)) != cudaSuccess ||
-      (e = cudaMalloc(&d->d_wh, ws * 2)) != cudaSuccess || (e = cudaMalloc(&d->d_wl, ws * 2)) != cudaSuccess ||
-      (e = cudaMalloc(&d->d_part, sizeof(float) * (size_t)(d->m / 128) * B)) != cudaSuccess ||
-      (e = cudaMalloc(&d->d_scal, sizeof(float) * 2 * (size_t)B)) != cudaSuccess) {
+  if ((e = cudaMalloc(&d->d_xt, 2 * xs * 2)) != cudaSuccess || (e = cudaMalloc(&d->d_wt, 2 * ws * 2)) != cudaSuccess ||
+      (e = cudaMalloc(&d->d_part, sizeof(float) * (size_t)std::max<int64_t>(d->m / 128, 64) * B)) != cudaSuccess ||
+      (e = cudaMalloc(&d->d_npart, sizeof(float) * (size_t)std::max<int64_t>(2 * d->n / 128, 64) * B)) !=
+          cudaSuccess ||
+      (e = cudaMalloc(&d->d_scal, sizeof(float) * 3 * (size_t)B)) != cudaSuccess) {
     cudaGetLastError();
     dense_free_ws(d);
     return dfail(SR_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -409,11 +460,10 @@ sr_status check_call(sr_dense* d, int B) {
 }
 
 // One GEMM launch: output rows M (multiple of 128), reduction K (multiple of 64).
-sr_status run_gemm(sr_dense* d, sr::GemmArgs& g, const void* a_op, int64_t M, int64_t K, const __nv_bfloat16* bh,
-                   const __nv_bfloat16* bl, int B, cudaStream_t s) {
-  if (!encode_bf16(&g.ta, a_op, K, M, sr::kBM) || !encode_bf16(&g.tbh, bh, K, 2 * B, 2 * B) ||
-      !encode_bf16(&g.tbl, bl, K, 2 * B, 2 * B))
-    return dfail(SR_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+sr_status run_gemm(sr_dense* d, sr::GemmArgs& g, const void* a_op, int64_t M, int64_t K, const __nv_bfloat16* bt,
+                   int B, cudaStream_t s) {
+  g.a_tiles = (const __nv_bfloat16*)a_op;
+  g.b_tiles = bt;
   g.M = (int)M;
   g.K = (int)K;
   g.B = B;
@@ -430,10 +480,20 @@ sr_status run_gemm(sr_dense* d, sr::GemmArgs& g, const void* a_op, int64_t M, in
   return SR_OK;
 }
 
+// Position of element (r, k) of a row-major [rows][K] BF16 matrix in its tiled
+// form: tiles of 128 rows x 64 columns, ordered (r / 128, k / 64), each the
+// exact shared-memory image the MMA reads -- rows of 128 bytes whose 16-byte
+// chunks are permuted by the 128-byte swizzle (chunk c of row r at c ^ (r % 8)).
+size_t tiled_index(int64_t r, int64_t k, int64_t K) {
+  const int64_t tile = (r / sr::kBM) * (K / sr::kBK) + k / sr::kBK;
+  const int64_t rr = r % sr::kBM, kk = k % sr::kBK;
+  const int64_t chunk = (kk / 8) ^ (rr % 8);
+  return (size_t)(tile * sr::kBM * sr::kBK + rr * sr::kBK + chunk * 8 + kk % 8);
+}
+
 sr_status prep_x(sr_dense* d, const float2* x, int B, cudaStream_t s) {
   const size_t total = (size_t)B * d->n;
-  sr::k_dense_prep_x<<<(unsigned)std::min<size_t>(4096, (total + 255) / 256), 256, 0, s>>>(x, (int)d->n, B, d->d_xh,
-                                                                                        d->d_xl);
+  sr::k_dense_prep_x<<<(unsigned)std::min<size_t>(4096, (total + 255) / 256), 256, 0, s>>>(x, (int)d->n, B, d->d_xt);
   sr::count_launch();
   SR_DCUDA(cudaGetLastError(), "launch(dense prep x)");
   return SR_OK;
@@ -459,10 +519,10 @@ sr_status sr_dense_create(int64_t n, int64_t m, const float* a_host, sr_dense** 
     for (int64_t j = 0; j < n; ++j) {
       const __nv_bfloat16 re = __float2bfloat16_rn(a_host[(i * n + j) * 2]);
       const __nv_bfloat16 im = __float2bfloat16_rn(a_host[(i * n + j) * 2 + 1]);
-      af[(size_t)i * 2 * n + 2 * j] = re;
-      af[(size_t)i * 2 * n + 2 * j + 1] = im;
-      aa[(size_t)(2 * j) * m + i] = re;
-      aa[(size_t)(2 * j + 1) * m + i] = im;
+      af[tiled_index(i, 2 * j, 2 * n)] = re;
+      af[tiled_index(i, 2 * j + 1, 2 * n)] = im;
+      aa[tiled_index(2 * j, i, m)] = re;
+      aa[tiled_index(2 * j + 1, i, m)] = im;
     }
   if (e == cudaSuccess) e = cudaMalloc(&d->d_af, cnt * 2);
   if (e == cudaSuccess) e = cudaMalloc(&d->d_aa, cnt * 2);
@@ -500,7 +560,7 @@ sr_status sr_dense_forward(sr_dense* d, const void* x, void* z, int B, void* str
   memset(&g, 0, sizeof(g));
   g.mode = sr::kDenseStoreZ;
   g.z = (float2*)z;
-  return run_gemm(d, g, d->d_af, d->m, 2 * d->n, d->d_xh, d->d_xl, B, s);
+  return run_gemm(d, g, d->d_af, d->m, 2 * d->n, d->d_xt, B, s);
 }
 
 sr_status sr_dense_adjoint(sr_dense* d, const void* w, void* x, int B, void* stream) {
@@ -510,14 +570,14 @@ sr_status sr_dense_adjoint(sr_dense* d, const void* w, void* x, int B, void* str
   cudaStream_t s = (cudaStream_t)stream;
   const size_t total = (size_t)B * d->m;
   sr::k_dense_prep_w<<<(unsigned)std::min<size_t>(4096, (total + 255) / 256), 256, 0, s>>>(
-      (const float2*)w, (int)d->m, B, d->d_wh, d->d_wl);
+      (const float2*)w, (int)d->m, B, d->d_wt);
   sr::count_launch();
   SR_DCUDA(cudaGetLastError(), "launch(dense prep w)");
   sr::GemmArgs g;
   memset(&g, 0, sizeof(g));
   g.mode = sr::kDenseStoreX;
   g.x = (float2*)x;
-  return run_gemm(d, g, d->d_aa, 2 * d->n, d->m, d->d_wh, d->d_wl, B, s);
+  return run_gemm(d, g, d->d_aa, 2 * d->n, d->m, d->d_wt, B, s);
 }
 
 sr_status sr_dense_gd_solve(sr_dense* d, const float* y, void* x, int iters, const sr_gd_opts* opts,
@@ -542,23 +602,79 @@ sr_status sr_dense_gd_solve(sr_dense* d, const float* y, void* x, int iters, con
     memset(&f, 0, sizeof(f));
     f.mode = sr::kDenseGdFwd;
     f.y = y;
-    f.w_hi = d->d_wh;
-    f.w_lo = d->d_wl;
+    f.w_out = d->d_wt;
     f.loss_part = d->d_part;
-    if ((st = run_gemm(d, f, d->d_af, d->m, 2 * d->n, d->d_xh, d->d_xl, B, s)) != SR_OK) return st;
+    if ((st = run_gemm(d, f, d->d_af, d->m, 2 * d->n, d->d_xt, B, s)) != SR_OK) return st;
     sr::GemmArgs g;
     memset(&g, 0, sizeof(g));
     g.mode = sr::kDenseGdAdj;
     g.x = (float2*)x;
     g.mu = d->d_scal + B;
     g.mu_scale = tau0 > 0.f ? (float)(1.0 - std::exp(-(double)(it + 1) / (double)tau0)) : 1.0f;
-    g.xo_hi = d->d_xh;
-    g.xo_lo = d->d_xl;
+    g.xo_out = d->d_xt;
     g.loss_part = d->d_part;
     g.loss_tiles = (int)(d->m / sr::kBM);
     g.loss_out = loss_hist ? loss_hist + (size_t)it * B : nullptr;
-    if ((st = run_gemm(d, g, d->d_aa, 2 * d->n, d->m, d->d_wh, d->d_wl, B, s)) != SR_OK) return st;
+    if ((st = run_gemm(d, g, d->d_aa, 2 * d->n, d->m, d->d_wt, B, s)) != SR_OK) return st;
   }
+  return SR_OK;
+}
+
+sr_status sr_dense_spectral_init(sr_dense* d, const float* y, const void* v0, int iters,
+                                 const sr_spectral_opts* opts, void* x_out, int B, void* stream) {
+  sr_status st = check_call(d, B);
+  if (st != SR_OK) return st;
+  if (!y || !v0 || !x_out) return dfail(SR_ERR_INVALID_ARG, "NULL array argument");
+  if (iters < 0) return dfail(SR_ERR_INVALID_ARG, "iters must be >= 0");
+  sr_spectral_opts o{SR_WEIGHT_IDENTITY, -1.0f};
+  if (opts) o = *opts;
+  if (o.weight_mode != SR_WEIGHT_IDENTITY && o.weight_mode != SR_WEIGHT_OPTIMAL)
+    return dfail(SR_ERR_INVALID_ARG, "unknown weight_mode");
+  if (o.weight_mode == SR_WEIGHT_OPTIMAL && !(o.lambda < 0.f && std::isfinite(o.lambda)))
+    return dfail(SR_ERR_INVALID_ARG, "lambda must be finite and < 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = (int)d->n, m = (int)d->m;
+  float2* u = (float2*)x_out;
+  if (x_out != v0)
+    SR_DCUDA(cudaMemcpyAsync(x_out, v0, (size_t)B * n * sizeof(float2), cudaMemcpyDeviceToDevice, s),
+             "cudaMemcpyAsync(v0)");
+  const int chunks = (int)std::min<int64_t>(64, (m + 4095) / 4096);
+  SR_DCUDA(sr::launch_sum_rows(y, B, m, d->d_part, chunks, s), "launch(sum y)");
+  SR_DCUDA(sr::launch_finish_scalars(d->d_part, chunks, B, 0.f, m, d->d_scal, nullptr, s), "launch(sum y)");
+  // ||v0||^2 as one partial per problem ([B][1] = [1][B])
+  SR_DCUDA(sr::launch_norm_rows(u, B, n, d->d_npart, 1, s), "launch(norm v0)");
+  float* inv = d->d_scal + 2 * B;
+  sr::k_dense_inv_norm<<<(B + 127) / 128, 128, 0, s>>>(d->d_npart, 1, B, inv);
+  sr::count_launch();
+  if ((st = prep_x(d, u, B, s)) != SR_OK) return st;
+  const int adj_tiles = 2 * n / sr::kBM;
+  for (int it = 0; it < iters; ++it) {
+    sr::GemmArgs f;
+    memset(&f, 0, sizeof(f));
+    f.mode = sr::kDenseSpecFwd;
+    f.y = y;
+    f.sumy = d->d_scal;
+    f.inv_norm = inv;
+    f.lam = o.lambda;
+    f.weight_mode = o.weight_mode;
+    f.w_out = d->d_wt;
+    if ((st = run_gemm(d, f, d->d_af, m, 2 * n, d->d_xt, B, s)) != SR_OK) return st;
+    sr::GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.mode = sr::kDenseSpecAdj;
+    g.x = u;
+    g.inv_norm = inv;
+    g.shift = o.weight_mode == SR_WEIGHT_IDENTITY ? 0.f : -2.0f * o.lambda;
+    g.xo_out = d->d_xt;
+    g.norm_part = d->d_npart;
+    if ((st = run_gemm(d, g, d->d_aa, 2 * n, m, d->d_wt, B, s)) != SR_OK) return st;
+    sr::k_dense_inv_norm<<<(B + 127) / 128, 128, 0, s>>>(d->d_npart, adj_tiles, B, inv);
+    sr::count_launch();
+    SR_DCUDA(cudaGetLastError(), "launch(inverse norm)");
+  }
+  // x0 = sqrt(sum y) u / ||u||
+  SR_DCUDA(sr::launch_norm_rows(u, B, n, d->d_npart, 1, s), "launch(norm u)");
+  SR_DCUDA(sr::launch_scale_rows(u, B, n, d->d_npart, 1, d->d_scal, s), "launch(scale)");
   return SR_OK;
 }
 

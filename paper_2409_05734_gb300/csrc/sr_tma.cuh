@@ -66,6 +66,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
   }
 }
 
+// As mbar_wait_bounded, for threads that expect a long wait (the end of a whole
+// main loop): they poll every `sleep_ns` nanoseconds and leave the shared-memory
+// pipe to the barrier traffic of the threads that keep the loop going.
+__device__ __forceinline__ bool mbar_wait_bounded_sleep(uint32_t bar, uint32_t parity, unsigned sleep_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    __nanosleep(sleep_ns);
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
 // 2D tiled TMA load of one box at element coordinates (x, y) into shared
 // memory at `dst`, completing `bytes` transactions on barrier `bar`.
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {

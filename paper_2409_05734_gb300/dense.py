@@ -62,6 +62,19 @@ class DenseModel:
                        "sr_dense_adjoint")
         return x
 
+    def spectral_init(self, y: torch.Tensor, v0: torch.Tensor, iters: int, weight: str = "identity",
+                      lam: float = -1.0, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Power iteration on M = A^H diag(T(y_hat)) A from v0 (Eq. 3-4); returns sqrt(sum y) v."""
+        B = v0.shape[0]
+        mode = {"identity": _lib.SR_WEIGHT_IDENTITY, "optimal": _lib.SR_WEIGHT_OPTIMAL}[weight]
+        opts = _lib.SpectralOpts(mode, float(lam))
+        x = out if out is not None else torch.empty_like(v0)
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_dense_spectral_init(self._h, _p(y.contiguous()), _p(v0.contiguous()), int(iters),
+                                                        C.byref(opts), _p(x), B, _stream_handle()),
+                       "sr_dense_spectral_init")
+        return x
+
     def gd_solve(self, y: torch.Tensor, x: torch.Tensor, iters: int, mu0: float = 0.1, tau0: float = 0.0,
                  record_loss: bool = False):
         B = x.shape[0]

@@ -65,6 +65,24 @@ def test_dense_gradient_descent(DenseModel):
     assert np.max(np.abs(hh - hist) / hist) <= 1e-3
 
 
+@pytest.mark.parametrize("weight", ["identity", "optimal"])
+def test_dense_spectral_init(DenseModel, weight):
+    n, m, B, T = 128, 512, 8, 40
+    A = S.dense_iid_matrix_bf16(9, m, n)
+    model = DenseModel(A)
+    fwd, adj = O.dense_ops(A)
+    xt = S.signal_gaussian(5, B, n)
+    y = np.abs(fwd(xt)) ** 2
+    v0 = S.start_vector(5, B, n)
+    ref = O.spectral_init(y, v0, fwd, adj, T, mode=weight, lam=-1.0)
+    got = model.spectral_init(dev(y, torch.float32), dev(v0), T, weight=weight, lam=-1.0).cpu().numpy()
+    model.check()
+    for b in range(B):
+        assert rel(got[b], ref[b]) <= 1e-4
+    got0 = model.spectral_init(dev(y, torch.float32), dev(v0), 0).cpu().numpy()
+    assert rel(got0, O.spectral_init(y, v0, fwd, adj, 0)) <= 1e-6
+
+
 def test_dense_comparison_size_sampled(DenseModel):
     """The comparison shape: n = 4096, m = 16384, B = 64; sampled output rows."""
     n, m, B = 4096, 16384, 64
