@@ -29,8 +29,13 @@
  *   (cudaMalloc) first; call sr_plan_reserve() beforehand to keep later calls
  *   free of allocation. Concurrent calls on one plan must not overlap in time
  *   (they share the workspace); use one plan per stream.
- * - Supported sizes: m a power of two with 4 <= m <= 2^24, 1 <= n <= m,
- *   1 <= L <= 8, 1 <= B <= 65535. Other sizes return SR_ERR_UNSUPPORTED.
+ * - Supported sizes: m = 2^a with 4 <= m <= 2^24, or m = 3 * 2^a with
+ *   4 <= 2^a <= 2^22 (oversampling ratios such as 1.5, 3 and 6; the DFT of
+ *   length m is then one radix-3 step around three power-of-two DFTs, run
+ *   through an inner plan that holds a second workspace of 2 * B_cap * m c64);
+ *   1 <= n <= m, 1 <= L <= 8, 1 <= B <= 65535 (B <= 21845 when m = 3 * 2^a).
+ *   Other sizes return SR_ERR_UNSUPPORTED. sr_forward_noalloc takes
+ *   power-of-two m only.
  * - Every call returns SR_OK or an error code; sr_last_error() gives a
  *   thread-local message for the last failing call on the calling thread.
  */

@@ -75,10 +75,14 @@ int ilog2(int64_t v) {
   return r;
 }
 
+// m = 3 * 2^k with 2^k >= 4 (the radix-3 lengths)
+bool is_three_pow2(int64_t m) { return m % 3 == 0 && is_pow2(m / 3) && m / 3 >= 4; }
+
 sr_status check_sizes(int64_t n, int64_t m, int L) {
   if (L < 1 || L > 8) return fail(SR_ERR_UNSUPPORTED, "L must be in [1, 8]");
-  if (!is_pow2(m) || m < 4 || m > (int64_t(1) << 24))
-    return fail(SR_ERR_UNSUPPORTED, "m must be a power of two in [4, 2^24]");
+  const bool ok = (is_pow2(m) && m >= 4 && m <= (int64_t(1) << 24)) ||
+                  (is_three_pow2(m) && m / 3 <= (int64_t(1) << 22));
+  if (!ok) return fail(SR_ERR_UNSUPPORTED, "m must be 2^a in [4, 2^24] or 3 * 2^a with 2^a in [4, 2^22]");
   if (n < 1 || n > m) return fail(SR_ERR_UNSUPPORTED, "n must satisfy 1 <= n <= m");
   return SR_OK;
 }
@@ -114,7 +118,9 @@ void free_workspace(Plan* p) {
 }
 
 // Size of one bank of per-tile partial sums per problem.
-int part_stride(const Plan& p) { return std::max(std::max(p.geom[0].cpp, p.geom[1].cpp), 64); }
+int part_stride(const Plan& p) {
+  return std::max(std::max(std::max(p.geom[0].cpp, p.geom[1].cpp), p.r3_chunks), 64);
+}
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -310,7 +316,17 @@ struct PassTimer {
   }
 };
 
+sr_status run_chain_r3(const Plan& p, const Chain& c, int B, cudaStream_t s);
+
+// Number of partial sums per problem the last stage of a chain writes (norm
+// partials of the spectral update).
+int final_partials(const Plan& p, int nfft, int s0) {
+  if (p.inner) return p.r3_chunks;
+  return p.geom[sr::s2_layout((s0 + nfft - 1) % 2)].cpp;
+}
+
 sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
+  if (p.inner) return run_chain_r3(p, c, B, s);
   const sr::PassArgs base = base_args(p);
   float2* cur = p.d_e0;
   float2* nxt = p.d_e1;
@@ -384,6 +400,78 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
   return SR_OK;
 }
 
+// A chain on a plan of length m = 3 mp: every DFT is split (with the operation
+// that precedes it) -> DFT of length mp over 3B sequences on the inner plan ->
+// combine; the last combine applies D_1^H (if asked), prunes to n_out and
+// applies the output mode. Buffers: e0 holds the 3B sequences (the inner chain
+// reads and rewrites it in place), e1 the natural-order vector between DFTs.
+sr_status run_chain_r3(const Plan& p, const Chain& c, int B, cudaStream_t s) {
+  const Plan& in = *p.inner;
+  const float2* src = c.xin;
+  int64_t n_src = c.n_in;
+  for (int k = 0; k < c.nfft; ++k) {
+    sr::R3SplitArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
+    sa.src = src;
+    sa.n_src = n_src;
+    sa.u = p.d_e0;
+    sa.mp = p.mp;
+    sa.chunks = p.r3_chunks;
+    sa.op = k == 0 ? c.first_op : c.mid[k].op;
+    sa.dp = p.d_dp + (size_t)(k == 0 ? c.first_d : c.mid[k].d) * p.m;
+    if (k == 0) {
+      sa.norm_in = c.norm_in;
+      sa.norm_in_count = c.norm_in_count;
+    }
+    sa.y = c.y;
+    sa.sumy = c.sumy;
+    sa.lam = c.lam;
+    sa.weight_mode = c.weight_mode;
+    sa.part_out = c.loss_part;
+    SR_CUDA(sr::launch_r3_split(sa, B, s), "launch(radix-3 split)");
+    Chain ic;
+    ic.nfft = 1;
+    ic.dir[0] = c.dir[k];
+    ic.xin = p.d_e0;
+    ic.n_in = (int)p.mp;
+    ic.xout = p.d_e0;
+    ic.n_out = (int)p.mp;
+    sr_status st = run_chain(in, ic, 3 * B, s);
+    if (st != SR_OK) return st;
+    sr::R3CombineArgs ca;
+    std::memset(&ca, 0, sizeof(ca));
+    ca.U = p.d_e0;
+    ca.mp = p.mp;
+    ca.chunks = p.r3_chunks;
+    ca.tw3 = p.d_tw3;
+    if (k + 1 < c.nfft) {
+      ca.op = sr::kOpNone;
+      ca.xout = p.d_e1;
+      ca.n_out = p.m;
+      ca.out_mode = sr::kOutStore;
+    } else {
+      ca.op = c.last_op;
+      ca.dp = p.d_dp;
+      ca.xout = c.xout;
+      ca.n_out = c.n_out;
+      ca.out_mode = c.out_mode;
+      ca.mu = c.mu;
+      ca.mu_scale = c.mu_scale;
+      ca.shift = c.shift;
+      ca.norm_in = c.norm_in;
+      ca.norm_in_count = c.norm_in_count;
+      ca.part_out = c.spec_part_out;
+      ca.loss_part = c.loss_part;
+      ca.loss_cpp = p.r3_chunks;
+      ca.loss_out = c.loss_out;
+    }
+    SR_CUDA(sr::launch_r3_combine(ca, c.dir[k], B, s), "launch(radix-3 combine)");
+    src = p.d_e1;
+    n_src = p.m;
+  }
+  return SR_OK;
+}
+
 // The 2L DFTs of one gradient or power-iteration step: A (D_1 first), then A^H.
 Chain round_trip_chain(const Plan& p, int epilogue_op) {
   Chain c;
@@ -418,6 +506,10 @@ sr_status check_plan_call(sr_plan* plan, int B) {
   sr_status st = check_device(p);
   if (st != SR_OK) return st;
   if ((double)B * (double)p->m > 4.0e9) return fail(SR_ERR_UNSUPPORTED, "B*m too large");
+  if (p->inner) {
+    if (3 * B > 65535) return fail(SR_ERR_UNSUPPORTED, "B must be <= 21845 when m = 3 * 2^a");
+    if ((st = ensure_workspace(p->inner, 3 * B)) != SR_OK) return st;
+  }
   return ensure_workspace(p, B);
 }
 
@@ -454,24 +546,52 @@ sr_status sr_plan_create(int64_t n, int64_t m, int L, uint64_t seed, sr_plan** o
     delete p;
     return cuda_fail(e, "cudaGetDevice");
   }
-  const int a = ilog2(m);
-  p->m1 = 1 << ((a + 1) / 2);
-  p->m2 = (int)(m / p->m1);
-  p->lmax = p->m1;
-  p->tw_shift = (a + 1) / 2;
-  p->geom[sr::kLayoutX] = sr::make_geom(m, p->m1);
-  p->geom[sr::kLayoutY] = sr::make_geom(m, p->m2);
-  e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
-  for (int lay = 0; lay < 2 && e == cudaSuccess; ++lay)
-    e = sr::pass_occupancy(p->geom[lay], p->per_sm_mid[lay], p->per_sm_last[lay]);
-  if (e != cudaSuccess) {
-    delete p;
-    return cuda_fail(e, "plan geometry");
+  if (is_three_pow2(m)) {
+    // m = 3 mp: the power-of-two DFTs run on an inner plan of length mp
+    p->mp = m / 3;
+    p->r3_chunks = (int)std::min<int64_t>(256, std::max<int64_t>(1, p->mp / 1024));
+    sr_plan* in = nullptr;
+    if ((st = sr_plan_create(p->mp, p->mp, 1, 0, &in)) != SR_OK) {
+      delete p;
+      return st;
+    }
+    p->inner = in;
+    p->num_sms = in->num_sms;
+    std::vector<float2> tw3((size_t)(2 * p->mp));
+    for (int64_t j = 0; j < 2 * p->mp; ++j) tw3[j] = root_of_unity(j, m);
+    if ((st = dalloc(&p->d_tw3, tw3.size())) != SR_OK) {
+      sr_plan_destroy(p);
+      return st;
+    }
+    e = cudaMemcpy(p->d_tw3, tw3.data(), tw3.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      sr_plan_destroy(p);
+      return cuda_fail(e, "cudaMemcpy(radix-3 twiddles)");
+    }
+  } else {
+    const int a = ilog2(m);
+    p->m1 = 1 << ((a + 1) / 2);
+    p->m2 = (int)(m / p->m1);
+    p->lmax = p->m1;
+    p->tw_shift = (a + 1) / 2;
+    p->geom[sr::kLayoutX] = sr::make_geom(m, p->m1);
+    p->geom[sr::kLayoutY] = sr::make_geom(m, p->m2);
+    e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    for (int lay = 0; lay < 2 && e == cudaSuccess; ++lay)
+      e = sr::pass_occupancy(p->geom[lay], p->per_sm_mid[lay], p->per_sm_last[lay]);
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, "plan geometry");
+    }
+    if ((st = upload_twiddles(p)) != SR_OK) {
+      sr_plan_destroy(p);
+      return st;
+    }
   }
   p->theta.resize((size_t)L * m);
   gen_phases(seed, L, m, p->theta.data());
   if ((st = dalloc(&p->d_dp, (size_t)L * m)) != SR_OK || (st = upload_diagonals(p)) != SR_OK ||
-      (st = upload_twiddles(p)) != SR_OK || (st = dalloc(&p->d_err, 1)) != SR_OK) {
+      (st = dalloc(&p->d_err, 1)) != SR_OK) {
     sr_plan_destroy(p);
     return st;
   }
@@ -497,6 +617,8 @@ sr_status sr_plan_destroy(sr_plan* plan) {
   cudaFree(plan->d_twl);
   cudaFree(plan->d_tw_hi);
   cudaFree(plan->d_tw_lo);
+  cudaFree(plan->d_tw3);
+  if (plan->inner) sr_plan_destroy(static_cast<sr_plan*>(plan->inner));
   delete plan;
   return SR_OK;
 }
@@ -636,7 +758,7 @@ sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int it
   const int init_chunks = std::min(64, (n + 4095) / 4096);
   float* bank[2] = {part_bank(p, 0, B), part_bank(p, 1, B)};
   SR_CUDA(sr::launch_norm_rows(v, B, n, bank[1], init_chunks, s), "launch(norm v0)");
-  const int last_cpp = p.geom[sr::s2_layout((2 * p.L - 1) % 2)].cpp;
+  const int last_cpp = final_partials(p, 2 * p.L, 0);
   Chain c = round_trip_chain(p, sr::kOpSpecEpilogue);
   c.xin = v;
   c.n_in = n;
@@ -703,6 +825,7 @@ sr_status sr_plan_check(sr_plan* plan) {
     SR_CUDA(cudaMemset(plan->d_err, 0, sizeof(int)), "cudaMemset(status)");
     return fail((sr_status)code, "a device-side wait of a pass kernel gave up");
   }
+  if (plan->inner) return sr_plan_check(static_cast<sr_plan*>(plan->inner));
   return SR_OK;
 }
 

@@ -98,6 +98,49 @@ struct PassArgs {
   int* err;                // device status word (SR_ERR_TIMEOUT on a failed wait)
 };
 
+// Radix-3 chain step (radix3.cu): split = operation at natural index, then the
+// stride-3 de-interleave u[(3b + r) mp + j] = v[b][3j + r]; combine = twiddles
+// and radix-3 butterfly back to natural order, with the chain's output mode.
+struct R3SplitArgs {
+  const float2* src;       // [B][n_src], entries >= n_src read as zero (U)
+  int64_t n_src;
+  float2* u;               // [3B][mp]
+  int64_t mp;
+  int chunks;              // blocks per problem
+  int op;                  // PassOp
+  const float2* dp;        // diagonal (kOpDiag / kOpDiagConj)
+  const float* norm_in;    // input scale 1/||v|| from partials [B][norm_in_count], or null
+  int norm_in_count;
+  const float* y;          // epilogues
+  const float* sumy;
+  float lam;
+  int weight_mode;
+  float* part_out;         // kOpGdEpilogue: loss partials [B][chunks]
+};
+
+struct R3CombineArgs {
+  const float2* U;         // [3B][mp]
+  int64_t mp;
+  int chunks;
+  const float2* tw3;       // W_m^j (forward sign), j < 2 mp
+  int op;                  // kOpNone or kOpDiagConj (D_1^H)
+  const float2* dp;
+  float2* xout;            // [B][n_out], natural order
+  int64_t n_out;
+  int out_mode;            // OutMode
+  const float* mu;
+  float mu_scale, shift;
+  const float* norm_in;
+  int norm_in_count;
+  float* part_out;         // kOutSpec: norm partials [B][chunks]
+  const float* loss_part;  // loss history: partials [B][loss_cpp]
+  int loss_cpp;
+  float* loss_out;
+};
+
+cudaError_t launch_r3_split(const R3SplitArgs& a, int B, cudaStream_t s);
+cudaError_t launch_r3_combine(const R3CombineArgs& a, int dir, int B, cudaStream_t s);
+
 struct Plan {
   int64_t n = 0, m = 0;
   int L = 0;
@@ -130,6 +173,12 @@ struct Plan {
   float* d_theta_f = nullptr;
   bool host_theta_stale = false;
   CUtensorMap tmap[2][2];  // [buffer e0/e1][layout]: rows of the exchange buffer
+  // m = 3 mp: DFTs of length mp over 3B sequences run on `inner` (a power-of-two
+  // plan, n = m = mp), with the radix-3 split and combine around them
+  Plan* inner = nullptr;
+  int64_t mp = 0;
+  int r3_chunks = 0;             // blocks per problem of the split / combine kernels
+  float2* d_tw3 = nullptr;       // W_m^j, j < 2 mp
   // optional per-pass event timing (sr_plan_set_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev[3];  // pairs (start, end) per pass class

@@ -61,7 +61,9 @@ def test_host_argument_errors(lib):
     assert "L >= 1" in lib.sr_last_error().decode()
     h = C.c_void_p()
     # sizes are validated before any CUDA call
-    assert lib.sr_plan_create(10, 12, 2, 0, C.byref(h)) == 2   # m not a power of two
+    assert lib.sr_plan_create(10, 20, 2, 0, C.byref(h)) == 2   # m neither 2^a nor 3 * 2^a
+    assert lib.sr_plan_create(5, 6, 2, 0, C.byref(h)) == 2     # m = 3 * 2 (radix-3 needs 3 * 2^a, 2^a >= 4)
+    assert lib.sr_plan_create(3, 9, 2, 0, C.byref(h)) == 2     # 3^2 is not supported
     assert lib.sr_plan_create(20, 16, 2, 0, C.byref(h)) == 2   # n > m
     assert lib.sr_plan_create(4, 16, 0, 0, C.byref(h)) == 2    # L < 1
     assert lib.sr_plan_create(4, 16, 9, 0, C.byref(h)) == 2    # L > 8
