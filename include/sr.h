@@ -112,6 +112,14 @@ sr_status sr_plan_info(const sr_plan* plan, int64_t* n, int64_t* m, int* L);
 /* Grows the workspace to hold B problems (synchronous cudaMalloc). */
 sr_status sr_plan_reserve(sr_plan* plan, int B);
 
+/* Autotunes the persistent grid of the middle and last pass kernels for
+ * batches of B problems: times a few GD steps (on scratch data) for every
+ * count of co-resident CTAs per SM from the kernels' occupancy down to 1 and
+ * keeps the fastest for later calls. Synchronises the stream; allocates and
+ * frees scratch (not capturable). The paper has no counterpart (a launch
+ * parameter of this implementation). */
+sr_status sr_plan_autotune(sr_plan* plan, int B, void* stream);
+
 /* ---- operator applications (Sec. III, Eq. 5) --------------------------------
  * sr_forward: z = A x.    x: c64[B][n] (input), z: c64[B][m] (output).
  * sr_adjoint: x = A^H z = U^H D_1^H F^H ... D_L^H F^H z.
@@ -214,6 +222,43 @@ sr_status sr_dense_spectral_init(sr_dense* model, const float* y, const void* v0
                                  const sr_spectral_opts* opts, void* x_out, int B, void* stream);
 /* As sr_plan_check, for the dense model's kernels. */
 sr_status sr_dense_check(sr_dense* model);
+
+/* ---- ragged batches of independent problems -------------------------------
+ * A batch of `count` problems with their own sizes n_i, m_i, L_i and phase
+ * seeds (the paper's recovery experiments solve many independent problems;
+ * Sec. IV). The library buckets problems of equal (n, m, L) into one batched
+ * plan whose diagonal tables hold each problem's own phases theta(seed_i), and
+ * runs the buckets as concurrent branches (one stream each, forked from and
+ * joined back into the caller's stream), so a whole ragged GD step is one
+ * capturable sequence and a CUDA graph of it has one branch per bucket.
+ *
+ * Data layout: the library chooses where each problem lives in the
+ * concatenated buffers: x_cat (c64, problem i at x_off[i], n_i values) and
+ * y_cat (f32 for measurements, or c64 for sr_ragged_forward's output; problem
+ * i at y_off[i], m_i values), both from sr_ragged_layout; problems of a
+ * bucket are adjacent. Sizes as for sr_plan_create; autotune != 0 runs
+ * sr_plan_autotune on every bucket at creation. */
+typedef struct sr_ragged sr_ragged;
+sr_status sr_ragged_create(int count, const int64_t* n, const int64_t* m, const int* L, const uint64_t* seeds,
+                           int autotune, sr_ragged** out);
+sr_status sr_ragged_destroy(sr_ragged* r); /* NULL accepted */
+/* x_off, y_off: int64[count] (either may be NULL); totals in values. */
+sr_status sr_ragged_layout(const sr_ragged* r, int64_t* x_off, int64_t* y_off, int64_t* x_total,
+                           int64_t* y_total, int* buckets);
+/* z_cat (c64, y layout) = A_i x_i for every problem. */
+sr_status sr_ragged_forward(sr_ragged* r, const void* x_cat, void* z_cat, void* stream);
+/* Spectral initialisation of every problem (as sr_spectral_init). */
+sr_status sr_ragged_spectral_init(sr_ragged* r, const float* y_cat, const void* v0_cat, int iters,
+                                  const sr_spectral_opts* opts, void* x_cat, void* stream);
+/* GD on every problem in place (as sr_gd_solve). loss_hist: NULL or
+ * float[iters][count] (problem i in column i), written at the end of the call;
+ * it needs sr_ragged_reserve(r, iters) beforehand (scratch of iters * count
+ * floats), which keeps the call free of allocation. */
+sr_status sr_ragged_reserve(sr_ragged* r, int iters);
+sr_status sr_ragged_gd_solve(sr_ragged* r, const float* y_cat, void* x_cat, int iters, const sr_gd_opts* opts,
+                             float* loss_hist, void* stream);
+/* As sr_plan_check, over every bucket's plan. */
+sr_status sr_ragged_check(sr_ragged* r);
 
 /* ---- device status -----------------------------------------------------------
  * sr_plan_check: waits for the device (cudaDeviceSynchronize) and reports the

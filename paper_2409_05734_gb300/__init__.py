@@ -9,6 +9,7 @@ from .buildlib import build, library_path
 from .plan import Plan, phases
 from .autograd import StructuredRandomOp, structured_random
 from .dense import DenseModel
+from .ragged import Ragged
 
 __all__ = ["Plan", "phases", "build", "library_path", "StructuredRandomOp", "structured_random",
-           "DenseModel"]
+           "DenseModel", "Ragged"]

@@ -58,6 +58,17 @@ SIGNATURES = [
     ("sr_dense_spectral_init", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(SpectralOpts), _VP, C.c_int, _VP]),
     ("sr_dense_check", C.c_int, [_VP]),
     ("sr_plan_check", C.c_int, [_VP]),
+    ("sr_plan_autotune", C.c_int, [_VP, C.c_int, _VP]),
+    ("sr_ragged_create", C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_uint64), C.c_int, C.POINTER(_VP)]),
+    ("sr_ragged_destroy", C.c_int, [_VP]),
+    ("sr_ragged_layout", C.c_int, [_VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    ("sr_ragged_forward", C.c_int, [_VP, _VP, _VP, _VP]),
+    ("sr_ragged_spectral_init", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(SpectralOpts), _VP, _VP]),
+    ("sr_ragged_reserve", C.c_int, [_VP, C.c_int]),
+    ("sr_ragged_gd_solve", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(GdOpts), _VP, _VP]),
+    ("sr_ragged_check", C.c_int, [_VP]),
     ("sr_kernel_launches", C.c_uint64, []),
     ("sr_plan_set_timing", C.c_int, [_VP, C.c_int]),
     ("sr_plan_get_timing", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),

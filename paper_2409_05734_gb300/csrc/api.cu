@@ -284,6 +284,7 @@ sr::PassArgs base_args(const Plan& p) {
   sr::PassArgs a;
   std::memset(&a, 0, sizeof(a));
   a.m = (int)p.m;
+  a.dp_stride = p.dp_stride;
   a.twl = p.d_twl;
   a.tw_hi = p.d_tw_hi;
   a.tw_lo = p.d_tw_lo;
@@ -419,6 +420,7 @@ sr_status run_chain_r3(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     sa.chunks = p.r3_chunks;
     sa.op = k == 0 ? c.first_op : c.mid[k].op;
     sa.dp = p.d_dp + (size_t)(k == 0 ? c.first_d : c.mid[k].d) * p.m;
+    sa.dp_stride = p.dp_stride;
     if (k == 0) {
       sa.norm_in = c.norm_in;
       sa.norm_in_count = c.norm_in_count;
@@ -452,6 +454,7 @@ sr_status run_chain_r3(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     } else {
       ca.op = c.last_op;
       ca.dp = p.d_dp;
+      ca.dp_stride = p.dp_stride;
       ca.xout = c.xout;
       ca.n_out = c.n_out;
       ca.out_mode = c.out_mode;
@@ -506,6 +509,8 @@ sr_status check_plan_call(sr_plan* plan, int B) {
   sr_status st = check_device(p);
   if (st != SR_OK) return st;
   if ((double)B * (double)p->m > 4.0e9) return fail(SR_ERR_UNSUPPORTED, "B*m too large");
+  if (p->batch_fixed && B != p->batch_fixed)
+    return fail(SR_ERR_INVALID_ARG, "this plan holds per-problem phases for a fixed batch size");
   if (p->inner) {
     if (3 * B > 65535) return fail(SR_ERR_UNSUPPORTED, "B must be <= 21845 when m = 3 * 2^a");
     if ((st = ensure_workspace(p->inner, 3 * B)) != SR_OK) return st;
@@ -519,6 +524,38 @@ struct sr_plan : public Plan {};
 
 namespace sr {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+// Gives each of B problems of the plan its own phases theta(seed_b): the
+// diagonal table becomes [B][L][m] (problem stride L * m), filled from the same
+// generator as sr_plan_create. Calls with another batch size are then invalid;
+// used for batches of independent problems of one shape.
+sr_status plan_set_problem_phases(sr_plan* plan, int B, const uint64_t* seeds) {
+  if (!plan || !seeds || B < 1) return fail(SR_ERR_INVALID_ARG, "bad arguments");
+  Plan& p = *plan;
+  const int64_t lm = (int64_t)p.L * p.m;
+  const double scale = 1.0 / std::sqrt((double)p.m);
+  std::vector<double> th((size_t)lm);
+  std::vector<float2> host((size_t)B * lm);
+  for (int b = 0; b < B; ++b) {
+    gen_phases(seeds[b], p.L, p.m, th.data());
+    for (int64_t i = 0; i < lm; ++i)
+      host[(size_t)b * lm + i] = make_float2((float)(std::cos(th[i]) * scale), (float)(std::sin(th[i]) * scale));
+  }
+  float2* d = nullptr;
+  sr_status st = dalloc(&d, host.size());
+  if (st != SR_OK) return st;
+  cudaError_t e = cudaMemcpy(d, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "cudaMemcpy(problem diagonals)");
+  }
+  cudaFree(p.d_dp);
+  p.d_dp = d;
+  p.dp_stride = lm;
+  p.batch_fixed = B;
+  gen_phases(seeds[0], p.L, p.m, p.theta.data());
+  return SR_OK;
+}
 }  // namespace sr
 
 extern "C" {
@@ -674,6 +711,71 @@ sr_status sr_plan_info(const sr_plan* plan, int64_t* n, int64_t* m, int* L) {
 }
 
 sr_status sr_plan_reserve(sr_plan* plan, int B) { return check_plan_call(plan, B); }
+
+sr_status sr_plan_autotune(sr_plan* plan, int B, void* stream) {
+  sr_status st = check_plan_call(plan, B);
+  if (st != SR_OK) return st;
+  Plan& p = plan->inner ? *plan->inner : *plan;
+  const int Bt = plan->inner ? 3 * B : B;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Candidate persistent-grid sizes of the middle and last passes: c CTAs per
+  // SM, capped by each kernel's occupancy. Timed on one GD step chain of the
+  // plan over B problems of scratch data.
+  int occ_mid[2][3], occ_last[2][2];
+  std::memcpy(occ_mid, p.per_sm_mid, sizeof(occ_mid));
+  std::memcpy(occ_last, p.per_sm_last, sizeof(occ_last));
+  int max_occ = 1;
+  for (int l = 0; l < 2; ++l) {
+    for (int k = 0; k < 3; ++k) max_occ = std::max(max_occ, occ_mid[l][k]);
+    for (int k = 0; k < 2; ++k) max_occ = std::max(max_occ, occ_last[l][k]);
+  }
+  float* y = nullptr;
+  float2* x = nullptr;
+  if ((st = dalloc(&y, (size_t)B * plan->m)) != SR_OK) return st;
+  if ((st = dalloc(&x, (size_t)B * plan->n)) != SR_OK) {
+    cudaFree(y);
+    return st;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMemsetAsync(y, 0x3F, sizeof(float) * (size_t)B * plan->m, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x, 0x3F, sizeof(float2) * (size_t)B * plan->n, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best_ms = 0.f;
+  int best_c = max_occ;
+  const sr_gd_opts o{1e-6f, 0.f};
+  for (int c = max_occ; c >= 1 && e == cudaSuccess && st == SR_OK; --c) {
+    for (int l = 0; l < 2; ++l) {
+      for (int k = 0; k < 3; ++k) p.per_sm_mid[l][k] = std::min(c, occ_mid[l][k]);
+      for (int k = 0; k < 2; ++k) p.per_sm_last[l][k] = std::min(c, occ_last[l][k]);
+    }
+    if ((st = sr_gd_solve(plan, y, x, 2, &o, nullptr, B, stream)) != SR_OK) break;
+    e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess && (st = sr_gd_solve(plan, y, x, 5, &o, nullptr, B, stream)) != SR_OK) break;
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && (c == max_occ || ms < best_ms)) {
+      best_ms = ms;
+      best_c = c;
+    }
+  }
+  (void)Bt;
+  for (int l = 0; l < 2; ++l) {
+    for (int k = 0; k < 3; ++k) p.per_sm_mid[l][k] = std::min(best_c, occ_mid[l][k]);
+    for (int k = 0; k < 2; ++k) p.per_sm_last[l][k] = std::min(best_c, occ_last[l][k]);
+  }
+  p.tuned_per_sm = best_c;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(y);
+  cudaFree(x);
+  if (st != SR_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  return SR_OK;
+}
 
 sr_status sr_forward(sr_plan* plan, const void* x, void* z, int B, void* stream) {
   sr_status st = check_plan_call(plan, B);

@@ -96,6 +96,7 @@ sr_status sr_forward_noalloc(const sr_plan* plan_in, const void* x, void* z, int
   sr::PassArgs base;
   memset(&base, 0, sizeof(base));
   base.m = (int)plan->m;
+  base.dp_stride = plan->dp_stride;
   base.twl = plan->d_twl;
   base.tw_hi = plan->d_tw_hi;
   base.tw_lo = plan->d_tw_lo;

@@ -146,7 +146,8 @@ __device__ __forceinline__ void twiddle_store(float2 (&v)[TL::E], const PassArgs
 // Measurements an epilogue needs at (line g, frequency f), natural index
 // f*NL + g, loaded before the pass's first FFT so that their latency overlaps
 // it. (Diagonal entries are read where they are applied: they are shared by
-// all problems and stay in L2.)
+// all problems of a batch -- or, with dp_stride != 0, one table per problem --
+// and stay in L2.)
 template <class TL>
 struct OpData {
   float y[TL::E];
@@ -163,11 +164,13 @@ template <class TL>
 __device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, const OpData<TL>& od, int b, int g,
                                          int p, fsum2& acc) {
   if (a.op == kOpDiag) {
+    const float2* dp = a.dp + (size_t)b * a.dp_stride;
 #pragma unroll
-    for (int j = 0; j < TL::E; ++j) v[j] = cmul(v[j], __ldg(&a.dp[(p + j * TL::P) * a.nl + g]));
+    for (int j = 0; j < TL::E; ++j) v[j] = cmul(v[j], __ldg(&dp[(p + j * TL::P) * a.nl + g]));
   } else if (a.op == kOpDiagConj) {
+    const float2* dp = a.dp + (size_t)b * a.dp_stride;
 #pragma unroll
-    for (int j = 0; j < TL::E; ++j) v[j] = cmulc(v[j], __ldg(&a.dp[(p + j * TL::P) * a.nl + g]));
+    for (int j = 0; j < TL::E; ++j) v[j] = cmulc(v[j], __ldg(&dp[(p + j * TL::P) * a.nl + g]));
   } else if (a.op == kOpGdEpilogue) {
     // z -> r = |z|^2 - y, w = r z (Eq. 2); loss partial sum of r^2
 #pragma unroll
@@ -226,11 +229,13 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     v[j] = nat < a.n_in ? xb[nat] : make_float2(0.f, 0.f);
   }
   if (a.op == kOpDiag) {
+    const float2* dp = a.dp + (size_t)b * a.dp_stride;
 #pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = cmul(v[j], __ldg(&a.dp[(p + j * P) * a.nl + g]));
+    for (int j = 0; j < E; ++j) v[j] = cmul(v[j], __ldg(&dp[(p + j * P) * a.nl + g]));
   } else if (a.op == kOpDiagConj) {
+    const float2* dp = a.dp + (size_t)b * a.dp_stride;
 #pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&a.dp[(p + j * P) * a.nl + g]));
+    for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&dp[(p + j * P) * a.nl + g]));
   }
   __syncthreads();
   const float sc = s_scale;
@@ -407,7 +412,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
       const int nat = (p + j * P) * a.nl + g;
       if (nat >= a.n_out) continue;
       float2 val = v[j];
-      if (a.op == kOpDiagConj) val = cmulc(val, __ldg(&a.dp[nat]));
+      if (a.op == kOpDiagConj) val = cmulc(val, __ldg(&a.dp[(size_t)b * a.dp_stride + nat]));
       if (a.out_mode == kOutStore) {
         xb[nat] = val;
       } else if (a.out_mode == kOutGrad) {

@@ -44,9 +44,9 @@ __global__ void k_r3_split(const R3SplitArgs a) {
       float2 v = k < a.n_src ? src[k] : make_float2(0.f, 0.f);
       v = cscale(v, scale);
       if (a.op == kOpDiag) {
-        v = cmul(v, __ldg(&a.dp[k]));
+        v = cmul(v, __ldg(&a.dp[(size_t)b * a.dp_stride + k]));
       } else if (a.op == kOpDiagConj) {
-        v = cmulc(v, __ldg(&a.dp[k]));
+        v = cmulc(v, __ldg(&a.dp[(size_t)b * a.dp_stride + k]));
       } else if (a.op == kOpGdEpilogue) {
         const float res = cabs2(v) - yb[k];  // r = |z|^2 - y (Eq. 2)
         acc_add(acc, res * res);
@@ -109,7 +109,7 @@ __global__ void k_r3_combine(const R3CombineArgs a) {
       const int64_t nat = k + s * mp;
       if (nat >= a.n_out) continue;
       float2 val = X[s];
-      if (a.op == kOpDiagConj) val = cmulc(val, __ldg(&a.dp[nat]));
+      if (a.op == kOpDiagConj) val = cmulc(val, __ldg(&a.dp[(size_t)b * a.dp_stride + nat]));
       if (a.out_mode == kOutStore) {
         xb[nat] = val;
       } else if (a.out_mode == kOutGrad) {

@@ -79,6 +79,7 @@ struct PassArgs {
   // fused operation
   int op;
   const float2* dp;        // diagonal D_l (natural order, 1/sqrt(m) folded in)
+  int64_t dp_stride;       // complex values between problems' tables (0: one table for the batch)
   const float* y;          // measurements [B][m], natural order
   const float* sumy;       // [B]
   float lam;
@@ -109,6 +110,7 @@ struct R3SplitArgs {
   int chunks;              // blocks per problem
   int op;                  // PassOp
   const float2* dp;        // diagonal (kOpDiag / kOpDiagConj)
+  int64_t dp_stride;       // complex values between problems' tables (0: one table)
   const float* norm_in;    // input scale 1/||v|| from partials [B][norm_in_count], or null
   int norm_in_count;
   const float* y;          // epilogues
@@ -125,6 +127,7 @@ struct R3CombineArgs {
   const float2* tw3;       // W_m^j (forward sign), j < 2 mp
   int op;                  // kOpNone or kOpDiagConj (D_1^H)
   const float2* dp;
+  int64_t dp_stride;
   float2* xout;            // [B][n_out], natural order
   int64_t n_out;
   int out_mode;            // OutMode
@@ -150,7 +153,10 @@ struct Plan {
   int m1 = 0, m2 = 0, lmax = 0;
   int tw_shift = 0;
   std::vector<double> theta;     // host copy, [L][m]
-  float2* d_dp = nullptr;        // diagonals, [L][m], natural order
+  float2* d_dp = nullptr;        // diagonals, [L][m] natural order (per problem: [B][L][m])
+  int64_t dp_stride = 0;         // L * m when every problem of the batch has its own phases
+  int batch_fixed = 0;           // with per-problem phases: the only valid batch size
+  int tuned_per_sm = 0;          // persistent-grid CTAs per SM chosen by sr_plan_autotune (0: occupancy)
   float2* d_twl = nullptr;       // [lmax]
   float2* d_tw_hi = nullptr;
   float2* d_tw_lo = nullptr;
@@ -216,5 +222,8 @@ cudaError_t launch_theta_grad(const float2* q, int nq, const float2* d, const fl
                               cudaStream_t s);
 cudaError_t launch_conj_diag_prune(const float2* h, const float2* d, int m, int n, int B, float2* out,
                                    cudaStream_t s);
+
+// Per-problem phases for a batch of B problems of one shape (api.cu).
+sr_status plan_set_problem_phases(sr_plan* plan, int B, const uint64_t* seeds);
 
 }  // namespace sr

@@ -99,6 +99,11 @@ class Plan:
                        "sr_backward")
         return gx, gth
 
+    def autotune(self, B: int) -> None:
+        """Choose the persistent grid size of the pass kernels for batches of B (timed on the GPU)."""
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_plan_autotune(self._h, int(B), _stream_handle()), "sr_plan_autotune")
+
     def reserve(self, B: int) -> None:
         with torch.cuda.device(self.device):
             _lib.check(self._lib.sr_plan_reserve(self._h, int(B)), "sr_plan_reserve")

@@ -1,0 +1,128 @@
+"""GPU parity of ragged batches (independent problems with their own sizes,
+layer counts and phase seeds) against the FP64 oracle run problem by problem,
+plus graph capture and autotuning, which must not change any result."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sr():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2409_05734_gb300 import buildlib
+    buildlib.build()
+    import paper_2409_05734_gb300 as pkg
+    return pkg
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+# (n, m, L): repeated shapes share a bucket; power-of-two and radix-3 lengths
+SHAPES = [(64, 256, 2), (64, 256, 2), (64, 256, 2), (100, 512, 1), (100, 512, 1), (30, 96, 3),
+          (1024, 4096, 2), (1024, 4096, 2), (500, 1536, 2), (16, 64, 1), (3000, 16384, 3)]
+BASE = 20240905
+
+
+def make(sr, shapes=SHAPES, autotune=False):
+    n = [s[0] for s in shapes]
+    m = [s[1] for s in shapes]
+    L = [s[2] for s in shapes]
+    seeds = [BASE + 1000 * i for i in range(len(shapes))]
+    return sr.Ragged(n, m, L, seeds, autotune=autotune), seeds
+
+
+def test_ragged_layout_groups_buckets(sr):
+    r, _ = make(sr)
+    assert r.buckets == len(set(SHAPES))
+    # every problem has its own disjoint slice
+    spans = sorted((r.x_off[i], r.x_off[i] + r.n[i]) for i in range(r.count))
+    assert spans[0][0] == 0 and all(a[1] == b[0] for a, b in zip(spans, spans[1:])) and spans[-1][1] == r.x_total
+    spans = sorted((r.y_off[i], r.y_off[i] + r.m[i]) for i in range(r.count))
+    assert all(a[1] == b[0] for a, b in zip(spans, spans[1:])) and spans[-1][1] == r.y_total
+
+
+def test_ragged_forward_each_problem(sr):
+    r, seeds = make(sr)
+    xs = [S.signal_gaussian(s, 1, n)[0] for s, (n, _, _) in zip(seeds, SHAPES)]
+    z = r.forward(torch.from_numpy(r.pack(xs, "x")).to(torch.complex64).cuda()).cpu().numpy()
+    r.check()
+    for i, (n, m, L) in enumerate(SHAPES):
+        zo = O.forward(xs[i], S.phases(seeds[i], L, m), m)
+        zi = z[r.y_off[i]:r.y_off[i] + m]
+        assert rel(zi, zo) <= 1e-5, i
+        assert np.max(np.abs(zi - zo)) <= 2e-5 * np.sqrt(np.mean(np.abs(zo) ** 2)), i
+
+
+def _problem_data(r, seeds):
+    xt, ys, v0 = [], [], []
+    for i, (n, m, L) in enumerate(SHAPES):
+        x = S.signal_gaussian(seeds[i], 1, n)[0]
+        xt.append(x)
+        ys.append(np.abs(O.forward(x, S.phases(seeds[i], L, m), m)) ** 2)
+        v0.append(S.start_vector(seeds[i], 1, n)[0])
+    return xt, ys, v0
+
+
+def test_ragged_solver_each_problem(sr):
+    r, seeds = make(sr)
+    xt, ys, v0 = _problem_data(r, seeds)
+    y_cat = torch.from_numpy(r.pack(ys, "y")).float().cuda()
+    v0_cat = torch.from_numpy(r.pack(v0, "x")).to(torch.complex64).cuda()
+    x = r.spectral_init(y_cat, v0_cat, 20, weight="optimal")
+    x0 = x.clone().cpu().numpy()
+    _, hist = r.gd_solve(y_cat, x, 40, mu0=0.1, tau0=10.0, record_loss=True)
+    r.check()
+    xg = x.cpu().numpy()
+    h = hist.cpu().numpy().astype(np.float64)
+    for i, (n, m, L) in enumerate(SHAPES):
+        fwd, adj = O.structured_ops(S.phases(seeds[i], L, m), n, m)
+        x0o = O.spectral_init(ys[i][None], v0[i][None], fwd, adj, 20, mode="optimal")
+        assert rel(x0[r.x_off[i]:r.x_off[i] + n], x0o[0]) <= 1e-4, i
+        xTo, ho = O.gradient_descent(x0o, ys[i][None], fwd, adj, 40, mu0=0.1, tau0=10.0)
+        assert rel(xg[r.x_off[i]:r.x_off[i] + n], xTo[0]) <= 1e-3, i
+        assert np.max(np.abs(h[:, i] - ho[:, 0]) / ho[:, 0]) <= 1e-3, i
+
+
+def test_ragged_graph_capture_and_autotune_change_nothing(sr):
+    r, seeds = make(sr)
+    ra, _ = make(sr, autotune=True)
+    xt, ys, v0 = _problem_data(r, seeds)
+    y_cat = torch.from_numpy(r.pack(ys, "y")).float().cuda()
+    x_init = torch.from_numpy(r.pack(v0, "x")).to(torch.complex64).cuda()
+    x_eager = x_init.clone()
+    r.gd_solve(y_cat, x_eager, 10, mu0=0.05)
+    x_tuned = x_init.clone()
+    ra.gd_solve(y_cat, x_tuned, 10, mu0=0.05)
+    # one GD run captured as a CUDA graph (the buckets become parallel branches)
+    x_graph = x_init.clone()
+    r.gd_solve(y_cat, x_graph.clone(), 1, mu0=0.05)  # warm-up outside capture
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        r.gd_solve(y_cat, x_graph, 10, mu0=0.05)
+    g.replay()
+    torch.cuda.synchronize()
+    r.check()
+    ra.check()
+    assert torch.equal(x_eager, x_graph)
+    assert torch.equal(x_eager, x_tuned)
+
+
+def test_ragged_rejects_bad_arguments(sr):
+    with pytest.raises(Exception):
+        sr.Ragged([10], [20], [2], [1])  # m neither 2^a nor 3 * 2^a
+    with pytest.raises(Exception):
+        sr.Ragged([10, 5], [64], [2], [1])
+    r, _ = make(sr, shapes=[(8, 32, 1)])
+    y = torch.zeros(r.y_total, device="cuda")
+    x = torch.zeros(r.x_total, dtype=torch.complex64, device="cuda")
+    hist = torch.empty((5, 1), device="cuda")
+    with pytest.raises(Exception):
+        r.gd_solve(y, x, 5, loss_hist=hist)  # loss history without reserve
