@@ -39,6 +39,12 @@ WORKLOAD = dict(name="structured-L2-n16384-m65536-B64-sp100-gd500", n=2 ** 14, m
                 spectral_iters=100, gd_iters=500, weight="optimal", lam=-1.0, mu0=0.15, tau0=100.0,
                 seed=20240905)
 FLUSH_BYTES = 512 << 20  # > 129 MB L2: written between timed steps
+# Ragged batch: 256 independent problems, n = 2^k (k uniform in 10..16), alpha
+# in {2, 4, 8}, L in {1, 2, 3}, own phase seeds, Poisson measurements at a mean
+# of 100 photons per measurement; one autotuned ragged handle, the solve
+# replayed as a CUDA graph with one branch per shape bucket.
+RAGGED = dict(count=256, k_lo=10, k_hi=16, alphas=(2, 4, 8), Ls=(1, 2, 3), photons=100.0, spectral_iters=50,
+              gd_iters=200, mu0=0.1, tau0=50.0, seed=20240905)
 # Structured (L = 2) against dense i.i.d. at equal recovery error (Sec. IV): both
 # models solve the same B signals from their own noiseless y with the same
 # spectral initialisation and step rule; each runs the fewest GD iterations (a
@@ -58,7 +64,23 @@ def parse_args():
     ap.add_argument("--no-dense", action="store_true", help="skip the dense i.i.d. comparison")
     ap.add_argument("--no-graph", action="store_true", help="launch directly instead of replaying a CUDA graph")
     ap.add_argument("--no-library", action="store_true", help="skip the cuFFT pipeline comparison")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch workload")
     return ap.parse_args()
+
+
+def max_over_ranks_of(torch, v: float, world: int, device) -> float:
+    """The largest of every rank's v (the job's time is its slowest rank's)."""
+    if world == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_throughput(world: int, B: int, iters: int, ms_step: float) -> float:
+    """Problem-iterations per second of all ranks: each rank solves its own batch
+    of B problems (weak scaling), the step time is the maximum over ranks."""
+    return world * B * iters / (ms_step / 1e3)
 
 
 def dist_env():
@@ -392,6 +414,85 @@ def cufft_pipeline(torch, plan, W, y, x_true, fused_ms_per_iter, iters=20):
             "speedup_of_fused": t / fused_ms_per_iter}
 
 
+def ragged_workload(torch, dev, flush, reps: int = 3):
+    """The ragged batch of RAGGED: problem-iterations per second of the whole
+    graph-captured solve, its algorithmic HBM bytes per second, and accuracy."""
+    from paper_2409_05734_gb300 import Ragged, _lib
+    import synthetic as S
+    R = RAGGED
+    rng = np.random.default_rng(R["seed"])
+    count = R["count"]
+    n = (2 ** rng.integers(R["k_lo"], R["k_hi"] + 1, count)).astype(np.int64)
+    alpha = rng.choice(R["alphas"], count)
+    m = (n * alpha).astype(np.int64)
+    L = rng.choice(R["Ls"], count).astype(np.int32)
+    seeds = R["seed"] + 1000 * np.arange(count, dtype=np.uint64)
+    rg = Ragged(n, m, L, seeds, autotune=True)
+    x_true = torch.from_numpy(rg.pack([S.signal_gaussian(int(seeds[i]), 1, int(n[i]))[0] for i in range(count)],
+                                      "x")).to(torch.complex64).to(dev)
+    v0 = torch.from_numpy(rg.pack([S.start_vector(int(seeds[i]), 1, int(n[i]))[0] for i in range(count)],
+                                  "x")).to(torch.complex64).to(dev)
+    inten = rg.forward(x_true).abs() ** 2
+    # Poisson counts at a mean of `photons` per measurement: gamma_i = photons m_i / sum|A x_i|^2
+    gamma = torch.empty_like(inten)
+    for i in range(count):
+        sl = slice(int(rg.y_off[i]), int(rg.y_off[i] + m[i]))
+        gamma[sl] = R["photons"] * float(m[i]) / float(inten[sl].sum())
+    g = torch.Generator(device=dev).manual_seed(R["seed"])
+    y = (torch.poisson(gamma * inten, generator=g) / gamma).contiguous()
+    x = torch.empty_like(v0)
+
+    def solve():
+        rg.spectral_init(y, v0, R["spectral_iters"], weight="optimal", out=x)
+        rg.gd_solve(y, x, R["gd_iters"], mu0=R["mu0"], tau0=R["tau0"])
+
+    solve()
+    torch.cuda.synchronize()
+    lib = _lib.load()
+    graph = torch.cuda.CUDAGraph()
+    l0 = lib.sr_kernel_launches()
+    with torch.cuda.graph(graph):
+        solve()
+    launches = lib.sr_kernel_launches() - l0
+    graph.replay()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    rg.check()
+    ms = statistics.median(times)
+    iters = R["spectral_iters"] + R["gd_iters"]
+    nbytes = sum(iteration_bytes(dict(n=int(n[i]), m=int(m[i]), L=int(L[i]), B=1)) for i in range(count))
+    errs = []
+    xh, xt = x.cpu().numpy(), x_true.cpu().numpy()
+    for i in range(count):
+        a, b = xh[rg.x_off[i]:rg.x_off[i] + n[i]], xt[rg.x_off[i]:rg.x_off[i] + n[i]]
+        inner = np.vdot(a, b)
+        ph = inner / abs(inner) if abs(inner) > 0 else 1.0
+        errs.append(np.linalg.norm(ph * a - b) / np.linalg.norm(b))
+    errs = np.array(errs)
+    fin = np.isfinite(errs)
+    by_alpha = {int(a): float(np.median(errs[(alpha == a) & fin])) if np.any((alpha == a) & fin) else None
+                for a in R["alphas"]}
+    by_L = {int(l): {"median_rel_err": float(np.median(errs[(L == l) & fin])) if np.any((L == l) & fin) else None,
+                     "diverged": int(np.sum((L == l) & ~fin)), "problems": int(np.sum(L == l))} for l in R["Ls"]}
+    return {"workload": f"{count} problems: n = 2^k, k ~ U{{{R['k_lo']}..{R['k_hi']}}}, alpha ~ U{list(R['alphas'])}, "
+                        f"L ~ U{list(R['Ls'])}, own phases; Poisson y at {R['photons']:.0f} photons/measurement; "
+                        f"{R['spectral_iters']} power + {R['gd_iters']} GD iterations; autotuned; CUDA graph",
+            "buckets": rg.buckets, "total_m": int(m.sum()), "ms_per_solve": ms,
+            "problem_iters_per_s": count * iters / (ms / 1e3),
+            "algorithmic_gbs": nbytes * iters / (ms / 1e3) / 1e9, "gpu_launches_per_solve": int(launches),
+            "median_rel_err_global_phase": float(np.median(errs[fin])) if np.any(fin) else None,
+            "median_rel_err_by_alpha": by_alpha, "by_L": by_L, "diverged": int(np.sum(~fin)),
+            "frac_rel_err_below_0.1": float(np.mean(errs[fin] < 1e-1)) if np.any(fin) else 0.0}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -428,11 +529,7 @@ def run_ours(args):
             torch.distributed.barrier()
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(torch, v, world, dev)
 
     # One step (the whole solve) is captured once as a CUDA graph and replayed:
     # the library makes no allocation and no host synchronisation inside a solve
@@ -477,7 +574,7 @@ def run_ours(args):
     ms_local = sum(a.elapsed_time(b) for a, b in evs) / args.steps
     ms_step = max_over_ranks(ms_local)
     iters = W["spectral_iters"] + W["gd_iters"]
-    value = world * B * iters / (ms_step / 1e3)
+    value = whole_job_throughput(world, B, iters, ms_step)
 
     # accuracy of the solve (relative error up to a global phase, cosine similarity)
     inner = torch.sum(torch.conj(x) * x_true, dim=1, keepdim=True)
@@ -547,6 +644,8 @@ def run_ours(args):
         line["library_comparison"] = cufft_pipeline(torch, plan, W, y, x_true, ms_step / iters)
     if rank == 0 and not args.no_dense:
         line["dense_iid_comparison"] = dense_comparison(torch, dev, flush)
+    if rank == 0 and not args.no_ragged:
+        line["ragged_batch"] = ragged_workload(torch, dev, flush)
     if rank == 0 and not args.no_cpu_baseline:
         sp, gd = 20, 200
         v, dt = oracle_sample(W, sp, gd, W["seed"])

@@ -268,6 +268,14 @@ sr_status sr_ragged_check(sr_ragged* r);
  * recorded status. */
 sr_status sr_plan_check(sr_plan* plan);
 
+/* Exercises the failure path (the paper has no counterpart): launches one
+ * kernel that waits, through the pass kernels' bounded wait, on an mbarrier
+ * that nothing completes. The wait gives up after the library's limit (100 ms
+ * of GPU time), records SR_ERR_TIMEOUT in the plan's status and returns, so
+ * the next sr_plan_check reports SR_ERR_TIMEOUT (and clears it) while the CUDA
+ * context stays usable. */
+sr_status sr_plan_selftest_timeout(sr_plan* plan, void* stream);
+
 /* ---- profiling ------------------------------------------------------------
  * sr_kernel_launches: number of CUDA kernels this library has launched in the
  * process so far (all plans, all devices).

@@ -931,6 +931,14 @@ sr_status sr_plan_check(sr_plan* plan) {
   return SR_OK;
 }
 
+sr_status sr_plan_selftest_timeout(sr_plan* plan, void* stream) {
+  if (!plan) return fail(SR_ERR_INVALID_ARG, "plan is NULL");
+  sr_status st = check_device(plan);
+  if (st != SR_OK) return st;
+  SR_CUDA(sr::launch_wait_probe(plan->d_err, (cudaStream_t)stream), "launch(wait probe)");
+  return SR_OK;
+}
+
 uint64_t sr_kernel_launches(void) {
   return sr::launches_so_far();
 }

@@ -100,6 +100,24 @@ __global__ void k_conj_diag_prune(const float2* __restrict__ h, const float2* __
   }
 }
 
+// Failure-path probe: one thread waits on an mbarrier that nothing ever
+// completes, through the same bounded wait the pass kernels use; when the wait
+// gives up it records SR_ERR_TIMEOUT in the plan's status word and returns.
+// No copy is in flight, so the kernel ends cleanly.
+__global__ void k_wait_probe(int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(smem_addr(&bar), 1);
+  mbar_init_fence();
+  if (!mbar_wait_bounded(smem_addr(&bar), 0)) atomicExch(err, (int)SR_ERR_TIMEOUT);
+}
+
+cudaError_t launch_wait_probe(int* err, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(err);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launchers
 
 constexpr size_t kSmemBudget = 220 * 1024;

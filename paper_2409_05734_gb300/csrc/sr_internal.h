@@ -223,6 +223,9 @@ cudaError_t launch_theta_grad(const float2* q, int nq, const float2* d, const fl
 cudaError_t launch_conj_diag_prune(const float2* h, const float2* d, int m, int n, int B, float2* out,
                                    cudaStream_t s);
 
+// Kernel whose bounded wait never completes and records SR_ERR_TIMEOUT in *err.
+cudaError_t launch_wait_probe(int* err, cudaStream_t s);
+
 // Per-problem phases for a batch of B problems of one shape (api.cu).
 sr_status plan_set_problem_phases(sr_plan* plan, int B, const uint64_t* seeds);
 

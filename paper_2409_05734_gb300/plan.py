@@ -99,6 +99,11 @@ class Plan:
                        "sr_backward")
         return gx, gth
 
+    def selftest_timeout(self) -> None:
+        """Launch the failure-path probe: the next check() raises SR_ERR_TIMEOUT."""
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_plan_selftest_timeout(self._h, _stream_handle()), "sr_plan_selftest_timeout")
+
     def autotune(self, B: int) -> None:
         """Choose the persistent grid size of the pass kernels for batches of B (timed on the GPU)."""
         with torch.cuda.device(self.device):
