@@ -4,7 +4,7 @@ Test infrastructure only (see the package docstring).
 
 A = F D_L ... F D_1 U (Sec. III, Eq. 5) with D_l = diag(exp(i theta_l)); the
 phases theta_l are the real parameters of the model (Sec. III) and are
-differentiated here as in the differentiable-operator form of the build.
+differentiated here as the differentiable operator (autograd) of the library does.
 
 Gradient convention (the one of PyTorch for complex tensors): for a real loss
 L, the gradient of a complex variable w is G_w = dL/dRe(w) + i dL/dIm(w)
