@@ -278,6 +278,11 @@ struct Chain {
   float lam = 0.f;
   int weight_mode = SR_WEIGHT_IDENTITY;
   float* loss_part = nullptr;
+  // GD loop fusion (power-of-two plans): the exchange buffer e0 already holds
+  // the FIRST output of this step (written by the previous step's fused last
+  // pass), and/or the last pass also runs the next step's FIRST into e0.
+  bool skip_first = false;
+  bool fuse_next_first = false;
 };
 
 sr::PassArgs base_args(const Plan& p) {
@@ -334,7 +339,7 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
   int cur_idx = 0;  // which exchange buffer `cur` is (selects its tensor maps)
   int loss_cpp = 0;
   // FIRST
-  {
+  if (!c.skip_first) {
     sr::PassArgs a = base;
     a.out_dir = c.dir[0];
     a.xin = c.xin;
@@ -396,7 +401,12 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     a.loss_cpp = loss_cpp;
     a.loss_out = c.loss_out;
     PassTimer tm(p, 2, s);
-    SR_CUDA(sr::launch_last(p, lay, a, B, s), "launch(last pass)");
+    if (c.fuse_next_first) {
+      a.eout = p.d_e0;  // the next step's FIRST output (cur is e1 here: 2L - 1 middle passes)
+      SR_CUDA(sr::launch_last_first(p, lay, a, B, s), "launch(fused last/first pass)");
+    } else {
+      SR_CUDA(sr::launch_last(p, lay, a, B, s), "launch(last pass)");
+    }
   }
   return SR_OK;
 }
@@ -615,7 +625,7 @@ sr_status sr_plan_create(int64_t n, int64_t m, int L, uint64_t seed, sr_plan** o
     p->geom[sr::kLayoutY] = sr::make_geom(m, p->m2);
     e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     for (int lay = 0; lay < 2 && e == cudaSuccess; ++lay)
-      e = sr::pass_occupancy(p->geom[lay], p->per_sm_mid[lay], p->per_sm_last[lay]);
+      e = sr::pass_occupancy(p->geom[lay], p->per_sm_mid[lay], p->per_sm_last[lay], &p->per_sm_lf[lay]);
     if (e != cudaSuccess) {
       delete p;
       return cuda_fail(e, "plan geometry");
@@ -721,13 +731,15 @@ sr_status sr_plan_autotune(sr_plan* plan, int B, void* stream) {
   // Candidate persistent-grid sizes of the middle and last passes: c CTAs per
   // SM, capped by each kernel's occupancy. Timed on one GD step chain of the
   // plan over B problems of scratch data.
-  int occ_mid[2][3], occ_last[2][2];
+  int occ_mid[2][3], occ_last[2][2], occ_lf[2];
   std::memcpy(occ_mid, p.per_sm_mid, sizeof(occ_mid));
   std::memcpy(occ_last, p.per_sm_last, sizeof(occ_last));
+  std::memcpy(occ_lf, p.per_sm_lf, sizeof(occ_lf));
   int max_occ = 1;
   for (int l = 0; l < 2; ++l) {
     for (int k = 0; k < 3; ++k) max_occ = std::max(max_occ, occ_mid[l][k]);
     for (int k = 0; k < 2; ++k) max_occ = std::max(max_occ, occ_last[l][k]);
+    max_occ = std::max(max_occ, occ_lf[l]);
   }
   float* y = nullptr;
   float2* x = nullptr;
@@ -748,6 +760,7 @@ sr_status sr_plan_autotune(sr_plan* plan, int B, void* stream) {
     for (int l = 0; l < 2; ++l) {
       for (int k = 0; k < 3; ++k) p.per_sm_mid[l][k] = std::min(c, occ_mid[l][k]);
       for (int k = 0; k < 2; ++k) p.per_sm_last[l][k] = std::min(c, occ_last[l][k]);
+      p.per_sm_lf[l] = std::min(c, occ_lf[l]);
     }
     if ((st = sr_gd_solve(plan, y, x, 2, &o, nullptr, B, stream)) != SR_OK) break;
     e = cudaEventRecord(e0, s);
@@ -765,6 +778,7 @@ sr_status sr_plan_autotune(sr_plan* plan, int B, void* stream) {
   for (int l = 0; l < 2; ++l) {
     for (int k = 0; k < 3; ++k) p.per_sm_mid[l][k] = std::min(best_c, occ_mid[l][k]);
     for (int k = 0; k < 2; ++k) p.per_sm_last[l][k] = std::min(best_c, occ_last[l][k]);
+    p.per_sm_lf[l] = std::min(best_c, occ_lf[l]);
   }
   p.tuned_per_sm = best_c;
   if (e0) cudaEventDestroy(e0);
@@ -908,9 +922,14 @@ sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters, const s
   c.mu = p.d_scal + B;
   c.y = y;
   c.loss_part = part_bank(p, 2, B);
+  // Consecutive steps share a kernel: the last pass of step t also runs the
+  // first pass of step t+1 (same lines, x_{t+1} still in registers).
+  const bool fuse = !p.inner && (2 * p.L - 1) % 2 == 1;
   for (int it = 0; it < iters; ++it) {
     c.loss_out = loss_hist ? loss_hist + (size_t)it * B : nullptr;
     c.mu_scale = tau0 > 0.f ? (float)(1.0 - std::exp(-(double)(it + 1) / (double)tau0)) : 1.0f;
+    c.skip_first = fuse && it > 0;
+    c.fuse_next_first = fuse && it + 1 < iters;
     if ((st = run_chain(p, c, B, s)) != SR_OK) return st;
   }
   return SR_OK;

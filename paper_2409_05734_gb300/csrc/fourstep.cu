@@ -204,15 +204,30 @@ cudaError_t launch_last(const Plan& p, Layout lay, const PassArgs& a, int B, cud
   return launch_pipe(true, p, lay, a, B, s);
 }
 
-cudaError_t pass_occupancy(const LineGeom& g, int* per_sm_mid, int* per_sm_last) {
-  // per_sm_mid[3]: direction pairs (-,-), (-,+), (+,+); per_sm_last[2]: (-), (+)
+cudaError_t launch_last_first(const Plan& p, Layout lay, const PassArgs& a0, int B, cudaStream_t s) {
+  const LineGeom& g = p.geom[lay];
+  auto fn = reinterpret_cast<void (*)(PassArgs, int)>(const_cast<void*>(pick_last_first(g.ell, g.T)));
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = allow_smem((const void*)fn, g.smem_pipe);
+  if (e != cudaSuccess) return e;
+  const PassArgs a = with_geom(a0, p, g, B);
+  const int grid = std::max(1, std::min(a.ntiles, p.per_sm_lf[lay] * p.num_sms));
+  fn<<<grid, g.threads, g.smem_pipe, s>>>(a, g.nbuf);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t pass_occupancy(const LineGeom& g, int* per_sm_mid, int* per_sm_last, int* per_sm_lf) {
+  // per_sm_mid[3]: direction pairs (-,-), (-,+), (+,+); per_sm_last[2]: (-), (+); per_sm_lf: fused
   const int pairs[3][2] = {{-1, -1}, {-1, 1}, {1, 1}};
-  for (int k = 0; k < 5; ++k) {
-    const void* fn = k < 3 ? pick_mid(g.ell, g.T, pairs[k][0], pairs[k][1]) : pick_last(g.ell, g.T, k == 3 ? -1 : 1);
+  for (int k = 0; k < 6; ++k) {
+    const void* fn = k < 3   ? pick_mid(g.ell, g.T, pairs[k][0], pairs[k][1])
+                     : k < 5 ? pick_last(g.ell, g.T, k == 3 ? -1 : 1)
+                             : pick_last_first(g.ell, g.T);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem(fn, g.smem_pipe);
     if (e != cudaSuccess) return e;
-    int* out = k < 3 ? &per_sm_mid[k] : &per_sm_last[k - 3];
+    int* out = k < 3 ? &per_sm_mid[k] : k < 5 ? &per_sm_last[k - 3] : per_sm_lf;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, g.threads, g.smem_pipe);
     if (e != cudaSuccess) return e;
     *out = std::max(1, *out);

@@ -1,0 +1,15 @@
+// Instantiations of the fused LAST + FIRST kernel of the GD loop for every
+// tile shape (see passes.cuh).
+#include "passes.cuh"
+
+namespace sr {
+
+const void* pick_last_first(int ell, int T) {
+#define SR_PICK_LF(E_, T_) \
+  if (ell == E_ && T == T_) return reinterpret_cast<const void*>(&k_last_first<E_, T_>);
+  SR_TILE_SHAPES(SR_PICK_LF)
+#undef SR_PICK_LF
+  return nullptr;
+}
+
+}  // namespace sr

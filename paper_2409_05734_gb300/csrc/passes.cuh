@@ -439,6 +439,64 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 }
 
 
+// LAST of one GD step fused with FIRST of the next. Both work on the lines of
+// layout X: step 2 of the final inverse DFT, D_1^H, the update
+// x <- x - mu_t 2 (.) on the kept entries (U^H), and then, still in registers,
+// U (zeros beyond n), D_1 and step 1 of the next step's first forward DFT, with
+// the four-step twiddles, into the exchange buffer `eout`. Each D_1 entry is
+// loaded once for both uses.
+template <int ELL, int T>
+__global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
+    k_last_first(const __grid_constant__ PassArgs a, int nbuf) {
+  using TL = Tile<ELL, T>;
+  constexpr int E = TL::E, P = TL::P;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ float s_mu;
+  unsigned char* smem = aligned_smem(smem_raw);
+  const PipeSmem L = pipe_layout(ELL, T, nbuf, true);
+  float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
+  float2* tw = reinterpret_cast<float2*>(smem + L.tw);
+  float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
+  const int tid = threadIdx.x;
+  int t, p;
+  thread_coords<TL>(t, p);
+  load_line_twiddles<ELL>(a, tw);
+  __syncthreads();
+  pipe_tiles<ELL, T>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
+    const int g = g0 + t;
+    if (tid == 0) s_mu = a.mu[b];
+    RowTw<TL> rw;
+    rw.load(a, g0, -1);
+    const float2 A = tw_m(a, g * p, -1);
+    line_fft<ELL, T, 1>(v, scratch, p, t, tw);
+    __syncthreads();  // tile scalar visible
+    const float mu2 = 2.0f * s_mu * a.mu_scale;
+    float2* xb = a.xout + (size_t)b * a.n_out;
+    const float2* dp = a.dp + (size_t)b * a.dp_stride;
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int nat = (p + j * P) * a.nl + g;
+      if (nat < a.n_out) {
+        const float2 d = __ldg(&dp[nat]);
+        const float2 gr = cmulc(v[j], d);
+        float2 x = xb[nat];
+        x.x = fmaf(-mu2, gr.x, x.x);
+        x.y = fmaf(-mu2, gr.y, x.y);
+        xb[nat] = x;
+        v[j] = cmul(x, d);
+      } else {
+        v[j] = make_float2(0.f, 0.f);
+      }
+    }
+    if (a.loss_out && g0 == 0 && tid == 0)
+      a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
+    rw.store(rowtw);
+    __syncthreads();  // the first FFT's scratch reads done; row twiddles visible
+    line_fft<ELL, T, -1>(v, scratch, p, t, tw);
+    twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+  });
+}
+
 // Every (line length, lines per CTA) pair make_geom produces for m = 4 .. 2^24.
 #define SR_TILE_SHAPES(X)                                                                                      \
   X(2, 2) X(2, 4) X(4, 2) X(4, 4) X(4, 8) X(8, 4) X(8, 8) X(8, 16) X(16, 8) X(16, 16) X(16, 32) X(32, 16)    \
@@ -449,5 +507,6 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 const void* pick_first(int ell, int T, int db);
 const void* pick_mid(int ell, int T, int da, int db);
 const void* pick_last(int ell, int T, int da);
+const void* pick_last_first(int ell, int T);
 
 }  // namespace sr
