@@ -283,6 +283,9 @@ struct Chain {
   // pass), and/or the last pass also runs the next step's FIRST into e0.
   bool skip_first = false;
   bool fuse_next_first = false;
+  // power iteration: apply 1/||v|| (norm_in) in the spectral epilogue instead
+  // of at the chain's input (the operations before it are linear)
+  bool norm_at_epilogue = false;
 };
 
 sr::PassArgs base_args(const Plan& p) {
@@ -344,7 +347,7 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     a.out_dir = c.dir[0];
     a.xin = c.xin;
     a.n_in = c.n_in;
-    a.norm_in = c.norm_in;
+    a.norm_in = c.norm_at_epilogue ? nullptr : c.norm_in;
     a.norm_in_count = c.norm_in_count;
     a.op = c.first_op;
     a.dp = p.d_dp + (size_t)c.first_d * p.m;
@@ -371,6 +374,10 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
       a.sumy = c.sumy;
       a.lam = c.lam;
       a.weight_mode = c.weight_mode;
+      if (c.norm_at_epilogue) {
+        a.norm_in = c.norm_in;
+        a.norm_in_count = c.norm_in_count;
+      }
     }
     {
       PassTimer tm(p, 1, s);
@@ -886,12 +893,18 @@ sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int it
   c.sumy = p.d_scal;
   c.lam = o.lambda;
   c.weight_mode = o.weight_mode;
+  // Consecutive steps share a kernel (see sr_gd_solve); the iterate then enters
+  // each step unnormalised and its 1/||u|| is applied in the spectral epilogue.
+  const bool fuse = !p.inner;
+  c.norm_at_epilogue = fuse;
   int prev = 1, prev_count = init_chunks;
   for (int it = 0; it < iters; ++it) {
     const int cur = it % 2;
     c.norm_in = bank[prev];
     c.norm_in_count = prev_count;
     c.spec_part_out = bank[cur];
+    c.skip_first = fuse && it > 0;
+    c.fuse_next_first = fuse && it + 1 < iters;
     if ((st = run_chain(p, c, B, s)) != SR_OK) return st;
     prev = cur;
     prev_count = last_cpp;

@@ -151,6 +151,7 @@ __device__ __forceinline__ void twiddle_store(float2 (&v)[TL::E], const PassArgs
 template <class TL>
 struct OpData {
   float y[TL::E];
+  float vscale = 1.0f;  // spectral epilogue: 1/||u|| of the current iterate (when applied here)
   __device__ __forceinline__ void load_y(const PassArgs& a, int op, int b, int g, int p) {
     if (op == kOpGdEpilogue || op == kOpSpecEpilogue) {
       const float* yb = a.y + (size_t)b * a.m + g;
@@ -180,7 +181,8 @@ __device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, 
       v[j] = cscale(v[j], r);
     }
   } else if (a.op == kOpSpecEpilogue) {
-    // z -> T(y_hat) z, y_hat = m y / sum(y) (Eq. 3)
+    // z -> T(y_hat) z, y_hat = m y / sum(y) (Eq. 3); times 1/||u|| when the
+    // iterate's normalisation is applied here rather than at the chain's input
     const float scale = (float)a.m / __ldg(&a.sumy[b]);
 #pragma unroll
     for (int j = 0; j < TL::E; ++j) {
@@ -188,7 +190,7 @@ __device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, 
       float w;
       if (a.weight_mode == SR_WEIGHT_IDENTITY) w = yh;
       else w = yh > 0.f ? fmaxf(1.0f - 1.0f / yh, a.lam) : a.lam;
-      v[j] = cscale(v[j], w);
+      v[j] = cscale(v[j], w * od.vscale);
     }
   }
 }
@@ -354,15 +356,23 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   thread_coords<TL>(t, p);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
+  __shared__ float s_vscale;
   pipe_tiles<ELL, T>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
     const int g = g0 + t;
     OpData<TL> od;
     od.load_y(a, a.op, b, g, p);
+    const bool vs = a.op == kOpSpecEpilogue && a.norm_in;
+    if (vs && tid == 0)
+      s_vscale = 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count));
     RowTw<TL> rw;
     rw.load(a, g0, DB);
     const float2 A = tw_m(a, g * p, DB);
     line_fft<ELL, T, DA>(v, scratch, p, t, tw);
     fsum2 acc{0.f, 0.f};
+    if (vs) {
+      __syncthreads();  // s_vscale visible
+      od.vscale = s_vscale;
+    }
     apply_op<TL>(v, a, od, b, g, p, acc);
     if (a.op == kOpGdEpilogue) {
       const float s = block_sum(acc, red);
@@ -439,19 +449,22 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 }
 
 
-// LAST of one GD step fused with FIRST of the next. Both work on the lines of
-// layout X: step 2 of the final inverse DFT, D_1^H, the update
-// x <- x - mu_t 2 (.) on the kept entries (U^H), and then, still in registers,
-// U (zeros beyond n), D_1 and step 1 of the next step's first forward DFT, with
-// the four-step twiddles, into the exchange buffer `eout`. Each D_1 entry is
-// loaded once for both uses.
+// LAST of one GD or power-iteration step fused with FIRST of the next. Both
+// work on the lines of layout X: step 2 of the final inverse DFT, D_1^H, the
+// update on the kept entries (U^H) -- x <- x - mu_t 2 (.) for GD, or
+// u <- (.) + shift v (with norm partials of u) for the power iteration, whose
+// 1/||u|| the next step applies in its spectral epilogue -- and then, still in
+// registers, U (zeros beyond n), D_1 and step 1 of the next step's first
+// forward DFT, with the four-step twiddles, into the exchange buffer `eout`.
+// Each D_1 entry is loaded once for both uses.
 template <int ELL, int T>
 __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     k_last_first(const __grid_constant__ PassArgs a, int nbuf) {
   using TL = Tile<ELL, T>;
   constexpr int E = TL::E, P = TL::P;
   extern __shared__ unsigned char smem_raw[];
-  __shared__ float s_mu;
+  __shared__ float red[64];
+  __shared__ float s_mu, s_inv_old;
   unsigned char* smem = aligned_smem(smem_raw);
   const PipeSmem L = pipe_layout(ELL, T, nbuf, true);
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
@@ -462,17 +475,24 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   thread_coords<TL>(t, p);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
+  const bool spec = a.out_mode == kOutSpec;
   pipe_tiles<ELL, T>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
     const int g = g0 + t;
-    if (tid == 0) s_mu = a.mu[b];
+    if (tid == 0) {
+      s_mu = spec ? 0.f : a.mu[b];
+      s_inv_old = spec && a.norm_in
+                      ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count))
+                      : 1.0f;
+    }
     RowTw<TL> rw;
     rw.load(a, g0, -1);
     const float2 A = tw_m(a, g * p, -1);
     line_fft<ELL, T, 1>(v, scratch, p, t, tw);
-    __syncthreads();  // tile scalar visible
-    const float mu2 = 2.0f * s_mu * a.mu_scale;
+    __syncthreads();  // tile scalars visible
+    const float mu2 = 2.0f * s_mu * a.mu_scale, sh = a.shift * s_inv_old;
     float2* xb = a.xout + (size_t)b * a.n_out;
     const float2* dp = a.dp + (size_t)b * a.dp_stride;
+    fsum2 acc{0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int nat = (p + j * P) * a.nl + g;
@@ -480,13 +500,22 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
         const float2 d = __ldg(&dp[nat]);
         const float2 gr = cmulc(v[j], d);
         float2 x = xb[nat];
-        x.x = fmaf(-mu2, gr.x, x.x);
-        x.y = fmaf(-mu2, gr.y, x.y);
+        if (spec) {  // u = M v + shift v with v = x / ||x|| (x unnormalised)
+          x = make_float2(fmaf(sh, x.x, gr.x), fmaf(sh, x.y, gr.y));
+          acc_add(acc, cabs2(x));
+        } else {     // x <- x - mu_t 2 A^H(r z)
+          x.x = fmaf(-mu2, gr.x, x.x);
+          x.y = fmaf(-mu2, gr.y, x.y);
+        }
         xb[nat] = x;
         v[j] = cmul(x, d);
       } else {
         v[j] = make_float2(0.f, 0.f);
       }
+    }
+    if (spec) {
+      const float s = block_sum(acc, red);
+      if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = s;
     }
     if (a.loss_out && g0 == 0 && tid == 0)
       a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
