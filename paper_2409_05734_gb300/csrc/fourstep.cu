@@ -185,7 +185,7 @@ cudaError_t launch_first(const Plan& p, Layout lay, const PassArgs& a0, int B, c
 static cudaError_t launch_pipe(bool last, const Plan& p, Layout lay, const PassArgs& a0, int B, cudaStream_t s) {
   const LineGeom& g = p.geom[lay];
   auto fn = reinterpret_cast<void (*)(PassArgs, int)>(
-      const_cast<void*>(last ? pick_last(g.ell, g.T, a0.in_dir) : pick_mid(g.ell, g.T, a0.in_dir, a0.out_dir)));
+      const_cast<void*>(last ? pick_last(g.ell, g.T, a0.in_dir, g.nl) : pick_mid(g.ell, g.T, a0.in_dir, a0.out_dir, g.nl)));
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = allow_smem((const void*)fn, g.smem_pipe);
   if (e != cudaSuccess) return e;
@@ -206,7 +206,7 @@ cudaError_t launch_last(const Plan& p, Layout lay, const PassArgs& a, int B, cud
 
 cudaError_t launch_last_first(const Plan& p, Layout lay, const PassArgs& a0, int B, cudaStream_t s) {
   const LineGeom& g = p.geom[lay];
-  auto fn = reinterpret_cast<void (*)(PassArgs, int)>(const_cast<void*>(pick_last_first(g.ell, g.T)));
+  auto fn = reinterpret_cast<void (*)(PassArgs, int)>(const_cast<void*>(pick_last_first(g.ell, g.T, g.nl)));
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = allow_smem((const void*)fn, g.smem_pipe);
   if (e != cudaSuccess) return e;
@@ -221,9 +221,9 @@ cudaError_t pass_occupancy(const LineGeom& g, int* per_sm_mid, int* per_sm_last,
   // per_sm_mid[3]: direction pairs (-,-), (-,+), (+,+); per_sm_last[2]: (-), (+); per_sm_lf: fused
   const int pairs[3][2] = {{-1, -1}, {-1, 1}, {1, 1}};
   for (int k = 0; k < 6; ++k) {
-    const void* fn = k < 3   ? pick_mid(g.ell, g.T, pairs[k][0], pairs[k][1])
-                     : k < 5 ? pick_last(g.ell, g.T, k == 3 ? -1 : 1)
-                             : pick_last_first(g.ell, g.T);
+    const void* fn = k < 3   ? pick_mid(g.ell, g.T, pairs[k][0], pairs[k][1], g.nl)
+                     : k < 5 ? pick_last(g.ell, g.T, k == 3 ? -1 : 1, g.nl)
+                             : pick_last_first(g.ell, g.T, g.nl);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem(fn, g.smem_pipe);
     if (e != cudaSuccess) return e;

@@ -4,7 +4,11 @@
 
 namespace sr {
 
-const void* pick_last(int ell, int T, int da) {
+const void* pick_last(int ell, int T, int da, int nl) {
+  if (SR_NL_SPECIAL(ell, T, nl)) {
+    if (da < 0) return reinterpret_cast<const void*>(&k_last<256, 16, -1, 256>);
+    return reinterpret_cast<const void*>(&k_last<256, 16, 1, 256>);
+  }
 #define SR_PICK_LAST(E_, T_)                                                  \
   if (ell == E_ && T == T_) {                                                 \
     if (da < 0) return reinterpret_cast<const void*>(&k_last<E_, T_, -1>);    \

@@ -1,10 +1,11 @@
-// Instantiations of the fused LAST + FIRST kernel of the GD loop for every
-// tile shape (see passes.cuh).
+// Instantiations of the fused LAST + FIRST kernel of the GD and power-iteration
+// loops for every tile shape (see passes.cuh).
 #include "passes.cuh"
 
 namespace sr {
 
-const void* pick_last_first(int ell, int T) {
+const void* pick_last_first(int ell, int T, int nl) {
+  if (SR_NL_SPECIAL(ell, T, nl)) return reinterpret_cast<const void*>(&k_last_first<256, 16, 256>);
 #define SR_PICK_LF(E_, T_) \
   if (ell == E_ && T == T_) return reinterpret_cast<const void*>(&k_last_first<E_, T_>);
   SR_TILE_SHAPES(SR_PICK_LF)

@@ -33,15 +33,28 @@ __host__ __device__ constexpr int pass_threads(int ell) { return ell <= 512 ? 25
 // box (T rows) fills a 1024-byte swizzle period.
 __host__ __device__ constexpr bool uses_tma(int ell, int T) { return ell >= 16 && T >= 8; }
 
-template <int ELL, int T_>
+// Tile shape: lines of ELL points, T lines per CTA. NLC is the number of lines
+// NL = m / ELL when it is fixed at compile time (specialised kernels for the
+// most used lengths: every per-slot offset of the natural-order and exchange
+// accesses then folds into an immediate), or 0 to read it from the arguments.
+template <int ELL, int T_, int NLC_ = 0>
 struct Tile {
   static constexpr int T = T_;
+  static constexpr int NLC = NLC_;
   static constexpr int E = LineShape<ELL>::E, P = LineShape<ELL>::P;
   static constexpr int THREADS = T * P;
   static constexpr bool TMA = uses_tma(ELL, T);
   static constexpr int BOX = T * 128;  // bytes of one box: 16 complex values x T rows
   static constexpr int MIN_CTAS = THREADS <= 256 ? 3 : 1;
   static_assert(THREADS <= 512, "tile too large");
+  static_assert(NLC == 0 || NLC % T == 0, "lines per CTA must divide the line count");
+  __device__ __forceinline__ static int nl(const PassArgs& a) { return NLC ? NLC : a.nl; }
+  __device__ __forceinline__ static int m(const PassArgs& a) { return NLC ? NLC * ELL : a.m; }
+  __device__ __forceinline__ static int cpp(const PassArgs& a) { return NLC ? NLC / T : a.cpp; }
+  // split point of the two-level W_m table: ceil(log2(m) / 2)
+  __device__ __forceinline__ static int tw_shift(const PassArgs& a) {
+    return NLC ? (ilog2c(NLC * ELL) + 1) / 2 : a.tw_shift;
+  }
 };
 
 // Thread coordinates (line t, butterfly column p) with their ranges stated to
@@ -94,8 +107,10 @@ __device__ __forceinline__ unsigned char* aligned_smem(unsigned char* raw) {
 
 // W_m^e = W_m^(hi part) * W_m^(lo part), both tables rounded from double;
 // conjugated when dir > 0.
+template <class TL>
 __device__ __forceinline__ float2 tw_m(const PassArgs& a, int e, int dir) {
-  const float2 w = cmul(__ldg(&a.tw_hi[e >> a.tw_shift]), __ldg(&a.tw_lo[e & ((1 << a.tw_shift) - 1)]));
+  const int sh = TL::tw_shift(a);
+  const float2 w = cmul(__ldg(&a.tw_hi[e >> sh]), __ldg(&a.tw_lo[e & ((1 << sh) - 1)]));
   return dir > 0 ? conjf2(w) : w;
 }
 
@@ -117,7 +132,7 @@ struct RowTw {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       const int i = threadIdx.x + k * TL::THREADS;
-      if (i < TL::E * TL::T) w[k] = tw_m(a, (g0 + i % TL::T) * TL::P * (i / TL::T), dir);
+      if (i < TL::E * TL::T) w[k] = tw_m<TL>(a, (g0 + i % TL::T) * TL::P * (i / TL::T), dir);
     }
   }
   __device__ __forceinline__ void store(float2* rowtw) const {
@@ -135,11 +150,11 @@ struct RowTw {
 template <class TL>
 __device__ __forceinline__ void twiddle_store(float2 (&v)[TL::E], const PassArgs& a, int b, int g, int t, int p,
                                               float2 A, const float2* rowtw) {
-  float2* eb = a.eout + (size_t)b * a.m + g;
+  float2* eb = a.eout + (size_t)b * TL::m(a) + g;
 #pragma unroll
   for (int j = 0; j < TL::E; ++j) {
     const float2 w = cmul(A, rowtw[j * TL::T + t]);
-    eb[(size_t)(p + j * TL::P) * a.nl] = cmul(v[j], w);
+    eb[(size_t)(p + j * TL::P) * TL::nl(a)] = cmul(v[j], w);
   }
 }
 
@@ -154,9 +169,9 @@ struct OpData {
   float vscale = 1.0f;  // spectral epilogue: 1/||u|| of the current iterate (when applied here)
   __device__ __forceinline__ void load_y(const PassArgs& a, int op, int b, int g, int p) {
     if (op == kOpGdEpilogue || op == kOpSpecEpilogue) {
-      const float* yb = a.y + (size_t)b * a.m + g;
+      const float* yb = a.y + (size_t)b * TL::m(a) + g;
 #pragma unroll
-      for (int j = 0; j < TL::E; ++j) y[j] = __ldg(&yb[(p + j * TL::P) * a.nl]);
+      for (int j = 0; j < TL::E; ++j) y[j] = __ldg(&yb[(p + j * TL::P) * TL::nl(a)]);
     }
   }
 };
@@ -167,11 +182,11 @@ __device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, 
   if (a.op == kOpDiag) {
     const float2* dp = a.dp + (size_t)b * a.dp_stride;
 #pragma unroll
-    for (int j = 0; j < TL::E; ++j) v[j] = cmul(v[j], __ldg(&dp[(p + j * TL::P) * a.nl + g]));
+    for (int j = 0; j < TL::E; ++j) v[j] = cmul(v[j], __ldg(&dp[(p + j * TL::P) * TL::nl(a) + g]));
   } else if (a.op == kOpDiagConj) {
     const float2* dp = a.dp + (size_t)b * a.dp_stride;
 #pragma unroll
-    for (int j = 0; j < TL::E; ++j) v[j] = cmulc(v[j], __ldg(&dp[(p + j * TL::P) * a.nl + g]));
+    for (int j = 0; j < TL::E; ++j) v[j] = cmulc(v[j], __ldg(&dp[(p + j * TL::P) * TL::nl(a) + g]));
   } else if (a.op == kOpGdEpilogue) {
     // z -> r = |z|^2 - y, w = r z (Eq. 2); loss partial sum of r^2
 #pragma unroll
@@ -183,7 +198,7 @@ __device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, 
   } else if (a.op == kOpSpecEpilogue) {
     // z -> T(y_hat) z, y_hat = m y / sum(y) (Eq. 3); times 1/||u|| when the
     // iterate's normalisation is applied here rather than at the chain's input
-    const float scale = (float)a.m / __ldg(&a.sumy[b]);
+    const float scale = (float)TL::m(a) / __ldg(&a.sumy[b]);
 #pragma unroll
     for (int j = 0; j < TL::E; ++j) {
       const float yh = od.y[j] * scale;
@@ -217,7 +232,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   RowTw<TL> rw;
   rw.load(a, g0, DB);
   rw.store(rowtw);
-  const float2 A = tw_m(a, g * p, DB);
+  const float2 A = tw_m<TL>(a, g * p, DB);
   if (tid == 0)
     s_scale = a.norm_in ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count))
                         : 1.0f;
@@ -253,8 +268,8 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 // 16 values x T rows) into `buf`, completing on barrier `bar`.
 template <class TL, int ELL>
 __device__ __forceinline__ void issue_tile(const PassArgs& a, int tile, uint32_t buf, uint32_t bar) {
-  const int b = tile / a.cpp, g0 = (tile - b * a.cpp) * TL::T;
-  const int row = b * a.nl + g0;
+  const int b = tile / TL::cpp(a), g0 = (tile - b * TL::cpp(a)) * TL::T;
+  const int row = b * TL::nl(a) + g0;
   mbar_arrive_expect_tx(bar, (uint32_t)(TL::T * ELL * 8));
 #pragma unroll 1
   for (int kb = 0; kb < ELL / 16; ++kb) tma_load_2d(buf + (uint32_t)(kb * TL::BOX), &a.tmap, kb * 32, row, bar);
@@ -263,11 +278,10 @@ __device__ __forceinline__ void issue_tile(const PassArgs& a, int tile, uint32_t
 // Shared pipeline of the persistent MID / LAST passes: for every tile of this
 // CTA, loads the T input lines (rows of the exchange buffer) into registers
 // (slot j = position p + j*P) and calls body(v, b, g0).
-template <int ELL, int T, class Body>
+template <int ELL, class TL, class Body>
 __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned char* smem, const PipeSmem& L,
                                            Body&& body) {
-  using TL = Tile<ELL, T>;
-  constexpr int E = TL::E, P = TL::P;
+  constexpr int E = TL::E, P = TL::P, T = TL::T;
   const int tid = threadIdx.x;
   int t, p;
   thread_coords<TL>(t, p);
@@ -287,7 +301,7 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
     if (tid == 0 && tile < a.ntiles) issue_tile<TL, ELL>(a, tile, in0, bar0);
   }
   for (int k = 0; tile < a.ntiles; ++k, tile += gridDim.x) {
-    const int b = tile / a.cpp, g0 = (tile - b * a.cpp) * T, g = g0 + t;
+    const int b = tile / TL::cpp(a), g0 = (tile - b * TL::cpp(a)) * T, g = g0 + t;
     const int next = tile + (int)gridDim.x;
     float2 v[E];
     if constexpr (TL::TMA) {
@@ -330,19 +344,23 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
         }
       }
     } else {
-      const float2* src = a.ein + (size_t)b * a.m + (size_t)g * ELL;
+      const float2* src = a.ein + (size_t)b * TL::m(a) + (size_t)g * ELL;
 #pragma unroll
       for (int j = 0; j < E; ++j) v[j] = src[p + j * P];
     }
     body(v, b, g0);
-    __syncthreads();  // scratch, tables and input buffer free for the next tile
+    // Scratch, tables and shared scalars are free for the next tile. With one
+    // TMA staging buffer the barrier that follows the next tile's register load
+    // already orders this tile's last shared-memory reads before the next
+    // tile's first writes, so no barrier is needed here.
+    if (!(TL::TMA && nbuf == 1)) __syncthreads();
   }
 }
 
-template <int ELL, int T, int DA, int DB>
+template <int ELL, int T, int DA, int DB, int NLC = 0>
 __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     k_mid(const __grid_constant__ PassArgs a, int nbuf) {
-  using TL = Tile<ELL, T>;
+  using TL = Tile<ELL, T, NLC>;
   constexpr int E = TL::E;
   extern __shared__ unsigned char smem_raw[];
   __shared__ float red[64];
@@ -357,7 +375,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
   __shared__ float s_vscale;
-  pipe_tiles<ELL, T>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
+  pipe_tiles<ELL, TL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
     const int g = g0 + t;
     OpData<TL> od;
     od.load_y(a, a.op, b, g, p);
@@ -366,7 +384,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
       s_vscale = 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count));
     RowTw<TL> rw;
     rw.load(a, g0, DB);
-    const float2 A = tw_m(a, g * p, DB);
+    const float2 A = tw_m<TL>(a, g * p, DB);
     line_fft<ELL, T, DA>(v, scratch, p, t, tw);
     fsum2 acc{0.f, 0.f};
     if (vs) {
@@ -376,7 +394,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     apply_op<TL>(v, a, od, b, g, p, acc);
     if (a.op == kOpGdEpilogue) {
       const float s = block_sum(acc, red);
-      if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = s;
+      if (tid == 0) a.part_out[(size_t)b * TL::cpp(a) + g0 / T] = s;
     }
     rw.store(rowtw);
     __syncthreads();  // first FFT's scratch reads done; row twiddles visible
@@ -385,10 +403,10 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   });
 }
 
-template <int ELL, int T, int DA>
+template <int ELL, int T, int DA, int NLC = 0>
 __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     k_last(const __grid_constant__ PassArgs a, int nbuf) {
-  using TL = Tile<ELL, T>;
+  using TL = Tile<ELL, T, NLC>;
   constexpr int E = TL::E, P = TL::P;
   extern __shared__ unsigned char smem_raw[];
   __shared__ float red[64];
@@ -402,7 +420,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   thread_coords<TL>(t, p);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
-  pipe_tiles<ELL, T>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
+  pipe_tiles<ELL, TL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
     const int g = g0 + t;
     if (tid == 0) {
       s_inv_old = (a.out_mode == kOutSpec && a.norm_in)
@@ -419,7 +437,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     fsum2 acc{0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-      const int nat = (p + j * P) * a.nl + g;
+      const int nat = (p + j * P) * TL::nl(a) + g;
       if (nat >= a.n_out) continue;
       float2 val = v[j];
       if (a.op == kOpDiagConj) val = cmulc(val, __ldg(&a.dp[(size_t)b * a.dp_stride + nat]));
@@ -441,7 +459,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     }
     if (a.out_mode == kOutSpec) {
       const float s = block_sum(acc, red);
-      if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = s;
+      if (tid == 0) a.part_out[(size_t)b * TL::cpp(a) + g0 / T] = s;
     }
     if (a.loss_out && g0 == 0 && tid == 0)
       a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
@@ -457,10 +475,10 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 // registers, U (zeros beyond n), D_1 and step 1 of the next step's first
 // forward DFT, with the four-step twiddles, into the exchange buffer `eout`.
 // Each D_1 entry is loaded once for both uses.
-template <int ELL, int T>
+template <int ELL, int T, int NLC = 0>
 __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     k_last_first(const __grid_constant__ PassArgs a, int nbuf) {
-  using TL = Tile<ELL, T>;
+  using TL = Tile<ELL, T, NLC>;
   constexpr int E = TL::E, P = TL::P;
   extern __shared__ unsigned char smem_raw[];
   __shared__ float red[64];
@@ -476,7 +494,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
   const bool spec = a.out_mode == kOutSpec;
-  pipe_tiles<ELL, T>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
+  pipe_tiles<ELL, TL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
     const int g = g0 + t;
     if (tid == 0) {
       s_mu = spec ? 0.f : a.mu[b];
@@ -486,7 +504,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     }
     RowTw<TL> rw;
     rw.load(a, g0, -1);
-    const float2 A = tw_m(a, g * p, -1);
+    const float2 A = tw_m<TL>(a, g * p, -1);
     line_fft<ELL, T, 1>(v, scratch, p, t, tw);
     __syncthreads();  // tile scalars visible
     const float mu2 = 2.0f * s_mu * a.mu_scale, sh = a.shift * s_inv_old;
@@ -495,7 +513,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     fsum2 acc{0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-      const int nat = (p + j * P) * a.nl + g;
+      const int nat = (p + j * P) * TL::nl(a) + g;
       if (nat < a.n_out) {
         const float2 d = __ldg(&dp[nat]);
         const float2 gr = cmulc(v[j], d);
@@ -515,7 +533,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     }
     if (spec) {
       const float s = block_sum(acc, red);
-      if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = s;
+      if (tid == 0) a.part_out[(size_t)b * TL::cpp(a) + g0 / T] = s;
     }
     if (a.loss_out && g0 == 0 && tid == 0)
       a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
@@ -534,8 +552,12 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 // Kernel entry points by tile shape and transform direction (nullptr when the
 // combination is not instantiated). Defined in pass_first.cu / pass_mid.cu / pass_last.cu.
 const void* pick_first(int ell, int T, int db);
-const void* pick_mid(int ell, int T, int da, int db);
-const void* pick_last(int ell, int T, int da);
-const void* pick_last_first(int ell, int T);
+// nl selects a kernel specialised for that line count when one exists.
+const void* pick_mid(int ell, int T, int da, int db, int nl);
+const void* pick_last(int ell, int T, int da, int nl);
+const void* pick_last_first(int ell, int T, int nl);
+
+// Line counts with specialised kernels: (ELL, T, NL) = (256, 16, 256), i.e. m = 2^16.
+#define SR_NL_SPECIAL(ell, T, nl) ((ell) == 256 && (T) == 16 && (nl) == 256)
 
 }  // namespace sr
