@@ -274,7 +274,7 @@ def traffic_from_profile(name: str):
     vals = {}
     for line in open(path):
         if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
+            k, v = line.strip()[2:].rsplit(":", 1)  # keys may hold a colon ("sha256[:16]")
             vals[k.strip()] = v.strip()
     if vals.get("kernel sources sha256[:16]") != want:
         return None

@@ -54,3 +54,24 @@ def test_reference_arm_skips_nonzero_ranks(monkeypatch, capsys):
                                       "--warmup", "0"])
     assert bench.main() == 0
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_read_from_profile_summary_keyed_to_sources(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from a committed ncu summary only while
+    the pass kernels' sources still hash to the value the summary records."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    h = hashlib.sha256()
+    for f in ("passes.cuh", "sr_device.cuh", "sr_tma.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2409_05734_gb300", "csrc", f), "rb").read())
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "k.md").write_text(f"# summary\n- dram_bytes_per_launch: 1234\n"
+                               f"- kernel sources sha256[:16]: {h.hexdigest()[:16]}\n- a note: with a colon\n")
+    (prof / "stale.md").write_text("- dram_bytes_per_launch: 1234\n- kernel sources sha256[:16]: 0000000000000000\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "paper_2409_05734_gb300").symlink_to(os.path.join(ROOT, "paper_2409_05734_gb300"))
+    assert bench.traffic_from_profile("k.md") == 1234.0
+    assert bench.traffic_from_profile("stale.md") is None
+    assert bench.traffic_from_profile("missing.md") is None
