@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--no-graph", action="store_true", help="launch directly instead of replaying a CUDA graph")
     ap.add_argument("--no-library", action="store_true", help="skip the cuFFT pipeline comparison")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch workload")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the radix-3 and differentiable-operator workloads")
     return ap.parse_args()
 
 
@@ -451,6 +453,100 @@ def cufft_pipeline(torch, plan, W, y, x_true, fused_ms_per_iter, iters=20):
             "speedup_of_fused": t / fused_ms_per_iter}
 
 
+def timed_graph(torch, fn, flush, reps=3):
+    """Median device time (ms) of fn captured as a CUDA graph and replayed, L2
+    flushed before each replay."""
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    g.replay()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def radix3_workload(torch, dev, flush):
+    """The oversampling ratios 1.5, 3 and 6 of the recovery sweep (m = 3 * 2^a):
+    n = 2^16, L = 2, B = 8 noiseless problems, 20 power + 100 GD iterations."""
+    from paper_2409_05734_gb300 import Plan
+    import synthetic as S
+    out = {}
+    n, L, B, sp, gd = 2 ** 16, 2, 8, 20, 100
+    for alpha, m in ((1.5, 3 * 2 ** 15), (3, 3 * 2 ** 16), (6, 3 * 2 ** 17)):
+        plan = Plan(n, m, L, 31)
+        plan.reserve(B)
+        x_true = torch.from_numpy(S.signal_gaussian(31, B, n)).to(torch.complex64).to(dev)
+        y = (plan.forward(x_true).abs() ** 2).contiguous()
+        v0 = torch.from_numpy(S.start_vector(31, B, n)).to(torch.complex64).to(dev)
+        x = torch.empty_like(v0)
+
+        def solve():
+            plan.spectral_init(y, v0, sp, weight="optimal", out=x)
+            plan.gd_solve(y, x, gd, mu0=0.15, tau0=100.0)
+
+        ms = timed_graph(torch, solve, flush)
+        it = sp + gd
+        W = dict(n=n, m=m, L=L, B=B)
+        out[f"alpha={alpha}"] = {"m": m, "ms_per_solve": ms, "problem_iters_per_s": B * it / (ms / 1e3),
+                                 "algorithmic_gbs": iteration_bytes(W) * it / (ms / 1e3) / 1e9}
+        plan.check()
+        del plan
+    return {"workload": f"n = 2^16, L = {L}, B = {B}, x ~ CN(0, I), noiseless, {sp} power + {gd} GD iterations; "
+                        "m = 3 * 2^a runs each DFT as split -> power-of-two DFT of 3B sequences -> radix-3 combine",
+            **out}
+
+
+def autograd_workload(torch, dev, flush):
+    """Forward and backward of the differentiable operator (x, theta) -> z = A x at
+    B = 8, n = 2^20, m = 2^22, L = 2, driven by a loss on |z|^2."""
+    from paper_2409_05734_gb300 import Plan, structured_random
+    import synthetic as S
+    B, n, m, L = 8, 2 ** 20, 2 ** 22, 2
+    plan = Plan(n, m, L, 11)
+    plan.reserve(B)
+    theta = torch.tensor(S.phases(11, L, m).astype(np.float32), device=dev, requires_grad=True)
+    x = torch.from_numpy(S.signal_gaussian(11, B, n)).to(torch.complex64).to(dev).requires_grad_(True)
+    wgt = torch.rand((B, m), device=dev, generator=torch.Generator(device=dev).manual_seed(3))
+
+    def step():
+        theta.grad = None
+        x.grad = None
+        z = structured_random(x, theta, plan)
+        torch.sum(wgt * (z.real ** 2 + z.imag ** 2)).backward()
+
+    step()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    plan.check()
+    ms = statistics.median(ts)
+    # compulsory bytes per problem: forward 56m + 8n (L = 2 DFTs through the
+    # exchange buffers, x read, z written); backward about 100m (G_z read, the
+    # h chain, the recomputed layer input, both theta-gradient reductions)
+    nbytes = B * (56 * m + 8 * n + 100 * m)
+    return {"workload": f"B = {B}, n = 2^20, m = 2^22, L = {L}: z = A x by the autograd function, "
+                        "loss sum(w |z|^2), backward to x and theta (direct launches)",
+            "ms_per_forward_backward": ms, "problems_per_s": B / (ms / 1e3),
+            "algorithmic_gbs": nbytes / (ms / 1e3) / 1e9}
+
+
 def ragged_workload(torch, dev, flush, reps: int = 3):
     """The ragged batch of RAGGED: problem-iterations per second of the whole
     graph-captured solve, its algorithmic HBM bytes per second, and accuracy."""
@@ -691,6 +787,9 @@ def run_ours(args):
         line["library_comparison"] = cufft_pipeline(torch, plan, W, y, x_true, ms_step / iters)
     if rank == 0 and not args.no_dense:
         line["dense_iid_comparison"] = dense_comparison(torch, dev, flush)
+    if rank == 0 and not args.no_extra:
+        line["radix3_batch"] = radix3_workload(torch, dev, flush)
+        line["differentiable_operator"] = autograd_workload(torch, dev, flush)
     if rank == 0 and not args.no_ragged:
         line["ragged_batch"] = ragged_workload(torch, dev, flush)
     if rank == 0 and not args.no_cpu_baseline:
