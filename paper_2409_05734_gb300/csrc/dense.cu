@@ -124,19 +124,44 @@ __device__ __forceinline__ void store_split(__nv_bfloat16* t, int twoB, int c, i
   t[i + (size_t)twoB * 64] = l;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constant__ GemmArgs a, int stages) {
+// Thread-block-cluster helpers (split-K pairs): barrier over both CTAs, the
+// address in CTA `rank` of a shared location, and a store there.
+__device__ __forceinline__ void pair_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t pair_map(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void pair_store(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void pair_store_i(uint32_t addr, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// split = 1: one CTA per 128-row output tile. split = 2 (launched as clusters
+// of two CTAs): the two CTAs of a cluster share a tile and each sums half of
+// the K range; after both main loops, rank 1 stores its FP32 sums into rank
+// 0's (drained) stage ring through distributed shared memory, and rank 0 adds
+// them and runs the epilogue.
+__global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constant__ GemmArgs a, int stages,
+                                                              int split) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], done_bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_fail;
+  __shared__ int s_fail, s_peer_ok;
   __shared__ float red[4][128];
+  const int tile = blockIdx.x / split, rank = split == 2 ? (int)(blockIdx.x & 1) : 0;
+  const int ntiles = (int)gridDim.x / split;
   const uint32_t base_a = smem_addr(smem_raw);
   const uint32_t base = (base_a + 1023u) & ~1023u;
   const int N = 2 * a.B;
   const uint32_t a_bytes = kBM * 128, b_bytes = (uint32_t)N * 128;
   const uint32_t stage_bytes = a_bytes + 2 * b_bytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kBM;
+  const int m0 = tile * kBM;
   // TMEM columns of one accumulator: N, and every column the epilogue reads
   // (32-column loads at c0 and B + c0 for c0 < B). Successive K-stages rotate
   // over `nacc` accumulators (as many as the 512 columns hold, up to 4) that the
@@ -161,11 +186,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  const int KT = a.K / kBK;
+  const int KT = a.K / kBK / split;   // k-tiles of this CTA
+  const int kbeg = rank * KT;          // its first k-tile
   // CTAs start their K sweep at staggered offsets so that the vector operand's
   // tiles are not requested by every CTA at the same moment (K order only
   // changes the FP32 summation order, which stays fixed per output row).
-  const int kt0 = (int)(((long long)blockIdx.x * KT) / gridDim.x);
+  const int kt0 = (int)(((long long)tile * KT) / ntiles);
 
   // Lanes 1-31 of the producer and MMA warps park at __syncwarp (not in a spin
   // on the done barrier, which would steal the warp's issue slots from lane 0).
@@ -181,8 +207,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
         const uint32_t st = base + (uint32_t)s * stage_bytes;
         const uint32_t fb = smem_addr(&full_bar[s]);
         mbar_arrive_expect_tx(fb, stage_bytes);
-        const int kx = ((kt + kt0) % KT) * kBK;
-        bulk_load(st, a.a_tiles + ((size_t)blockIdx.x * KT + (kx / kBK)) * (kBM * kBK), a_bytes, fb);
+        const int kx = (kbeg + (kt + kt0) % KT) * kBK;
+        bulk_load(st, a.a_tiles + ((size_t)tile * (a.K / kBK) + (kx / kBK)) * (kBM * kBK), a_bytes, fb);
         bulk_load(st + a_bytes, a.b_tiles + (size_t)(kx / kBK) * (2 * N * kBK), 2 * b_bytes, fb);
       }
     }
@@ -219,7 +245,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
   ok = __syncthreads_and(ok) && !s_fail;
   const int row = m0 + warp * 32 + lane;  // output row of this thread
   const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-  if (ok) {
+  // split-K: partial sums of rank 1 at part[((c0 / 32) * 2 + re/im) * 32 + i][128 rows]
+  const float* part = reinterpret_cast<const float*>(smem_raw + (base - base_a));
+  if (split == 2) {
+    pair_sync();  // both main loops done: rank 0's stage ring is free
+    if (rank == 1) {
+      if (ok) {
+        const uint32_t rbase = pair_map(base, 0);
+        const int rl = warp * 32 + lane;
+        for (int c0 = 0; c0 < a.B; c0 += 32) {
+          float re[32], im[32];
+          tmem_ld32(tl + (uint32_t)c0, re);
+          tmem_ld32(tl + (uint32_t)(a.B + c0), im);
+          for (int q = 1; q < nacc && q < KT; ++q) {
+            float r2[32], i2[32];
+            tmem_ld32(tl + (uint32_t)q * acc_cols + (uint32_t)c0, r2);
+            tmem_ld32(tl + (uint32_t)q * acc_cols + (uint32_t)(a.B + c0), i2);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              re[i] += r2[i];
+              im[i] += i2[i];
+            }
+          }
+          const uint32_t cb = rbase + (uint32_t)(((c0 / 32) * 2) * 32 * 128 + rl) * 4u;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            pair_store(cb + (uint32_t)(i * 128) * 4u, re[i]);
+            pair_store(cb + (uint32_t)((32 + i) * 128) * 4u, im[i]);
+          }
+        }
+      }
+      if (threadIdx.x == 0) pair_store_i(pair_map(smem_addr(&s_peer_ok), 0), ok ? 1 : 0);
+    }
+    pair_sync();  // rank 1's partial sums and status are in rank 0's shared memory
+    if (rank == 0) ok = ok && s_peer_ok;
+  }
+  if (ok && rank == 0) {
     for (int c0 = 0; c0 < a.B; c0 += 32) {
       float re[32], im[32];
       tmem_ld32(tl + (uint32_t)c0, re);
@@ -232,6 +293,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
         for (int i = 0; i < 32; ++i) {
           re[i] += r2[i];
           im[i] += i2[i];
+        }
+      }
+      if (split == 2) {
+        const float* pc = part + ((c0 / 32) * 2) * 32 * 128 + warp * 32 + lane;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          re[i] += pc[i * 128];
+          im[i] += pc[(32 + i) * 128];
         }
       }
       const int nb = min(32, a.B - c0);
@@ -254,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
         }
         __syncthreads();
         if ((int)threadIdx.x < nb)
-          a.loss_part[(size_t)blockIdx.x * a.B + c0 + threadIdx.x] =
+          a.loss_part[(size_t)tile * a.B + c0 + threadIdx.x] =
               ((red[0][threadIdx.x] + red[1][threadIdx.x]) + red[2][threadIdx.x]) + red[3][threadIdx.x];
         __syncthreads();
       } else if (a.mode == kDenseSpecFwd) {
@@ -322,13 +391,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
           }
           __syncthreads();
           if ((int)threadIdx.x < nb)
-            a.norm_part[(size_t)blockIdx.x * a.B + c0 + threadIdx.x] =
+            a.norm_part[(size_t)tile * a.B + c0 + threadIdx.x] =
                 ((red[0][threadIdx.x] + red[1][threadIdx.x]) + red[2][threadIdx.x]) + red[3][threadIdx.x];
           __syncthreads();
         }
       }
     }
-    if (a.mode == kDenseGdAdj && a.loss_out && blockIdx.x == 0) {
+    if (a.mode == kDenseGdAdj && a.loss_out && tile == 0) {
       for (int b = threadIdx.x; b < a.B; b += blockDim.x) {
         fsum2 acc{0.f, 0.f};
         for (int t = 0; t < a.loss_tiles; ++t) acc_add(acc, a.loss_part[(size_t)t * a.B + b]);
@@ -389,6 +458,7 @@ namespace {
 struct sr_dense {
   int64_t n = 0, m = 0;
   int device = 0;
+  int num_sms = 0;
   __nv_bfloat16* d_af = nullptr;  // Af [m][2n] as tiles [m/128][2n/64][128][64] (swizzled images)
   __nv_bfloat16* d_aa = nullptr;  // Aa [2n][m] as tiles [2n/128][m/64][128][64]
   int* d_err = nullptr;
@@ -474,9 +544,24 @@ sr_status run_gemm(sr_dense* d, sr::GemmArgs& g, const void* a_op, int64_t M, in
   const size_t smem = gemm_smem(B, &stages);
   SR_DCUDA(cudaFuncSetAttribute(sr::k_dense_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
            "cudaFuncSetAttribute");
-  sr::k_dense_gemm<<<(unsigned)(M / sr::kBM), sr::kThreads, smem, s>>>(g, stages);
+  // Split the K range over a pair of CTAs when the tiles alone would leave
+  // SMs idle and twice as many CTAs still fit (the adjoint at n << m).
+  const int tiles = (int)(M / sr::kBM);
+  const int split = (2 * tiles <= d->num_sms && (K / sr::kBK) % 2 == 0) ? 2 : 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(tiles * split));
+  cfg.blockDim = dim3(sr::kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)split;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = split == 2 ? 1 : 0;
+  SR_DCUDA(cudaLaunchKernelEx(&cfg, sr::k_dense_gemm, g, stages, split), "launch(dense gemm)");
   sr::count_launch();
-  SR_DCUDA(cudaGetLastError(), "launch(dense gemm)");
   return SR_OK;
 }
 
@@ -513,6 +598,7 @@ sr_status sr_dense_create(int64_t n, int64_t m, const float* a_host, sr_dense** 
   d->n = n;
   d->m = m;
   cudaError_t e = cudaGetDevice(&d->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d->num_sms, cudaDevAttrMultiProcessorCount, d->device);
   const size_t cnt = (size_t)m * n * 2;
   std::vector<__nv_bfloat16> af(cnt), aa(cnt);
   for (int64_t i = 0; i < m; ++i)
