@@ -502,7 +502,7 @@ def radix3_workload(torch, dev, flush):
         plan.check()
         del plan
     return {"workload": f"n = 2^16, L = {L}, B = {B}, x ~ CN(0, I), noiseless, {sp} power + {gd} GD iterations; "
-                        "m = 3 * 2^a runs each DFT as split -> power-of-two DFT of 3B sequences -> radix-3 combine",
+                        "m = 3 * 2^a runs each DFT as a power-of-two DFT of 3B stride-3 subsequences (gathered by its first pass) -> radix-3 combine",
             **out}
 
 

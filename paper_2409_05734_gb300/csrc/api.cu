@@ -119,7 +119,10 @@ void free_workspace(Plan* p) {
 
 // Size of one bank of per-tile partial sums per problem.
 int part_stride(const Plan& p) {
-  return std::max(std::max(std::max(p.geom[0].cpp, p.geom[1].cpp), p.r3_chunks), 64);
+  int s = std::max(std::max(std::max(p.geom[0].cpp, p.geom[1].cpp), p.r3_chunks), 64);
+  // radix-3: the inner first pass writes 3 banks of its tile partials per problem
+  if (p.inner) s = std::max(s, 3 * std::max(p.inner->geom[0].cpp, p.inner->geom[1].cpp));
+  return s;
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -286,6 +289,12 @@ struct Chain {
   // power iteration: apply 1/||v|| (norm_in) in the spectral epilogue instead
   // of at the chain's input (the operations before it are linear)
   bool norm_at_epilogue = false;
+  // radix-3 chains: the first pass of this inner chain reads the outer
+  // vector (PassArgs::r3), applying first_op with the outer plan's tables
+  bool r3_first = false;
+  int ym = 0;
+  const float2* first_dp = nullptr;
+  int64_t first_dp_stride = 0;
 };
 
 sr::PassArgs base_args(const Plan& p) {
@@ -351,6 +360,17 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     a.norm_in_count = c.norm_in_count;
     a.op = c.first_op;
     a.dp = p.d_dp + (size_t)c.first_d * p.m;
+    if (c.r3_first) {
+      a.r3 = 1;
+      a.ym = c.ym;
+      a.dp = c.first_dp;
+      a.dp_stride = c.first_dp_stride;
+      a.y = c.y;
+      a.sumy = c.sumy;
+      a.lam = c.lam;
+      a.weight_mode = c.weight_mode;
+      a.part_out = c.loss_part;
+    }
     a.eout = cur;
     PassTimer tm(p, 0, s);
     SR_CUDA(sr::launch_first(p, sr::s1_layout(c.s0), a, B, s), "launch(first pass)");
@@ -418,43 +438,40 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
   return SR_OK;
 }
 
-// A chain on a plan of length m = 3 mp: every DFT is split (with the operation
-// that precedes it) -> DFT of length mp over 3B sequences on the inner plan ->
-// combine; the last combine applies D_1^H (if asked), prunes to n_out and
-// applies the output mode. Buffers: e0 holds the 3B sequences (the inner chain
-// reads and rewrites it in place), e1 the natural-order vector between DFTs.
+// A chain on a plan of length m = 3 mp: every DFT is a power-of-two DFT of
+// length mp over 3B sequences on the inner plan, whose first pass gathers the
+// stride-3 subsequences of the outer vector (with the operation that precedes
+// the DFT), then a combine; the last combine applies D_1^H (if asked), prunes
+// to n_out and applies the output mode. Buffers: the inner chain writes the 3B
+// transformed sequences to e0, e1 holds the natural-order vector between DFTs.
 sr_status run_chain_r3(const Plan& p, const Chain& c, int B, cudaStream_t s) {
   const Plan& in = *p.inner;
   const float2* src = c.xin;
   int64_t n_src = c.n_in;
+  // loss partials of the GD epilogue: [3B][inner cpp] = [B][3 inner cpp]
+  const int loss_cpp = 3 * in.geom[sr::s1_layout(0)].cpp;
   for (int k = 0; k < c.nfft; ++k) {
-    sr::R3SplitArgs sa;
-    std::memset(&sa, 0, sizeof(sa));
-    sa.src = src;
-    sa.n_src = n_src;
-    sa.u = p.d_e0;
-    sa.mp = p.mp;
-    sa.chunks = p.r3_chunks;
-    sa.op = k == 0 ? c.first_op : c.mid[k].op;
-    sa.dp = p.d_dp + (size_t)(k == 0 ? c.first_d : c.mid[k].d) * p.m;
-    sa.dp_stride = p.dp_stride;
-    if (k == 0) {
-      sa.norm_in = c.norm_in;
-      sa.norm_in_count = c.norm_in_count;
-    }
-    sa.y = c.y;
-    sa.sumy = c.sumy;
-    sa.lam = c.lam;
-    sa.weight_mode = c.weight_mode;
-    sa.part_out = c.loss_part;
-    SR_CUDA(sr::launch_r3_split(sa, B, s), "launch(radix-3 split)");
     Chain ic;
     ic.nfft = 1;
     ic.dir[0] = c.dir[k];
-    ic.xin = p.d_e0;
-    ic.n_in = (int)p.mp;
+    ic.xin = src;
+    ic.n_in = (int)n_src;
     ic.xout = p.d_e0;
     ic.n_out = (int)p.mp;
+    ic.r3_first = true;
+    ic.first_op = k == 0 ? c.first_op : c.mid[k].op;
+    ic.first_dp = p.d_dp + (size_t)(k == 0 ? c.first_d : c.mid[k].d) * p.m;
+    ic.first_dp_stride = p.dp_stride;
+    ic.ym = (int)p.m;
+    if (k == 0) {
+      ic.norm_in = c.norm_in;
+      ic.norm_in_count = c.norm_in_count;
+    }
+    ic.y = c.y;
+    ic.sumy = c.sumy;
+    ic.lam = c.lam;
+    ic.weight_mode = c.weight_mode;
+    ic.loss_part = c.loss_part;
     sr_status st = run_chain(in, ic, 3 * B, s);
     if (st != SR_OK) return st;
     sr::R3CombineArgs ca;
@@ -482,7 +499,7 @@ sr_status run_chain_r3(const Plan& p, const Chain& c, int B, cudaStream_t s) {
       ca.norm_in_count = c.norm_in_count;
       ca.part_out = c.spec_part_out;
       ca.loss_part = c.loss_part;
-      ca.loss_cpp = p.r3_chunks;
+      ca.loss_cpp = loss_cpp;
       ca.loss_out = c.loss_out;
     }
     SR_CUDA(sr::launch_r3_combine(ca, c.dir[k], B, s), "launch(radix-3 combine)");

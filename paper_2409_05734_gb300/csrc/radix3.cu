@@ -4,11 +4,12 @@
 // With u_r[j] = v[3j + r] (r = 0, 1, 2; j < mp) and U_r = DFT_mp(u_r),
 //   DFT_m(v)[k' + s mp] = sum_r W_m^{r k'} W_3^{r s} U_r[k'],   k' < mp, s < 3,
 // where W_N = exp(-2 pi i / N) (forward sign; the inverse conjugates every W).
-// A chain step is then: a split kernel (the operation that precedes the DFT --
-// a diagonal, the GD or spectral epilogue -- applied at natural index, then the
-// stride-3 de-interleave into 3B sequences), the power-of-two DFT of those 3B
-// sequences by the four-step passes, and a combine kernel (twiddles, radix-3
-// butterfly, natural-order output with the chain's output mode).
+// A chain step is then: the power-of-two DFT of the 3B sequences u_r by the
+// four-step passes, whose first pass gathers the stride-3 subsequences of the
+// natural-order vector and applies the operation that precedes the DFT (a
+// diagonal, the GD or spectral epilogue) at the outer index, and a combine
+// kernel (twiddles, radix-3 butterfly, natural-order output with the chain's
+// output mode).
 #include <algorithm>
 
 #include "sr_device.cuh"
@@ -19,52 +20,6 @@ namespace {
 
 // sqrt(3)/2: imaginary part of exp(-2 pi i / 3) up to sign.
 constexpr float kS3 = 0.86602540378443864676f;
-
-__global__ void k_r3_split(const R3SplitArgs a) {
-  __shared__ float red[64];
-  __shared__ float s_scale;
-  const int b = blockIdx.y, c = blockIdx.x;
-  const int64_t mp = a.mp, m = 3 * mp;
-  const int64_t len = (mp + a.chunks - 1) / a.chunks;
-  const int64_t lo = c * len, hi = min(mp, lo + len);
-  if (threadIdx.x == 0)
-    s_scale = a.norm_in ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count))
-                        : 1.0f;
-  __syncthreads();
-  const float scale = s_scale;
-  const float2* src = a.src + (size_t)b * a.n_src;
-  const float* yb = a.y ? a.y + (size_t)b * m : nullptr;
-  const float ysc = (a.op == kOpSpecEpilogue) ? (float)m / a.sumy[b] : 0.f;
-  float2* u = a.u + (size_t)(3 * b) * mp;
-  fsum2 acc{0.f, 0.f};
-  for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const int64_t k = 3 * j + r;
-      float2 v = k < a.n_src ? src[k] : make_float2(0.f, 0.f);
-      v = cscale(v, scale);
-      if (a.op == kOpDiag) {
-        v = cmul(v, __ldg(&a.dp[(size_t)b * a.dp_stride + k]));
-      } else if (a.op == kOpDiagConj) {
-        v = cmulc(v, __ldg(&a.dp[(size_t)b * a.dp_stride + k]));
-      } else if (a.op == kOpGdEpilogue) {
-        const float res = cabs2(v) - yb[k];  // r = |z|^2 - y (Eq. 2)
-        acc_add(acc, res * res);
-        v = cscale(v, res);
-      } else if (a.op == kOpSpecEpilogue) {
-        const float yh = yb[k] * ysc;  // y_hat = m y / sum(y)
-        float t = yh;
-        if (a.weight_mode == SR_WEIGHT_OPTIMAL) t = yh > 0.f ? fmaxf(1.0f - 1.0f / yh, a.lam) : a.lam;
-        v = cscale(v, t);
-      }
-      u[(size_t)r * mp + j] = v;
-    }
-  }
-  if (a.op == kOpGdEpilogue) {
-    const float s = block_sum(acc, red);
-    if (threadIdx.x == 0) a.part_out[(size_t)b * a.chunks + c] = s;
-  }
-}
 
 template <int DIR>
 __global__ void k_r3_combine(const R3CombineArgs a) {
@@ -136,12 +91,6 @@ __global__ void k_r3_combine(const R3CombineArgs a) {
 }
 
 }  // namespace
-
-cudaError_t launch_r3_split(const R3SplitArgs& a, int B, cudaStream_t s) {
-  k_r3_split<<<dim3(a.chunks, B), 256, 0, s>>>(a);
-  count_launch();
-  return cudaGetLastError();
-}
 
 cudaError_t launch_r3_combine(const R3CombineArgs& a, int dir, int B, cudaStream_t s) {
   if (dir > 0) k_r3_combine<1><<<dim3(a.chunks, B), 256, 0, s>>>(a);

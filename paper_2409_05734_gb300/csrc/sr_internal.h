@@ -85,6 +85,10 @@ struct PassArgs {
   float lam;
   int weight_mode;
   float* part_out;         // per-tile partial sums [B * cpp]
+  // first pass of a radix-3 chain: inner problem 3 bo + r reads element
+  // 3 nat + r of outer problem bo; y and D are the outer plan's (length ym)
+  int r3;
+  int ym;
   // first pass: optional scaling of the input by 1/sqrt(sum of partials)
   const float* norm_in;
   int norm_in_count;
@@ -99,27 +103,10 @@ struct PassArgs {
   int* err;                // device status word (SR_ERR_TIMEOUT on a failed wait)
 };
 
-// Radix-3 chain step (radix3.cu): split = operation at natural index, then the
-// stride-3 de-interleave u[(3b + r) mp + j] = v[b][3j + r]; combine = twiddles
-// and radix-3 butterfly back to natural order, with the chain's output mode.
-struct R3SplitArgs {
-  const float2* src;       // [B][n_src], entries >= n_src read as zero (U)
-  int64_t n_src;
-  float2* u;               // [3B][mp]
-  int64_t mp;
-  int chunks;              // blocks per problem
-  int op;                  // PassOp
-  const float2* dp;        // diagonal (kOpDiag / kOpDiagConj)
-  int64_t dp_stride;       // complex values between problems' tables (0: one table)
-  const float* norm_in;    // input scale 1/||v|| from partials [B][norm_in_count], or null
-  int norm_in_count;
-  const float* y;          // epilogues
-  const float* sumy;
-  float lam;
-  int weight_mode;
-  float* part_out;         // kOpGdEpilogue: loss partials [B][chunks]
-};
-
+// Radix-3 chain step (radix3.cu): the stride-3 de-interleave and the operation
+// before each DFT happen in the inner plan's first pass (PassArgs::r3); combine
+// = twiddles and radix-3 butterfly back to natural order, with the chain's
+// output mode.
 struct R3CombineArgs {
   const float2* U;         // [3B][mp]
   int64_t mp;
@@ -141,7 +128,6 @@ struct R3CombineArgs {
   float* loss_out;
 };
 
-cudaError_t launch_r3_split(const R3SplitArgs& a, int B, cudaStream_t s);
 cudaError_t launch_r3_combine(const R3CombineArgs& a, int dir, int B, cudaStream_t s);
 
 struct Plan {
@@ -181,10 +167,11 @@ struct Plan {
   bool host_theta_stale = false;
   CUtensorMap tmap[2][2];  // [buffer e0/e1][layout]: rows of the exchange buffer
   // m = 3 mp: DFTs of length mp over 3B sequences run on `inner` (a power-of-two
-  // plan, n = m = mp), with the radix-3 split and combine around them
+  // plan, n = m = mp; its first pass gathers the stride-3 subsequences), then
+  // the radix-3 combine
   Plan* inner = nullptr;
   int64_t mp = 0;
-  int r3_chunks = 0;             // blocks per problem of the split / combine kernels
+  int r3_chunks = 0;             // blocks per problem of the combine kernel
   float2* d_tw3 = nullptr;       // W_m^j, j < 2 mp
   // optional per-pass event timing (sr_plan_set_timing)
   bool timing = false;
