@@ -12,6 +12,8 @@ What it computes, in float64 / complex128, following the paper step by step:
   a step), the structured sensing operator A = F D_L ... F D_1 U of Sec. III,
   Eq. 5 (alpha > 1 branch) and its adjoint, and an explicitly materialised
   dense copy of A for tiny sizes.
+* ``operator2d`` -- the same model on h x w images with the unitary 2D DFT of
+  an S x S zero-padded grid (the form the experiments of Sec. IV run).
 * ``recovery``  -- the l2 intensity loss and its gradient (Sec. II-B-1, Eq. 2),
   the spectral initialisation by shifted power iteration on the weighted
   covariance (Sec. II-B-2, Eq. 3-4), gradient descent (Sec. IV-A), and the
@@ -49,6 +51,16 @@ from .recovery import (
     relative_error_global_phase,
     structured_ops,
 )
+from .operator2d import (
+    unitary_fft2,
+    unitary_ifft2,
+    zero_pad_2d,
+    crop_2d,
+    forward_2d,
+    adjoint_2d,
+    dense_structured_matrix_2d,
+    structured_ops_2d,
+)
 from .dense_iid import dense_forward, dense_adjoint, dense_ops
 from . import autodiff
 
@@ -57,5 +69,6 @@ __all__ = [
     "adjoint", "dense_structured_matrix", "intensity_loss", "loss_and_grad",
     "spectral_weights", "spectral_init", "gradient_descent", "step_ramp", "cosine_similarity",
     "relative_error_global_phase", "structured_ops", "dense_forward", "dense_adjoint",
-    "dense_ops", "autodiff",
+    "dense_ops", "autodiff", "unitary_fft2", "unitary_ifft2", "zero_pad_2d", "crop_2d",
+    "forward_2d", "adjoint_2d", "dense_structured_matrix_2d", "structured_ops_2d",
 ]

@@ -13,7 +13,8 @@ bit for bit.
 
 Counter convention (one Philox block per drawn element):
     ctr = (index mod 2^32, index div 2^32, sub, stream),  key = (seed mod 2^32, seed div 2^32)
-Streams: 0 signal x, 1 phases theta, 2 start vector v0, 3 noise, 4 dense i.i.d. matrix.
+Streams: 0 signal x, 1 phases theta, 2 start vector v0, 3 noise, 4 dense i.i.d. matrix,
+5 phase-image ellipses.
 A uniform draw is u = (word >> 8) * 2^-24, exact in float64, in [0, 1).
 """
 from __future__ import annotations
@@ -25,6 +26,7 @@ STREAM_THETA = 1
 STREAM_START = 2
 STREAM_NOISE = 3
 STREAM_DENSE = 4
+STREAM_IMAGE = 5
 
 # Philox4x32 constants as published: the two round multipliers and the two
 # Weyl-sequence key increments (golden ratio and sqrt(3)-1 in 0.32 fixed point).
@@ -117,6 +119,38 @@ def signal_amplitude_phase(seed: int, B: int, n: int) -> np.ndarray:
     a = uniform_from_word(w0)
     phi = 2.0 * np.pi * uniform_from_word(w1)
     return (a * np.exp(1j * phi)).reshape(B, n)
+
+
+def phase_image_ellipses(seed: int, B: int, h: int, w: int, count: int = 10) -> np.ndarray:
+    """Phantom-like phase images, [B, h*w] row-major, unit magnitude.
+
+    Stands in for the paper's benchmark image (Sec. IV-A: a Shepp-Logan phantom
+    whose grey levels in [0, 1) become phases in [-pi/2, pi/2)): each image sums
+    `count` random filled ellipses (centre, semi-axes, rotation and grey-level
+    increment drawn from Philox stream 5, sub-stream = image index), clips the
+    grey level to [0, 1) and maps it linearly to a phase phi in [-pi/2, pi/2),
+    x = exp(i phi).
+    """
+    yy, xx = np.meshgrid((np.arange(h) + 0.5) / h * 2.0 - 1.0, (np.arange(w) + 0.5) / w * 2.0 - 1.0,
+                         indexing="ij")
+    out = np.empty((B, h * w), dtype=np.complex128)
+    for b in range(B):
+        w0, w1, w2, w3 = _blocks(seed, 2 * count, b, STREAM_IMAGE)
+        u = np.stack([uniform_from_word(w0), uniform_from_word(w1), uniform_from_word(w2),
+                      uniform_from_word(w3)])  # [4, 2 * count]
+        grey = np.zeros((h, w))
+        for e in range(count):
+            cy, cx = 1.2 * u[0, e] - 0.6, 1.2 * u[1, e] - 0.6
+            ay, ax = 0.1 + 0.6 * u[2, e], 0.1 + 0.6 * u[3, e]
+            rot = np.pi * u[0, count + e]
+            inc = 0.1 + 0.4 * u[1, count + e]
+            cs, sn = np.cos(rot), np.sin(rot)
+            dy, dx = yy - cy, xx - cx
+            py, px = cs * dy + sn * dx, -sn * dy + cs * dx
+            grey += inc * ((py / ay) ** 2 + (px / ax) ** 2 <= 1.0)
+        grey = np.clip(grey, 0.0, np.nextafter(1.0, 0.0))
+        out[b] = np.exp(1j * np.pi * (grey - 0.5)).reshape(-1)
+    return out
 
 
 def start_vector(seed: int, B: int, n: int) -> np.ndarray:
