@@ -506,6 +506,42 @@ def radix3_workload(torch, dev, flush):
             **out}
 
 
+def two_d_workload(torch, dev, flush):
+    """The 2D model the experiments of Sec. IV run: B = 64 phantom-like 128 x 128
+    phase images zero-padded to 256 x 256 (alpha = 4), L = 2, noiseless, 100 power
+    + 500 GD iterations (the headline's solve), graph-replayed; and L = 3, whose
+    odd layer count leaves the forward on the transposed grid."""
+    from paper_2409_05734_gb300 import Plan2D
+    import synthetic as S
+    out = {}
+    h = w = 128
+    S_, B, sp, gd = 256, 64, 100, 500
+    x_np = S.phase_image_ellipses(20240905, B, h, w)
+    x_true = torch.from_numpy(x_np).to(torch.complex64).to(dev)
+    for L in (2, 3):
+        plan = Plan2D(h, w, S_, L, 20240905)
+        plan.reserve(B)
+        y = (plan.forward(x_true).abs() ** 2).contiguous()
+        v0 = torch.from_numpy(S.start_vector(20240905, B, h * w)).to(torch.complex64).to(dev)
+        x = torch.empty_like(v0)
+
+        def solve():
+            plan.spectral_init(y, v0, sp, weight="optimal", out=x)
+            plan.gd_solve(y, x, gd, mu0=0.15, tau0=100.0)
+
+        ms = timed_graph(torch, solve, flush)
+        it = sp + gd
+        W = dict(n=h * w, m=S_ * S_, L=L, B=B)
+        out[f"L={L}"] = {"ms_per_solve": ms, "problem_iters_per_s": B * it / (ms / 1e3),
+                         "algorithmic_gbs": iteration_bytes(W) * it / (ms / 1e3) / 1e9,
+                         "median_rel_err_global_phase": median_rel_err(torch, x, x_true)}
+        plan.check()
+        del plan
+    return {"workload": f"B = {B} phantom-like phase images {h} x {w} (Philox ellipses, phase in [-pi/2, pi/2)) "
+                        f"in a {S_} x {S_} grid (alpha = 4), 2D unitary DFTs, noiseless, {sp} power (optimal "
+                        f"weights) + {gd} GD iterations, graph-replayed", **out}
+
+
 def autograd_workload(torch, dev, flush):
     """Forward and backward of the differentiable operator (x, theta) -> z = A x at
     B = 8, n = 2^20, m = 2^22, L = 2, driven by a loss on |z|^2."""
@@ -789,6 +825,7 @@ def run_ours(args):
         line["dense_iid_comparison"] = dense_comparison(torch, dev, flush)
     if rank == 0 and not args.no_extra:
         line["radix3_batch"] = radix3_workload(torch, dev, flush)
+        line["two_dimensional"] = two_d_workload(torch, dev, flush)
         line["differentiable_operator"] = autograd_workload(torch, dev, flush)
     if rank == 0 and not args.no_ragged:
         line["ragged_batch"] = ragged_workload(torch, dev, flush)

@@ -95,6 +95,19 @@ sr_status sr_phases(uint64_t seed, int L, int64_t m, double* theta);
 sr_status sr_plan_create(int64_t n, int64_t m, int L, uint64_t seed, sr_plan** out);
 sr_status sr_plan_destroy(sr_plan* plan); /* NULL is accepted (no-op) */
 
+/* sr_plan_create_2d: the 2D form of the operator that the experiments of
+ * Sec. IV run (a 2D FFT on zero-padded images): A = F2 D_L ... F2 D_1 U2 with
+ * x an h x w image (row-major, n = h*w entries, pixel (r, c) at r*w + c), U2
+ * placing it in the top-left corner of an S x S grid (zeros elsewhere), F2 the
+ * unitary 2D DFT of the grid, F2[(a,b),(r,c)] = exp(-2 pi i (r a + c b)/S) / S,
+ * and D_l = diag(exp(i theta_l)) over the grid in row-major order (m = S*S;
+ * theta as sr_phases(seed, L, S*S)). z = A x and every m-length array (y, the
+ * adjoint's input) are row-major grids. S must be a power of two in
+ * [2, 4096] and 1 <= h, w <= S (else SR_ERR_UNSUPPORTED). The plan accepts
+ * every call of a 1D plan except sr_plan_set_phases_device, sr_backward,
+ * sr_forward_noalloc and the ragged calls (SR_ERR_UNSUPPORTED). */
+sr_status sr_plan_create_2d(int64_t h, int64_t w, int64_t S, int L, uint64_t seed, sr_plan** out);
+
 /* Copies the plan's phases (double[L*m], host) out / replaces them from host
  * memory (the diagonal tables are rebuilt synchronously). */
 sr_status sr_plan_get_phases(const sr_plan* plan, double* theta);

@@ -3,6 +3,7 @@
 // twiddle tables computed in double and rounded to float), workspace, and the
 // orchestration of the pass kernels into the operator applications and solver
 // loops of the paper (Sec. II-B, Sec. III).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -112,8 +113,10 @@ void free_workspace(Plan* p) {
   cudaFree(p->d_e1);
   cudaFree(p->d_part);
   cudaFree(p->d_scal);
+  cudaFree(p->d_yt);
   p->d_e0 = p->d_e1 = nullptr;
   p->d_part = p->d_scal = nullptr;
+  p->d_yt = nullptr;
   p->B_cap = 0;
 }
 
@@ -169,7 +172,8 @@ sr_status ensure_workspace(Plan* p, int B) {
   sr_status st;
   if ((st = dalloc(&p->d_e0, bm)) != SR_OK || (st = dalloc(&p->d_e1, bm)) != SR_OK ||
       (st = dalloc(&p->d_part, (size_t)kPartBanks * B * part_stride(*p))) != SR_OK ||
-      (st = dalloc(&p->d_scal, (size_t)4 * B)) != SR_OK) {
+      (st = dalloc(&p->d_scal, (size_t)4 * B)) != SR_OK ||
+      (p->two_d && p->L % 2 == 1 && (st = dalloc(&p->d_yt, bm)) != SR_OK)) {
     free_workspace(p);
     return st;
   }
@@ -215,7 +219,12 @@ sr_status upload_diagonals(Plan* p) {
   const double scale = 1.0 / std::sqrt((double)m);
   std::vector<float2> host((size_t)p->L * m);
   for (size_t i = 0; i < host.size(); ++i) {
-    const double t = p->theta[i];
+    // 2D grids: layers 2, 4, ... act on the transposed grid (see grid_index),
+    // so their tables are stored transposed: entry (r, c) holds D(c, r)
+    size_t src = i;
+    const int64_t l = (int64_t)(i / m), k = (int64_t)(i % m);
+    if (p->two_d && l % 2 == 1) src = (size_t)(l * m + (k % p->gS) * p->gS + k / p->gS);
+    const double t = p->theta[src];
     host[i] = make_float2((float)(std::cos(t) * scale), (float)(std::sin(t) * scale));
   }
   SR_CUDA(cudaMemcpy(p->d_dp, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice),
@@ -236,6 +245,11 @@ sr_status upload_twiddles(Plan* p) {
   std::vector<float2> lo(nlo), hi(nhi);
   for (int64_t j = 0; j < nlo; ++j) lo[j] = root_of_unity(j, p->m);
   for (int64_t j = 0; j < nhi; ++j) hi[j] = root_of_unity(j * nlo, p->m);
+  if (p->two_d) {
+    // the 2D DFT of an S x S grid is the four-step DFT without its twiddles
+    std::fill(lo.begin(), lo.end(), make_float2(1.f, 0.f));
+    std::fill(hi.begin(), hi.end(), make_float2(1.f, 0.f));
+  }
   sr_status st;
   if ((st = dalloc(&p->d_twl, twl.size())) != SR_OK || (st = dalloc(&p->d_tw_lo, lo.size())) != SR_OK ||
       (st = dalloc(&p->d_tw_hi, hi.size())) != SR_OK)
@@ -293,6 +307,10 @@ struct Chain {
   // vector (PassArgs::r3), applying first_op with the outer plan's tables
   bool r3_first = false;
   int ym = 0;
+  // 2D plans: the chain's input / output is the transpose of the grid
+  // (the forward's output and the adjoint's input when L is odd)
+  int in_tr = 0;
+  int out_tr = 0;
   const float2* first_dp = nullptr;
   int64_t first_dp_stride = 0;
 };
@@ -360,6 +378,11 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     a.norm_in_count = c.norm_in_count;
     a.op = c.first_op;
     a.dp = p.d_dp + (size_t)c.first_d * p.m;
+    if (p.two_d) {
+      a.in_h = c.n_in == p.m ? p.gS : p.gh;
+      a.in_w = c.n_in == p.m ? p.gS : p.gw;
+      a.in_tr = c.in_tr;
+    }
     if (c.r3_first) {
       a.r3 = 1;
       a.ym = c.ym;
@@ -427,6 +450,11 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     a.loss_part = c.loss_part;
     a.loss_cpp = loss_cpp;
     a.loss_out = c.loss_out;
+    if (p.two_d) {
+      a.out_h = c.n_out == p.m ? p.gS : p.gh;
+      a.out_w = c.n_out == p.m ? p.gS : p.gw;
+      a.out_tr = c.out_tr;
+    }
     PassTimer tm(p, 2, s);
     if (c.fuse_next_first) {
       a.eout = p.d_e0;  // the next step's FIRST output (cur is e1 here: 2L - 1 middle passes)
@@ -525,6 +553,17 @@ Chain round_trip_chain(const Plan& p, int epilogue_op) {
   return c;
 }
 
+// The measurements in the layout of the epilogue pass: y itself, or for 2D
+// plans with odd L (the grid is transposed after L twiddle-free DFTs) a
+// transposed copy in the plan's workspace.
+sr_status epilogue_y(Plan* p, const float* y, int B, cudaStream_t s, const float** out) {
+  *out = y;
+  if (!(p->two_d && p->L % 2 == 1)) return SR_OK;
+  SR_CUDA(sr::launch_transpose_grids(y, p->d_yt, p->gS, B, s), "launch(transpose y)");
+  *out = p->d_yt;
+  return SR_OK;
+}
+
 // sum(y) per problem (and the GD step mu0 * m / sum(y)) into the scalar workspace.
 sr_status prepare_y(Plan* p, const float* y, int B, float mu0, cudaStream_t s) {
   const int chunks = (int)std::min<int64_t>(64, (p->m + 4095) / 4096);
@@ -601,7 +640,12 @@ sr_status sr_phases(uint64_t seed, int L, int64_t m, double* theta) {
   return SR_OK;
 }
 
-sr_status sr_plan_create(int64_t n, int64_t m, int L, uint64_t seed, sr_plan** out) {
+}  // extern "C"
+
+namespace {
+// Plan construction shared by the 1D and the 2D entry points; gS > 0 makes a
+// 2D plan of gh x gw images in a gS x gS grid (n = gh * gw, m = gS * gS).
+sr_status create_plan(int64_t n, int64_t m, int L, uint64_t seed, int gh, int gw, int gS, sr_plan** out) {
   if (!out) return fail(SR_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   sr_status st = check_sizes(n, m, L);
@@ -612,6 +656,10 @@ sr_status sr_plan_create(int64_t n, int64_t m, int L, uint64_t seed, sr_plan** o
   p->m = m;
   p->L = L;
   p->seed = seed;
+  p->two_d = gS > 0;
+  p->gh = gh;
+  p->gw = gw;
+  p->gS = gS;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) {
     delete p;
@@ -674,6 +722,21 @@ sr_status sr_plan_create(int64_t n, int64_t m, int L, uint64_t seed, sr_plan** o
   *out = p;
   return SR_OK;
 }
+}  // namespace
+
+extern "C" {
+
+sr_status sr_plan_create(int64_t n, int64_t m, int L, uint64_t seed, sr_plan** out) {
+  return create_plan(n, m, L, seed, 0, 0, 0, out);
+}
+
+sr_status sr_plan_create_2d(int64_t h, int64_t w, int64_t S, int L, uint64_t seed, sr_plan** out) {
+  if (!out) return fail(SR_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (S < 2 || S > 4096 || !is_pow2(S)) return fail(SR_ERR_UNSUPPORTED, "S must be a power of two in [2, 4096]");
+  if (h < 1 || w < 1 || h > S || w > S) return fail(SR_ERR_UNSUPPORTED, "need 1 <= h <= S and 1 <= w <= S");
+  return create_plan(h * w, S * S, L, seed, (int)h, (int)w, (int)S, out);
+}
 
 sr_status sr_plan_destroy(sr_plan* plan) {
   if (!plan) return SR_OK;
@@ -711,6 +774,7 @@ sr_status sr_plan_get_phases(const sr_plan* plan_c, double* theta) {
 
 sr_status sr_plan_set_phases_device(sr_plan* plan, const float* theta, void* stream) {
   if (!plan || !theta) return fail(SR_ERR_INVALID_ARG, "NULL argument");
+  if (plan->two_d) return fail(SR_ERR_UNSUPPORTED, "device phases are not supported on 2D plans");
   sr_status st = check_device(plan);
   if (st != SR_OK) return st;
   const size_t count = (size_t)plan->L * plan->m;
@@ -832,6 +896,7 @@ sr_status sr_forward(sr_plan* plan, const void* x, void* z, int B, void* stream)
   c.xout = (float2*)z;
   c.n_out = (int)p.m;
   c.out_mode = sr::kOutStore;
+  c.out_tr = p.two_d && p.L % 2 == 1;  // 2D: L twiddle-free DFTs leave the grid transposed for odd L
   return run_chain(p, c, B, (cudaStream_t)stream);
 }
 
@@ -849,6 +914,7 @@ sr_status sr_adjoint(sr_plan* plan, const void* z, void* x, int B, void* stream)
   c.last_op = sr::kOpDiagConj;
   c.xin = (const float2*)z;
   c.n_in = (int)p.m;
+  c.in_tr = p.two_d && p.L % 2 == 1;  // 2D: read the grid in the layout the forward leaves it in
   c.xout = (float2*)x;
   c.n_out = (int)p.n;
   c.out_mode = sr::kOutStore;
@@ -863,13 +929,15 @@ sr_status sr_loss_grad(sr_plan* plan, const void* x, const float* y, float* loss
   Plan& p = *plan;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = prepare_y(&p, y, B, 0.f, s)) != SR_OK) return st;
+  const float* ye = nullptr;
+  if ((st = epilogue_y(&p, y, B, s, &ye)) != SR_OK) return st;
   Chain c = round_trip_chain(p, sr::kOpGdEpilogue);
   c.xin = (const float2*)x;
   c.n_in = (int)p.n;
   c.xout = (float2*)grad;
   c.n_out = (int)p.n;
   c.out_mode = sr::kOutGrad;
-  c.y = y;
+  c.y = ye;
   c.loss_part = part_bank(p, 2, B);
   c.loss_out = loss;
   return run_chain(p, c, B, s);
@@ -894,6 +962,8 @@ sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int it
     SR_CUDA(cudaMemcpyAsync(x_out, v0, (size_t)B * n * sizeof(float2), cudaMemcpyDeviceToDevice, s),
             "cudaMemcpyAsync(v0)");
   if ((st = prepare_y(&p, y, B, 0.f, s)) != SR_OK) return st;
+  const float* ye = nullptr;
+  if ((st = epilogue_y(&p, y, B, s, &ye)) != SR_OK) return st;
   float2* v = (float2*)x_out;
   const int init_chunks = std::min(64, (n + 4095) / 4096);
   float* bank[2] = {part_bank(p, 0, B), part_bank(p, 1, B)};
@@ -906,7 +976,7 @@ sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int it
   c.n_out = n;
   c.out_mode = sr::kOutSpec;
   c.shift = o.weight_mode == SR_WEIGHT_IDENTITY ? 0.f : -2.0f * o.lambda;
-  c.y = y;
+  c.y = ye;
   c.sumy = p.d_scal;
   c.lam = o.lambda;
   c.weight_mode = o.weight_mode;
@@ -943,6 +1013,8 @@ sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters, const s
   Plan& p = *plan;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = prepare_y(&p, y, B, mu0, s)) != SR_OK) return st;
+  const float* ye = nullptr;
+  if ((st = epilogue_y(&p, y, B, s, &ye)) != SR_OK) return st;
   Chain c = round_trip_chain(p, sr::kOpGdEpilogue);
   c.xin = (const float2*)x;
   c.n_in = (int)p.n;
@@ -950,7 +1022,7 @@ sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters, const s
   c.n_out = (int)p.n;
   c.out_mode = sr::kOutGd;
   c.mu = p.d_scal + B;
-  c.y = y;
+  c.y = ye;
   c.loss_part = part_bank(p, 2, B);
   // Consecutive steps share a kernel: the last pass of step t also runs the
   // first pass of step t+1 (same lines, x_{t+1} still in registers).
@@ -1021,6 +1093,7 @@ sr_status sr_backward(sr_plan* plan, const void* x, const void* gz, void* grad_x
   sr_status st = check_plan_call(plan, B);
   if (st != SR_OK) return st;
   if (!x || !gz) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
+  if (plan->two_d) return fail(SR_ERR_UNSUPPORTED, "the backward pass is not supported on 2D plans");
   if (!grad_x && !grad_theta) return SR_OK;
   if ((st = ensure_backward_buffers(plan, B)) != SR_OK) return st;
   Plan& p = *plan;

@@ -100,6 +100,31 @@ __global__ void k_conj_diag_prune(const float2* __restrict__ h, const float2* __
   }
 }
 
+// yt[b] = transpose of the S x S row-major grid y[b], through 32 x 32 tiles in
+// shared memory (both sides coalesced). Grid (S/32 or 1, S/32 or 1, B) of
+// 32 x 8 threads; S a power of two.
+__global__ void k_transpose_grids(const float* __restrict__ y, float* __restrict__ yt, int S) {
+  __shared__ float tile[32][33];
+  const size_t base = (size_t)blockIdx.z * S * S;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    if (r < S && c < S) tile[k][threadIdx.x] = y[base + (size_t)r * S + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int r = c0 + k, c = r0 + threadIdx.x;  // output row = input column
+    if (r < S && c < S) yt[base + (size_t)r * S + c] = tile[threadIdx.x][k];
+  }
+}
+
+cudaError_t launch_transpose_grids(const float* y, float* yt, int S, int B, cudaStream_t s) {
+  const int t = (S + 31) / 32;
+  k_transpose_grids<<<dim3(t, t, B), dim3(32, 8), 0, s>>>(y, yt, S);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // Failure-path probe: one thread waits on an mbarrier that nothing ever
 // completes, through the same bounded wait the pass kernels use; when the wait
 // gives up it records SR_ERR_TIMEOUT in the plan's status word and returns.
@@ -172,7 +197,7 @@ static PassArgs with_geom(const PassArgs& a0, const Plan& p, const LineGeom& g, 
 
 cudaError_t launch_first(const Plan& p, Layout lay, const PassArgs& a0, int B, cudaStream_t s) {
   const LineGeom& g = p.geom[lay];
-  auto fn = reinterpret_cast<void (*)(PassArgs)>(const_cast<void*>(pick_first(g.ell, g.T, a0.out_dir)));
+  auto fn = reinterpret_cast<void (*)(PassArgs)>(const_cast<void*>(pick_first(g.ell, g.T, a0.out_dir, p.two_d)));
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = allow_smem((const void*)fn, g.smem_first);
   if (e != cudaSuccess) return e;
@@ -185,7 +210,7 @@ cudaError_t launch_first(const Plan& p, Layout lay, const PassArgs& a0, int B, c
 static cudaError_t launch_pipe(bool last, const Plan& p, Layout lay, const PassArgs& a0, int B, cudaStream_t s) {
   const LineGeom& g = p.geom[lay];
   auto fn = reinterpret_cast<void (*)(PassArgs, int)>(
-      const_cast<void*>(last ? pick_last(g.ell, g.T, a0.in_dir, g.nl) : pick_mid(g.ell, g.T, a0.in_dir, a0.out_dir, g.nl)));
+      const_cast<void*>(last ? pick_last(g.ell, g.T, a0.in_dir, g.nl, p.two_d) : pick_mid(g.ell, g.T, a0.in_dir, a0.out_dir, g.nl)));
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = allow_smem((const void*)fn, g.smem_pipe);
   if (e != cudaSuccess) return e;
@@ -206,7 +231,7 @@ cudaError_t launch_last(const Plan& p, Layout lay, const PassArgs& a, int B, cud
 
 cudaError_t launch_last_first(const Plan& p, Layout lay, const PassArgs& a0, int B, cudaStream_t s) {
   const LineGeom& g = p.geom[lay];
-  auto fn = reinterpret_cast<void (*)(PassArgs, int)>(const_cast<void*>(pick_last_first(g.ell, g.T, g.nl)));
+  auto fn = reinterpret_cast<void (*)(PassArgs, int)>(const_cast<void*>(pick_last_first(g.ell, g.T, g.nl, p.two_d)));
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = allow_smem((const void*)fn, g.smem_pipe);
   if (e != cudaSuccess) return e;
@@ -222,8 +247,8 @@ cudaError_t pass_occupancy(const LineGeom& g, int* per_sm_mid, int* per_sm_last,
   const int pairs[3][2] = {{-1, -1}, {-1, 1}, {1, 1}};
   for (int k = 0; k < 6; ++k) {
     const void* fn = k < 3   ? pick_mid(g.ell, g.T, pairs[k][0], pairs[k][1], g.nl)
-                     : k < 5 ? pick_last(g.ell, g.T, k == 3 ? -1 : 1, g.nl)
-                             : pick_last_first(g.ell, g.T, g.nl);
+                     : k < 5 ? pick_last(g.ell, g.T, k == 3 ? -1 : 1, g.nl, 0)
+                             : pick_last_first(g.ell, g.T, g.nl, 0);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem(fn, g.smem_pipe);
     if (e != cudaSuccess) return e;

@@ -210,9 +210,24 @@ __device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, 
   }
 }
 
+// 2D grids (S x S, row-major; MAP = 1 kernels). Without its twiddles the
+// four-step DFT of a grid is the 2D DFT with its output transposed, so a chain
+// alternates between the grid and its transpose: layout element (row, col)
+// holds signal entry (col, row) when `tr` is set. Flat index of the entry of an
+// h x w row-major signal that layout element (row, col) holds, or -1 outside
+// the h x w corner (the zero padding U2 and the crop U2^H).
+__device__ __forceinline__ int grid_index(int row, int col, int h, int w, int tr) {
+  if (tr) {
+    const int t = row;
+    row = col;
+    col = t;
+  }
+  return (row < h && col < w) ? row * w + col : -1;
+}
+
 // ------------------------------------------------------------ FIRST pass
 
-template <int ELL, int T, int DB>
+template <int ELL, int T, int DB, int MAP = 0>
 __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     k_first(const __grid_constant__ PassArgs a) {
   using TL = Tile<ELL, T>;
@@ -243,13 +258,20 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   // Natural-order input, zero beyond n_in (the padding U): element (line g,
   // position q) is x[q*NL + g]; the warp reads T consecutive elements.
   const float2* xb = a.xin + (size_t)bo * a.n_in;
+  // (2D grids: the signal entry at grid_index, tables at the layout index nat)
   float2 v[E];
   int idx[E];
 #pragma unroll
   for (int j = 0; j < E; ++j) {
     const int nat = (p + j * P) * a.nl + g;
-    idx[j] = a.r3 ? 3 * nat + rr : nat;
-    v[j] = idx[j] < a.n_in ? xb[idx[j]] : make_float2(0.f, 0.f);
+    if constexpr (MAP) {
+      idx[j] = nat;
+      const int xi = grid_index(p + j * P, g, a.in_h, a.in_w, a.in_tr);
+      v[j] = xi >= 0 ? xb[xi] : make_float2(0.f, 0.f);
+    } else {
+      idx[j] = a.r3 ? 3 * nat + rr : nat;
+      v[j] = idx[j] < a.n_in ? xb[idx[j]] : make_float2(0.f, 0.f);
+    }
   }
   if (a.op == kOpDiag) {
     const float2* dp = a.dp + (size_t)bo * a.dp_stride;
@@ -431,7 +453,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   });
 }
 
-template <int ELL, int T, int DA, int NLC = 0>
+template <int ELL, int T, int DA, int NLC = 0, int MAP = 0>
 __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     k_last(const __grid_constant__ PassArgs a, int nbuf) {
   using TL = Tile<ELL, T, NLC>;
@@ -466,22 +488,28 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int nat = (p + j * P) * TL::nl(a) + g;
-      if (nat >= a.n_out) continue;
+      int oi = nat;  // output index (2D grids: grid_index; tables stay at nat)
+      if constexpr (MAP) {
+        oi = grid_index(p + j * P, g, a.out_h, a.out_w, a.out_tr);
+        if (oi < 0) continue;
+      } else {
+        if (nat >= a.n_out) continue;
+      }
       float2 val = v[j];
       if (a.op == kOpDiagConj) val = cmulc(val, __ldg(&a.dp[(size_t)b * a.dp_stride + nat]));
       if (a.out_mode == kOutStore) {
-        xb[nat] = val;
+        xb[oi] = val;
       } else if (a.out_mode == kOutGrad) {
-        xb[nat] = cscale(val, 2.0f);
+        xb[oi] = cscale(val, 2.0f);
       } else if (a.out_mode == kOutGd) {
-        float2 x = xb[nat];
+        float2 x = xb[oi];
         x.x = fmaf(-mu2, val.x, x.x);
         x.y = fmaf(-mu2, val.y, x.y);
-        xb[nat] = x;
+        xb[oi] = x;
       } else {  // kOutSpec
-        const float2 old = xb[nat];
+        const float2 old = xb[oi];
         const float2 u = make_float2(fmaf(sh, old.x, val.x), fmaf(sh, old.y, val.y));
-        xb[nat] = u;
+        xb[oi] = u;
         acc_add(acc, cabs2(u));
       }
     }
@@ -503,7 +531,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 // registers, U (zeros beyond n), D_1 and step 1 of the next step's first
 // forward DFT, with the four-step twiddles, into the exchange buffer `eout`.
 // Each D_1 entry is loaded once for both uses.
-template <int ELL, int T, int NLC = 0>
+template <int ELL, int T, int NLC = 0, int MAP = 0>
 __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     k_last_first(const __grid_constant__ PassArgs a, int nbuf) {
   using TL = Tile<ELL, T, NLC>;
@@ -542,10 +570,12 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int nat = (p + j * P) * TL::nl(a) + g;
-      if (nat < a.n_out) {
+      // signal index (2D grids: grid_index, with U2 and U2^H the same corner)
+      const int xi = MAP ? grid_index(p + j * P, g, a.out_h, a.out_w, 0) : (nat < a.n_out ? nat : -1);
+      if (xi >= 0) {
         const float2 d = __ldg(&dp[nat]);
         const float2 gr = cmulc(v[j], d);
-        float2 x = xb[nat];
+        float2 x = xb[xi];
         if (spec) {  // u = M v + shift v with v = x / ||x|| (x unnormalised)
           x = make_float2(fmaf(sh, x.x, gr.x), fmaf(sh, x.y, gr.y));
           acc_add(acc, cabs2(x));
@@ -553,7 +583,7 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
           x.x = fmaf(-mu2, gr.x, x.x);
           x.y = fmaf(-mu2, gr.y, x.y);
         }
-        xb[nat] = x;
+        xb[xi] = x;
         v[j] = cmul(x, d);
       } else {
         v[j] = make_float2(0.f, 0.f);
@@ -577,13 +607,19 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   X(2, 2) X(2, 4) X(4, 2) X(4, 4) X(4, 8) X(8, 4) X(8, 8) X(8, 16) X(16, 8) X(16, 16) X(16, 32) X(32, 16)    \
   X(32, 32) X(32, 64) X(64, 32) X(64, 64) X(128, 32) X(256, 16) X(512, 8) X(1024, 8) X(2048, 4) X(4096, 2)
 
+// The (line length, lines per CTA) pairs of square grids m = S * S, S = 2 .. 4096
+// (line length S): the shapes with 2D-grid (MAP = 1) kernels.
+#define SR_SQUARE_SHAPES(X) \
+  X(2, 2) X(4, 4) X(8, 8) X(16, 16) X(32, 32) X(64, 64) X(128, 32) X(256, 16) X(512, 8) X(1024, 8) X(2048, 4) X(4096, 2)
+
 // Kernel entry points by tile shape and transform direction (nullptr when the
-// combination is not instantiated). Defined in pass_first.cu / pass_mid.cu / pass_last.cu.
-const void* pick_first(int ell, int T, int db);
+// combination is not instantiated). Defined in pass_first.cu / pass_mid.cu /
+// pass_last.cu / pass_last_first.cu. map != 0 selects the 2D-grid variants.
+const void* pick_first(int ell, int T, int db, int map);
 // nl selects a kernel specialised for that line count when one exists.
 const void* pick_mid(int ell, int T, int da, int db, int nl);
-const void* pick_last(int ell, int T, int da, int nl);
-const void* pick_last_first(int ell, int T, int nl);
+const void* pick_last(int ell, int T, int da, int nl, int map);
+const void* pick_last_first(int ell, int T, int nl, int map);
 
 // Line counts with specialised kernels: (ELL, T, NL) = (256, 16, 256), i.e. m = 2^16.
 #define SR_NL_SPECIAL(ell, T, nl) ((ell) == 256 && (T) == 16 && (nl) == 256)

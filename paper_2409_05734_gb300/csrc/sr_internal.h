@@ -89,6 +89,10 @@ struct PassArgs {
   // 3 nat + r of outer problem bo; y and D are the outer plan's (length ym)
   int r3;
   int ym;
+  // 2D grids (MAP = 1 kernels): signal shapes and transposition of the first
+  // pass's input and the last pass's output (see grid_index)
+  int in_h, in_w, in_tr;
+  int out_h, out_w, out_tr;
   // first pass: optional scaling of the input by 1/sqrt(sum of partials)
   const float* norm_in;
   int norm_in_count;
@@ -143,6 +147,12 @@ struct Plan {
   int64_t dp_stride = 0;         // L * m when every problem of the batch has its own phases
   int batch_fixed = 0;           // with per-problem phases: the only valid batch size
   int tuned_per_sm = 0;          // persistent-grid CTAs per SM chosen by sr_plan_autotune (0: occupancy)
+  // 2D model on h x w images in an S x S grid (m = S * S, n = h * w): unit
+  // four-step twiddles, diagonals of even layers stored transposed, and for
+  // odd L a transposed copy of y (d_yt, [B][m]) for the epilogues
+  bool two_d = false;
+  int gh = 0, gw = 0, gS = 0;
+  float* d_yt = nullptr;
   float2* d_twl = nullptr;       // [lmax]
   float2* d_tw_hi = nullptr;
   float2* d_tw_lo = nullptr;
@@ -193,6 +203,8 @@ Layout s2_layout(int parity);
 // Pass launchers (fourstep.cu). B problems; the middle and last passes run a
 // persistent grid of min(tiles, per_sm * SMs) CTAs.
 cudaError_t launch_first(const Plan& p, Layout lay, const PassArgs& a, int B, cudaStream_t s);
+// yt[b] = y[b]^T for B row-major S x S float grids (2D plans with odd L)
+cudaError_t launch_transpose_grids(const float* y, float* yt, int S, int B, cudaStream_t s);
 cudaError_t launch_mid(const Plan& p, Layout lay, const PassArgs& a, int B, cudaStream_t s);
 cudaError_t launch_last(const Plan& p, Layout lay, const PassArgs& a, int B, cudaStream_t s);
 // LAST of a GD step fused with FIRST of the next (same layout X lines).

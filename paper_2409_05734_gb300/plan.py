@@ -31,14 +31,17 @@ class Plan:
     def __init__(self, n: int, m: int, L: int = 2, seed: int = 0, device=None):
         self._lib = _lib.load()
         self.n, self.m, self.L, self.seed = int(n), int(m), int(L), int(seed)
-        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-        if dev.type != "cuda":
-            raise ValueError("a plan lives on a CUDA device")
-        self.device = torch.device("cuda", dev.index if dev.index is not None else torch.cuda.current_device())
+        self._set_device(device)
         h = C.c_void_p()
         with torch.cuda.device(self.device):
             _lib.check(self._lib.sr_plan_create(self.n, self.m, self.L, self.seed, C.byref(h)), "sr_plan_create")
         self._h = h
+
+    def _set_device(self, device):
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if dev.type != "cuda":
+            raise ValueError("a plan lives on a CUDA device")
+        self.device = torch.device("cuda", dev.index if dev.index is not None else torch.cuda.current_device())
 
     # -------------------------------------------------------------- lifecycle
     def close(self):
@@ -206,3 +209,21 @@ def phases(seed: int, L: int, m: int) -> np.ndarray:
     out = np.empty((L, m), dtype=np.float64)
     _lib.check(lib.sr_phases(int(seed), int(L), int(m), out.ctypes.data_as(C.POINTER(C.c_double))), "sr_phases")
     return out
+
+
+class Plan2D(Plan):
+    """The 2D form of the operator (Sec. IV runs it with a 2D FFT on images):
+    A = F2 D_L ... F2 D_1 U2 on h x w images (row-major, n = h*w) zero-padded
+    into the top-left of an S x S grid (m = S*S, row-major). Same calls as
+    Plan, except set_phases_device and backward."""
+
+    def __init__(self, h: int, w: int, S: int, L: int = 2, seed: int = 0, device=None):
+        self._lib = _lib.load()
+        self.h, self.w, self.S = int(h), int(w), int(S)
+        self.n, self.m, self.L, self.seed = self.h * self.w, self.S * self.S, int(L), int(seed)
+        self._set_device(device)
+        hd = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_plan_create_2d(self.h, self.w, self.S, self.L, self.seed, C.byref(hd)),
+                       "sr_plan_create_2d")
+        self._h = hd
