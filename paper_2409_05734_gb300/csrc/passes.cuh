@@ -571,8 +571,15 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     for (int j = 0; j < E; ++j) {
       const int nat = (p + j * P) * TL::nl(a) + g;
       // signal index (2D grids: grid_index, with U2 and U2^H the same corner)
-      const int xi = MAP ? grid_index(p + j * P, g, a.out_h, a.out_w, 0) : (nat < a.n_out ? nat : -1);
-      if (xi >= 0) {
+      int xi = nat;
+      bool keep;
+      if constexpr (MAP) {
+        xi = grid_index(p + j * P, g, a.out_h, a.out_w, 0);
+        keep = xi >= 0;
+      } else {
+        keep = nat < a.n_out;
+      }
+      if (keep) {
         const float2 d = __ldg(&dp[nat]);
         const float2 gr = cmulc(v[j], d);
         float2 x = xb[xi];
