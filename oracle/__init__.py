@@ -36,6 +36,9 @@ from .operator import (
     unitary_fft,
     unitary_ifft,
     zero_pad,
+    trim,
+    untrim,
+    trim_offset,
     forward,
     adjoint,
     dense_structured_matrix,
@@ -65,7 +68,7 @@ from .dense_iid import dense_forward, dense_adjoint, dense_ops
 from . import autodiff
 
 __all__ = [
-    "dft_matrix", "dft_naive", "unitary_fft", "unitary_ifft", "zero_pad", "forward",
+    "dft_matrix", "dft_naive", "unitary_fft", "unitary_ifft", "zero_pad", "trim", "untrim", "trim_offset", "forward",
     "adjoint", "dense_structured_matrix", "intensity_loss", "loss_and_grad",
     "spectral_weights", "spectral_init", "gradient_descent", "step_ramp", "cosine_similarity",
     "relative_error_global_phase", "structured_ops", "dense_forward", "dense_adjoint",

@@ -9,6 +9,10 @@ Readings of the paper used here (Sec. III, Eq. 5, alpha > 1 branch):
   the structured matrix unitary (Sec. IV-A), which fixes the 1/sqrt(m).
 * D_l = diag(exp(i*theta_l)), theta_l ~ U[0, 2*pi) (Sec. III).
 * U zero-pads x in C^n to C^m by placing x in entries 0..n-1.
+* alpha < 1 (m < n, Sec. III, the undersampling paragraph after Eq. 5): the
+  DFTs have length n (no padding) and S "trims the edges" of the result,
+  read as keeping the m central entries off .. off+m-1 with
+  off = floor((n - m) / 2); theta then has shape [L, n].
 """
 from __future__ import annotations
 
@@ -47,23 +51,50 @@ def zero_pad(x: np.ndarray, m: int) -> np.ndarray:
     return out
 
 
-def forward(x: np.ndarray, theta: np.ndarray, m: int, fft=unitary_fft) -> np.ndarray:
-    """z = A x with A = F D_L ... F D_1 U (Sec. III, Eq. 5, alpha > 1).
+def trim_offset(n: int, m: int) -> int:
+    """First kept entry of S: the m central entries of a length-n vector."""
+    return (n - m) // 2
 
-    x: [..., n] complex; theta: [L, m] phases of the diagonals; returns [..., m].
+
+def trim(v: np.ndarray, m: int) -> np.ndarray:
+    """S: C^n -> C^m, keeps entries off .. off+m-1 (Sec. III, alpha < 1)."""
+    off = trim_offset(v.shape[-1], m)
+    return v[..., off:off + m].copy()
+
+
+def untrim(w: np.ndarray, n: int) -> np.ndarray:
+    """S^H: C^m -> C^n, w placed at entries off .. off+m-1, zeros elsewhere."""
+    m = w.shape[-1]
+    off = trim_offset(n, m)
+    out = np.zeros(w.shape[:-1] + (n,), dtype=np.complex128)
+    out[..., off:off + m] = w
+    return out
+
+
+def forward(x: np.ndarray, theta: np.ndarray, m: int, fft=unitary_fft) -> np.ndarray:
+    """z = A x with A = F D_L ... F D_1 U (Sec. III, Eq. 5, alpha >= 1), or
+    A = S F D_L ... F D_1 when m < n (alpha < 1).
+
+    x: [..., n] complex; theta: [L, max(n, m)] phases of the diagonals; returns [..., m].
     """
-    v = zero_pad(np.asarray(x, dtype=np.complex128), m)
+    x = np.asarray(x, dtype=np.complex128)
+    n = x.shape[-1]
+    v = zero_pad(x, m) if m >= n else x
     for l in range(theta.shape[0]):
         v = fft(np.exp(1j * theta[l]) * v)
-    return v
+    return v if m >= n else trim(v, m)
 
 
 def adjoint(z: np.ndarray, theta: np.ndarray, n: int, ifft=unitary_ifft) -> np.ndarray:
-    """A^H z = U^H D_1^H F^H ... D_L^H F^H z (conjugate transpose of Eq. 5).
+    """A^H z = U^H D_1^H F^H ... D_L^H F^H z (conjugate transpose of Eq. 5), or
+    D_1^H F^H ... D_L^H F^H S^H z when m < n.
 
-    z: [..., m]; returns the first n entries, [..., n].
+    z: [..., m]; returns [..., n].
     """
     v = np.asarray(z, dtype=np.complex128)
+    m = v.shape[-1]
+    if m < n:
+        v = untrim(v, n)
     for l in reversed(range(theta.shape[0])):
         v = np.exp(-1j * theta[l]) * ifft(v)
     return v[..., :n].copy()
@@ -75,9 +106,15 @@ def dense_structured_matrix(theta: np.ndarray, n: int, m: int) -> np.ndarray:
     Built from the naive DFT matrix and explicit diagonal matrices only, so it
     shares no code path with ``forward`` beyond the definition itself.
     """
-    F = dft_matrix(m)
-    U = np.eye(m, n, dtype=np.complex128)
-    A = U
+    N = max(n, m)
+    F = dft_matrix(N)
+    A = np.eye(N, n, dtype=np.complex128)  # U (the identity when m < n)
     for l in range(theta.shape[0]):
         A = F @ (np.diag(np.exp(1j * theta[l])) @ A)
+    if m < n:  # S: rows off .. off+m-1
+        off = (n - m) // 2
+        Sm = np.zeros((m, n), dtype=np.complex128)
+        for i in range(m):
+            Sm[i, off + i] = 1.0
+        A = Sm @ A
     return A
