@@ -91,7 +91,13 @@ sr_status sr_phases(uint64_t seed, int L, int64_t m, double* theta);
  * phases of sr_phases(seed, L, m), on the current CUDA device. Builds the
  * device tables (D_l = exp(i theta_l)/sqrt(m) rounded to float, twiddles
  * computed in double and rounded). *out receives the plan; release it with
- * sr_plan_destroy. */
+ * sr_plan_destroy.
+ * m < n selects the undersampling branch of Sec. III (the paragraph after
+ * Eq. 5): A = S F D_L ... F D_1 with DFTs of length n (n = 2^a in [4, 2^24],
+ * else SR_ERR_UNSUPPORTED), phases sr_phases(seed, L, n), and S keeping the m
+ * entries off .. off+m-1 of the result, off = floor((n - m) / 2). Every
+ * m-length array (z, y, the adjoint's input) holds those m entries. Such plans
+ * refuse sr_backward, sr_forward_noalloc and the ragged calls. */
 sr_status sr_plan_create(int64_t n, int64_t m, int L, uint64_t seed, sr_plan** out);
 sr_status sr_plan_destroy(sr_plan* plan); /* NULL is accepted (no-op) */
 
@@ -108,12 +114,13 @@ sr_status sr_plan_destroy(sr_plan* plan); /* NULL is accepted (no-op) */
  * sr_forward_noalloc and the ragged calls (SR_ERR_UNSUPPORTED). */
 sr_status sr_plan_create_2d(int64_t h, int64_t w, int64_t S, int L, uint64_t seed, sr_plan** out);
 
-/* Copies the plan's phases (double[L*m], host) out / replaces them from host
- * memory (the diagonal tables are rebuilt synchronously). */
+/* Copies the plan's phases (double[L*N], host, N = max(n, m) the DFT length)
+ * out / replaces them from host memory (the diagonal tables are rebuilt
+ * synchronously). */
 sr_status sr_plan_get_phases(const sr_plan* plan, double* theta);
 sr_status sr_plan_set_phases(sr_plan* plan, const double* theta);
 
-/* Replaces the phases from DEVICE memory (float[L*m], e.g. a trainable
+/* Replaces the phases from DEVICE memory (float[L*N], e.g. a trainable
  * tensor): the diagonal tables are rebuilt on `stream` (D = exp(i theta)/sqrt(m)
  * in float). The host copy returned by sr_plan_get_phases is refreshed from
  * them on its next call (which then synchronises the device). */

@@ -114,6 +114,8 @@ void free_workspace(Plan* p) {
   cudaFree(p->d_part);
   cudaFree(p->d_scal);
   cudaFree(p->d_yt);
+  cudaFree(p->d_zw);
+  p->d_zw = nullptr;
   p->d_e0 = p->d_e1 = nullptr;
   p->d_part = p->d_scal = nullptr;
   p->d_yt = nullptr;
@@ -173,7 +175,8 @@ sr_status ensure_workspace(Plan* p, int B) {
   if ((st = dalloc(&p->d_e0, bm)) != SR_OK || (st = dalloc(&p->d_e1, bm)) != SR_OK ||
       (st = dalloc(&p->d_part, (size_t)kPartBanks * B * part_stride(*p))) != SR_OK ||
       (st = dalloc(&p->d_scal, (size_t)4 * B)) != SR_OK ||
-      (p->two_d && p->L % 2 == 1 && (st = dalloc(&p->d_yt, bm)) != SR_OK)) {
+      (p->two_d && p->L % 2 == 1 && (st = dalloc(&p->d_yt, bm)) != SR_OK) ||
+      (p->mo < p->m && (st = dalloc(&p->d_zw, (size_t)B * (size_t)p->mo)) != SR_OK)) {
     free_workspace(p);
     return st;
   }
@@ -313,6 +316,10 @@ struct Chain {
   int out_tr = 0;
   const float2* first_dp = nullptr;
   int64_t first_dp_stride = 0;
+  // alpha < 1: the first pass reads / the last pass writes the window of the
+  // length-m vector starting at this offset (S^H / S)
+  int in_off = 0;
+  int out_off = 0;
 };
 
 sr::PassArgs base_args(const Plan& p) {
@@ -383,16 +390,22 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
       a.in_w = c.n_in == p.m ? p.gS : p.gw;
       a.in_tr = c.in_tr;
     }
-    if (c.r3_first) {
-      a.r3 = 1;
+    a.in_off = c.in_off;
+    if (c.first_op == sr::kOpGdEpilogue || c.first_op == sr::kOpSpecEpilogue) {
+      // the epilogue in the first pass (radix-3 chains, alpha < 1 adjoint chains)
       a.ym = c.ym;
-      a.dp = c.first_dp;
-      a.dp_stride = c.first_dp_stride;
       a.y = c.y;
       a.sumy = c.sumy;
       a.lam = c.lam;
       a.weight_mode = c.weight_mode;
       a.part_out = c.loss_part;
+      if (c.first_op == sr::kOpGdEpilogue) loss_cpp = p.geom[sr::s1_layout(c.s0)].cpp;
+    }
+    if (c.r3_first) {
+      a.r3 = 1;
+      a.ym = c.ym;
+      a.dp = c.first_dp;
+      a.dp_stride = c.first_dp_stride;
     }
     a.eout = cur;
     PassTimer tm(p, 0, s);
@@ -450,6 +463,7 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     a.loss_part = c.loss_part;
     a.loss_cpp = loss_cpp;
     a.loss_out = c.loss_out;
+    a.out_off = c.out_off;
     if (p.two_d) {
       a.out_h = c.n_out == p.m ? p.gS : p.gh;
       a.out_w = c.n_out == p.m ? p.gS : p.gw;
@@ -564,12 +578,59 @@ sr_status epilogue_y(Plan* p, const float* y, int B, cudaStream_t s, const float
   return SR_OK;
 }
 
+// z = A x: L forward DFTs, D_l before DFT l; for 2D plans with odd L the
+// output is stored through the transposition, for alpha < 1 only the window.
+Chain forward_chain(const Plan& p) {
+  Chain c;
+  c.nfft = p.L;
+  c.s0 = 0;
+  for (int k = 0; k < p.L; ++k) c.dir[k] = -1;
+  c.first_op = sr::kOpDiag;
+  for (int k = 1; k < p.L; ++k) c.mid[k] = MidOp{sr::kOpDiag, k};
+  c.last_op = sr::kOpNone;
+  c.n_in = (int)p.n;
+  c.n_out = (int)p.mo;
+  c.out_off = (int)p.off;
+  c.out_mode = sr::kOutStore;
+  c.out_tr = p.two_d && p.L % 2 == 1;  // 2D: L twiddle-free DFTs leave the grid transposed for odd L
+  return c;
+}
+
+// x = A^H w: L inverse DFTs; the first pass reads the window (alpha < 1) or the
+// grid in the layout the forward leaves it in (2D, odd L).
+Chain adjoint_chain(const Plan& p) {
+  Chain c;
+  c.nfft = p.L;
+  c.s0 = p.L % 2;  // keeps every D_l in the layout it was stored in
+  for (int k = 0; k < p.L; ++k) c.dir[k] = +1;
+  c.first_op = sr::kOpNone;
+  for (int k = 1; k < p.L; ++k) c.mid[k] = MidOp{sr::kOpDiagConj, p.L - k};
+  c.last_op = sr::kOpDiagConj;
+  c.n_in = (int)p.mo;
+  c.in_off = (int)p.off;
+  c.in_tr = p.two_d && p.L % 2 == 1;
+  c.n_out = (int)p.n;
+  c.out_mode = sr::kOutStore;
+  return c;
+}
+
+// alpha < 1 solver steps: the adjoint half reads A v from the window buffer
+// and applies the epilogue (GD residual or spectral weights) in its first pass.
+Chain window_adjoint_chain(const Plan& p, int epilogue_op, const float* y) {
+  Chain c = adjoint_chain(p);
+  c.first_op = epilogue_op;
+  c.xin = p.d_zw;  // the window: entry i sits at off + i of the length-m vector (in_off)
+  c.y = y;
+  c.ym = (int)p.mo;
+  return c;
+}
+
 // sum(y) per problem (and the GD step mu0 * m / sum(y)) into the scalar workspace.
 sr_status prepare_y(Plan* p, const float* y, int B, float mu0, cudaStream_t s) {
-  const int chunks = (int)std::min<int64_t>(64, (p->m + 4095) / 4096);
+  const int chunks = (int)std::min<int64_t>(64, (p->mo + 4095) / 4096);
   float* part = part_bank(*p, 3, B);
-  SR_CUDA(sr::launch_sum_rows(y, B, (int)p->m, part, chunks, s), "launch(sum y)");
-  SR_CUDA(sr::launch_finish_scalars(part, chunks, B, mu0, (int)p->m, p->d_scal, p->d_scal + B, s),
+  SR_CUDA(sr::launch_sum_rows(y, B, (int)p->mo, part, chunks, s), "launch(sum y)");
+  SR_CUDA(sr::launch_finish_scalars(part, chunks, B, mu0, (int)p->mo, p->d_scal, p->d_scal + B, s),
           "launch(step size)");
   return SR_OK;
 }
@@ -654,6 +715,8 @@ sr_status create_plan(int64_t n, int64_t m, int L, uint64_t seed, int gh, int gw
   if (!p) return fail(SR_ERR_OOM, "host allocation failed");
   p->n = n;
   p->m = m;
+  p->mo = m;
+  p->off = 0;
   p->L = L;
   p->seed = seed;
   p->two_d = gS > 0;
@@ -727,6 +790,18 @@ sr_status create_plan(int64_t n, int64_t m, int L, uint64_t seed, int gh, int gw
 extern "C" {
 
 sr_status sr_plan_create(int64_t n, int64_t m, int L, uint64_t seed, sr_plan** out) {
+  if (m >= 1 && m < n) {
+    // alpha < 1: DFTs of length n, then S keeps the m central entries
+    if (!out) return fail(SR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!(is_pow2(n) && n >= 4 && n <= (int64_t(1) << 24)))
+      return fail(SR_ERR_UNSUPPORTED, "with m < n, n must be 2^a in [4, 2^24]");
+    sr_status st = create_plan(n, n, L, seed, 0, 0, 0, out);
+    if (st != SR_OK) return st;
+    (*out)->mo = m;
+    (*out)->off = (n - m) / 2;
+    return SR_OK;
+  }
   return create_plan(n, m, L, seed, 0, 0, 0, out);
 }
 
@@ -803,7 +878,7 @@ sr_status sr_plan_set_phases(sr_plan* plan, const double* theta) {
 sr_status sr_plan_info(const sr_plan* plan, int64_t* n, int64_t* m, int* L) {
   if (!plan) return fail(SR_ERR_INVALID_ARG, "plan is NULL");
   if (n) *n = plan->n;
-  if (m) *m = plan->m;
+  if (m) *m = plan->mo;  // measurements (the DFT length is max(n, m))
   if (L) *L = plan->L;
   return SR_OK;
 }
@@ -884,19 +959,9 @@ sr_status sr_forward(sr_plan* plan, const void* x, void* z, int B, void* stream)
   if (st != SR_OK) return st;
   if (!x || !z) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
   Plan& p = *plan;
-  Chain c;
-  c.nfft = p.L;
-  c.s0 = 0;
-  for (int k = 0; k < p.L; ++k) c.dir[k] = -1;
-  c.first_op = sr::kOpDiag;
-  for (int k = 1; k < p.L; ++k) c.mid[k] = MidOp{sr::kOpDiag, k};
-  c.last_op = sr::kOpNone;
+  Chain c = forward_chain(p);
   c.xin = (const float2*)x;
-  c.n_in = (int)p.n;
   c.xout = (float2*)z;
-  c.n_out = (int)p.m;
-  c.out_mode = sr::kOutStore;
-  c.out_tr = p.two_d && p.L % 2 == 1;  // 2D: L twiddle-free DFTs leave the grid transposed for odd L
   return run_chain(p, c, B, (cudaStream_t)stream);
 }
 
@@ -905,19 +970,9 @@ sr_status sr_adjoint(sr_plan* plan, const void* z, void* x, int B, void* stream)
   if (st != SR_OK) return st;
   if (!x || !z) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
   Plan& p = *plan;
-  Chain c;
-  c.nfft = p.L;
-  c.s0 = p.L % 2;  // keeps every D_l in the layout it was stored in
-  for (int k = 0; k < p.L; ++k) c.dir[k] = +1;
-  c.first_op = sr::kOpNone;
-  for (int k = 1; k < p.L; ++k) c.mid[k] = MidOp{sr::kOpDiagConj, p.L - k};
-  c.last_op = sr::kOpDiagConj;
+  Chain c = adjoint_chain(p);
   c.xin = (const float2*)z;
-  c.n_in = (int)p.m;
-  c.in_tr = p.two_d && p.L % 2 == 1;  // 2D: read the grid in the layout the forward leaves it in
   c.xout = (float2*)x;
-  c.n_out = (int)p.n;
-  c.out_mode = sr::kOutStore;
   return run_chain(p, c, B, (cudaStream_t)stream);
 }
 
@@ -931,6 +986,18 @@ sr_status sr_loss_grad(sr_plan* plan, const void* x, const float* y, float* loss
   if ((st = prepare_y(&p, y, B, 0.f, s)) != SR_OK) return st;
   const float* ye = nullptr;
   if ((st = epilogue_y(&p, y, B, s, &ye)) != SR_OK) return st;
+  if (p.mo < p.m) {
+    Chain f = forward_chain(p);
+    f.xin = (const float2*)x;
+    f.xout = p.d_zw;
+    if ((st = run_chain(p, f, B, s)) != SR_OK) return st;
+    Chain a = window_adjoint_chain(p, sr::kOpGdEpilogue, ye);
+    a.loss_part = part_bank(p, 2, B);
+    a.loss_out = loss;
+    a.xout = (float2*)grad;
+    a.out_mode = sr::kOutGrad;
+    return run_chain(p, a, B, s);
+  }
   Chain c = round_trip_chain(p, sr::kOpGdEpilogue);
   c.xin = (const float2*)x;
   c.n_in = (int)p.n;
@@ -969,6 +1036,34 @@ sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int it
   float* bank[2] = {part_bank(p, 0, B), part_bank(p, 1, B)};
   SR_CUDA(sr::launch_norm_rows(v, B, n, bank[1], init_chunks, s), "launch(norm v0)");
   const int last_cpp = final_partials(p, 2 * p.L, 0);
+  if (p.mo < p.m) {
+    // alpha < 1: forward chain of v / ||v|| into the window, adjoint chain with
+    // the spectral weights in its first pass and the update u = M v + s v last
+    Chain f = forward_chain(p);
+    f.xin = v;
+    f.xout = p.d_zw;
+    Chain a = window_adjoint_chain(p, sr::kOpSpecEpilogue, ye);
+    a.sumy = p.d_scal;
+    a.lam = o.lambda;
+    a.weight_mode = o.weight_mode;
+    a.norm_at_epilogue = true;  // no input scale in its first pass; the last pass uses norm_in
+    a.xout = v;
+    a.out_mode = sr::kOutSpec;
+    a.shift = o.weight_mode == SR_WEIGHT_IDENTITY ? 0.f : -2.0f * o.lambda;
+    int prev = 1, prev_count = init_chunks;
+    for (int it = 0; it < iters; ++it) {
+      const int cur = it % 2;
+      f.norm_in = a.norm_in = bank[prev];
+      f.norm_in_count = a.norm_in_count = prev_count;
+      a.spec_part_out = bank[cur];
+      if ((st = run_chain(p, f, B, s)) != SR_OK) return st;
+      if ((st = run_chain(p, a, B, s)) != SR_OK) return st;
+      prev = cur;
+      prev_count = last_cpp;
+    }
+    SR_CUDA(sr::launch_scale_rows(v, B, n, bank[prev], prev_count, p.d_scal, s), "launch(scale)");
+    return SR_OK;
+  }
   Chain c = round_trip_chain(p, sr::kOpSpecEpilogue);
   c.xin = v;
   c.n_in = n;
@@ -1015,6 +1110,25 @@ sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters, const s
   if ((st = prepare_y(&p, y, B, mu0, s)) != SR_OK) return st;
   const float* ye = nullptr;
   if ((st = epilogue_y(&p, y, B, s, &ye)) != SR_OK) return st;
+  if (p.mo < p.m) {
+    // alpha < 1: forward chain into the window, adjoint chain with the GD
+    // residual in its first pass and the update x -= mu_t 2 A^H(r z) last
+    Chain f = forward_chain(p);
+    f.xin = (const float2*)x;
+    f.xout = p.d_zw;
+    Chain a = window_adjoint_chain(p, sr::kOpGdEpilogue, ye);
+    a.loss_part = part_bank(p, 2, B);
+    a.xout = (float2*)x;
+    a.out_mode = sr::kOutGd;
+    a.mu = p.d_scal + B;
+    for (int it = 0; it < iters; ++it) {
+      a.loss_out = loss_hist ? loss_hist + (size_t)it * B : nullptr;
+      a.mu_scale = tau0 > 0.f ? (float)(1.0 - std::exp(-(double)(it + 1) / (double)tau0)) : 1.0f;
+      if ((st = run_chain(p, f, B, s)) != SR_OK) return st;
+      if ((st = run_chain(p, a, B, s)) != SR_OK) return st;
+    }
+    return SR_OK;
+  }
   Chain c = round_trip_chain(p, sr::kOpGdEpilogue);
   c.xin = (const float2*)x;
   c.n_in = (int)p.n;
@@ -1094,6 +1208,7 @@ sr_status sr_backward(sr_plan* plan, const void* x, const void* gz, void* grad_x
   if (st != SR_OK) return st;
   if (!x || !gz) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
   if (plan->two_d) return fail(SR_ERR_UNSUPPORTED, "the backward pass is not supported on 2D plans");
+  if (plan->mo < plan->m) return fail(SR_ERR_UNSUPPORTED, "the backward pass is not supported for m < n");
   if (!grad_x && !grad_theta) return SR_OK;
   if ((st = ensure_backward_buffers(plan, B)) != SR_OK) return st;
   Plan& p = *plan;

@@ -67,6 +67,7 @@ sr_status sr_forward_noalloc(const sr_plan* plan_in, const void* x, void* z, int
   if (B < 1) return noalloc_fail(SR_ERR_INVALID_ARG, "B must be >= 1");
   if (plan->inner) return noalloc_fail(SR_ERR_UNSUPPORTED, "only power-of-two m is supported");
   if (plan->two_d) return noalloc_fail(SR_ERR_UNSUPPORTED, "2D plans are not supported");
+  if (plan->mo < plan->m) return noalloc_fail(SR_ERR_UNSUPPORTED, "m < n is not supported");
   if ((size_t)B * (size_t)plan->m > kNoallocMaxElements)
     return noalloc_fail(SR_ERR_UNSUPPORTED, "B*m = " + std::to_string((size_t)B * plan->m) +
                                                 " exceeds the static scratch of " +

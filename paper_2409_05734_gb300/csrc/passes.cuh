@@ -269,8 +269,10 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
       const int xi = grid_index(p + j * P, g, a.in_h, a.in_w, a.in_tr);
       v[j] = xi >= 0 ? xb[xi] : make_float2(0.f, 0.f);
     } else {
-      idx[j] = a.r3 ? 3 * nat + rr : nat;
-      v[j] = idx[j] < a.n_in ? xb[idx[j]] : make_float2(0.f, 0.f);
+      // in_off: the input is the window off .. off+n_in-1 of the length-m
+      // vector (S^H of the alpha < 1 branch; zero outside)
+      idx[j] = a.r3 ? 3 * nat + rr : nat - a.in_off;
+      v[j] = (unsigned)idx[j] < (unsigned)a.n_in ? xb[idx[j]] : make_float2(0.f, 0.f);
     }
   }
   if (a.op == kOpDiag) {
@@ -281,24 +283,26 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     const float2* dp = a.dp + (size_t)bo * a.dp_stride;
 #pragma unroll
     for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&dp[idx[j]]));
-  } else if (a.op == kOpGdEpilogue) {  // (radix-3 chains) r = |z|^2 - y, w = r z, loss partials
+  } else if (a.op == kOpGdEpilogue) {  // (radix-3, alpha < 1 chains) r = |z|^2 - y, w = r z, loss partials
     __shared__ float red[64];
     const float* yb = a.y + (size_t)bo * a.ym;
     fsum2 acc{0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-      const float res = cabs2(v[j]) - __ldg(&yb[idx[j]]);
-      acc_add(acc, res * res);
-      v[j] = cscale(v[j], res);
+      if ((unsigned)idx[j] < (unsigned)a.ym) {  // outside the measurement window: w = 0
+        const float res = cabs2(v[j]) - __ldg(&yb[idx[j]]);
+        acc_add(acc, res * res);
+        v[j] = cscale(v[j], res);
+      }
     }
     const float sum = block_sum(acc, red);
     if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = sum;
-  } else if (a.op == kOpSpecEpilogue) {  // (radix-3 chains) w = T(y_hat) z
+  } else if (a.op == kOpSpecEpilogue) {  // (radix-3, alpha < 1 chains) w = T(y_hat) z
     const float* yb = a.y + (size_t)bo * a.ym;
     const float ysc = (float)a.ym / __ldg(&a.sumy[bo]);
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-      const float yh = __ldg(&yb[idx[j]]) * ysc;
+      const float yh = (unsigned)idx[j] < (unsigned)a.ym ? __ldg(&yb[idx[j]]) * ysc : 0.f;
       float w = yh;
       if (a.weight_mode == SR_WEIGHT_OPTIMAL) w = yh > 0.f ? fmaxf(1.0f - 1.0f / yh, a.lam) : a.lam;
       v[j] = cscale(v[j], w);
@@ -488,12 +492,14 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int nat = (p + j * P) * TL::nl(a) + g;
-      int oi = nat;  // output index (2D grids: grid_index; tables stay at nat)
+      // output index: the prefix n_out (U^H), the window out_off .. out_off+n_out-1
+      // (S of the alpha < 1 branch), or grid_index (2D grids); tables stay at nat
+      int oi = nat - a.out_off;
       if constexpr (MAP) {
         oi = grid_index(p + j * P, g, a.out_h, a.out_w, a.out_tr);
         if (oi < 0) continue;
       } else {
-        if (nat >= a.n_out) continue;
+        if ((unsigned)oi >= (unsigned)a.n_out) continue;
       }
       float2 val = v[j];
       if (a.op == kOpDiagConj) val = cmulc(val, __ldg(&a.dp[(size_t)b * a.dp_stride + nat]));

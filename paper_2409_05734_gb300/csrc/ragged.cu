@@ -115,6 +115,8 @@ sr_status sr_ragged_create(int count, const int64_t* n, const int64_t* m, const 
   if (!out || !n || !m || !L || !seeds) return rfail(SR_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
   if (count < 1) return rfail(SR_ERR_INVALID_ARG, "count must be >= 1");
+  for (int i = 0; i < count; ++i)
+    if (n[i] > m[i]) return rfail(SR_ERR_UNSUPPORTED, "ragged batches need n <= m (alpha >= 1)");
   sr_ragged* r = new (std::nothrow) sr_ragged();
   if (!r) return rfail(SR_ERR_OOM, "host allocation failed");
   r->count = count;

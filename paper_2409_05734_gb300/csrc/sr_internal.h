@@ -93,6 +93,9 @@ struct PassArgs {
   // pass's input and the last pass's output (see grid_index)
   int in_h, in_w, in_tr;
   int out_h, out_w, out_tr;
+  // alpha < 1: first pass input / last pass output is the window of the
+  // length-m vector starting at this offset (0 otherwise)
+  int in_off, out_off;
   // first pass: optional scaling of the input by 1/sqrt(sum of partials)
   const float* norm_in;
   int norm_in_count;
@@ -150,6 +153,13 @@ struct Plan {
   // 2D model on h x w images in an S x S grid (m = S * S, n = h * w): unit
   // four-step twiddles, diagonals of even layers stored transposed, and for
   // odd L a transposed copy of y (d_yt, [B][m]) for the epilogues
+  // alpha < 1 (m < n): the DFTs have length m = n here and the operator keeps
+  // the mo entries off .. off+mo-1 of the result (mo = m otherwise); the
+  // solver steps run a forward chain into d_zw ([B][mo]) and an adjoint chain
+  // whose first pass applies the epilogue
+  int64_t mo = 0;
+  int64_t off = 0;
+  float2* d_zw = nullptr;
   bool two_d = false;
   int gh = 0, gw = 0, gS = 0;
   float* d_yt = nullptr;

@@ -26,11 +26,16 @@ def _p(t) -> C.c_void_p:
 
 
 class Plan:
-    """Structured random operator A = F D_L ... F D_1 U (Sec. III, Eq. 5) on one GPU."""
+    """Structured random operator A = F D_L ... F D_1 U (Sec. III, Eq. 5) on one GPU.
+
+    m < n selects the alpha < 1 branch A = S F D_L ... F D_1: DFTs of length n,
+    S keeping the m central entries. The phases have shape [L, N] with
+    N = max(n, m), the DFT length."""
 
     def __init__(self, n: int, m: int, L: int = 2, seed: int = 0, device=None):
         self._lib = _lib.load()
         self.n, self.m, self.L, self.seed = int(n), int(m), int(L), int(seed)
+        self.N = max(self.n, self.m)
         self._set_device(device)
         h = C.c_void_p()
         with torch.cuda.device(self.device):
@@ -64,13 +69,13 @@ class Plan:
     # ----------------------------------------------------------------- phases
     @property
     def phases(self) -> np.ndarray:
-        out = np.empty((self.L, self.m), dtype=np.float64)
+        out = np.empty((self.L, self.N), dtype=np.float64)
         _lib.check(self._lib.sr_plan_get_phases(self._h, out.ctypes.data_as(C.POINTER(C.c_double))),
                    "sr_plan_get_phases")
         return out
 
     def set_phases(self, theta) -> None:
-        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(self.L, self.m)
+        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(self.L, self.N)
         with torch.cuda.device(self.device):
             _lib.check(self._lib.sr_plan_set_phases(self._h, th.ctypes.data_as(C.POINTER(C.c_double))),
                        "sr_plan_set_phases")
@@ -81,9 +86,9 @@ class Plan:
             _lib.check(self._lib.sr_plan_check(self._h), "sr_plan_check")
 
     def set_phases_device(self, theta: torch.Tensor) -> None:
-        """Phases from a device float32 tensor [L, m]; tables rebuilt on the current stream."""
-        if theta.dtype != torch.float32 or theta.device != self.device or tuple(theta.shape) != (self.L, self.m):
-            raise ValueError(f"theta must be a float32 [{self.L}, {self.m}] tensor on {self.device}")
+        """Phases from a device float32 tensor [L, N]; tables rebuilt on the current stream."""
+        if theta.dtype != torch.float32 or theta.device != self.device or tuple(theta.shape) != (self.L, self.N):
+            raise ValueError(f"theta must be a float32 [{self.L}, {self.N}] tensor on {self.device}")
         theta = theta.contiguous()
         with torch.cuda.device(self.device):
             _lib.check(self._lib.sr_plan_set_phases_device(self._h, _p(theta), _stream_handle()),
@@ -221,6 +226,7 @@ class Plan2D(Plan):
         self._lib = _lib.load()
         self.h, self.w, self.S = int(h), int(w), int(S)
         self.n, self.m, self.L, self.seed = self.h * self.w, self.S * self.S, int(L), int(seed)
+        self.N = self.m
         self._set_device(device)
         hd = C.c_void_p()
         with torch.cuda.device(self.device):
