@@ -81,6 +81,34 @@ def gradient_descent(x0: np.ndarray, y: np.ndarray, fwd, adj, iters: int,
     return x, np.array(hist)
 
 
+def gradient_descent_early_stop(x0: np.ndarray, y: np.ndarray, fwd, adj, max_iters: int, rel_tol: float,
+                                check_every: int, mu0: float = MU0_DEFAULT, tau0: float = 0.0):
+    """Gradient descent with early stopping (Sec. IV-A runs GD "with early
+    stopping" without stating the rule). Reading: after every `check_every`
+    iterations, stop once every problem's loss changed over the last
+    iteration by at most rel_tol of its previous value,
+    |L(x_{t-1}) - L(x_t)| <= rel_tol * L(x_{t-1}), where t is the chunk's
+    last iteration and L(x_t) the loss at the iterate that iteration updates.
+
+    Returns (x, loss history [iterations run, ...], iterations run).
+    """
+    if check_every < 2:
+        raise ValueError("check_every must be >= 2")
+    x = np.array(x0, dtype=np.complex128, copy=True)
+    y = np.asarray(y, dtype=np.float64)
+    m = y.shape[-1]
+    mu = (mu0 * m / np.sum(y, axis=-1))[..., None]
+    hist = []
+    for t in range(max_iters):
+        loss, g = loss_and_grad(x, y, fwd, adj)
+        hist.append(loss)
+        x = x - (step_ramp(t, tau0) * mu) * g
+        if (t + 1) % check_every == 0 and t + 1 < max_iters:
+            if np.all(np.abs(hist[t - 1] - hist[t]) <= rel_tol * hist[t - 1]):
+                return x, np.array(hist), t + 1
+    return x, np.array(hist), max_iters
+
+
 def spectral_weights(y: np.ndarray, mode: str = "identity", lam: float = -1.0) -> np.ndarray:
     """Weights of the covariance of Eq. 3 on y_hat = m*y/sum(y).
 
