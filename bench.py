@@ -542,6 +542,56 @@ def two_d_workload(torch, dev, flush):
                         f"weights) + {gd} GD iterations, graph-replayed", **out}
 
 
+def forward_time_vs_size(torch, dev, flush, reps: int = 5):
+    """Forward time against image size at alpha = 1 (Sec. IV-C, Fig. 4): the 2D
+    structured model (L = 2, S x S images, no padding) for S = 16 .. 4096 and the
+    dense i.i.d. model (n = m = S^2, BF16 matrix) while it fits comfortably
+    (S <= 128: 1 GiB), both on batches of 8 images (the dense kernel's
+    smallest batch). Median of `reps` event-timed calls, L2 flushed before each."""
+    from paper_2409_05734_gb300 import DenseModel, Plan2D
+    B = 8
+    gen = torch.Generator(device=dev).manual_seed(5)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    rows = []
+    for k in range(4, 13):
+        S_ = 1 << k
+        n = S_ * S_
+        x = torch.randn((B, n), dtype=torch.complex64, device=dev, generator=gen)
+        plan = Plan2D(S_, S_, S_, 2, 7)
+        plan.reserve(B)
+        z = torch.empty((B, n), dtype=torch.complex64, device=dev)
+        row = {"S": S_, "pixels": n, "structured_ms": timed(lambda: plan.forward(x, out=z))}
+        plan.check()
+        del plan
+        if S_ <= 128:
+            rng = np.random.default_rng(S_)
+            a = rng.standard_normal((n, n, 2), dtype=np.float32) * np.float32(1.0 / np.sqrt(2.0 * n))
+            dense = DenseModel(a.view(np.complex64)[..., 0])
+            del a
+            row["dense_ms"] = timed(lambda: dense.forward(x))
+            dense.check()
+            del dense
+        rows.append(row)
+        del x, z
+        torch.cuda.empty_cache()
+    return {"workload": f"alpha = 1, B = {B} images per forward, structured 2D model L = 2 (S x S) "
+                        "against the dense i.i.d. model (BF16, n = m = S^2, S <= 128)", "rows": rows}
+
+
 def autograd_workload(torch, dev, flush):
     """Forward and backward of the differentiable operator (x, theta) -> z = A x at
     B = 8, n = 2^20, m = 2^22, L = 2, driven by a loss on |z|^2."""
@@ -826,6 +876,7 @@ def run_ours(args):
     if rank == 0 and not args.no_extra:
         line["radix3_batch"] = radix3_workload(torch, dev, flush)
         line["two_dimensional"] = two_d_workload(torch, dev, flush)
+        line["forward_time_vs_size"] = forward_time_vs_size(torch, dev, flush)
         line["differentiable_operator"] = autograd_workload(torch, dev, flush)
     if rank == 0 and not args.no_ragged:
         line["ragged_batch"] = ragged_workload(torch, dev, flush)

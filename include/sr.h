@@ -191,6 +191,19 @@ sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int it
 sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters,
                       const sr_gd_opts* opts, float* loss_hist, int B, void* stream);
 
+/* sr_gd_solve_early_stop: the same iteration with early stopping (Sec. IV-A
+ * runs GD "with early stopping" and states no rule). Runs chunks of
+ * check_every (>= 2) iterations; after each chunk it reads the losses of the
+ * chunk's last two iterations t-1, t and stops once, for every problem,
+ * |L(x_{t-1}) - L(x_t)| <= rel_tol * L(x_{t-1}); at most max_iters
+ * iterations. *iters_run (host int) receives the number run. loss_hist
+ * (float[max_iters][B], device) or NULL as for sr_gd_solve. Each check
+ * synchronises `stream` (one 8*B-byte device-to-host copy), so the call cannot
+ * be captured in a CUDA graph. B <= 65535. rel_tol must be finite and >= 0. */
+sr_status sr_gd_solve_early_stop(sr_plan* plan, const float* y, void* x, int max_iters,
+                                 const sr_gd_opts* opts, float rel_tol, int check_every,
+                                 float* loss_hist, int* iters_run, int B, void* stream);
+
 /* ---- forward without allocation (the paper has no counterpart) ---------------
  * sr_forward_noalloc: z = A x exactly like sr_forward, for callers that cannot
  * allocate device memory when they make the call -- code running while a CUDA

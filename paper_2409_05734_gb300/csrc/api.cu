@@ -785,6 +785,72 @@ sr_status create_plan(int64_t n, int64_t m, int L, uint64_t seed, int gh, int gw
   *out = p;
   return SR_OK;
 }
+// Validation and the per-problem step mu0 * m / sum(y) shared by the GD entry points.
+sr_status gd_setup(sr_plan* plan, const float* y, void* x, int iters, const sr_gd_opts* opts, int B, void* stream,
+                   float* mu0_out, float* tau0_out) {
+  sr_status st = check_plan_call(plan, B);
+  if (st != SR_OK) return st;
+  if (!y || !x) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
+  if (iters < 0) return fail(SR_ERR_INVALID_ARG, "iters must be >= 0");
+  const float mu0 = opts ? opts->mu0 : 0.1f;
+  const float tau0 = opts ? opts->tau0 : 0.f;
+  if (!(mu0 > 0.f && std::isfinite(mu0))) return fail(SR_ERR_INVALID_ARG, "mu0 must be finite and > 0");
+  if (!(tau0 >= 0.f && std::isfinite(tau0))) return fail(SR_ERR_INVALID_ARG, "tau0 must be finite and >= 0");
+  *mu0_out = mu0;
+  *tau0_out = tau0;
+  return prepare_y(plan, y, B, mu0, (cudaStream_t)stream);
+}
+
+// GD iterations t0 .. t0+count-1 on x (the warm-up factor uses the global
+// index t); loss_row(t) is where iteration t's loss goes, or nullptr.
+template <class RowFn>
+sr_status gd_iterations(Plan& p, const float* ye, void* x, int t0, int count, float tau0, int B, cudaStream_t s,
+                        RowFn loss_row) {
+  sr_status st;
+  auto ramp = [&](int t) {
+    return tau0 > 0.f ? (float)(1.0 - std::exp(-(double)(t + 1) / (double)tau0)) : 1.0f;
+  };
+  if (p.mo < p.m) {
+    // alpha < 1: forward chain into the window, adjoint chain with the GD
+    // residual in its first pass and the update x -= mu_t 2 A^H(r z) last
+    Chain f = forward_chain(p);
+    f.xin = (const float2*)x;
+    f.xout = p.d_zw;
+    Chain a = window_adjoint_chain(p, sr::kOpGdEpilogue, ye);
+    a.loss_part = part_bank(p, 2, B);
+    a.xout = (float2*)x;
+    a.out_mode = sr::kOutGd;
+    a.mu = p.d_scal + B;
+    for (int t = t0; t < t0 + count; ++t) {
+      a.loss_out = loss_row(t);
+      a.mu_scale = ramp(t);
+      if ((st = run_chain(p, f, B, s)) != SR_OK) return st;
+      if ((st = run_chain(p, a, B, s)) != SR_OK) return st;
+    }
+    return SR_OK;
+  }
+  Chain c = round_trip_chain(p, sr::kOpGdEpilogue);
+  c.xin = (const float2*)x;
+  c.n_in = (int)p.n;
+  c.xout = (float2*)x;
+  c.n_out = (int)p.n;
+  c.out_mode = sr::kOutGd;
+  c.mu = p.d_scal + B;
+  c.y = ye;
+  c.loss_part = part_bank(p, 2, B);
+  // Consecutive steps share a kernel: the last pass of step t also runs the
+  // first pass of step t+1 (same lines, x_{t+1} still in registers).
+  const bool fuse = !p.inner && (2 * p.L - 1) % 2 == 1;
+  for (int t = t0; t < t0 + count; ++t) {
+    c.loss_out = loss_row(t);
+    c.mu_scale = ramp(t);
+    c.skip_first = fuse && t > t0;
+    c.fuse_next_first = fuse && t + 1 < t0 + count;
+    if ((st = run_chain(p, c, B, s)) != SR_OK) return st;
+  }
+  return SR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -827,6 +893,7 @@ sr_status sr_plan_destroy(sr_plan* plan) {
   cudaFree(plan->d_tw_hi);
   cudaFree(plan->d_tw_lo);
   cudaFree(plan->d_tw3);
+  cudaFree(plan->d_es);
   if (plan->inner) sr_plan_destroy(static_cast<sr_plan*>(plan->inner));
   delete plan;
   return SR_OK;
@@ -1097,56 +1164,53 @@ sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int it
 
 sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters, const sr_gd_opts* opts, float* loss_hist,
                       int B, void* stream) {
-  sr_status st = check_plan_call(plan, B);
+  float mu0 = 0.f, tau0 = 0.f;
+  sr_status st = gd_setup(plan, y, x, iters, opts, B, stream, &mu0, &tau0);
   if (st != SR_OK) return st;
-  if (!y || !x) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
-  if (iters < 0) return fail(SR_ERR_INVALID_ARG, "iters must be >= 0");
-  const float mu0 = opts ? opts->mu0 : 0.1f;
-  const float tau0 = opts ? opts->tau0 : 0.f;
-  if (!(mu0 > 0.f && std::isfinite(mu0))) return fail(SR_ERR_INVALID_ARG, "mu0 must be finite and > 0");
-  if (!(tau0 >= 0.f && std::isfinite(tau0))) return fail(SR_ERR_INVALID_ARG, "tau0 must be finite and >= 0");
+  const float* ye = nullptr;
+  if ((st = epilogue_y(plan, y, B, (cudaStream_t)stream, &ye)) != SR_OK) return st;
+  return gd_iterations(*plan, ye, x, 0, iters, tau0, B, (cudaStream_t)stream,
+                       [&](int t) { return loss_hist ? loss_hist + (size_t)t * B : nullptr; });
+}
+
+sr_status sr_gd_solve_early_stop(sr_plan* plan, const float* y, void* x, int max_iters, const sr_gd_opts* opts,
+                                 float rel_tol, int check_every, float* loss_hist, int* iters_run, int B,
+                                 void* stream) {
+  if (!iters_run) return fail(SR_ERR_INVALID_ARG, "iters_run is NULL");
+  *iters_run = 0;
+  if (check_every < 2) return fail(SR_ERR_INVALID_ARG, "check_every must be >= 2");
+  if (!(rel_tol >= 0.f && std::isfinite(rel_tol))) return fail(SR_ERR_INVALID_ARG, "rel_tol must be finite and >= 0");
+  float mu0 = 0.f, tau0 = 0.f;
+  sr_status st = gd_setup(plan, y, x, max_iters, opts, B, stream, &mu0, &tau0);
+  if (st != SR_OK) return st;
   Plan& p = *plan;
   cudaStream_t s = (cudaStream_t)stream;
-  if ((st = prepare_y(&p, y, B, mu0, s)) != SR_OK) return st;
   const float* ye = nullptr;
   if ((st = epilogue_y(&p, y, B, s, &ye)) != SR_OK) return st;
-  if (p.mo < p.m) {
-    // alpha < 1: forward chain into the window, adjoint chain with the GD
-    // residual in its first pass and the update x -= mu_t 2 A^H(r z) last
-    Chain f = forward_chain(p);
-    f.xin = (const float2*)x;
-    f.xout = p.d_zw;
-    Chain a = window_adjoint_chain(p, sr::kOpGdEpilogue, ye);
-    a.loss_part = part_bank(p, 2, B);
-    a.xout = (float2*)x;
-    a.out_mode = sr::kOutGd;
-    a.mu = p.d_scal + B;
-    for (int it = 0; it < iters; ++it) {
-      a.loss_out = loss_hist ? loss_hist + (size_t)it * B : nullptr;
-      a.mu_scale = tau0 > 0.f ? (float)(1.0 - std::exp(-(double)(it + 1) / (double)tau0)) : 1.0f;
-      if ((st = run_chain(p, f, B, s)) != SR_OK) return st;
-      if ((st = run_chain(p, a, B, s)) != SR_OK) return st;
+  if (!p.d_es && (st = dalloc(&p.d_es, (size_t)2 * 65535)) != SR_OK) return st;
+  std::vector<float> last(2 * (size_t)B);
+  for (int t0 = 0; t0 < max_iters; t0 += check_every) {
+    const int count = std::min(check_every, max_iters - t0);
+    const int t1 = t0 + count;
+    // the losses of the chunk's last two iterations go to d_es as well
+    // (rows of loss_hist when it is given)
+    st = gd_iterations(p, ye, x, t0, count, tau0, B, s, [&](int t) -> float* {
+      if (loss_hist) return loss_hist + (size_t)t * B;
+      return t >= t1 - 2 ? p.d_es + (size_t)(t - (t1 - 2)) * B : nullptr;
+    });
+    if (st != SR_OK) return st;
+    *iters_run = t1;
+    if (count < check_every || t1 >= max_iters) break;
+    const float* rows = loss_hist ? loss_hist + (size_t)(t1 - 2) * B : p.d_es;
+    SR_CUDA(cudaMemcpyAsync(last.data(), rows, last.size() * sizeof(float), cudaMemcpyDeviceToHost, s),
+            "cudaMemcpyAsync(losses)");
+    SR_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    bool all = true;
+    for (int b = 0; b < B && all; ++b) {
+      const double prev = last[b], cur = last[(size_t)B + b];
+      all = std::fabs(prev - cur) <= (double)rel_tol * prev;
     }
-    return SR_OK;
-  }
-  Chain c = round_trip_chain(p, sr::kOpGdEpilogue);
-  c.xin = (const float2*)x;
-  c.n_in = (int)p.n;
-  c.xout = (float2*)x;
-  c.n_out = (int)p.n;
-  c.out_mode = sr::kOutGd;
-  c.mu = p.d_scal + B;
-  c.y = ye;
-  c.loss_part = part_bank(p, 2, B);
-  // Consecutive steps share a kernel: the last pass of step t also runs the
-  // first pass of step t+1 (same lines, x_{t+1} still in registers).
-  const bool fuse = !p.inner && (2 * p.L - 1) % 2 == 1;
-  for (int it = 0; it < iters; ++it) {
-    c.loss_out = loss_hist ? loss_hist + (size_t)it * B : nullptr;
-    c.mu_scale = tau0 > 0.f ? (float)(1.0 - std::exp(-(double)(it + 1) / (double)tau0)) : 1.0f;
-    c.skip_first = fuse && it > 0;
-    c.fuse_next_first = fuse && it + 1 < iters;
-    if ((st = run_chain(p, c, B, s)) != SR_OK) return st;
+    if (all) break;
   }
   return SR_OK;
 }

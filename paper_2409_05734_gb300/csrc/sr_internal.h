@@ -160,6 +160,7 @@ struct Plan {
   int64_t mo = 0;
   int64_t off = 0;
   float2* d_zw = nullptr;
+  float* d_es = nullptr;  // early stopping: the last two losses of a chunk, [2][B]
   bool two_d = false;
   int gh = 0, gw = 0, gS = 0;
   float* d_yt = nullptr;

@@ -207,6 +207,23 @@ class Plan:
                                              _stream_handle()), "sr_gd_solve")
         return x, hist
 
+    def gd_solve_early_stop(self, y: torch.Tensor, x: torch.Tensor, max_iters: int, rel_tol: float,
+                            check_every: int = 50, mu0: float = 0.1, tau0: float = 0.0, record_loss: bool = False):
+        """GD with early stopping: every check_every iterations, stop once every
+        problem's last relative loss change is <= rel_tol. Synchronises at each
+        check. Returns (x, iterations run, loss history [run, B] or None)."""
+        y = self._f32(y, self.m, "y")
+        x = self._c64(x, self.n, "x")
+        B = self._batch(x)
+        hist = torch.empty((int(max_iters), B), dtype=torch.float32, device=self.device) if record_loss else None
+        opts = _lib.GdOpts(float(mu0), float(tau0))
+        run = C.c_int(0)
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_gd_solve_early_stop(self._h, _p(y), _p(x), int(max_iters), C.byref(opts),
+                                                        float(rel_tol), int(check_every), _p(hist), C.byref(run),
+                                                        B, _stream_handle()), "sr_gd_solve_early_stop")
+        return x, run.value, (hist[:run.value] if hist is not None else None)
+
 
 def phases(seed: int, L: int, m: int) -> np.ndarray:
     """Host-side phases a plan with this seed uses (sr_phases): float64 [L, m]."""

@@ -1,0 +1,77 @@
+"""GPU parity of GD with early stopping (sr_gd_solve_early_stop) against the
+oracle's rule (pinned in test_oracle_early_stop.py). The stop iteration is an
+integer decided by floating-point losses, so each case first checks on the
+oracle that the decision has a clear margin on both sides (the FP32 losses
+are accurate to about 1e-6 relative, which moves a relative change of 1e-3 by
+well under 1%)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Plan():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2409_05734_gb300 import buildlib
+    buildlib.build()
+    from paper_2409_05734_gb300 import Plan as P
+    return P
+
+
+def _noisy_problem(B, n, m, L, seed, sigma=0.05):
+    th = S.phases(seed, L, m)
+    fwd, adj = O.structured_ops(th, n, m)
+    x_true = S.signal_gaussian(seed, B, n)
+    y0 = np.abs(fwd(x_true)) ** 2
+    y = np.maximum(y0 + S.gaussian_noise(seed, y0.shape, sigma * y0.mean()), 0.0)
+    x0 = O.spectral_init(y, S.start_vector(seed, B, n), fwd, adj, 30, mode="optimal")
+    return y, x0, fwd, adj
+
+
+@pytest.mark.parametrize("B,n,m,L,seed,tol,every", [(3, 256, 1024, 2, 8, 1e-3, 10),
+                                                     (2, 1024, 4096, 2, 5, 1e-3, 10)])
+def test_early_stop_matches_oracle(Plan, B, n, m, L, seed, tol, every):
+    y, x0, fwd, adj = _noisy_problem(B, n, m, L, seed)
+    T = 400
+    x_o, h_o, t_o = O.gradient_descent_early_stop(x0, y, fwd, adj, T, tol, every, mu0=0.1, tau0=5.0)
+    assert every < t_o < T
+    # margins of the decision: below tol at the stop, clearly above one check earlier
+    ratio = lambda t: np.max(np.abs(h_o[t - 2] - h_o[t - 1]) / h_o[t - 2]) / tol
+    assert ratio(t_o) <= 0.95 and ratio(t_o - every) >= 1.05
+    plan = Plan(n, m, L, seed)
+    x = torch.from_numpy(x0).to(torch.complex64).cuda()
+    yd = torch.from_numpy(y).float().cuda()
+    _, t_g, h_g = plan.gd_solve_early_stop(yd, x, T, tol, check_every=every, mu0=0.1, tau0=5.0, record_loss=True)
+    plan.check()
+    assert t_g == t_o
+    xg = x.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(xg - x_o) / np.linalg.norm(x_o) <= 5e-4
+    hg = h_g.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(hg - h_o) / h_o) <= 1e-3
+
+
+def test_early_stop_without_history_and_limits(Plan):
+    """Without a loss history the rule reads its internal buffer; a zero
+    tolerance runs every iteration and matches sr_gd_solve (up to rounding:
+    chunk boundaries replace the fused last/first kernel by the separate ones)."""
+    B, n, m, L, seed = 2, 128, 512, 2, 3
+    y, x0, fwd, adj = _noisy_problem(B, n, m, L, seed)
+    plan = Plan(n, m, L, seed)
+    yd = torch.from_numpy(y).float().cuda()
+    x1 = torch.from_numpy(x0).to(torch.complex64).cuda()
+    x2 = x1.clone()
+    _, t, _ = plan.gd_solve_early_stop(yd, x1, 37, 0.0, check_every=5, mu0=0.1, tau0=5.0)
+    plan.gd_solve(yd, x2, 37, mu0=0.1, tau0=5.0)
+    plan.check()
+    assert t == 37
+    assert (torch.linalg.vector_norm(x1 - x2) / torch.linalg.vector_norm(x2)).item() <= 1e-6
+    _, t, _ = plan.gd_solve_early_stop(yd, x1, 100, 10.0, check_every=4, mu0=0.1, tau0=5.0)
+    assert t == 4
+    with pytest.raises(Exception):
+        plan.gd_solve_early_stop(yd, x1, 10, 1e-3, check_every=1)
