@@ -760,7 +760,8 @@ sr_status create_plan(int64_t n, int64_t m, int L, uint64_t seed, int gh, int gw
     p->geom[sr::kLayoutY] = sr::make_geom(m, p->m2);
     e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     for (int lay = 0; lay < 2 && e == cudaSuccess; ++lay)
-      e = sr::pass_occupancy(p->geom[lay], p->per_sm_mid[lay], p->per_sm_last[lay], &p->per_sm_lf[lay]);
+      e = sr::pass_occupancy(p->geom[lay], p->per_sm_mid[lay], p->per_sm_last[lay], &p->per_sm_lf[lay],
+                             &p->per_sm_first[lay]);
     if (e != cudaSuccess) {
       delete p;
       return cuda_fail(e, "plan geometry");

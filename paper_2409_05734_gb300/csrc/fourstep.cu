@@ -202,7 +202,8 @@ cudaError_t launch_first(const Plan& p, Layout lay, const PassArgs& a0, int B, c
   cudaError_t e = allow_smem((const void*)fn, g.smem_first);
   if (e != cudaSuccess) return e;
   const PassArgs a = with_geom(a0, p, g, B);
-  fn<<<a.ntiles, g.threads, g.smem_first, s>>>(a);
+  const int grid = std::max(1, std::min(a.ntiles, p.per_sm_first[lay] * p.num_sms));
+  fn<<<grid, g.threads, g.smem_first, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }
@@ -242,7 +243,16 @@ cudaError_t launch_last_first(const Plan& p, Layout lay, const PassArgs& a0, int
   return cudaGetLastError();
 }
 
-cudaError_t pass_occupancy(const LineGeom& g, int* per_sm_mid, int* per_sm_last, int* per_sm_lf) {
+cudaError_t pass_occupancy(const LineGeom& g, int* per_sm_mid, int* per_sm_last, int* per_sm_lf, int* per_sm_first) {
+  {
+    const void* fn = pick_first(g.ell, g.T, -1, 0);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(fn, g.smem_first);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm_first, fn, g.threads, g.smem_first);
+    if (e != cudaSuccess) return e;
+    *per_sm_first = std::max(1, *per_sm_first);
+  }
   // per_sm_mid[3]: direction pairs (-,-), (-,+), (+,+); per_sm_last[2]: (-), (+); per_sm_lf: fused
   const int pairs[3][2] = {{-1, -1}, {-1, 1}, {1, 1}};
   for (int k = 0; k < 6; ++k) {

@@ -242,78 +242,81 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   const int tid = threadIdx.x;
   int t, p;
   thread_coords<TL>(t, p);
-  const int b = blockIdx.x / a.cpp, g0 = (blockIdx.x - b * a.cpp) * T, g = g0 + t;
-  load_line_twiddles<ELL>(a, tw);
-  RowTw<TL> rw;
-  rw.load(a, g0, DB);
-  rw.store(rowtw);
-  const float2 A = tw_m<TL>(a, g * p, DB);
-  // Radix-3 lengths (a.r3): inner problem b = 3 bo + r holds the stride-3
-  // subsequence r of outer problem bo (element 3 nat + r), and the operation
-  // that precedes this DFT is applied at that outer natural index.
-  const int bo = a.r3 ? b / 3 : b, rr = a.r3 ? b - 3 * bo : 0;
-  if (tid == 0)
-    s_scale = a.norm_in ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)bo * a.norm_in_count, a.norm_in_count))
-                        : 1.0f;
-  // Natural-order input, zero beyond n_in (the padding U): element (line g,
-  // position q) is x[q*NL + g]; the warp reads T consecutive elements.
-  const float2* xb = a.xin + (size_t)bo * a.n_in;
-  // (2D grids: the signal entry at grid_index, tables at the layout index nat)
-  float2 v[E];
-  int idx[E];
-#pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const int nat = (p + j * P) * a.nl + g;
-    if constexpr (MAP) {
-      idx[j] = nat;
-      const int xi = grid_index(p + j * P, g, a.in_h, a.in_w, a.in_tr);
-      v[j] = xi >= 0 ? xb[xi] : make_float2(0.f, 0.f);
-    } else {
-      // in_off: the input is the window off .. off+n_in-1 of the length-m
-      // vector (S^H of the alpha < 1 branch; zero outside)
-      idx[j] = a.r3 ? 3 * nat + rr : nat - a.in_off;
-      v[j] = (unsigned)idx[j] < (unsigned)a.n_in ? xb[idx[j]] : make_float2(0.f, 0.f);
-    }
-  }
-  if (a.op == kOpDiag) {
-    const float2* dp = a.dp + (size_t)bo * a.dp_stride;
-#pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = cmul(v[j], __ldg(&dp[idx[j]]));
-  } else if (a.op == kOpDiagConj) {
-    const float2* dp = a.dp + (size_t)bo * a.dp_stride;
-#pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&dp[idx[j]]));
-  } else if (a.op == kOpGdEpilogue) {  // (radix-3, alpha < 1 chains) r = |z|^2 - y, w = r z, loss partials
-    __shared__ float red[64];
-    const float* yb = a.y + (size_t)bo * a.ym;
-    fsum2 acc{0.f, 0.f};
+  load_line_twiddles<ELL>(a, tw);  // once per CTA: the grid is persistent over the tiles
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int b = tile / a.cpp, g0 = (tile - b * a.cpp) * T, g = g0 + t;
+    RowTw<TL> rw;
+    rw.load(a, g0, DB);
+    rw.store(rowtw);
+    const float2 A = tw_m<TL>(a, g * p, DB);
+    // Radix-3 lengths (a.r3): inner problem b = 3 bo + r holds the stride-3
+    // subsequence r of outer problem bo (element 3 nat + r), and the operation
+    // that precedes this DFT is applied at that outer natural index.
+    const int bo = a.r3 ? b / 3 : b, rr = a.r3 ? b - 3 * bo : 0;
+    if (tid == 0)
+      s_scale = a.norm_in ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)bo * a.norm_in_count, a.norm_in_count))
+                          : 1.0f;
+    // Natural-order input, zero beyond n_in (the padding U): element (line g,
+    // position q) is x[q*NL + g]; the warp reads T consecutive elements.
+    const float2* xb = a.xin + (size_t)bo * a.n_in;
+    // (2D grids: the signal entry at grid_index, tables at the layout index nat)
+    float2 v[E];
+    int idx[E];
 #pragma unroll
     for (int j = 0; j < E; ++j) {
-      if ((unsigned)idx[j] < (unsigned)a.ym) {  // outside the measurement window: w = 0
-        const float res = cabs2(v[j]) - __ldg(&yb[idx[j]]);
-        acc_add(acc, res * res);
-        v[j] = cscale(v[j], res);
+      const int nat = (p + j * P) * a.nl + g;
+      if constexpr (MAP) {
+        idx[j] = nat;
+        const int xi = grid_index(p + j * P, g, a.in_h, a.in_w, a.in_tr);
+        v[j] = xi >= 0 ? xb[xi] : make_float2(0.f, 0.f);
+      } else {
+        // in_off: the input is the window off .. off+n_in-1 of the length-m
+        // vector (S^H of the alpha < 1 branch; zero outside)
+        idx[j] = a.r3 ? 3 * nat + rr : nat - a.in_off;
+        v[j] = (unsigned)idx[j] < (unsigned)a.n_in ? xb[idx[j]] : make_float2(0.f, 0.f);
       }
     }
-    const float sum = block_sum(acc, red);
-    if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = sum;
-  } else if (a.op == kOpSpecEpilogue) {  // (radix-3, alpha < 1 chains) w = T(y_hat) z
-    const float* yb = a.y + (size_t)bo * a.ym;
-    const float ysc = (float)a.ym / __ldg(&a.sumy[bo]);
+    if (a.op == kOpDiag) {
+      const float2* dp = a.dp + (size_t)bo * a.dp_stride;
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const float yh = (unsigned)idx[j] < (unsigned)a.ym ? __ldg(&yb[idx[j]]) * ysc : 0.f;
-      float w = yh;
-      if (a.weight_mode == SR_WEIGHT_OPTIMAL) w = yh > 0.f ? fmaxf(1.0f - 1.0f / yh, a.lam) : a.lam;
-      v[j] = cscale(v[j], w);
+      for (int j = 0; j < E; ++j) v[j] = cmul(v[j], __ldg(&dp[idx[j]]));
+    } else if (a.op == kOpDiagConj) {
+      const float2* dp = a.dp + (size_t)bo * a.dp_stride;
+#pragma unroll
+      for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&dp[idx[j]]));
+    } else if (a.op == kOpGdEpilogue) {  // (radix-3, alpha < 1 chains) r = |z|^2 - y, w = r z, loss partials
+      __shared__ float red[64];
+      const float* yb = a.y + (size_t)bo * a.ym;
+      fsum2 acc{0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        if ((unsigned)idx[j] < (unsigned)a.ym) {  // outside the measurement window: w = 0
+          const float res = cabs2(v[j]) - __ldg(&yb[idx[j]]);
+          acc_add(acc, res * res);
+          v[j] = cscale(v[j], res);
+        }
+      }
+      const float sum = block_sum(acc, red);
+      if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = sum;
+    } else if (a.op == kOpSpecEpilogue) {  // (radix-3, alpha < 1 chains) w = T(y_hat) z
+      const float* yb = a.y + (size_t)bo * a.ym;
+      const float ysc = (float)a.ym / __ldg(&a.sumy[bo]);
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const float yh = (unsigned)idx[j] < (unsigned)a.ym ? __ldg(&yb[idx[j]]) * ysc : 0.f;
+        float w = yh;
+        if (a.weight_mode == SR_WEIGHT_OPTIMAL) w = yh > 0.f ? fmaxf(1.0f - 1.0f / yh, a.lam) : a.lam;
+        v[j] = cscale(v[j], w);
+      }
     }
-  }
-  __syncthreads();
-  const float sc = s_scale;
+    __syncthreads();
+    const float sc = s_scale;
 #pragma unroll
-  for (int j = 0; j < E; ++j) v[j] = cscale(v[j], sc);
-  line_fft<ELL, T, DB>(v, scratch, p, t, tw);
-  twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+    for (int j = 0; j < E; ++j) v[j] = cscale(v[j], sc);
+    line_fft<ELL, T, DB>(v, scratch, p, t, tw);
+    twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+    __syncthreads();  // scratch, row twiddles and s_scale are reused by the next tile
+  }
 }
 
 // ------------------------------------------------------ MID and LAST passes

@@ -172,6 +172,7 @@ struct Plan {
   int per_sm_mid[2][3] = {{1, 1, 1}, {1, 1, 1}};  // co-resident CTAs per SM: [layout][direction pair]
   int per_sm_last[2][2] = {{1, 1}, {1, 1}};       // [layout][inverse]
   int per_sm_lf[2] = {1, 1};                      // fused LAST + FIRST, [layout]
+  int per_sm_first[2] = {1, 1};                   // FIRST (persistent over its tiles), [layout]
   // workspace
   int B_cap = 0;
   float2* d_e0 = nullptr;
@@ -222,7 +223,7 @@ cudaError_t launch_last(const Plan& p, Layout lay, const PassArgs& a, int B, cud
 cudaError_t launch_last_first(const Plan& p, Layout lay, const PassArgs& a, int B, cudaStream_t s);
 // Max co-resident CTAs per SM of the middle pass kernels (3 direction pairs)
 // and of the last pass kernels (2 directions) of a geometry.
-cudaError_t pass_occupancy(const LineGeom& g, int* per_sm_mid, int* per_sm_last, int* per_sm_lf);
+cudaError_t pass_occupancy(const LineGeom& g, int* per_sm_mid, int* per_sm_last, int* per_sm_lf, int* per_sm_first);
 // Helpers (fourstep.cu)
 cudaError_t launch_sum_rows(const float* y, int B, int m, float* part, int chunks, cudaStream_t s);
 cudaError_t launch_norm_rows(const float2* v, int B, int n, float* part, int chunks, cudaStream_t s);
