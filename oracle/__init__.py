@@ -48,6 +48,7 @@ from .recovery import (
     loss_and_grad,
     spectral_weights,
     spectral_init,
+    spectral_init_early_stop,
     gradient_descent,
     gradient_descent_early_stop,
     step_ramp,
@@ -71,7 +72,7 @@ from . import autodiff
 __all__ = [
     "dft_matrix", "dft_naive", "unitary_fft", "unitary_ifft", "zero_pad", "trim", "untrim", "trim_offset", "forward",
     "adjoint", "dense_structured_matrix", "intensity_loss", "loss_and_grad",
-    "spectral_weights", "spectral_init", "gradient_descent", "gradient_descent_early_stop", "step_ramp", "cosine_similarity",
+    "spectral_weights", "spectral_init", "spectral_init_early_stop", "gradient_descent", "gradient_descent_early_stop", "step_ramp", "cosine_similarity",
     "relative_error_global_phase", "structured_ops", "dense_forward", "dense_adjoint",
     "dense_ops", "autodiff", "unitary_fft2", "unitary_ifft2", "zero_pad_2d", "crop_2d",
     "forward_2d", "adjoint_2d", "dense_structured_matrix_2d", "structured_ops_2d",

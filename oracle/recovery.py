@@ -145,6 +145,37 @@ def spectral_init(y: np.ndarray, v0: np.ndarray, fwd, adj, iters: int,
     return np.sqrt(np.sum(y, axis=-1, keepdims=True)) * v
 
 
+def spectral_init_early_stop(y: np.ndarray, v0: np.ndarray, fwd, adj, max_iters: int, rel_tol: float,
+                             check_every: int, mode: str = "identity", lam: float = -1.0):
+    """Power iteration of Eq. 3-4 with early stopping (Sec. IV-A runs it "with
+    early stopping" without stating the rule). Reading: lambda_t = ||u_t||,
+    u_t = M v_t + s v_t with unit v_t, estimates the top eigenvalue of M + s I;
+    after every `check_every` steps stop once every problem has
+    |lambda_{t-1} - lambda_t| <= rel_tol * lambda_{t-1} (t the chunk's last step).
+
+    Returns (x0 = sqrt(sum y) v, [lambda_0 .. lambda_{run-1}], steps run).
+    """
+    if check_every < 2:
+        raise ValueError("check_every must be >= 2")
+    y = np.asarray(y, dtype=np.float64)
+    w = spectral_weights(y, mode, lam)
+    shift = 0.0 if mode == "identity" else -2.0 * lam
+    v = np.array(v0, dtype=np.complex128, copy=True)
+    v = v / np.linalg.norm(v, axis=-1, keepdims=True)
+    lams = []
+    run = max_iters
+    for t in range(max_iters):
+        u = adj(w * fwd(v)) + shift * v
+        nrm = np.linalg.norm(u, axis=-1, keepdims=True)
+        lams.append(nrm[..., 0])
+        v = u / nrm
+        if (t + 1) % check_every == 0 and t + 1 < max_iters:
+            if np.all(np.abs(lams[t - 1] - lams[t]) <= rel_tol * lams[t - 1]):
+                run = t + 1
+                break
+    return np.sqrt(np.sum(y, axis=-1, keepdims=True)) * v, np.array(lams), run
+
+
 def cosine_similarity(xh: np.ndarray, x: np.ndarray) -> np.ndarray:
     """|<x_hat, x>| / (||x_hat|| ||x||), <a, b> = a^H b (Sec. IV-A, Eq. 6)."""
     inner = np.sum(np.conj(xh) * x, axis=-1)

@@ -74,3 +74,52 @@ def test_relative_change_is_taken_against_the_previous_loss():
     assert r <= tol < abs(hr[t - 1, 0] - hr[t, 0]) / hr[t, 0]
     _, _, got = O.gradient_descent_early_stop(x0, y, fwd, adj, 100, tol, every, mu0=0.1, tau0=5.0)
     assert got == every
+
+
+# ------------------------------------------------------------ power iteration
+
+def _spec_problem(B=2, n=24, m=96, L=2, seed=4):
+    th = S.phases(seed, L, m)
+    fwd, adj = O.structured_ops(th, n, m)
+    y = np.abs(fwd(S.signal_gaussian(seed, B, n))) ** 2
+    return th, y, S.start_vector(seed, B, n), fwd, adj
+
+
+@pytest.mark.parametrize("mode", ["identity", "optimal"])
+def test_power_iteration_zero_and_huge_tolerance(mode):
+    th, y, v0, fwd, adj = _spec_problem()
+    x, lams, run = O.spectral_init_early_stop(y, v0, fwd, adj, 40, 0.0, 8, mode=mode)
+    assert run == 40 and np.array_equal(x, O.spectral_init(y, v0, fwd, adj, 40, mode=mode))
+    x, lams, run = O.spectral_init_early_stop(y, v0, fwd, adj, 40, 10.0, 8, mode=mode)
+    assert run == 8 and np.array_equal(x, O.spectral_init(y, v0, fwd, adj, 8, mode=mode))
+
+
+def test_power_iteration_estimates_by_brute_force_and_top_eigenvalue():
+    """lambda_t recomputed from scratch: v_t from t plain power steps, then
+    ||M v_t + s v_t|| with M formed explicitly; the stop point is the first
+    check where every change is within rel_tol; lambda converges to the top
+    eigenvalue of M + s I (dense eigensolver)."""
+    th, y, v0, fwd, adj = _spec_problem()
+    n, m, lam = 24, 96, -1.0
+    A = O.dense_structured_matrix(th, n, m)
+    w = O.spectral_weights(y, "optimal", lam)
+    s_ = -2.0 * lam
+    T, tol, every = 120, 1e-4, 6
+    x, lams, run = O.spectral_init_early_stop(y, v0, fwd, adj, T, tol, every, mode="optimal", lam=lam)
+    brute = np.zeros((run, y.shape[0]))
+    for t in range(run):
+        vt = O.spectral_init(y, v0, fwd, adj, t, mode="optimal", lam=lam) / np.sqrt(np.sum(y, -1, keepdims=True))
+        for b in range(y.shape[0]):
+            M = A.conj().T @ (w[b][:, None] * A) + s_ * np.eye(n)
+            brute[t, b] = np.linalg.norm(M @ vt[b])
+    assert np.allclose(lams, brute, rtol=1e-10)
+    want = T
+    for t in range(every - 1, T - 1, every):
+        if t < run and np.all(np.abs(brute[t - 1] - brute[t]) <= tol * brute[t - 1]):
+            want = t + 1
+            break
+    assert run == want and every < run < T
+    for b in range(y.shape[0]):
+        M = A.conj().T @ (w[b][:, None] * A) + s_ * np.eye(n)
+        top = np.max(np.linalg.eigvalsh(M))
+        assert abs(lams[-1, b] - top) <= 1e-2 * top
