@@ -179,6 +179,18 @@ sr_status sr_loss_grad(sr_plan* plan, const void* x, const float* y, float* loss
 sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int iters,
                            const sr_spectral_opts* opts, void* x_out, int B, void* stream);
 
+/* sr_spectral_init_early_stop: the same power iteration with early stopping
+ * (Sec. IV-A runs it "with early stopping" and states no rule). lambda_t =
+ * ||u_t|| estimates the top eigenvalue of M + s I; after every check_every
+ * (>= 2) steps it stops once, for every problem, |lambda_{t-1} - lambda_t| <=
+ * rel_tol * lambda_{t-1}; at most max_iters steps. *iters_run (host int)
+ * receives the number run. Each check synchronises `stream` (a copy of the
+ * norm partials to the host), so the call cannot be captured in a graph.
+ * rel_tol must be finite and >= 0. */
+sr_status sr_spectral_init_early_stop(sr_plan* plan, const float* y, const void* v0, int max_iters,
+                                      const sr_spectral_opts* opts, float rel_tol, int check_every,
+                                      void* x_out, int* iters_run, int B, void* stream);
+
 /* ---- gradient descent (Sec. II-B-1, Sec. IV-A) ------------------------------
  * `iters` steps x <- x - mu_t * 2 A^H((|Ax|^2 - y) * Ax) with
  *   mu_t = mu0 * (1 - exp(-(t+1)/tau0)) * m / sum(y)   (tau0 > 0), or

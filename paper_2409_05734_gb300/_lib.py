@@ -47,6 +47,8 @@ SIGNATURES = [
     ("sr_adjoint", C.c_int, [_VP, _VP, _VP, C.c_int, _VP]),
     ("sr_loss_grad", C.c_int, [_VP, _VP, _VP, _VP, _VP, C.c_int, _VP]),
     ("sr_spectral_init", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(SpectralOpts), _VP, C.c_int, _VP]),
+    ("sr_spectral_init_early_stop", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(SpectralOpts), C.c_float, C.c_int,
+                                              _VP, C.POINTER(C.c_int), C.c_int, _VP]),
     ("sr_gd_solve", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(GdOpts), _VP, C.c_int, _VP]),
     ("sr_gd_solve_early_stop", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(GdOpts), C.c_float, C.c_int, _VP,
                                          C.POINTER(C.c_int), C.c_int, _VP]),

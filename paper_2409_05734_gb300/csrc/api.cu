@@ -786,6 +786,115 @@ sr_status create_plan(int64_t n, int64_t m, int L, uint64_t seed, int gh, int gw
   *out = p;
   return SR_OK;
 }
+// Power iteration shared by the spectral entry points: the step chains, the
+// ping-pong banks of norm partials and the bank of the latest iterate.
+struct SpectralRun {
+  Plan* p = nullptr;
+  int B = 0;
+  cudaStream_t s = nullptr;
+  float2* v = nullptr;
+  float* bank[2] = {nullptr, nullptr};
+  int prev = 1, prev_count = 0, last_cpp = 0;
+  int done = 0;  // steps run so far
+  bool window = false, fuse = false;
+  Chain c, f, a;
+
+  sr_status setup(sr_plan* plan, const float* y, const void* v0, const sr_spectral_opts* opts, void* x_out, int nb,
+                  cudaStream_t st_) {
+    sr_status st = check_plan_call(plan, nb);
+    if (st != SR_OK) return st;
+    if (!y || !v0 || !x_out) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
+    sr_spectral_opts o{SR_WEIGHT_IDENTITY, -1.0f};
+    if (opts) o = *opts;
+    if (o.weight_mode != SR_WEIGHT_IDENTITY && o.weight_mode != SR_WEIGHT_OPTIMAL)
+      return fail(SR_ERR_INVALID_ARG, "unknown weight_mode");
+    if (o.weight_mode == SR_WEIGHT_OPTIMAL && !(o.lambda < 0.f && std::isfinite(o.lambda)))
+      return fail(SR_ERR_INVALID_ARG, "lambda must be finite and < 0");
+    p = plan;
+    B = nb;
+    s = st_;
+    const int n = (int)p->n;
+    if (x_out != v0)
+      SR_CUDA(cudaMemcpyAsync(x_out, v0, (size_t)B * n * sizeof(float2), cudaMemcpyDeviceToDevice, s),
+              "cudaMemcpyAsync(v0)");
+    if ((st = prepare_y(p, y, B, 0.f, s)) != SR_OK) return st;
+    const float* ye = nullptr;
+    if ((st = epilogue_y(p, y, B, s, &ye)) != SR_OK) return st;
+    v = (float2*)x_out;
+    prev_count = std::min(64, (n + 4095) / 4096);
+    bank[0] = part_bank(*p, 0, B);
+    bank[1] = part_bank(*p, 1, B);
+    SR_CUDA(sr::launch_norm_rows(v, B, n, bank[1], prev_count, s), "launch(norm v0)");
+    last_cpp = final_partials(*p, 2 * p->L, 0);
+    const float shift = o.weight_mode == SR_WEIGHT_IDENTITY ? 0.f : -2.0f * o.lambda;
+    window = p->mo < p->m;
+    if (window) {
+      // alpha < 1: forward chain of v / ||v|| into the window, adjoint chain with
+      // the spectral weights in its first pass and the update u = M v + s v last
+      f = forward_chain(*p);
+      f.xin = v;
+      f.xout = p->d_zw;
+      a = window_adjoint_chain(*p, sr::kOpSpecEpilogue, ye);
+      a.sumy = p->d_scal;
+      a.lam = o.lambda;
+      a.weight_mode = o.weight_mode;
+      a.norm_at_epilogue = true;  // no input scale in its first pass; the last pass uses norm_in
+      a.xout = v;
+      a.out_mode = sr::kOutSpec;
+      a.shift = shift;
+      return SR_OK;
+    }
+    c = round_trip_chain(*p, sr::kOpSpecEpilogue);
+    c.xin = v;
+    c.n_in = n;
+    c.xout = v;
+    c.n_out = n;
+    c.out_mode = sr::kOutSpec;
+    c.shift = shift;
+    c.y = ye;
+    c.sumy = p->d_scal;
+    c.lam = o.lambda;
+    c.weight_mode = o.weight_mode;
+    // Consecutive steps share a kernel (see sr_gd_solve); the iterate then enters
+    // each step unnormalised and its 1/||u|| is applied in the spectral epilogue.
+    fuse = !p->inner;
+    c.norm_at_epilogue = fuse;
+    return SR_OK;
+  }
+
+  // `count` more steps u = M v + s v (v = previous u / ||u||); the last of them
+  // does not fuse into a following FIRST, so calls can be chained.
+  sr_status steps(int count) {
+    sr_status st;
+    for (int it = 0; it < count; ++it, ++done) {
+      const int cur = done % 2;
+      if (window) {
+        f.norm_in = a.norm_in = bank[prev];
+        f.norm_in_count = a.norm_in_count = prev_count;
+        a.spec_part_out = bank[cur];
+        if ((st = run_chain(*p, f, B, s)) != SR_OK) return st;
+        if ((st = run_chain(*p, a, B, s)) != SR_OK) return st;
+      } else {
+        c.norm_in = bank[prev];
+        c.norm_in_count = prev_count;
+        c.spec_part_out = bank[cur];
+        c.skip_first = fuse && it > 0;
+        c.fuse_next_first = fuse && it + 1 < count;
+        if ((st = run_chain(*p, c, B, s)) != SR_OK) return st;
+      }
+      prev = cur;
+      prev_count = last_cpp;
+    }
+    return SR_OK;
+  }
+
+  // x = sqrt(sum y) v / ||v||
+  sr_status finish() {
+    SR_CUDA(sr::launch_scale_rows(v, B, (int)p->n, bank[prev], prev_count, p->d_scal, s), "launch(scale)");
+    return SR_OK;
+  }
+};
+
 // Validation and the per-problem step mu0 * m / sum(y) shared by the GD entry points.
 sr_status gd_setup(sr_plan* plan, const float* y, void* x, int iters, const sr_gd_opts* opts, int B, void* stream,
                    float* mu0_out, float* tau0_out) {
@@ -1080,87 +1189,48 @@ sr_status sr_loss_grad(sr_plan* plan, const void* x, const float* y, float* loss
 
 sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int iters, const sr_spectral_opts* opts,
                            void* x_out, int B, void* stream) {
-  sr_status st = check_plan_call(plan, B);
-  if (st != SR_OK) return st;
-  if (!y || !v0 || !x_out) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
   if (iters < 0) return fail(SR_ERR_INVALID_ARG, "iters must be >= 0");
-  sr_spectral_opts o{SR_WEIGHT_IDENTITY, -1.0f};
-  if (opts) o = *opts;
-  if (o.weight_mode != SR_WEIGHT_IDENTITY && o.weight_mode != SR_WEIGHT_OPTIMAL)
-    return fail(SR_ERR_INVALID_ARG, "unknown weight_mode");
-  if (o.weight_mode == SR_WEIGHT_OPTIMAL && !(o.lambda < 0.f && std::isfinite(o.lambda)))
-    return fail(SR_ERR_INVALID_ARG, "lambda must be finite and < 0");
-  Plan& p = *plan;
-  cudaStream_t s = (cudaStream_t)stream;
-  const int n = (int)p.n;
-  if (x_out != v0)
-    SR_CUDA(cudaMemcpyAsync(x_out, v0, (size_t)B * n * sizeof(float2), cudaMemcpyDeviceToDevice, s),
-            "cudaMemcpyAsync(v0)");
-  if ((st = prepare_y(&p, y, B, 0.f, s)) != SR_OK) return st;
-  const float* ye = nullptr;
-  if ((st = epilogue_y(&p, y, B, s, &ye)) != SR_OK) return st;
-  float2* v = (float2*)x_out;
-  const int init_chunks = std::min(64, (n + 4095) / 4096);
-  float* bank[2] = {part_bank(p, 0, B), part_bank(p, 1, B)};
-  SR_CUDA(sr::launch_norm_rows(v, B, n, bank[1], init_chunks, s), "launch(norm v0)");
-  const int last_cpp = final_partials(p, 2 * p.L, 0);
-  if (p.mo < p.m) {
-    // alpha < 1: forward chain of v / ||v|| into the window, adjoint chain with
-    // the spectral weights in its first pass and the update u = M v + s v last
-    Chain f = forward_chain(p);
-    f.xin = v;
-    f.xout = p.d_zw;
-    Chain a = window_adjoint_chain(p, sr::kOpSpecEpilogue, ye);
-    a.sumy = p.d_scal;
-    a.lam = o.lambda;
-    a.weight_mode = o.weight_mode;
-    a.norm_at_epilogue = true;  // no input scale in its first pass; the last pass uses norm_in
-    a.xout = v;
-    a.out_mode = sr::kOutSpec;
-    a.shift = o.weight_mode == SR_WEIGHT_IDENTITY ? 0.f : -2.0f * o.lambda;
-    int prev = 1, prev_count = init_chunks;
-    for (int it = 0; it < iters; ++it) {
-      const int cur = it % 2;
-      f.norm_in = a.norm_in = bank[prev];
-      f.norm_in_count = a.norm_in_count = prev_count;
-      a.spec_part_out = bank[cur];
-      if ((st = run_chain(p, f, B, s)) != SR_OK) return st;
-      if ((st = run_chain(p, a, B, s)) != SR_OK) return st;
-      prev = cur;
-      prev_count = last_cpp;
+  SpectralRun r;
+  sr_status st = r.setup(plan, y, v0, opts, x_out, B, (cudaStream_t)stream);
+  if (st != SR_OK) return st;
+  if ((st = r.steps(iters)) != SR_OK) return st;
+  return r.finish();
+}
+
+sr_status sr_spectral_init_early_stop(sr_plan* plan, const float* y, const void* v0, int max_iters,
+                                      const sr_spectral_opts* opts, float rel_tol, int check_every, void* x_out,
+                                      int* iters_run, int B, void* stream) {
+  if (!iters_run) return fail(SR_ERR_INVALID_ARG, "iters_run is NULL");
+  *iters_run = 0;
+  if (max_iters < 0) return fail(SR_ERR_INVALID_ARG, "max_iters must be >= 0");
+  if (check_every < 2) return fail(SR_ERR_INVALID_ARG, "check_every must be >= 2");
+  if (!(rel_tol >= 0.f && std::isfinite(rel_tol))) return fail(SR_ERR_INVALID_ARG, "rel_tol must be finite and >= 0");
+  SpectralRun r;
+  sr_status st = r.setup(plan, y, v0, opts, x_out, B, (cudaStream_t)stream);
+  if (st != SR_OK) return st;
+  const int stride = part_stride(*plan);
+  std::vector<float> banks(2 * (size_t)B * stride);
+  while (r.done < max_iters) {
+    const int count = std::min(check_every, max_iters - r.done);
+    if ((st = r.steps(count)) != SR_OK) return st;
+    *iters_run = r.done;
+    if (count < check_every || r.done >= max_iters) break;
+    // lambda_t^2 and lambda_{t-1}^2 are the sums of the two banks' partials
+    // (bank k holds problem b's last_cpp partials at k B stride + b last_cpp)
+    SR_CUDA(cudaMemcpyAsync(banks.data(), r.bank[0], banks.size() * sizeof(float), cudaMemcpyDeviceToHost, r.s),
+            "cudaMemcpyAsync(norm partials)");
+    SR_CUDA(cudaStreamSynchronize(r.s), "cudaStreamSynchronize");
+    bool all = true;
+    for (int b = 0; b < B && all; ++b) {
+      double sq[2] = {0.0, 0.0};
+      for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < r.last_cpp; ++i) sq[k] += banks[(size_t)k * B * stride + (size_t)b * r.last_cpp + i];
+      const double cur = std::sqrt(sq[r.prev]), prev = std::sqrt(sq[1 - r.prev]);
+      all = std::fabs(prev - cur) <= (double)rel_tol * prev;
     }
-    SR_CUDA(sr::launch_scale_rows(v, B, n, bank[prev], prev_count, p.d_scal, s), "launch(scale)");
-    return SR_OK;
+    if (all) break;
   }
-  Chain c = round_trip_chain(p, sr::kOpSpecEpilogue);
-  c.xin = v;
-  c.n_in = n;
-  c.xout = v;
-  c.n_out = n;
-  c.out_mode = sr::kOutSpec;
-  c.shift = o.weight_mode == SR_WEIGHT_IDENTITY ? 0.f : -2.0f * o.lambda;
-  c.y = ye;
-  c.sumy = p.d_scal;
-  c.lam = o.lambda;
-  c.weight_mode = o.weight_mode;
-  // Consecutive steps share a kernel (see sr_gd_solve); the iterate then enters
-  // each step unnormalised and its 1/||u|| is applied in the spectral epilogue.
-  const bool fuse = !p.inner;
-  c.norm_at_epilogue = fuse;
-  int prev = 1, prev_count = init_chunks;
-  for (int it = 0; it < iters; ++it) {
-    const int cur = it % 2;
-    c.norm_in = bank[prev];
-    c.norm_in_count = prev_count;
-    c.spec_part_out = bank[cur];
-    c.skip_first = fuse && it > 0;
-    c.fuse_next_first = fuse && it + 1 < iters;
-    if ((st = run_chain(p, c, B, s)) != SR_OK) return st;
-    prev = cur;
-    prev_count = last_cpp;
-  }
-  SR_CUDA(sr::launch_scale_rows(v, B, n, bank[prev], prev_count, p.d_scal, s), "launch(scale)");
-  return SR_OK;
+  return r.finish();
 }
 
 sr_status sr_gd_solve(sr_plan* plan, const float* y, void* x, int iters, const sr_gd_opts* opts, float* loss_hist,

@@ -191,6 +191,25 @@ class Plan:
                                                   _stream_handle()), "sr_spectral_init")
         return x
 
+    def spectral_init_early_stop(self, y: torch.Tensor, v0: torch.Tensor, max_iters: int, rel_tol: float,
+                                 check_every: int = 50, weight: str = "identity", lam: float = -1.0,
+                                 out: torch.Tensor | None = None):
+        """Power iteration with early stopping: every check_every steps, stop once
+        every problem's eigenvalue estimate ||M v + s v|| changed by <= rel_tol
+        relative. Synchronises at each check. Returns (x, steps run)."""
+        y = self._f32(y, self.m, "y")
+        v0 = self._c64(v0, self.n, "v0")
+        B = self._batch(v0)
+        mode = {"identity": _lib.SR_WEIGHT_IDENTITY, "optimal": _lib.SR_WEIGHT_OPTIMAL}[weight]
+        opts = _lib.SpectralOpts(mode, float(lam))
+        x = out if out is not None else torch.empty_like(v0)
+        run = C.c_int(0)
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_spectral_init_early_stop(self._h, _p(y), _p(v0), int(max_iters), C.byref(opts),
+                                                             float(rel_tol), int(check_every), _p(x), C.byref(run),
+                                                             B, _stream_handle()), "sr_spectral_init_early_stop")
+        return x, run.value
+
     def gd_solve(self, y: torch.Tensor, x: torch.Tensor, iters: int, mu0: float = 0.1, tau0: float = 0.0,
                  record_loss: bool = False, loss_hist: torch.Tensor | None = None):
         """In-place GD on x (Sec. II-B-1), step mu0 (1 - exp(-(t+1)/tau0)) m / sum(y)

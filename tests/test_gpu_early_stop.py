@@ -75,3 +75,38 @@ def test_early_stop_without_history_and_limits(Plan):
     assert t == 4
     with pytest.raises(Exception):
         plan.gd_solve_early_stop(yd, x1, 10, 1e-3, check_every=1)
+
+
+@pytest.mark.parametrize("B,n,m,L,seed,tol,every", [(3, 256, 1024, 2, 8, 1e-4, 5),
+                                                     (2, 1024, 4096, 2, 5, 1e-4, 6)])
+def test_power_iteration_early_stop_matches_oracle(Plan, B, n, m, L, seed, tol, every):
+    """The eigenvalue estimates change by ~1e-4 relative at the decision; FP32
+    norms are accurate to ~1e-6, so the margin asserted on the oracle (15%)
+    covers the FP32 error of the change by an order of magnitude."""
+    th = S.phases(seed, L, m)
+    fwd, adj = O.structured_ops(th, n, m)
+    y = np.abs(fwd(S.signal_gaussian(seed, B, n))) ** 2
+    v0 = S.start_vector(seed, B, n)
+    T = 400
+    x_o, lams, t_o = O.spectral_init_early_stop(y, v0, fwd, adj, T, tol, every, mode="optimal")
+    assert every < t_o < T
+    ratio = lambda t: np.max(np.abs(lams[t - 2] - lams[t - 1]) / lams[t - 2]) / tol
+    assert ratio(t_o) <= 0.9 and ratio(t_o - every) >= 1.1
+    plan = Plan(n, m, L, seed)
+    x, t_g = plan.spectral_init_early_stop(torch.from_numpy(y).float().cuda(),
+                                           torch.from_numpy(v0).to(torch.complex64).cuda(), T, tol,
+                                           check_every=every, weight="optimal")
+    plan.check()
+    assert t_g == t_o
+    xg = x.cpu().numpy().astype(np.complex128)
+    for b in range(B):
+        assert np.linalg.norm(xg[b] - x_o[b]) / np.linalg.norm(x_o[b]) <= 1e-4
+    # zero tolerance: every step runs and the result is that of sr_spectral_init
+    x2 = plan.spectral_init(torch.from_numpy(y).float().cuda(), torch.from_numpy(v0).to(torch.complex64).cuda(),
+                            37, weight="optimal")
+    x3, t3 = plan.spectral_init_early_stop(torch.from_numpy(y).float().cuda(),
+                                           torch.from_numpy(v0).to(torch.complex64).cuda(), 37, 0.0,
+                                           check_every=every, weight="optimal")
+    plan.check()
+    assert t3 == 37
+    assert (torch.linalg.vector_norm(x3 - x2) / torch.linalg.vector_norm(x2)).item() <= 1e-6
