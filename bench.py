@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch workload")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the radix-3 and differentiable-operator workloads")
+    ap.add_argument("--only", choices=sorted(EXTRA_LEGS),
+                    help="run only this extra workload and print its JSON (for profiling one leg)")
     return ap.parse_args()
 
 
@@ -897,10 +899,33 @@ def run_ours(args):
     return 0
 
 
+EXTRA_LEGS = {
+    "radix3": "radix3_workload",
+    "two_d": "two_d_workload",
+    "forward_curve": "forward_time_vs_size",
+    "autograd": "autograd_workload",
+}
+
+
+def run_only(args):
+    """One extra workload on its own (rank 0, one GPU): its JSON object."""
+    import torch
+    from paper_2409_05734_gb300 import buildlib
+    buildlib.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = globals()[EXTRA_LEGS[args.only]](torch, dev, flush)
+    print(json.dumps({"only": args.only, **out}))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_ours(args)
 
 
