@@ -64,6 +64,8 @@ OPERATOR_CASES = [
     (20000, 2 ** 16, 2, 2),
     (2 ** 14, 2 ** 16, 4, 1),
     (2 ** 17 - 5, 2 ** 19, 2, 1),
+    (2 ** 20 + 7, 2 ** 21, 2, 1),       # lines of 2048 (4 per tile, unswizzled TMA) and 1024
+    (3 * 2 ** 20, 2 ** 23, 3, 1),       # lines of 4096 (2 per tile) and 2048
     (7, 16, 2, 1000),
 ]
 
