@@ -594,6 +594,70 @@ def forward_time_vs_size(torch, dev, flush, reps: int = 5):
                         "against the dense i.i.d. model (BF16, n = m = S^2, S <= 128)", "rows": rows}
 
 
+# Run on demand (`--only sweep`, a few minutes of GPU time), not in the default bench.
+SWEEP = dict(n=2 ** 16, alphas=(1, 1.5, 2, 3, 4, 6, 8), Ls=(1, 2, 3, 4), snrs=(None, 40, 30, 20), seeds=32,
+             spectral_iters=1000, gd_iters=3000, mu0=0.15, tau0=100.0, weight="optimal", lam=-1.0, tol=1e-3,
+             base_seed=20240905)
+
+
+def robustness_sweep(torch, dev, flush):
+    """The robustness sweep: n = 2^16 complex Gaussian signals, L in {1..4},
+    alpha in {1, 1.5, 2, 3, 4, 6, 8}, Gaussian noise on y at SNR 40 / 30 / 20 dB
+    (and noiseless), 32 independent trials per cell (each problem of the batch
+    has its own phases), spectral initialisation + GD; success = relative error
+    below 1e-3 up to a global phase. Event-timed solves, L2 flushed before each."""
+    import math
+    from paper_2409_05734_gb300 import Plan
+    C = SWEEP
+    n, B, sp, gd = C["n"], C["seeds"], C["spectral_iters"], C["gd_iters"]
+    gen = torch.Generator(device=dev)
+    succ, med = {}, {}
+    total_ms, total_iters = 0.0, 0
+    for L in C["Ls"]:
+        for alpha in C["alphas"]:
+            m = int(round(alpha * n))
+            cell = C["base_seed"] + 100000 * L + int(10 * alpha) * 1000
+            plan = Plan(n, m, L, cell)
+            plan.set_batch_seeds([cell + b for b in range(B)])
+            plan.reserve(B)
+            gen.manual_seed(cell)
+            x_true = torch.randn((B, n), dtype=torch.complex64, device=dev, generator=gen)
+            v0 = torch.randn((B, n), dtype=torch.complex64, device=dev, generator=gen)
+            y0 = plan.forward(x_true).abs() ** 2
+            for snr in C["snrs"]:
+                y = y0
+                if snr is not None:  # SNR = ||y0||^2 / E||noise||^2, noise ~ N(0, sigma^2) per entry
+                    sigma = torch.linalg.vector_norm(y0, dim=1, keepdim=True) / math.sqrt(m * 10 ** (snr / 10))
+                    y = y0 + sigma * torch.randn(y0.shape, device=dev, generator=gen)
+                y = y.contiguous()
+                x = torch.empty_like(v0)
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                plan.spectral_init(y, v0, sp, weight=C["weight"], lam=C["lam"], out=x)
+                plan.gd_solve(y, x, gd, mu0=C["mu0"], tau0=C["tau0"])
+                e1.record()
+                torch.cuda.synchronize()
+                total_ms += e0.elapsed_time(e1)
+                total_iters += B * (sp + gd)
+                inner = torch.sum(torch.conj(x) * x_true, dim=1, keepdim=True)
+                phase = inner / inner.abs().clamp_min(1e-30)
+                err = (torch.linalg.vector_norm(phase * x - x_true, dim=1) /
+                       torch.linalg.vector_norm(x_true, dim=1)).cpu().numpy().astype(np.float64)
+                key = f"L={L} " + ("noiseless" if snr is None else f"{snr}dB")
+                ok = np.isfinite(err) & (err < C["tol"])
+                succ.setdefault(key, []).append(round(float(np.mean(ok)), 4))
+                med.setdefault(key, []).append(float(np.median(np.where(np.isfinite(err), err, np.inf))))
+            plan.check()
+            del plan
+    return {"workload": f"n = 2^16 complex Gaussian signals, {B} trials per cell with their own phases, "
+                        f"alpha {list(C['alphas'])}, L {list(C['Ls'])}, Gaussian noise on y at SNR 40 / 30 / 20 dB "
+                        f"and noiseless, {sp} power (optimal weights) + {gd} GD iterations; success = relative "
+                        f"error < {C['tol']} up to a global phase",
+            "alphas": list(C["alphas"]), "success_rate": succ, "median_rel_err": med,
+            "solve_ms_total": total_ms, "problem_iters_per_s": total_iters / (total_ms / 1e3)}
+
+
 def autograd_workload(torch, dev, flush):
     """Forward and backward of the differentiable operator (x, theta) -> z = A x at
     B = 8, n = 2^20, m = 2^22, L = 2, driven by a loss on |z|^2."""
@@ -904,6 +968,7 @@ EXTRA_LEGS = {
     "two_d": "two_d_workload",
     "forward_curve": "forward_time_vs_size",
     "autograd": "autograd_workload",
+    "sweep": "robustness_sweep",
 }
 
 

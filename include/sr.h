@@ -120,6 +120,15 @@ sr_status sr_plan_create_2d(int64_t h, int64_t w, int64_t S, int L, uint64_t see
 sr_status sr_plan_get_phases(const sr_plan* plan, double* theta);
 sr_status sr_plan_set_phases(sr_plan* plan, const double* theta);
 
+/* sr_plan_set_batch_phases: gives each of B problems its own operator, with
+ * the phases of sr_phases(seeds[b], L, N) for problem b (independent trials of
+ * the random model, as in a recovery sweep). The diagonal tables become
+ * [B][L][N] (host-built, synchronous); afterwards every call on the plan must
+ * use this batch size B (else SR_ERR_INVALID_ARG), and sr_plan_get_phases
+ * returns problem 0's phases. seeds: host uint64_t[B]. 2D plans return
+ * SR_ERR_UNSUPPORTED. */
+sr_status sr_plan_set_batch_phases(sr_plan* plan, int B, const uint64_t* seeds);
+
 /* Replaces the phases from DEVICE memory (float[L*N], e.g. a trainable
  * tensor): the diagonal tables are rebuilt on `stream` (D = exp(i theta)/sqrt(m)
  * in float). The host copy returned by sr_plan_get_phases is refreshed from

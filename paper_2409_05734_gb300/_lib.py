@@ -37,6 +37,7 @@ _VP = C.c_void_p
 SIGNATURES = [
     ("sr_phases", C.c_int, [C.c_uint64, C.c_int, C.c_int64, C.POINTER(C.c_double)]),
     ("sr_plan_create", C.c_int, [C.c_int64, C.c_int64, C.c_int, C.c_uint64, C.POINTER(_VP)]),
+    ("sr_plan_set_batch_phases", C.c_int, [_VP, C.c_int, C.POINTER(C.c_uint64)]),
     ("sr_plan_create_2d", C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_uint64, C.POINTER(_VP)]),
     ("sr_plan_destroy", C.c_int, [_VP]),
     ("sr_plan_get_phases", C.c_int, [_VP, C.POINTER(C.c_double)]),

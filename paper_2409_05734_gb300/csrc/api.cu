@@ -1009,6 +1009,15 @@ sr_status sr_plan_destroy(sr_plan* plan) {
   return SR_OK;
 }
 
+sr_status sr_plan_set_batch_phases(sr_plan* plan, int B, const uint64_t* seeds) {
+  if (!plan || !seeds || B < 1) return fail(SR_ERR_INVALID_ARG, "NULL argument or B < 1");
+  if (plan->two_d) return fail(SR_ERR_UNSUPPORTED, "per-problem phases are not supported on 2D plans");
+  if (plan->inner && 3 * B > 65535) return fail(SR_ERR_UNSUPPORTED, "B must be <= 21845 when m = 3 * 2^a");
+  sr_status st = check_device(plan);
+  if (st != SR_OK) return st;
+  return sr::plan_set_problem_phases(plan, B, seeds);
+}
+
 sr_status sr_plan_get_phases(const sr_plan* plan_c, double* theta) {
   if (!plan_c || !theta) return fail(SR_ERR_INVALID_ARG, "NULL argument");
   sr_plan* plan = const_cast<sr_plan*>(plan_c);

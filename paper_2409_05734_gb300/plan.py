@@ -80,6 +80,13 @@ class Plan:
             _lib.check(self._lib.sr_plan_set_phases(self._h, th.ctypes.data_as(C.POINTER(C.c_double))),
                        "sr_plan_set_phases")
 
+    def set_batch_seeds(self, seeds) -> None:
+        """Give problem b of every later call its own phases sr_phases(seeds[b], L, N)
+        (independent random operators in one batch); later calls must use B = len(seeds)."""
+        arr = (C.c_uint64 * len(seeds))(*[int(v) for v in seeds])
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_plan_set_batch_phases(self._h, len(seeds), arr), "sr_plan_set_batch_phases")
+
     def check(self) -> None:
         """Synchronise and raise if a kernel of this plan recorded a device-side error."""
         with torch.cuda.device(self.device):

@@ -43,3 +43,25 @@ def test_one_layer_plus_extra_fft(Plan, n, m, B):
     xa = plan.adjoint(torch.from_numpy(w).to(torch.complex64).cuda()).cpu().numpy()
     plan.check()
     assert rel(xa, want_a) <= 1e-5
+
+
+@pytest.mark.parametrize("n,m,L", [(100, 512, 2), (64, 192, 3), (512, 300, 2)])
+def test_batch_seeds_give_each_problem_its_own_operator(Plan, n, m, L):
+    """Problem b of the batch uses the phases of seeds[b] (power-of-two, radix-3
+    and alpha < 1 plans); a call with another batch size is refused."""
+    seeds = [11, 2024, 77, 5]
+    B = len(seeds)
+    N = max(n, m)
+    plan = Plan(n, m, L, 999)
+    plan.set_batch_seeds(seeds)
+    x = S.signal_gaussian(3, B, n)
+    z = plan.forward(torch.from_numpy(x).to(torch.complex64).cuda()).cpu().numpy()
+    w = S.complex_gaussian(4, (B, m), S.STREAM_NOISE)
+    xa = plan.adjoint(torch.from_numpy(w).to(torch.complex64).cuda()).cpu().numpy()
+    plan.check()
+    for b, sd in enumerate(seeds):
+        th = S.phases(sd, L, N)
+        assert rel(z[b], O.forward(x[b], th, m)) <= 1e-5
+        assert rel(xa[b], O.adjoint(w[b], th, n)) <= 1e-5
+    with pytest.raises(Exception):
+        plan.forward(torch.from_numpy(x[:2]).to(torch.complex64).cuda())
