@@ -650,7 +650,41 @@ def robustness_sweep(torch, dev, flush):
                 med.setdefault(key, []).append(float(np.median(np.where(np.isfinite(err), err, np.inf))))
             plan.check()
             del plan
-    return {"workload": f"n = 2^16 complex Gaussian signals, {B} trials per cell with their own phases, "
+    # the dense i.i.d. model at n = 4096 (one CN(0, 1/m) matrix per alpha, rounded
+    # to BF16 by the model; the 32 trials share it), same protocol and noise
+    from paper_2409_05734_gb300 import DenseModel
+    nd = 4096
+    dsucc, dmed = {}, {}
+    for alpha in C["alphas"]:
+        m = int(round(alpha * nd))
+        rng = np.random.default_rng(C["base_seed"] + int(10 * alpha))
+        a = rng.standard_normal((m, nd, 2), dtype=np.float32) * np.float32(1.0 / np.sqrt(2.0 * m))
+        dense = DenseModel(a.view(np.complex64)[..., 0])
+        del a
+        gen.manual_seed(C["base_seed"] + int(10 * alpha))
+        x_true = torch.randn((B, nd), dtype=torch.complex64, device=dev, generator=gen)
+        v0 = torch.randn((B, nd), dtype=torch.complex64, device=dev, generator=gen)
+        y0 = dense.forward(x_true).abs() ** 2
+        for snr in C["snrs"]:
+            y = y0
+            if snr is not None:
+                sigma = torch.linalg.vector_norm(y0, dim=1, keepdim=True) / math.sqrt(m * 10 ** (snr / 10))
+                y = y0 + sigma * torch.randn(y0.shape, device=dev, generator=gen)
+            y = y.contiguous()
+            x = dense.spectral_init(y, v0, sp, weight=C["weight"], lam=C["lam"])
+            dense.gd_solve(y, x, gd, mu0=C["mu0"], tau0=C["tau0"])
+            inner = torch.sum(torch.conj(x) * x_true, dim=1, keepdim=True)
+            phase = inner / inner.abs().clamp_min(1e-30)
+            err = (torch.linalg.vector_norm(phase * x - x_true, dim=1) /
+                   torch.linalg.vector_norm(x_true, dim=1)).cpu().numpy().astype(np.float64)
+            key = "noiseless" if snr is None else f"{snr}dB"
+            ok = np.isfinite(err) & (err < C["tol"])
+            dsucc.setdefault(key, []).append(round(float(np.mean(ok)), 4))
+            dmed.setdefault(key, []).append(float(np.median(np.where(np.isfinite(err), err, np.inf))))
+        dense.check()
+        del dense
+    return {"dense_iid_n4096": {"success_rate": dsucc, "median_rel_err": dmed},
+            "workload": f"n = 2^16 complex Gaussian signals, {B} trials per cell with their own phases, "
                         f"alpha {list(C['alphas'])}, L {list(C['Ls'])}, Gaussian noise on y at SNR 40 / 30 / 20 dB "
                         f"and noiseless, {sp} power (optimal weights) + {gd} GD iterations; success = relative "
                         f"error < {C['tol']} up to a global phase",
