@@ -110,3 +110,27 @@ def test_power_iteration_early_stop_matches_oracle(Plan, B, n, m, L, seed, tol, 
     plan.check()
     assert t3 == 37
     assert (torch.linalg.vector_norm(x3 - x2) / torch.linalg.vector_norm(x2)).item() <= 1e-6
+
+
+@pytest.mark.parametrize("kind", ["radix3", "alpha<1", "2d odd L"])
+def test_early_stop_calls_on_every_plan_kind(Plan, kind):
+    """With a zero tolerance both early-stopping calls run every step and give
+    the plain calls' results (chunk boundaries only change the kernel split)."""
+    from paper_2409_05734_gb300 import Plan2D
+    plan = {"radix3": lambda: Plan(100, 384, 2, 7),
+            "alpha<1": lambda: Plan(512, 300, 2, 7),
+            "2d odd L": lambda: Plan2D(12, 10, 16, 3, 7)}[kind]()
+    B = 2
+    x_true = torch.from_numpy(S.signal_gaussian(5, B, plan.n)).to(torch.complex64).cuda()
+    y = (plan.forward(x_true).abs() ** 2).contiguous()
+    v0 = torch.from_numpy(S.start_vector(5, B, plan.n)).to(torch.complex64).cuda()
+    a = plan.spectral_init(y, v0, 13, weight="optimal")
+    b, t = plan.spectral_init_early_stop(y, v0, 13, 0.0, check_every=5, weight="optimal")
+    assert t == 13
+    assert (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(a)).item() <= 1e-6
+    x1, x2 = a.clone(), a.clone()
+    plan.gd_solve(y, x1, 13, mu0=0.05, tau0=5.0)
+    _, t, _ = plan.gd_solve_early_stop(y, x2, 13, 0.0, check_every=5, mu0=0.05, tau0=5.0)
+    plan.check()
+    assert t == 13
+    assert (torch.linalg.vector_norm(x1 - x2) / torch.linalg.vector_norm(x1)).item() <= 1e-6
