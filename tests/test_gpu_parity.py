@@ -66,6 +66,7 @@ OPERATOR_CASES = [
     (2 ** 17 - 5, 2 ** 19, 2, 1),
     (2 ** 20 + 7, 2 ** 21, 2, 1),       # lines of 2048 (4 per tile, unswizzled TMA) and 1024
     (3 * 2 ** 20, 2 ** 23, 3, 1),       # lines of 4096 (2 per tile) and 2048
+    (2 ** 22 + 3, 2 ** 24, 2, 1),       # the largest power-of-two length
     (7, 16, 2, 1000),
 ]
 

@@ -54,6 +54,7 @@ CASES = [
     (2 ** 16, 3 * 2 ** 16, 3, 1),
     (2 ** 16, 3 * 2 ** 17, 2, 1),
     (7, 48, 2, 700),
+    (2 ** 22 - 1, 3 * 2 ** 22, 2, 1),  # the largest radix-3 length
 ]
 
 
