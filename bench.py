@@ -692,6 +692,36 @@ def robustness_sweep(torch, dev, flush):
             "solve_ms_total": total_ms, "problem_iters_per_s": total_iters / (total_ms / 1e3)}
 
 
+def small_m_workload(torch, dev, flush):
+    """Short transforms, which run as whole solves inside one CTA per problem
+    (m <= 4096): B = 64, n = m / 4, L = 2, noiseless, 100 power + 500 GD
+    iterations, graph-replayed, for m = 256, 1024 and 4096."""
+    from paper_2409_05734_gb300 import Plan
+    import synthetic as S
+    out = {}
+    B, L, sp, gd = 64, 2, 100, 500
+    for m in (256, 1024, 4096):
+        n = m // 4
+        plan = Plan(n, m, L, 41)
+        plan.reserve(B)
+        x_true = torch.from_numpy(S.signal_gaussian(41, B, n)).to(torch.complex64).to(dev)
+        y = (plan.forward(x_true).abs() ** 2).contiguous()
+        v0 = torch.from_numpy(S.start_vector(41, B, n)).to(torch.complex64).to(dev)
+        x = torch.empty_like(v0)
+
+        def solve():
+            plan.spectral_init(y, v0, sp, weight="optimal", out=x)
+            plan.gd_solve(y, x, gd, mu0=0.15, tau0=100.0)
+
+        ms = timed_graph(torch, solve, flush)
+        out[f"m={m}"] = {"n": n, "ms_per_solve": ms, "problem_iters_per_s": B * (sp + gd) / (ms / 1e3),
+                         "median_rel_err_global_phase": median_rel_err(torch, x, x_true)}
+        plan.check()
+        del plan
+    return {"workload": f"B = {B}, n = m / 4, L = {L}, x ~ CN(0, I), noiseless, {sp} power + {gd} GD iterations, "
+                        "one launch per call (whole solves in one CTA per problem)", **out}
+
+
 def autograd_workload(torch, dev, flush):
     """Forward and backward of the differentiable operator (x, theta) -> z = A x at
     B = 8, n = 2^20, m = 2^22, L = 2, driven by a loss on |z|^2."""
@@ -977,6 +1007,7 @@ def run_ours(args):
         line["radix3_batch"] = radix3_workload(torch, dev, flush)
         line["two_dimensional"] = two_d_workload(torch, dev, flush)
         line["forward_time_vs_size"] = forward_time_vs_size(torch, dev, flush)
+        line["small_m"] = small_m_workload(torch, dev, flush)
         line["differentiable_operator"] = autograd_workload(torch, dev, flush)
     if rank == 0 and not args.no_ragged:
         line["ragged_batch"] = ragged_workload(torch, dev, flush)
@@ -1003,6 +1034,7 @@ EXTRA_LEGS = {
     "forward_curve": "forward_time_vs_size",
     "autograd": "autograd_workload",
     "sweep": "robustness_sweep",
+    "small": "small_m_workload",
 }
 
 

@@ -364,6 +364,7 @@ sr_status run_chain_r3(const Plan& p, const Chain& c, int B, cudaStream_t s);
 // Number of partial sums per problem the last stage of a chain writes (norm
 // partials of the spectral update).
 int final_partials(const Plan& p, int nfft, int s0) {
+  if (sr::small_eligible(p)) return 1;  // the resident solver writes each norm whole
   if (p.inner) return p.r3_chunks;
   return p.geom[sr::s2_layout((s0 + nfft - 1) % 2)].cpp;
 }
@@ -786,6 +787,25 @@ sr_status create_plan(int64_t n, int64_t m, int L, uint64_t seed, int gh, int gw
   *out = p;
   return SR_OK;
 }
+// The fields of the resident small-m solver's arguments common to every call.
+sr::SmallArgs small_args(const Plan& p, const float* y, void* x, int B) {
+  sr::SmallArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.m = (int)p.m;
+  a.n = (int)p.n;
+  a.L = p.L;
+  a.B = B;
+  a.dp = p.d_dp;
+  a.dp_stride = p.dp_stride;
+  a.tw_hi = p.d_tw_hi;
+  a.tw_lo = p.d_tw_lo;
+  a.tw_shift = p.tw_shift;
+  a.y = y;
+  a.sumy = p.d_scal;
+  a.x = (float2*)x;
+  return a;
+}
+
 // Power iteration shared by the spectral entry points: the step chains, the
 // ping-pong banks of norm partials and the bank of the latest iterate.
 struct SpectralRun {
@@ -796,7 +816,9 @@ struct SpectralRun {
   float* bank[2] = {nullptr, nullptr};
   int prev = 1, prev_count = 0, last_cpp = 0;
   int done = 0;  // steps run so far
-  bool window = false, fuse = false;
+  bool window = false, fuse = false, small = false;
+  const float* ye = nullptr;
+  sr_spectral_opts o{SR_WEIGHT_IDENTITY, -1.0f};
   Chain c, f, a;
 
   sr_status setup(sr_plan* plan, const float* y, const void* v0, const sr_spectral_opts* opts, void* x_out, int nb,
@@ -804,7 +826,6 @@ struct SpectralRun {
     sr_status st = check_plan_call(plan, nb);
     if (st != SR_OK) return st;
     if (!y || !v0 || !x_out) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
-    sr_spectral_opts o{SR_WEIGHT_IDENTITY, -1.0f};
     if (opts) o = *opts;
     if (o.weight_mode != SR_WEIGHT_IDENTITY && o.weight_mode != SR_WEIGHT_OPTIMAL)
       return fail(SR_ERR_INVALID_ARG, "unknown weight_mode");
@@ -818,7 +839,6 @@ struct SpectralRun {
       SR_CUDA(cudaMemcpyAsync(x_out, v0, (size_t)B * n * sizeof(float2), cudaMemcpyDeviceToDevice, s),
               "cudaMemcpyAsync(v0)");
     if ((st = prepare_y(p, y, B, 0.f, s)) != SR_OK) return st;
-    const float* ye = nullptr;
     if ((st = epilogue_y(p, y, B, s, &ye)) != SR_OK) return st;
     v = (float2*)x_out;
     prev_count = std::min(64, (n + 4095) / 4096);
@@ -827,6 +847,7 @@ struct SpectralRun {
     SR_CUDA(sr::launch_norm_rows(v, B, n, bank[1], prev_count, s), "launch(norm v0)");
     last_cpp = final_partials(*p, 2 * p->L, 0);
     const float shift = o.weight_mode == SR_WEIGHT_IDENTITY ? 0.f : -2.0f * o.lambda;
+    small = sr::small_eligible(*p);
     window = p->mo < p->m;
     if (window) {
       // alpha < 1: forward chain of v / ||v|| into the window, adjoint chain with
@@ -866,6 +887,24 @@ struct SpectralRun {
   // does not fuse into a following FIRST, so calls can be chained.
   sr_status steps(int count) {
     sr_status st;
+    if (small) {  // all `count` steps in one launch of the resident solver
+      if (count <= 0) return SR_OK;
+      sr::SmallArgs sa = small_args(*p, ye, v, B);
+      sa.count = count;
+      sa.weight_mode = o.weight_mode;
+      sa.lam = o.lambda;
+      sa.shift = o.weight_mode == SR_WEIGHT_IDENTITY ? 0.f : -2.0f * o.lambda;
+      sa.norm_in = bank[prev];
+      sa.norm_in_count = prev_count;
+      const int last = (done + count - 1) % 2;
+      sa.norm_last = bank[last];
+      sa.norm_prev = bank[1 - last];
+      SR_CUDA(sr::launch_small(*p, sa, true, s), "launch(small power iteration)");
+      done += count;
+      prev = last;
+      prev_count = 1;
+      return SR_OK;
+    }
     for (int it = 0; it < count; ++it, ++done) {
       const int cur = done % 2;
       if (window) {
@@ -917,6 +956,23 @@ template <class RowFn>
 sr_status gd_iterations(Plan& p, const float* ye, void* x, int t0, int count, float tau0, int B, cudaStream_t s,
                         RowFn loss_row) {
   sr_status st;
+  if (sr::small_eligible(p)) {  // all `count` steps in one launch of the resident solver
+    if (count <= 0) return SR_OK;
+    sr::SmallArgs a = small_args(p, ye, x, B);
+    a.count = count;
+    a.mu = p.d_scal + B;
+    a.t0 = t0;
+    a.tau0 = tau0;
+    for (int t = t0; t < t0 + count; ++t) {
+      if (float* row = loss_row(t)) {  // rows are B apart from the first recorded step on
+        a.loss_hist = row;
+        a.loss_first = t;
+        break;
+      }
+    }
+    SR_CUDA(sr::launch_small(p, a, false, s), "launch(small solve)");
+    return SR_OK;
+  }
   auto ramp = [&](int t) {
     return tau0 > 0.f ? (float)(1.0 - std::exp(-(double)(t + 1) / (double)tau0)) : 1.0f;
   };
@@ -1172,6 +1228,15 @@ sr_status sr_loss_grad(sr_plan* plan, const void* x, const float* y, float* loss
   if ((st = prepare_y(&p, y, B, 0.f, s)) != SR_OK) return st;
   const float* ye = nullptr;
   if ((st = epilogue_y(&p, y, B, s, &ye)) != SR_OK) return st;
+  if (sr::small_eligible(p)) {
+    sr::SmallArgs a = small_args(p, ye, const_cast<void*>(x), B);
+    a.count = 1;
+    a.grad = 1;
+    a.g = (float2*)grad;
+    a.loss_out = loss;
+    SR_CUDA(sr::launch_small(p, a, false, s), "launch(small gradient)");
+    return SR_OK;
+  }
   if (p.mo < p.m) {
     Chain f = forward_chain(p);
     f.xin = (const float2*)x;

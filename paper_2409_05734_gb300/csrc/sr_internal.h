@@ -215,6 +215,40 @@ Layout s2_layout(int parity);
 // Pass launchers (fourstep.cu). B problems; the middle and last passes run a
 // persistent grid of min(tiles, per_sm * SMs) CTAs.
 cudaError_t launch_first(const Plan& p, Layout lay, const PassArgs& a, int B, cudaStream_t s);
+
+// Whole solves for short transforms (small.cu): power-of-two m <= kSmallMaxM,
+// 1D plans with n <= m. One CTA line per problem; all iterations in one launch.
+constexpr int kSmallMaxM = 4096;
+struct SmallArgs {
+  int m, n, L, B;
+  const float2* dp;        // diagonals, D_l at dp + b * dp_stride + l * m
+  int64_t dp_stride;
+  const float2* tw_hi;     // the plan's two-level W_m table
+  const float2* tw_lo;
+  int tw_shift;
+  const float* y;          // [B][m]
+  const float* sumy;       // [B]
+  float2* x;               // [B][n], updated in place (GD, power iteration)
+  int count;               // steps in this launch
+  // GD
+  const float* mu;         // [B]: mu0 m / sum(y)
+  int t0;                  // global index of the first step (warm-up factor)
+  float tau0;
+  float* loss_hist;        // rows of steps >= loss_first, [B] each, or nullptr
+  int loss_first;
+  int grad;                // one gradient evaluation: g = 2 A^H(r z), loss_out
+  float2* g;
+  float* loss_out;
+  // power iteration
+  int weight_mode;
+  float lam, shift;
+  const float* norm_in;    // partials of ||x||^2 of the incoming iterate
+  int norm_in_count;
+  float* norm_last;        // [B]: ||u||^2 of the last step
+  float* norm_prev;        // [B]: of the step before (count >= 2)
+};
+bool small_eligible(const Plan& p);
+cudaError_t launch_small(const Plan& p, const SmallArgs& a, bool spec, cudaStream_t s);
 // yt[b] = y[b]^T for B row-major S x S float grids (2D plans with odd L)
 cudaError_t launch_transpose_grids(const float* y, float* yt, int S, int B, cudaStream_t s);
 cudaError_t launch_mid(const Plan& p, Layout lay, const PassArgs& a, int B, cudaStream_t s);
