@@ -1,4 +1,4 @@
-// Whole solves for short transforms: power-of-two m <= 4096 (1D plans, n <= m).
+// Whole solves for short transforms: power-of-two m <= 8192 (1D plans, n <= m).
 //
 // The length-m DFT of one problem is a single line FFT (line_fft, radix-16
 // Stockham in shared memory), so every A and A^H of Sec. III, Eq. 5 runs
@@ -272,6 +272,7 @@ cudaError_t launch_small(const Plan& p, const SmallArgs& a, bool spec, cudaStrea
     case 1024: return launch_small_m<1024>(a, spec, p.num_sms, s);
     case 2048: return launch_small_m<2048>(a, spec, p.num_sms, s);
     case 4096: return launch_small_m<4096>(a, spec, p.num_sms, s);
+    case 8192: return launch_small_m<8192>(a, spec, p.num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -139,10 +139,12 @@ __device__ __forceinline__ int sidx(int pos, int t) { return pad16(pos) * T + t;
 //
 // Addressing is written as a per-thread base plus compile-time offsets. With
 // P and 16 powers of two and p < P: pad16(p + j*P) = pad16(p) + pad16(j*P);
-// the only stages that write back are stage 0 (radix 16, Ns = 1: position
-// 16(p + qP) + r, padded 17(p + qP) + r) and stage 1 (radix 16, Ns = 16, one
-// butterfly b = p per thread: position 256(p>>4) + (p&15) + 16r, padded
-// 272(p>>4) + (p&15) + 17r); and b mod Ns = (p mod Ns) + (qP mod Ns).
+// the stages that write back are radix 16: stage 0 (Ns = 1: position
+// 16(p + qP) + r, padded 17(p + qP) + r) and later stages with one butterfly
+// b = p per thread (P >= Ns): position 16 Ns (p / Ns) + (p mod Ns) + r Ns,
+// padded pad16(16 Ns (p / Ns) + (p mod Ns)) + r 17 Ns / 16 (stage 1 of lines
+// up to 4096 points, stages 1 and 2 of 8192-point lines); and
+// b mod Ns = (p mod Ns) + (qP mod Ns).
 template <int N, int T, int S>
 __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, const float2* tw) {
   using LS_ = LineShape<N>;
@@ -151,7 +153,7 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* 
   constexpr int Q = E / R;
   constexpr int Ns = LS_::span(S);
   constexpr bool LAST = (S == LS_::NSTAGE - 1);
-  static_assert(LAST || S <= 1, "only stages 0 and 1 write back");
+  static_assert(LAST || S == 0 || (R == 16 && Q == 1 && P >= Ns), "write-back stages: stage 0 or one butterfly per thread");
   if constexpr (S > 0) {
     const float2* rb = sm + pad16(p) * T + t;
 #pragma unroll
@@ -162,7 +164,7 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* 
   if constexpr (!LAST) {
     static_assert(R == 16, "write-back stages are radix 16");
     if constexpr (S == 0) wb += 17 * p * T;
-    else wb += (272 * (p >> 4) + (p & 15)) * T;
+    else wb += pad16(16 * Ns * (p / Ns) + (p & (Ns - 1))) * T;
   }
   const int kp = (P >= Ns) ? (p & (Ns - 1)) : p;  // runtime part of b mod Ns
 #pragma unroll
@@ -186,7 +188,7 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* 
       for (int r = 0; r < R; ++r) wb[(17 * q * P + r) * T] = a[r];
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) wb[17 * r * T] = a[r];
+      for (int r = 0; r < R; ++r) wb[r * (Ns + Ns / 16) * T] = a[r];
     }
   }
   if constexpr (!LAST) __syncthreads();

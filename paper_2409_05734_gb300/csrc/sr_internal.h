@@ -218,7 +218,7 @@ cudaError_t launch_first(const Plan& p, Layout lay, const PassArgs& a, int B, cu
 
 // Whole solves for short transforms (small.cu): power-of-two m <= kSmallMaxM,
 // 1D plans with n <= m. One CTA line per problem; all iterations in one launch.
-constexpr int kSmallMaxM = 4096;
+constexpr int kSmallMaxM = 8192;
 struct SmallArgs {
   int m, n, L, B;
   const float2* dp;        // diagonals, D_l at dp + b * dp_stride + l * m
