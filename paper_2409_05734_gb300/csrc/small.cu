@@ -241,15 +241,19 @@ cudaError_t launch_small_t(const SmallArgs& a, bool spec, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Problems per CTA: 256 threads per CTA, or fewer problems (down to one warp's
-// worth of threads) when that leaves SMs idle.
+// Problems per CTA: 256 threads per CTA while that gives every SM a CTA, else
+// one warp's worth of threads, else one problem per CTA (small batches of
+// short transforms are latency-bound: spreading them over more SMs wins).
 template <int M>
 cudaError_t launch_small_m(const SmallArgs& a, bool spec, int num_sms, cudaStream_t s) {
   constexpr int P = LineShape<M>::P;
   constexpr int TB = P >= 256 ? 1 : 256 / P;
   constexpr int TS = P >= 32 ? 1 : 32 / P;
-  if ((a.B + TB - 1) / TB >= num_sms || TB == TS) return launch_small_t<M, TB>(a, spec, s);
-  return launch_small_t<M, TS>(a, spec, s);
+  if ((a.B + TB - 1) / TB >= num_sms || TB == 1) return launch_small_t<M, TB>(a, spec, s);
+  if constexpr (TS != TB) {
+    if ((a.B + TS - 1) / TS >= num_sms || TS == 1) return launch_small_t<M, TS>(a, spec, s);
+  }
+  return launch_small_t<M, 1>(a, spec, s);
 }
 
 }  // namespace
