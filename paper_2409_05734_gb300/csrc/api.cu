@@ -1201,6 +1201,13 @@ sr_status sr_forward(sr_plan* plan, const void* x, void* z, int B, void* stream)
   if (st != SR_OK) return st;
   if (!x || !z) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
   Plan& p = *plan;
+  if (sr::small_eligible(p)) {  // one launch: the whole operator inside one CTA per problem
+    sr::SmallArgs a = small_args(p, nullptr, const_cast<void*>(x), B);
+    a.op = 1;
+    a.zout = (float2*)z;
+    SR_CUDA(sr::launch_small(p, a, false, (cudaStream_t)stream), "launch(small forward)");
+    return SR_OK;
+  }
   Chain c = forward_chain(p);
   c.xin = (const float2*)x;
   c.xout = (float2*)z;
@@ -1212,6 +1219,13 @@ sr_status sr_adjoint(sr_plan* plan, const void* z, void* x, int B, void* stream)
   if (st != SR_OK) return st;
   if (!x || !z) return fail(SR_ERR_INVALID_ARG, "NULL array argument");
   Plan& p = *plan;
+  if (sr::small_eligible(p)) {
+    sr::SmallArgs a = small_args(p, nullptr, x, B);
+    a.op = 2;
+    a.win = (const float2*)z;
+    SR_CUDA(sr::launch_small(p, a, false, (cudaStream_t)stream), "launch(small adjoint)");
+    return SR_OK;
+  }
   Chain c = adjoint_chain(p);
   c.xin = (const float2*)z;
   c.xout = (float2*)x;

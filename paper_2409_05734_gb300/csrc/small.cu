@@ -10,7 +10,8 @@
 // passes of an iteration times the iteration count.
 //
 // k_small_gd: GD steps x <- x - mu_t 2 A^H((|Ax|^2 - y) Ax) (Sec. II-B-1,
-// Eq. 2), or one gradient evaluation (loss and 2 A^H(r z)).
+// Eq. 2), one gradient evaluation (loss and 2 A^H(r z)), or the operator
+// alone (z = A x, x = A^H w).
 // k_small_spec: power-iteration steps u = A^H diag(T(y_hat)) A v + s v,
 // v = u / ||u|| (Sec. II-B-2, Eq. 3-4), with the norms of the last two steps.
 #include <algorithm>
@@ -101,6 +102,30 @@ __global__ void __launch_bounds__(T * LineShape<M>::P) k_small_gd(const SmallArg
   const int m = a.m, n = a.n;
   small_twiddles<M>(a, tw);
   const float2* dpb = a.dp + (size_t)(valid ? b : 0) * a.dp_stride;
+  if (a.op != 0) {  // the operator alone (Sec. III, Eq. 5): z = A x or x = A^H w
+    float2 v[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int k = p + j * P;
+      if (a.op == 1) v[j] = valid && k < n ? a.x[(size_t)b * n + k] : make_float2(0.f, 0.f);
+      else v[j] = valid ? a.win[(size_t)b * m + k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();  // twiddles
+    if (a.op == 1) {
+      small_forward<M, T>(v, dpb, m, a.L, p, t, scratch, tw);
+#pragma unroll
+      for (int j = 0; j < E; ++j)
+        if (valid) a.zout[(size_t)b * m + p + j * P] = v[j];
+    } else {
+      small_adjoint<M, T>(v, dpb, m, a.L, p, t, scratch, tw);
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int k = p + j * P;
+        if (valid && k < n) a.x[(size_t)b * n + k] = v[j];
+      }
+    }
+    return;
+  }
   float2 xr[E];
   float yr[E];
 #pragma unroll

@@ -239,6 +239,11 @@ struct SmallArgs {
   int grad;                // one gradient evaluation: g = 2 A^H(r z), loss_out
   float2* g;
   float* loss_out;
+  // the operator alone: z = A x (op = 1, zout [B][m]) or x = A^H w (op = 2,
+  // win [B][m] in, x [B][n] out); op = 0 for the solver modes
+  int op;
+  const float2* win;
+  float2* zout;
   // power iteration
   int weight_mode;
   float lam, shift;
