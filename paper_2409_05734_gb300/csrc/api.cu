@@ -793,6 +793,8 @@ sr::SmallArgs small_args(const Plan& p, const float* y, void* x, int B) {
   std::memset(&a, 0, sizeof(a));
   a.m = (int)p.m;
   a.n = (int)p.n;
+  a.mo = (int)p.mo;
+  a.off = (int)p.off;
   a.L = p.L;
   a.B = B;
   a.dp = p.d_dp;

@@ -107,15 +107,18 @@ __global__ void __launch_bounds__(T * LineShape<M>::P) k_small_gd(const SmallArg
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const int k = p + j * P;
+      const bool inwin = (unsigned)(k - a.off) < (unsigned)a.mo;  // S^H: zero outside the window
       if (a.op == 1) v[j] = valid && k < n ? a.x[(size_t)b * n + k] : make_float2(0.f, 0.f);
-      else v[j] = valid ? a.win[(size_t)b * m + k] : make_float2(0.f, 0.f);
+      else v[j] = valid && inwin ? a.win[(size_t)b * a.mo + (k - a.off)] : make_float2(0.f, 0.f);
     }
     __syncthreads();  // twiddles
     if (a.op == 1) {
       small_forward<M, T>(v, dpb, m, a.L, p, t, scratch, tw);
 #pragma unroll
-      for (int j = 0; j < E; ++j)
-        if (valid) a.zout[(size_t)b * m + p + j * P] = v[j];
+      for (int j = 0; j < E; ++j) {
+        const int k = p + j * P;
+        if (valid && (unsigned)(k - a.off) < (unsigned)a.mo) a.zout[(size_t)b * a.mo + (k - a.off)] = v[j];  // S
+      }
     } else {
       small_adjoint<M, T>(v, dpb, m, a.L, p, t, scratch, tw);
 #pragma unroll
@@ -128,11 +131,14 @@ __global__ void __launch_bounds__(T * LineShape<M>::P) k_small_gd(const SmallArg
   }
   float2 xr[E];
   float yr[E];
+  unsigned inwin = 0;  // bit j: entry p + j P is measured (the window of the alpha < 1 branch)
 #pragma unroll
   for (int j = 0; j < E; ++j) {
     const int k = p + j * P;
+    const bool in = (unsigned)(k - a.off) < (unsigned)a.mo;
+    inwin |= in ? (1u << j) : 0u;
     xr[j] = valid && k < n ? a.x[(size_t)b * n + k] : make_float2(0.f, 0.f);
-    yr[j] = valid ? __ldg(&a.y[(size_t)b * m + k]) : 0.f;
+    yr[j] = valid && in ? __ldg(&a.y[(size_t)b * a.mo + (k - a.off)]) : 0.f;
   }
   const float mu = valid && a.mu ? __ldg(&a.mu[b]) : 0.f;
   __syncthreads();  // twiddles
@@ -148,8 +154,12 @@ __global__ void __launch_bounds__(T * LineShape<M>::P) k_small_gd(const SmallArg
 #pragma unroll
     for (int j = 0; j < E; ++j) {
       const float r = cabs2(v[j]) - yr[j];
-      acc_add(acc, r * r);
-      v[j] = cscale(v[j], r);
+      if (inwin & (1u << j)) {
+        acc_add(acc, r * r);
+        v[j] = cscale(v[j], r);
+      } else {
+        v[j] = make_float2(0.f, 0.f);  // S^H S: unmeasured entries carry no residual
+      }
     }
     float* lrow = a.grad ? a.loss_out
                          : (a.loss_hist && step >= a.loss_first ? a.loss_hist + (size_t)(step - a.loss_first) * a.B
@@ -199,17 +209,18 @@ __global__ void __launch_bounds__(T * LineShape<M>::P) k_small_spec(const SmallA
   small_twiddles<M>(a, tw);
   const float2* dpb = a.dp + (size_t)(valid ? b : 0) * a.dp_stride;
   // weights T(y_hat), y_hat = m y / sum(y) (Eq. 3)
-  const float ysc = valid ? (float)m / __ldg(&a.sumy[b]) : 0.f;
+  const float ysc = valid ? (float)a.mo / __ldg(&a.sumy[b]) : 0.f;
   float2 ur[E];
   float wr[E];
 #pragma unroll
   for (int j = 0; j < E; ++j) {
     const int k = p + j * P;
+    const bool in = (unsigned)(k - a.off) < (unsigned)a.mo;
     ur[j] = valid && k < n ? a.x[(size_t)b * n + k] : make_float2(0.f, 0.f);
-    const float yh = valid ? __ldg(&a.y[(size_t)b * m + k]) * ysc : 0.f;
+    const float yh = valid && in ? __ldg(&a.y[(size_t)b * a.mo + (k - a.off)]) * ysc : 0.f;
     float w = yh;
     if (a.weight_mode == SR_WEIGHT_OPTIMAL) w = yh > 0.f ? fmaxf(1.0f - 1.0f / yh, a.lam) : a.lam;
-    wr[j] = w;
+    wr[j] = in ? w : 0.f;  // S^H S: unmeasured entries carry no weight
   }
   // ||u||^2 of the incoming iterate
   float nrm = valid ? sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count) : 1.f;
@@ -284,8 +295,7 @@ cudaError_t launch_small_m(const SmallArgs& a, bool spec, int num_sms, cudaStrea
 }  // namespace
 
 bool small_eligible(const Plan& p) {
-  return !p.inner && !p.two_d && p.mo == p.m && p.m >= 4 && p.m <= kSmallMaxM && (p.m & (p.m - 1)) == 0 &&
-         p.n <= p.m;
+  return !p.inner && !p.two_d && p.m >= 4 && p.m <= kSmallMaxM && (p.m & (p.m - 1)) == 0 && p.n <= p.m;
 }
 
 cudaError_t launch_small(const Plan& p, const SmallArgs& a, bool spec, cudaStream_t s) {

@@ -216,17 +216,19 @@ Layout s2_layout(int parity);
 // persistent grid of min(tiles, per_sm * SMs) CTAs.
 cudaError_t launch_first(const Plan& p, Layout lay, const PassArgs& a, int B, cudaStream_t s);
 
-// Whole solves for short transforms (small.cu): power-of-two m <= kSmallMaxM,
-// 1D plans with n <= m. One CTA line per problem; all iterations in one launch.
+// Whole solves for short transforms (small.cu): power-of-two m <= kSmallMaxM
+// (the DFT length; both alpha branches), 1D plans. One CTA line per problem;
+// all iterations in one launch.
 constexpr int kSmallMaxM = 8192;
 struct SmallArgs {
   int m, n, L, B;
+  int mo, off;             // measurements: entries off .. off+mo-1 of the length-m result (alpha < 1), else m, 0
   const float2* dp;        // diagonals, D_l at dp + b * dp_stride + l * m
   int64_t dp_stride;
   const float2* tw_hi;     // the plan's two-level W_m table
   const float2* tw_lo;
   int tw_shift;
-  const float* y;          // [B][m]
+  const float* y;          // [B][mo]
   const float* sumy;       // [B]
   float2* x;               // [B][n], updated in place (GD, power iteration)
   int count;               // steps in this launch
@@ -239,8 +241,8 @@ struct SmallArgs {
   int grad;                // one gradient evaluation: g = 2 A^H(r z), loss_out
   float2* g;
   float* loss_out;
-  // the operator alone: z = A x (op = 1, zout [B][m]) or x = A^H w (op = 2,
-  // win [B][m] in, x [B][n] out); op = 0 for the solver modes
+  // the operator alone: z = A x (op = 1, zout [B][mo]) or x = A^H w (op = 2,
+  // win [B][mo] in, x [B][n] out); op = 0 for the solver modes
   int op;
   const float2* win;
   float2* zout;
