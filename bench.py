@@ -722,6 +722,72 @@ def small_m_workload(torch, dev, flush):
                         "one launch per call (whole solves in one CTA per problem)", **out}
 
 
+def layers_experiment(torch, dev, flush):
+    """The layer experiment (Sec. IV-B, Fig. 5): spectral initialisation alone
+    (1000 power iterations, optimal weights) on n = 4096 complex Gaussian
+    signals and on phantom-like phase images (64 x 64), 32 trials per cell, alpha in {2, 3, 4, 6}, for structured models
+    with L = 1, 2, 3 (own phases per trial), the one-layer model with an extra
+    FFT (A = F D_1 F U: L = 2 with theta_1 = 0; one operator for all trials),
+    a random unitary model (the first n columns of a Haar unitary m x m
+    matrix, by QR of a complex Gaussian matrix with the diagonal phases of R
+    divided out; run by the dense model, which rounds it to BF16) and the
+    i.i.d. Gaussian model. Median cosine similarity (Eq. 6)."""
+    from paper_2409_05734_gb300 import DenseModel, Plan
+    import synthetic as S
+    n, B, sp = 4096, 32, 1000
+    alphas = (2, 3, 4, 6)
+    gen = torch.Generator(device=dev)
+    out, out_img = {}, {}
+    # phantom-like phase images (64 x 64, flattened), the paper's signal class
+    x_img = torch.from_numpy(S.phase_image_ellipses(20240905, B, 64, 64)).to(torch.complex64).to(dev)
+
+    def cos_sim(x, x_true):
+        inner = torch.sum(torch.conj(x) * x_true, dim=1).abs()
+        c = inner / (torch.linalg.vector_norm(x, dim=1) * torch.linalg.vector_norm(x_true, dim=1))
+        return float(torch.median(c).cpu())
+
+    for alpha in alphas:
+        m = alpha * n
+        seed = 20240905 + 100 * alpha
+        gen.manual_seed(seed)
+        x_true = torch.randn((B, n), dtype=torch.complex64, device=dev, generator=gen)
+        v0 = torch.randn((B, n), dtype=torch.complex64, device=dev, generator=gen)
+        models = []
+        for L in (1, 2, 3):
+            plan = Plan(n, m, L, seed + L)
+            plan.set_batch_seeds([seed + 1000 * L + b for b in range(B)])
+            models.append((f"structured L={L}", plan))
+        extra = Plan(n, m, 2, seed + 7)
+        th = extra.phases
+        th[0] = 0.0
+        extra.set_phases(th)
+        models.append(("one layer + extra FFT", extra))
+        gq = torch.Generator(device=dev).manual_seed(seed + 11)
+        G = torch.randn((m, n), dtype=torch.complex128, device=dev, generator=gq)
+        Q, R = torch.linalg.qr(G)
+        d = torch.diagonal(R)
+        Q = Q * (d / d.abs()).unsqueeze(0)  # Haar: G = (Q P)(P^H R) with P^H R of positive diagonal
+        models.append(("random unitary", DenseModel(Q.to(torch.complex64).cpu().numpy())))
+        del G, Q, R
+        rng = np.random.default_rng(seed + 13)
+        a = rng.standard_normal((m, n, 2), dtype=np.float32) * np.float32(1.0 / np.sqrt(2.0 * m))
+        models.append(("i.i.d. Gaussian", DenseModel(a.view(np.complex64)[..., 0])))
+        del a
+        for name, mod in models:
+            for sig, res in ((x_true, out), (x_img, out_img)):
+                y = (mod.forward(sig).abs() ** 2).contiguous()
+                x = mod.spectral_init(y, v0, sp, weight="optimal", lam=-1.0)
+                mod.check()
+                res.setdefault(name, []).append(round(cos_sim(x, sig), 4))
+        del models
+        torch.cuda.empty_cache()
+    return {"workload": f"n = {n}, {B} trials, alpha {list(alphas)}, spectral initialisation alone ({sp} power "
+                        f"iterations, optimal weights, lambda = -1), noiseless; complex Gaussian signals and "
+                        f"phantom-like 64 x 64 phase images",
+            "alphas": list(alphas), "median_cosine_similarity": out,
+            "median_cosine_similarity_phase_images": out_img}
+
+
 def autograd_workload(torch, dev, flush):
     """Forward and backward of the differentiable operator (x, theta) -> z = A x at
     B = 8, n = 2^20, m = 2^22, L = 2, driven by a loss on |z|^2."""
@@ -1035,6 +1101,7 @@ EXTRA_LEGS = {
     "autograd": "autograd_workload",
     "sweep": "robustness_sweep",
     "small": "small_m_workload",
+    "layers": "layers_experiment",
 }
 
 
