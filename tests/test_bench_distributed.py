@@ -75,3 +75,12 @@ def test_traffic_read_from_profile_summary_keyed_to_sources(tmp_path, monkeypatc
     assert bench.traffic_from_profile("k.md") == 1234.0
     assert bench.traffic_from_profile("stale.md") is None
     assert bench.traffic_from_profile("missing.md") is None
+
+
+def test_only_legs_resolve_to_workload_functions():
+    """`bench.py --only NAME` runs the function EXTRA_LEGS names; every name must
+    resolve (a CPU check of the dispatch table, no GPU work)."""
+    import bench
+    for name, fn in bench.EXTRA_LEGS.items():
+        assert callable(getattr(bench, fn)), name
+    assert {"sweep", "layers", "small", "autograd", "radix3", "two_d", "forward_curve"} <= set(bench.EXTRA_LEGS)
