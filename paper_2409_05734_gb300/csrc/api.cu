@@ -125,6 +125,8 @@ void free_workspace(Plan* p) {
 // Size of one bank of per-tile partial sums per problem.
 int part_stride(const Plan& p) {
   int s = std::max(std::max(std::max(p.geom[0].cpp, p.geom[1].cpp), p.r3_chunks), 64);
+  for (int lay = 0; lay < 2; ++lay)  // the GD epilogue's per-warp loss partials
+    s = std::max(s, p.geom[lay].cpp * sr::epilogue_partials_per_tile(p.geom[lay]));
   // radix-3: the inner first pass writes 3 banks of its tile partials per problem
   if (p.inner) s = std::max(s, 3 * std::max(p.inner->geom[0].cpp, p.inner->geom[1].cpp));
   return s;
@@ -425,7 +427,7 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     if (a.op == sr::kOpGdEpilogue) {
       a.y = c.y;
       a.part_out = c.loss_part;
-      loss_cpp = p.geom[lay].cpp;
+      loss_cpp = p.geom[lay].cpp * sr::epilogue_partials_per_tile(p.geom[lay]);
     } else if (a.op == sr::kOpSpecEpilogue) {
       a.y = c.y;
       a.sumy = c.sumy;

@@ -450,8 +450,14 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     }
     apply_op<TL>(v, a, od, b, g, p, acc);
     if (a.op == kOpGdEpilogue) {
-      const float s = block_sum(acc, red);
-      if (tid == 0) a.part_out[(size_t)b * TL::cpp(a) + g0 / T] = s;
+      if constexpr (TL::THREADS % 32 == 0) {
+        // one partial per warp (no CTA barrier): [B][tiles][warps]
+        const float s = warp_sum(acc);
+        if ((tid & 31) == 0) a.part_out[((size_t)b * TL::cpp(a) + g0 / T) * (TL::THREADS / 32) + (tid >> 5)] = s;
+      } else {
+        const float s = block_sum(acc, red);
+        if (tid == 0) a.part_out[(size_t)b * TL::cpp(a) + g0 / T] = s;
+      }
     }
     rw.store(rowtw);
     __syncthreads();  // first FFT's scratch reads done; row twiddles visible

@@ -251,6 +251,16 @@ __device__ __forceinline__ fsum2 acc_merge(fsum2 A, fsum2 B) {
   return fsum2{s, A.c + B.c + e};
 }
 
+// Warp-wide compensated sum (fixed order); result valid in lane 0.
+__device__ __forceinline__ float warp_sum(fsum2 A) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    fsum2 B{__shfl_down_sync(0xffffffffu, A.s, off), __shfl_down_sync(0xffffffffu, A.c, off)};
+    if ((threadIdx.x & 31) + off < 32) A = acc_merge(A, B);
+  }
+  return A.s + A.c;
+}
+
 // Block-wide compensated sum; result valid in thread 0. `red` holds >= 64 floats.
 // Blocks that are not whole warps (tiny sizes, < 32 threads) reduce serially.
 __device__ __forceinline__ float block_sum(fsum2 A, float* red) {

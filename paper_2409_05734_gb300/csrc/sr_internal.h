@@ -215,6 +215,9 @@ Layout s2_layout(int parity);
 // Pass launchers (fourstep.cu). B problems; the middle and last passes run a
 // persistent grid of min(tiles, per_sm * SMs) CTAs.
 cudaError_t launch_first(const Plan& p, Layout lay, const PassArgs& a, int B, cudaStream_t s);
+// Loss partials a middle pass writes per tile: one per warp when the CTA is
+// whole warps, else one.
+inline int epilogue_partials_per_tile(const LineGeom& g) { return g.threads % 32 == 0 ? g.threads / 32 : 1; }
 
 // Whole solves for short transforms (small.cu): power-of-two m <= kSmallMaxM
 // (the DFT length; both alpha branches), 1D plans. One CTA line per problem;
