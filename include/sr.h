@@ -225,6 +225,22 @@ sr_status sr_gd_solve_early_stop(sr_plan* plan, const float* y, void* x, int max
                                  const sr_gd_opts* opts, float rel_tol, int check_every,
                                  float* loss_hist, int* iters_run, int B, void* stream);
 
+/* ---- accuracy metrics (Sec. IV-A, Eq. 6) --------------------------------------
+ * For B estimates x_hat[b] and references x[b] (both c64[B][n], device):
+ *   cos_out[b]    = |<x_hat, x>| / (||x_hat|| ||x||),  <a, b> = a^H b  (Eq. 6)
+ *   relerr_out[b] = min over phi of ||exp(i phi) x_hat - x|| / ||x||
+ * (recovery is only possible up to a global phase, Sec. II-A). The minimum is
+ * attained at exp(i phi) = <x_hat, x> / |<x_hat, x>| (phi = 0 when the inner
+ * product is zero), and the distance is summed directly at that phase. Sums
+ * are compensated FP32 in a fixed order (deterministic); each problem is one
+ * thread-block cluster of up to 8 CTAs that reduce through distributed shared
+ * memory, so the call uses no workspace and never allocates. A zero-norm
+ * vector gives NaN (cos) or NaN/inf (relerr), as the definitions do.
+ * cos_out, relerr_out: float[B] on the device; either may be NULL.
+ * n >= 1, 1 <= B <= 65535. */
+sr_status sr_metrics(const void* x_hat, const void* x_ref, int64_t n, int B, float* cos_out, float* relerr_out,
+                     void* stream);
+
 /* ---- forward without allocation (the paper has no counterpart) ---------------
  * sr_forward_noalloc: z = A x exactly like sr_forward, for callers that cannot
  * allocate device memory when they make the call -- code running while a CUDA
@@ -239,6 +255,10 @@ sr_status sr_gd_solve_early_stop(sr_plan* plan, const float* y, void* x, int max
  *   return SR_ERR_UNSUPPORTED and launch nothing.
  * - The first call on a device looks up the scratch array's device address
  *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   The address is cached per device and CUDA context: after cudaDeviceReset
+ *   the next call looks it up again (again before any capture).
+ * - A plan given per-problem phases (sr_plan_set_batch_phases) accepts only
+ *   that batch size; another B returns SR_ERR_INVALID_ARG.
  * - All calls share the one scratch array, which keeps the last call's
  *   contents (every element is rewritten before it is read, so nothing needs
  *   clearing). Calls that overlap on the GPU -- concurrent streams, or several

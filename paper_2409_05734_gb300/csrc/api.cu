@@ -132,39 +132,12 @@ int part_stride(const Plan& p) {
   return s;
 }
 
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-sr_status get_encoder(EncodeTiledFn* fn) {
-  static EncodeTiledFn cached = nullptr;
-  if (!cached) {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f)
-      return fail(SR_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    cached = reinterpret_cast<EncodeTiledFn>(f);
-  }
-  *fn = cached;
-  return SR_OK;
-}
-
-// Rows of an exchange buffer as a 2D tensor for the TMA loads of the passes
-// that read it: `rows` rows of `ell` complex values (2*ell floats), loaded in
-// boxes of 16 complex values (128 bytes) x T rows with 128-byte swizzle.
-sr_status encode_rows(CUtensorMap* map, float2* base, int ell, int64_t rows, int T) {
-  EncodeTiledFn enc;
-  sr_status st = get_encoder(&enc);
-  if (st != SR_OK) return st;
-  const cuuint64_t dims[2] = {(cuuint64_t)(2 * ell), (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)ell * 8};
-  const cuuint32_t box[2] = {32, (cuuint32_t)T};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(SR_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+// sr::encode_rows (defined below the anonymous namespace) with its failures
+// reported through sr_last_error.
+sr_status encode_exchange_rows(CUtensorMap* map, float2* base, int ell, int64_t rows, int T) {
+  const cudaError_t e = sr::encode_rows(map, base, ell, rows, T);
+  if (e == cudaErrorNotSupported) return fail(SR_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (e != cudaSuccess) return fail(SR_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   return SR_OK;
 }
 constexpr int kPartBanks = 4;  // 0,1: power-iteration norms (ping-pong), 2: loss, 3: sums
@@ -186,7 +159,7 @@ sr_status ensure_workspace(Plan* p, int B) {
     const sr::LineGeom& g = p->geom[lay];
     if (g.ell < 16) continue;  // short lines are read without TMA
     for (int buf = 0; buf < 2; ++buf) {
-      st = encode_rows(&p->tmap[buf][lay], buf ? p->d_e1 : p->d_e0, g.ell, (int64_t)B * g.nl, g.T);
+      st = encode_exchange_rows(&p->tmap[buf][lay], buf ? p->d_e1 : p->d_e0, g.ell, (int64_t)B * g.nl, g.T);
       if (st != SR_OK) {
         free_workspace(p);
         return st;
@@ -661,6 +634,42 @@ struct sr_plan : public Plan {};
 
 namespace sr {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once per process (the static's
+// initialisation is thread-safe); nullptr when the driver lacks it.
+EncodeTiledFn tensor_map_encoder() {
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    const cudaError_t e =
+        cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+}  // namespace
+
+cudaError_t encode_rows(CUtensorMap* map, float2* base, int ell, int64_t rows, int T) {
+  const EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * ell), (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ell * 8};
+  const cuuint32_t box[2] = {32, (cuuint32_t)T};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 // Gives each of B problems of the plan its own phases theta(seed_b): the
 // diagonal table becomes [B][L][m] (problem stride L * m), filled from the same

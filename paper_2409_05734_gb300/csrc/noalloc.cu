@@ -20,11 +20,18 @@ namespace {
 constexpr size_t kNoallocMaxElements = SR_FORWARD_NOALLOC_MAX_ELEMENTS;  // B * m limit per call
 static __device__ __align__(256) float2 g_noalloc_scratch[2 * kNoallocMaxElements];
 
-// Device address of the scratch, looked up once per device. In host code the
-// array's name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress with that device current.
+// Device address of the scratch, looked up once per device and CUDA context.
+// In host code the array's name is only a host-side stand-in, so the address
+// must come from cudaGetSymbolAddress with that device current. The context
+// is part of the key: after cudaDeviceReset the primary context (and the
+// module holding the array) is created anew, and an address cached from the
+// old context would no longer belong to the library.
 constexpr int kMaxDevices = 64;
-float2* g_scratch_ptr[kMaxDevices] = {nullptr};
+struct ScratchSlot {
+  CUcontext ctx = nullptr;
+  float2* ptr = nullptr;
+};
+ScratchSlot g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
 
 sr_status noalloc_fail(sr_status st, const std::string& msg) {
@@ -32,29 +39,21 @@ sr_status noalloc_fail(sr_status st, const std::string& msg) {
   return st;
 }
 
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// Same tensor description the plan uses for its own exchange buffers: rows of
-// `ell` complex values, boxes of 16 values x T rows, 128-byte swizzle.
-bool encode_rows(CUtensorMap* map, float2* base, int ell, int64_t rows, int T) {
-  static EncodeTiledFn enc = nullptr;
-  if (!enc) {
+// The calling thread's current CUDA context (the driver's cuCtxGetCurrent,
+// looked up once per process; the static's initialisation is thread-safe).
+bool current_context(CUcontext* ctx) {
+  using GetCurrentFn = CUresult (*)(CUcontext*);
+  static const GetCurrentFn fn = []() -> GetCurrentFn {
     void* f = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !f)
-      return false;
-    enc = reinterpret_cast<EncodeTiledFn>(f);
-  }
-  const cuuint64_t dims[2] = {(cuuint64_t)(2 * ell), (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)ell * 8};
-  const cuuint32_t box[2] = {32, (cuuint32_t)T};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<GetCurrentFn>(f);
+  }();
+  return fn && fn(ctx) == CUDA_SUCCESS && *ctx != nullptr;
 }
 
 }  // namespace
@@ -68,6 +67,11 @@ sr_status sr_forward_noalloc(const sr_plan* plan_in, const void* x, void* z, int
   if (plan->inner) return noalloc_fail(SR_ERR_UNSUPPORTED, "only power-of-two m is supported");
   if (plan->two_d) return noalloc_fail(SR_ERR_UNSUPPORTED, "2D plans are not supported");
   if (plan->mo < plan->m) return noalloc_fail(SR_ERR_UNSUPPORTED, "m < n is not supported");
+  // A plan with per-problem phases holds diagonal tables for exactly
+  // batch_fixed problems; any other B would read past them.
+  if (plan->batch_fixed && B != plan->batch_fixed)
+    return noalloc_fail(SR_ERR_INVALID_ARG, "this plan holds per-problem phases for a batch of " +
+                                                std::to_string(plan->batch_fixed) + " problems");
   if ((size_t)B * (size_t)plan->m > kNoallocMaxElements)
     return noalloc_fail(SR_ERR_UNSUPPORTED, "B*m = " + std::to_string((size_t)B * plan->m) +
                                                 " exceeds the static scratch of " +
@@ -75,17 +79,28 @@ sr_status sr_forward_noalloc(const sr_plan* plan_in, const void* x, void* z, int
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device || dev < 0 || dev >= kMaxDevices)
     return noalloc_fail(SR_ERR_INVALID_ARG, "current CUDA device differs from the plan's device");
+  // cudaSetDevice on the current device makes its primary context current on
+  // this thread (a thread whose first CUDA call this is has none yet).
+  CUcontext ctx = nullptr;
+  if (cudaSetDevice(dev) != cudaSuccess || !current_context(&ctx)) {
+    cudaGetLastError();
+    return noalloc_fail(SR_ERR_CUDA, "no current CUDA context on this thread");
+  }
   float2* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchSlot& slot = g_scratch[dev];
+    if (!slot.ptr || slot.ctx != ctx) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p)
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
         return noalloc_fail(SR_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_scratch_ptr[dev] = static_cast<float2*>(p);
+      }
+      slot.ptr = static_cast<float2*>(p);
+      slot.ctx = ctx;
     }
-    scratch = g_scratch_ptr[dev];
+    scratch = slot.ptr;
   }
   float2* e0 = scratch;
   float2* e1 = scratch + kNoallocMaxElements;
@@ -126,7 +141,7 @@ sr_status sr_forward_noalloc(const sr_plan* plan_in, const void* x, void* z, int
     a.in_dir = -1;
     a.out_dir = -1;
     a.ein = cur;
-    if (g.ell >= 16 && g.T >= 8 && !encode_rows(&a.tmap, cur, g.ell, (int64_t)B * g.nl, g.T))
+    if (g.ell >= 16 && g.T >= 8 && sr::encode_rows(&a.tmap, cur, g.ell, (int64_t)B * g.nl, g.T) != cudaSuccess)
       return noalloc_fail(SR_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     cudaError_t e;
     if (!last) {

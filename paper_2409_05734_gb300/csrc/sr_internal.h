@@ -201,6 +201,13 @@ struct Plan {
   size_t ev_used[3] = {0, 0, 0};
 };
 
+// Encodes `rows` rows of `ell` complex values starting at `base` (an exchange
+// buffer) as a 2D tensor for the TMA loads of the passes that read it: boxes of
+// 16 complex values (128 bytes) x T rows, 128-byte swizzle. cudaErrorNotSupported
+// when the driver has no tensor-map encoder, cudaErrorInvalidValue when the
+// encoder rejects the description (api.cu).
+cudaError_t encode_rows(CUtensorMap* map, float2* base, int ell, int64_t rows, int T);
+
 // Sets the thread-local message sr_last_error() returns.
 void set_last_error(const std::string& msg);
 
