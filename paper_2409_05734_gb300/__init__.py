@@ -6,10 +6,10 @@ descent run in hand-written CUDA kernels for sm_103a behind a C ABI
 (include/sr.h, libsr.so). This package is the thin Python binding.
 """
 from .buildlib import build, library_path
-from .plan import Plan, Plan2D, phases
+from .plan import Plan, Plan2D, metrics, phases
 from .autograd import StructuredRandomOp, structured_random
 from .dense import DenseModel
 from .ragged import Ragged
 
-__all__ = ["Plan", "Plan2D", "phases", "build", "library_path", "StructuredRandomOp", "structured_random",
+__all__ = ["Plan", "Plan2D", "metrics", "phases", "build", "library_path", "StructuredRandomOp", "structured_random",
            "DenseModel", "Ragged"]

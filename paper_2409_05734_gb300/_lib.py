@@ -56,6 +56,7 @@ SIGNATURES = [
     ("sr_plan_set_phases_device", C.c_int, [_VP, _VP, _VP]),
     ("sr_backward", C.c_int, [_VP, _VP, _VP, _VP, _VP, C.c_int, _VP]),
     ("sr_forward_noalloc", C.c_int, [_VP, _VP, _VP, C.c_int, _VP]),
+    ("sr_metrics", C.c_int, [_VP, _VP, C.c_int64, C.c_int, _VP, _VP, _VP]),
     ("sr_dense_create", C.c_int, [C.c_int64, C.c_int64, _VP, C.POINTER(_VP)]),
     ("sr_dense_destroy", C.c_int, [_VP]),
     ("sr_dense_forward", C.c_int, [_VP, _VP, _VP, C.c_int, _VP]),

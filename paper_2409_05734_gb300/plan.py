@@ -259,6 +259,26 @@ def phases(seed: int, L: int, m: int) -> np.ndarray:
     return out
 
 
+def metrics(x_hat: torch.Tensor, x_ref: torch.Tensor):
+    """(cosine similarity of Eq. 6, relative error up to a global phase) per
+    problem of two complex64 [B, n] device tensors, as float32 [B] tensors on
+    the same device (sr_metrics)."""
+    lib = _lib.load()
+    for name, t in (("x_hat", x_hat), ("x_ref", x_ref)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.complex64 or not t.is_cuda:
+            raise TypeError(f"{name} must be a complex64 CUDA tensor")
+    if x_hat.shape != x_ref.shape or x_hat.device != x_ref.device:
+        raise ValueError("x_hat and x_ref must have the same shape and device")
+    a = x_hat.reshape(-1, x_hat.shape[-1]).contiguous()
+    b = x_ref.reshape(-1, x_ref.shape[-1]).contiguous()
+    B, n = a.shape
+    cos = torch.empty(B, dtype=torch.float32, device=a.device)
+    err = torch.empty(B, dtype=torch.float32, device=a.device)
+    with torch.cuda.device(a.device):
+        _lib.check(lib.sr_metrics(_p(a), _p(b), n, B, _p(cos), _p(err), _stream_handle()), "sr_metrics")
+    return cos, err
+
+
 class Plan2D(Plan):
     """The 2D form of the operator (Sec. IV runs it with a 2D FFT on images):
     A = F2 D_L ... F2 D_1 U2 on h x w images (row-major, n = h*w) zero-padded
