@@ -45,7 +45,9 @@ def test_dense_forward_adjoint(DenseModel, n, m, B):
     w = S.complex_gaussian(2, (B, m), S.STREAM_NOISE)
     xa = model.adjoint(dev(w)).cpu().numpy()
     model.check()
-    assert rel(xa, O.dense_adjoint(A, w)) <= 2e-5
+    xo = O.dense_adjoint(A, w)
+    assert rel(xa, xo) <= 2e-5
+    assert np.max(np.abs(xa - xo)) <= 1e-4 * np.sqrt(np.mean(np.abs(xo) ** 2))
 
 
 def test_dense_gradient_descent(DenseModel):
@@ -61,6 +63,7 @@ def test_dense_gradient_descent(DenseModel):
     _, h = model.gd_solve(dev(y, torch.float32), x, 40, mu0=0.1, tau0=10.0, record_loss=True)
     model.check()
     assert rel(x.cpu().numpy(), xT) <= 1e-4
+    assert np.max(np.abs(x.cpu().numpy() - xT)) <= 1e-3 * np.sqrt(np.mean(np.abs(xT) ** 2))
     hh = h.cpu().numpy().astype(np.float64)
     assert np.max(np.abs(hh - hist) / hist) <= 1e-3
 
@@ -79,6 +82,7 @@ def test_dense_spectral_init(DenseModel, weight):
     model.check()
     for b in range(B):
         assert rel(got[b], ref[b]) <= 1e-4
+        assert np.max(np.abs(got[b] - ref[b])) <= 1e-3 * np.sqrt(np.mean(np.abs(ref[b]) ** 2))
     got0 = model.spectral_init(dev(y, torch.float32), dev(v0), 0).cpu().numpy()
     assert rel(got0, O.spectral_init(y, v0, fwd, adj, 0)) <= 1e-6
 
@@ -96,9 +100,11 @@ def test_dense_comparison_size_sampled(DenseModel):
     rows = rng.integers(0, m, 256)
     zo = x @ A[rows].T
     assert rel(z[:, rows], zo) <= 2e-5
+    assert np.max(np.abs(z[:, rows] - zo)) <= 1e-4 * np.sqrt(np.mean(np.abs(zo) ** 2))
     w = S.complex_gaussian(4, (B, m), S.STREAM_NOISE)
     xa = model.adjoint(dev(w)).cpu().numpy()
     model.check()
     cols = rng.integers(0, n, 128)
     xo = w @ np.conj(A[:, cols])
     assert rel(xa[:, cols], xo) <= 2e-5
+    assert np.max(np.abs(xa[:, cols] - xo)) <= 1e-4 * np.sqrt(np.mean(np.abs(xo) ** 2))

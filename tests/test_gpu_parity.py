@@ -190,6 +190,39 @@ def test_full_size_batch_sampled(Plan):
         assert np.max(np.abs(hg[:, b] - hb[:, 0]) / hb[:, 0]) <= 1e-3
 
 
+def test_headline_solve_matches_oracle(Plan):
+    """The benchmark's whole solve at its own configuration: B = 64 signals,
+    n = 2^14 (amplitude U[0, 1] times a random phase), alpha = 4 (m = 2^16),
+    L = 2, noiseless y, 100 power iterations with the optimal weight
+    (lambda = -1), then 500 GD steps at mu0 = 0.15, tau0 = 100. Sampled problems
+    of the batch are solved by the FP64 oracle from the same inputs; the final
+    reconstruction errors up to a global phase agree within 1e-4 (the target),
+    and the iterates themselves agree within 1e-4 in norm (5e-4 of the RMS per
+    element) after the spectral start and after the whole solve."""
+    n, m, L, B = 2 ** 14, 2 ** 16, 2, 64
+    seed = 20240905
+    plan = Plan(n, m, L, seed)
+    theta = S.phases(seed, L, m)
+    fwd, adj = O.structured_ops(theta, n, m)
+    x_true = S.signal_amplitude_phase(seed, B, n)
+    y_o = np.abs(fwd(x_true)) ** 2
+    v0 = S.start_vector(seed, B, n)
+    y = dev(y_o, torch.float32)
+    x0 = plan.spectral_init(y, dev(v0), 100, weight="optimal", lam=-1.0)
+    x0g = host(x0)
+    plan.gd_solve(y, x0, 500, mu0=0.15, tau0=100.0)
+    plan.check()
+    xg = host(x0)
+    for b in (0, 37, 63):
+        x0o = O.spectral_init(y_o[b:b + 1], v0[b:b + 1], fwd, adj, 100, mode="optimal", lam=-1.0)
+        assert_close_elementwise(x0g[b:b + 1], x0o, tol_norm=1e-4, tol_elem=5e-4)
+        xTo, _ = O.gradient_descent(x0o, y_o[b:b + 1], fwd, adj, 500, mu0=0.15, tau0=100.0)
+        assert_close_elementwise(xg[b:b + 1], xTo, tol_norm=1e-4, tol_elem=5e-4)
+        e_gpu = O.relative_error_global_phase(xg[b:b + 1], x_true[b:b + 1])[0]
+        e_or = O.relative_error_global_phase(xTo, x_true[b:b + 1])[0]
+        assert abs(e_gpu - e_or) <= 1e-4, (b, e_gpu, e_or)
+
+
 def test_results_are_deterministic(Plan):
     plan = Plan(3000, 16384, 2, 5)
     x = dev(S.signal_gaussian(5, 4, 3000))

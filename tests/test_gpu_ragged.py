@@ -26,8 +26,11 @@ def rel(a, b):
 
 
 # (n, m, L): repeated shapes share a bucket; power-of-two and radix-3 lengths
+# (the four-step buckets reach m = 2^17 and 2^19, the largest lengths of the
+# benchmark's ragged workload)
 SHAPES = [(64, 256, 2), (64, 256, 2), (64, 256, 2), (100, 512, 1), (100, 512, 1), (30, 96, 3),
-          (1024, 4096, 2), (1024, 4096, 2), (500, 1536, 2), (16, 64, 1), (3000, 16384, 3)]
+          (1024, 4096, 2), (1024, 4096, 2), (500, 1536, 2), (16, 64, 1), (3000, 16384, 3),
+          (20000, 2 ** 17, 2), (20000, 2 ** 17, 2), (2 ** 16, 2 ** 19, 3)]
 BASE = 20240905
 
 
