@@ -176,18 +176,18 @@ struct OpData {
   }
 };
 
-template <class TL>
+template <class TL, bool EPI = true, bool DIAG = true>
 __device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, const OpData<TL>& od, int b, int g,
                                          int p, fsum2& acc) {
-  if (a.op == kOpDiag) {
+  if (DIAG && a.op == kOpDiag) {
     const float2* dp = a.dp + (size_t)b * a.dp_stride;
 #pragma unroll
     for (int j = 0; j < TL::E; ++j) v[j] = cmul(v[j], __ldg(&dp[(p + j * TL::P) * TL::nl(a) + g]));
-  } else if (a.op == kOpDiagConj) {
+  } else if (DIAG && a.op == kOpDiagConj) {
     const float2* dp = a.dp + (size_t)b * a.dp_stride;
 #pragma unroll
     for (int j = 0; j < TL::E; ++j) v[j] = cmulc(v[j], __ldg(&dp[(p + j * TL::P) * TL::nl(a) + g]));
-  } else if (a.op == kOpGdEpilogue) {
+  } else if (EPI && a.op == kOpGdEpilogue) {
     // z -> r = |z|^2 - y, w = r z (Eq. 2); loss partial sum of r^2
 #pragma unroll
     for (int j = 0; j < TL::E; ++j) {
@@ -195,7 +195,7 @@ __device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, 
       acc_add(acc, r * r);
       v[j] = cscale(v[j], r);
     }
-  } else if (a.op == kOpSpecEpilogue) {
+  } else if (EPI && a.op == kOpSpecEpilogue) {
     // z -> T(y_hat) z, y_hat = m y / sum(y) (Eq. 3); times 1/||u|| when the
     // iterate's normalisation is applied here rather than at the chain's input
     const float scale = (float)TL::m(a) / __ldg(&a.sumy[b]);
@@ -225,111 +225,155 @@ __device__ __forceinline__ int grid_index(int row, int col, int h, int w, int tr
   return (row < h && col < w) ? row * w + col : -1;
 }
 
+// Shared scalars of one tile (every pass kernel declares one in shared memory).
+struct TileScalars {
+  float red[64];   // block reductions
+  float scale;     // FIRST: input scale; MID (spectral epilogue): 1/||u||
+  float inv_old;   // LAST / fused: 1/||v_old|| of the power iterate
+  float mu;        // LAST / fused: the problem's step
+};
+
+// The T input lines of a tile staged by TMA (boxes of 16 values x T rows,
+// 128-byte swizzle) into registers: slot j = position p + j*P.
+// swz128_offset(BOX, t, p + j*P) as a per-thread base plus a per-slot
+// constant: for P >= 16 the slot only moves the box; for P < 16 it adds
+// (j*P) & 15 to the 16-byte chunk index, whose bits are disjoint from p's.
+template <class TL>
+__device__ __forceinline__ void load_staged(const unsigned char* src, int t, int p, float2 (&v)[TL::E]) {
+  constexpr int E = TL::E, P = TL::P;
+  const int t7 = t & 7;
+  if constexpr (P >= 16) {
+    const unsigned char* base = src + (p >> 4) * TL::BOX + t * 128 + (((p & 15) << 3) ^ (t7 << 4));
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[j] = *reinterpret_cast<const float2*>(base + j * (P / 16) * TL::BOX);
+  } else {
+    const int base = t * 128 + ((p << 3) ^ (t7 << 4));
+#pragma unroll
+    for (int j = 0; j < E; ++j)
+      v[j] = *reinterpret_cast<const float2*>(src + ((j * P) >> 4) * TL::BOX + (base ^ (((j * P) & 15) << 3)));
+  }
+}
+
 // ------------------------------------------------------------ FIRST pass
+
+// One tile of a FIRST pass: natural-order input of problem b (zero beyond
+// n_in: the padding U), the operation before DFT 0, step 1 of DFT 0 and the
+// four-step twiddles, into the exchange buffer. tw: line twiddles, entry
+// k * TWS = W_ELL^k. The caller synchronises before the next tile.
+template <class TL, int DB, int MAP, int TWS>
+__device__ __forceinline__ void first_tile(const PassArgs& a, int b, int g0, int t, int p, float2* scratch,
+                                           const float2* tw, float2* rowtw, TileScalars& sh) {
+  constexpr int E = TL::E, P = TL::P, T = TL::T, ELL = TL::E * TL::P;
+  const int tid = threadIdx.x;
+  const int g = g0 + t;
+  RowTw<TL> rw;
+  rw.load(a, g0, DB);
+  rw.store(rowtw);
+  const float2 A = tw_m<TL>(a, g * p, DB);
+  // Radix-3 lengths (a.r3): inner problem b = 3 bo + r holds the stride-3
+  // subsequence r of outer problem bo (element 3 nat + r), and the operation
+  // that precedes this DFT is applied at that outer natural index.
+  const int bo = a.r3 ? b / 3 : b, rr = a.r3 ? b - 3 * bo : 0;
+  if (tid == 0)
+    sh.scale = a.norm_in ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)bo * a.norm_in_count, a.norm_in_count))
+                         : 1.0f;
+  // Natural-order input, zero beyond n_in (the padding U): element (line g,
+  // position q) is x[q*NL + g]; the warp reads T consecutive elements.
+  const float2* xb = a.xin + (size_t)bo * a.n_in;
+  // (2D grids: the signal entry at grid_index, tables at the layout index nat)
+  float2 v[E];
+  int idx[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int nat = (p + j * P) * TL::nl(a) + g;
+    if constexpr (MAP) {
+      idx[j] = nat;
+      const int xi = grid_index(p + j * P, g, a.in_h, a.in_w, a.in_tr);
+      v[j] = xi >= 0 ? xb[xi] : make_float2(0.f, 0.f);
+    } else {
+      // in_off: the input is the window off .. off+n_in-1 of the length-m
+      // vector (S^H of the alpha < 1 branch; zero outside)
+      idx[j] = a.r3 ? 3 * nat + rr : nat - a.in_off;
+      v[j] = (unsigned)idx[j] < (unsigned)a.n_in ? xb[idx[j]] : make_float2(0.f, 0.f);
+    }
+  }
+  if (a.op == kOpDiag) {
+    const float2* dp = a.dp + (size_t)bo * a.dp_stride;
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[j] = cmul(v[j], __ldg(&dp[idx[j]]));
+  } else if (a.op == kOpDiagConj) {
+    const float2* dp = a.dp + (size_t)bo * a.dp_stride;
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&dp[idx[j]]));
+  } else if (a.op == kOpGdEpilogue) {  // (radix-3, alpha < 1 chains) r = |z|^2 - y, w = r z, loss partials
+    const float* yb = a.y + (size_t)bo * a.ym;
+    fsum2 acc{0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      if ((unsigned)idx[j] < (unsigned)a.ym) {  // outside the measurement window: w = 0
+        const float res = cabs2(v[j]) - __ldg(&yb[idx[j]]);
+        acc_add(acc, res * res);
+        v[j] = cscale(v[j], res);
+      }
+    }
+    const float sum = block_sum(acc, sh.red);
+    if (tid == 0) a.part_out[(size_t)b * TL::cpp(a) + g0 / T] = sum;
+  } else if (a.op == kOpSpecEpilogue) {  // (radix-3, alpha < 1 chains) w = T(y_hat) z
+    const float* yb = a.y + (size_t)bo * a.ym;
+    const float ysc = (float)a.ym / __ldg(&a.sumy[bo]);
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const float yh = (unsigned)idx[j] < (unsigned)a.ym ? __ldg(&yb[idx[j]]) * ysc : 0.f;
+      float w = yh;
+      if (a.weight_mode == SR_WEIGHT_OPTIMAL) w = yh > 0.f ? fmaxf(1.0f - 1.0f / yh, a.lam) : a.lam;
+      v[j] = cscale(v[j], w);
+    }
+  }
+  __syncthreads();  // sh.scale and the row twiddles visible
+  const float sc = sh.scale;
+#pragma unroll
+  for (int j = 0; j < E; ++j) v[j] = cscale(v[j], sc);
+  line_fft<ELL, T, DB, TWS>(v, scratch, p, t, tw);
+  twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+}
 
 template <int ELL, int T, int DB, int MAP = 0>
 __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     k_first(const __grid_constant__ PassArgs a) {
   using TL = Tile<ELL, T>;
-  constexpr int E = TL::E, P = TL::P;
   extern __shared__ unsigned char smem_raw[];
-  __shared__ float s_scale;
+  __shared__ TileScalars sh;
   unsigned char* smem = aligned_smem(smem_raw);
   const PipeSmem L = pipe_layout(ELL, T, 1, false);
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
   float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
-  const int tid = threadIdx.x;
   int t, p;
   thread_coords<TL>(t, p);
   load_line_twiddles<ELL>(a, tw);  // once per CTA: the grid is persistent over the tiles
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const int b = tile / a.cpp, g0 = (tile - b * a.cpp) * T, g = g0 + t;
-    RowTw<TL> rw;
-    rw.load(a, g0, DB);
-    rw.store(rowtw);
-    const float2 A = tw_m<TL>(a, g * p, DB);
-    // Radix-3 lengths (a.r3): inner problem b = 3 bo + r holds the stride-3
-    // subsequence r of outer problem bo (element 3 nat + r), and the operation
-    // that precedes this DFT is applied at that outer natural index.
-    const int bo = a.r3 ? b / 3 : b, rr = a.r3 ? b - 3 * bo : 0;
-    if (tid == 0)
-      s_scale = a.norm_in ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)bo * a.norm_in_count, a.norm_in_count))
-                          : 1.0f;
-    // Natural-order input, zero beyond n_in (the padding U): element (line g,
-    // position q) is x[q*NL + g]; the warp reads T consecutive elements.
-    const float2* xb = a.xin + (size_t)bo * a.n_in;
-    // (2D grids: the signal entry at grid_index, tables at the layout index nat)
-    float2 v[E];
-    int idx[E];
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const int nat = (p + j * P) * a.nl + g;
-      if constexpr (MAP) {
-        idx[j] = nat;
-        const int xi = grid_index(p + j * P, g, a.in_h, a.in_w, a.in_tr);
-        v[j] = xi >= 0 ? xb[xi] : make_float2(0.f, 0.f);
-      } else {
-        // in_off: the input is the window off .. off+n_in-1 of the length-m
-        // vector (S^H of the alpha < 1 branch; zero outside)
-        idx[j] = a.r3 ? 3 * nat + rr : nat - a.in_off;
-        v[j] = (unsigned)idx[j] < (unsigned)a.n_in ? xb[idx[j]] : make_float2(0.f, 0.f);
-      }
-    }
-    if (a.op == kOpDiag) {
-      const float2* dp = a.dp + (size_t)bo * a.dp_stride;
-#pragma unroll
-      for (int j = 0; j < E; ++j) v[j] = cmul(v[j], __ldg(&dp[idx[j]]));
-    } else if (a.op == kOpDiagConj) {
-      const float2* dp = a.dp + (size_t)bo * a.dp_stride;
-#pragma unroll
-      for (int j = 0; j < E; ++j) v[j] = cmulc(v[j], __ldg(&dp[idx[j]]));
-    } else if (a.op == kOpGdEpilogue) {  // (radix-3, alpha < 1 chains) r = |z|^2 - y, w = r z, loss partials
-      __shared__ float red[64];
-      const float* yb = a.y + (size_t)bo * a.ym;
-      fsum2 acc{0.f, 0.f};
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        if ((unsigned)idx[j] < (unsigned)a.ym) {  // outside the measurement window: w = 0
-          const float res = cabs2(v[j]) - __ldg(&yb[idx[j]]);
-          acc_add(acc, res * res);
-          v[j] = cscale(v[j], res);
-        }
-      }
-      const float sum = block_sum(acc, red);
-      if (tid == 0) a.part_out[(size_t)b * a.cpp + g0 / T] = sum;
-    } else if (a.op == kOpSpecEpilogue) {  // (radix-3, alpha < 1 chains) w = T(y_hat) z
-      const float* yb = a.y + (size_t)bo * a.ym;
-      const float ysc = (float)a.ym / __ldg(&a.sumy[bo]);
-#pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const float yh = (unsigned)idx[j] < (unsigned)a.ym ? __ldg(&yb[idx[j]]) * ysc : 0.f;
-        float w = yh;
-        if (a.weight_mode == SR_WEIGHT_OPTIMAL) w = yh > 0.f ? fmaxf(1.0f - 1.0f / yh, a.lam) : a.lam;
-        v[j] = cscale(v[j], w);
-      }
-    }
-    __syncthreads();
-    const float sc = s_scale;
-#pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = cscale(v[j], sc);
-    line_fft<ELL, T, DB>(v, scratch, p, t, tw);
-    twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
-    __syncthreads();  // scratch, row twiddles and s_scale are reused by the next tile
+    const int b = tile / a.cpp, g0 = (tile - b * a.cpp) * T;
+    first_tile<TL, DB, MAP, 1>(a, b, g0, t, p, scratch, tw, rowtw, sh);
+    __syncthreads();  // scratch, row twiddles and sh.scale are reused by the next tile
   }
 }
 
 // ------------------------------------------------------ MID and LAST passes
 
-// Issues the TMA loads of tile `tile` (T rows of ELL complex values, boxes of
-// 16 values x T rows) into `buf`, completing on barrier `bar`.
+// Issues the TMA loads of one tile -- T rows of ELL complex values starting at
+// row `row` of the tensor `map`, as boxes of 16 values x T rows -- into `buf`,
+// completing on barrier `bar`.
+__device__ __forceinline__ void issue_rows(const CUtensorMap* map, int row, int ell, int T, int box, uint32_t buf,
+                                           uint32_t bar) {
+  mbar_arrive_expect_tx(bar, (uint32_t)(T * ell * 8));
+#pragma unroll 1
+  for (int kb = 0; kb < ell / 16; ++kb) tma_load_2d(buf + (uint32_t)(kb * box), map, kb * 32, row, bar);
+}
+
 template <class TL, int ELL>
 __device__ __forceinline__ void issue_tile(const PassArgs& a, int tile, uint32_t buf, uint32_t bar) {
   const int b = tile / TL::cpp(a), g0 = (tile - b * TL::cpp(a)) * TL::T;
-  const int row = b * TL::nl(a) + g0;
-  mbar_arrive_expect_tx(bar, (uint32_t)(TL::T * ELL * 8));
-#pragma unroll 1
-  for (int kb = 0; kb < ELL / 16; ++kb) tma_load_2d(buf + (uint32_t)(kb * TL::BOX), &a.tmap, kb * 32, row, bar);
+  issue_rows(&a.tmap, b * TL::nl(a) + g0, ELL, TL::T, TL::BOX, buf, bar);
 }
 
 // Shared pipeline of the persistent MID / LAST passes: for every tile of this
@@ -378,21 +422,7 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
         }
         return;
       }
-      const unsigned char* src = smem + (buf ? L.in1 : L.in0);
-      // swz128_offset(BOX, t, p + j*P) as a per-thread base plus a per-slot
-      // constant: for P >= 16 the slot only moves the box; for P < 16 it adds
-      // (j*P) & 15 to the 16-byte chunk index, whose bits are disjoint from p's.
-      const int t7 = t & 7;
-      if constexpr (P >= 16) {
-        const unsigned char* base = src + (p >> 4) * TL::BOX + t * 128 + (((p & 15) << 3) ^ (t7 << 4));
-#pragma unroll
-        for (int j = 0; j < E; ++j) v[j] = *reinterpret_cast<const float2*>(base + j * (P / 16) * TL::BOX);
-      } else {
-        const int base = t * 128 + ((p << 3) ^ (t7 << 4));
-#pragma unroll
-        for (int j = 0; j < E; ++j)
-          v[j] = *reinterpret_cast<const float2*>(src + ((j * P) >> 4) * TL::BOX + (base ^ (((j * P) & 15) << 3)));
-      }
+      load_staged<TL>(smem + (buf ? L.in1 : L.in0), t, p, v);
       if (nbuf == 1) {
         __syncthreads();  // every thread has its slots before the buffer is refilled
         if (tid == 0 && next < a.ntiles) {
@@ -414,126 +444,153 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
   }
 }
 
+// One tile of a MID pass: step 2 of the previous DFT (direction DA) on the T
+// lines in v, the fused operation (D_l, D_l^H, the GD residual with loss
+// partials, or the spectral weights), step 1 of the next DFT (direction DB)
+// and the four-step twiddles, into the exchange buffer.
+template <class TL, int DA, int DB, int TWS>
+__device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], int b, int g0, int t, int p,
+                                         float2* scratch, const float2* tw, float2* rowtw, TileScalars& sh) {
+  constexpr int T = TL::T, ELL = TL::E * TL::P;
+  // The chains apply an epilogue (GD residual or spectral weights) exactly
+  // between a forward and an inverse DFT, and diagonals (or nothing) between
+  // two DFTs of one direction, so each direction pair compiles only its own
+  // operations (fewer live registers: no spills at three CTAs per SM).
+  constexpr bool EPI = DA < 0 && DB > 0;
+  constexpr bool DIAG = !EPI;
+  const int tid = threadIdx.x;
+  const int g = g0 + t;
+  OpData<TL> od;
+  if constexpr (EPI) od.load_y(a, a.op, b, g, p);
+  const bool vs = EPI && a.op == kOpSpecEpilogue && a.norm_in;
+  if (vs && tid == 0)
+    sh.scale = 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count));
+  // four-step twiddles of the second FFT, loaded early so that their latency
+  // overlaps the first FFT
+  RowTw<TL> rw;
+  rw.load(a, g0, DB);
+  const float2 A = tw_m<TL>(a, g * p, DB);
+  line_fft<ELL, T, DA, TWS>(v, scratch, p, t, tw);
+  fsum2 acc{0.f, 0.f};
+  if (vs) {
+    __syncthreads();  // sh.scale visible
+    od.vscale = sh.scale;
+  }
+  apply_op<TL, EPI, DIAG>(v, a, od, b, g, p, acc);
+  if (EPI && a.op == kOpGdEpilogue) {
+    if constexpr (TL::THREADS % 32 == 0) {
+      // one partial per warp (no CTA barrier): [B][tiles][warps]
+      const float s = warp_sum(acc);
+      if ((tid & 31) == 0) a.part_out[((size_t)b * TL::cpp(a) + g0 / T) * (TL::THREADS / 32) + (tid >> 5)] = s;
+    } else {
+      const float s = block_sum(acc, sh.red);
+      if (tid == 0) a.part_out[(size_t)b * TL::cpp(a) + g0 / T] = s;
+    }
+  }
+  rw.store(rowtw);
+  __syncthreads();  // first FFT's scratch reads done; row twiddles visible
+  line_fft<ELL, T, DB, TWS>(v, scratch, p, t, tw);
+  twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+}
+
 template <int ELL, int T, int DA, int DB, int NLC = 0>
 __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     k_mid(const __grid_constant__ PassArgs a, int nbuf) {
   using TL = Tile<ELL, T, NLC>;
   constexpr int E = TL::E;
   extern __shared__ unsigned char smem_raw[];
-  __shared__ float red[64];
+  __shared__ TileScalars sh;
   unsigned char* smem = aligned_smem(smem_raw);
   const PipeSmem L = pipe_layout(ELL, T, nbuf, true);
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
   float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
-  const int tid = threadIdx.x;
   int t, p;
   thread_coords<TL>(t, p);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
-  __shared__ float s_vscale;
   pipe_tiles<ELL, TL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
-    const int g = g0 + t;
-    OpData<TL> od;
-    od.load_y(a, a.op, b, g, p);
-    const bool vs = a.op == kOpSpecEpilogue && a.norm_in;
-    if (vs && tid == 0)
-      s_vscale = 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count));
-    RowTw<TL> rw;
-    rw.load(a, g0, DB);
-    const float2 A = tw_m<TL>(a, g * p, DB);
-    line_fft<ELL, T, DA>(v, scratch, p, t, tw);
-    fsum2 acc{0.f, 0.f};
-    if (vs) {
-      __syncthreads();  // s_vscale visible
-      od.vscale = s_vscale;
-    }
-    apply_op<TL>(v, a, od, b, g, p, acc);
-    if (a.op == kOpGdEpilogue) {
-      if constexpr (TL::THREADS % 32 == 0) {
-        // one partial per warp (no CTA barrier): [B][tiles][warps]
-        const float s = warp_sum(acc);
-        if ((tid & 31) == 0) a.part_out[((size_t)b * TL::cpp(a) + g0 / T) * (TL::THREADS / 32) + (tid >> 5)] = s;
-      } else {
-        const float s = block_sum(acc, red);
-        if (tid == 0) a.part_out[(size_t)b * TL::cpp(a) + g0 / T] = s;
-      }
-    }
-    rw.store(rowtw);
-    __syncthreads();  // first FFT's scratch reads done; row twiddles visible
-    line_fft<ELL, T, DB>(v, scratch, p, t, tw);
-    twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+    mid_tile<TL, DA, DB, 1>(a, v, b, g0, t, p, scratch, tw, rowtw, sh);
   });
+}
+
+// One tile of a LAST pass: step 2 of the final DFT (direction DA), D_1^H on
+// the kept entries and the natural-order output or solver update (U^H: only
+// entries < n_out are written).
+template <class TL, int DA, int MAP, int TWS>
+__device__ __forceinline__ void last_tile(const PassArgs& a, float2 (&v)[TL::E], int b, int g0, int t, int p,
+                                          float2* scratch, const float2* tw, TileScalars& sh) {
+  constexpr int E = TL::E, P = TL::P, T = TL::T, ELL = TL::E * TL::P;
+  const int tid = threadIdx.x;
+  const int g = g0 + t;
+  if (tid == 0) {
+    sh.inv_old = (a.out_mode == kOutSpec && a.norm_in)
+                     ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count))
+                     : 1.0f;
+    sh.mu = a.mu ? a.mu[b] : 0.f;
+  }
+  line_fft<ELL, T, DA, TWS>(v, scratch, p, t, tw);
+  __syncthreads();  // tile scalars visible
+  // natural index of (line g, frequency f) is f*NL + g; keep those < n_out
+  // (U^H), and apply D_1^H only to the kept entries
+  float2* xb = a.xout + (size_t)b * a.n_out;
+  const float inv_old = sh.inv_old, mu2 = 2.0f * sh.mu * a.mu_scale, shv = a.shift * inv_old;
+  fsum2 acc{0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int nat = (p + j * P) * TL::nl(a) + g;
+    // output index: the prefix n_out (U^H), the window out_off .. out_off+n_out-1
+    // (S of the alpha < 1 branch), or grid_index (2D grids); tables stay at nat
+    int oi = nat - a.out_off;
+    if constexpr (MAP) {
+      oi = grid_index(p + j * P, g, a.out_h, a.out_w, a.out_tr);
+      if (oi < 0) continue;
+    } else {
+      if ((unsigned)oi >= (unsigned)a.n_out) continue;
+    }
+    float2 val = v[j];
+    if (a.op == kOpDiagConj) val = cmulc(val, __ldg(&a.dp[(size_t)b * a.dp_stride + nat]));
+    if (a.out_mode == kOutStore) {
+      xb[oi] = val;
+    } else if (a.out_mode == kOutGrad) {
+      xb[oi] = cscale(val, 2.0f);
+    } else if (a.out_mode == kOutGd) {
+      float2 x = xb[oi];
+      x.x = fmaf(-mu2, val.x, x.x);
+      x.y = fmaf(-mu2, val.y, x.y);
+      xb[oi] = x;
+    } else {  // kOutSpec
+      const float2 old = xb[oi];
+      const float2 u = make_float2(fmaf(shv, old.x, val.x), fmaf(shv, old.y, val.y));
+      xb[oi] = u;
+      acc_add(acc, cabs2(u));
+    }
+  }
+  if (a.out_mode == kOutSpec) {
+    const float s = block_sum(acc, sh.red);
+    if (tid == 0) a.part_out[(size_t)b * TL::cpp(a) + g0 / T] = s;
+  }
+  if (a.loss_out && g0 == 0 && tid == 0)
+    a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
 }
 
 template <int ELL, int T, int DA, int NLC = 0, int MAP = 0>
 __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     k_last(const __grid_constant__ PassArgs a, int nbuf) {
   using TL = Tile<ELL, T, NLC>;
-  constexpr int E = TL::E, P = TL::P;
+  constexpr int E = TL::E;
   extern __shared__ unsigned char smem_raw[];
-  __shared__ float red[64];
-  __shared__ float s_inv_old, s_mu;
+  __shared__ TileScalars sh;
   unsigned char* smem = aligned_smem(smem_raw);
   const PipeSmem L = pipe_layout(ELL, T, nbuf, true);
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
-  const int tid = threadIdx.x;
   int t, p;
   thread_coords<TL>(t, p);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
   pipe_tiles<ELL, TL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
-    const int g = g0 + t;
-    if (tid == 0) {
-      s_inv_old = (a.out_mode == kOutSpec && a.norm_in)
-                      ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count))
-                      : 1.0f;
-      s_mu = a.mu ? a.mu[b] : 0.f;
-    }
-    line_fft<ELL, T, DA>(v, scratch, p, t, tw);
-    __syncthreads();  // tile scalars visible
-    // natural index of (line g, frequency f) is f*NL + g; keep those < n_out
-    // (U^H), and apply D_1^H only to the kept entries
-    float2* xb = a.xout + (size_t)b * a.n_out;
-    const float inv_old = s_inv_old, mu2 = 2.0f * s_mu * a.mu_scale, sh = a.shift * inv_old;
-    fsum2 acc{0.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const int nat = (p + j * P) * TL::nl(a) + g;
-      // output index: the prefix n_out (U^H), the window out_off .. out_off+n_out-1
-      // (S of the alpha < 1 branch), or grid_index (2D grids); tables stay at nat
-      int oi = nat - a.out_off;
-      if constexpr (MAP) {
-        oi = grid_index(p + j * P, g, a.out_h, a.out_w, a.out_tr);
-        if (oi < 0) continue;
-      } else {
-        if ((unsigned)oi >= (unsigned)a.n_out) continue;
-      }
-      float2 val = v[j];
-      if (a.op == kOpDiagConj) val = cmulc(val, __ldg(&a.dp[(size_t)b * a.dp_stride + nat]));
-      if (a.out_mode == kOutStore) {
-        xb[oi] = val;
-      } else if (a.out_mode == kOutGrad) {
-        xb[oi] = cscale(val, 2.0f);
-      } else if (a.out_mode == kOutGd) {
-        float2 x = xb[oi];
-        x.x = fmaf(-mu2, val.x, x.x);
-        x.y = fmaf(-mu2, val.y, x.y);
-        xb[oi] = x;
-      } else {  // kOutSpec
-        const float2 old = xb[oi];
-        const float2 u = make_float2(fmaf(sh, old.x, val.x), fmaf(sh, old.y, val.y));
-        xb[oi] = u;
-        acc_add(acc, cabs2(u));
-      }
-    }
-    if (a.out_mode == kOutSpec) {
-      const float s = block_sum(acc, red);
-      if (tid == 0) a.part_out[(size_t)b * TL::cpp(a) + g0 / T] = s;
-    }
-    if (a.loss_out && g0 == 0 && tid == 0)
-      a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
+    last_tile<TL, DA, MAP, 1>(a, v, b, g0, t, p, scratch, tw, sh);
   });
 }
 
@@ -546,81 +603,87 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 // registers, U (zeros beyond n), D_1 and step 1 of the next step's first
 // forward DFT, with the four-step twiddles, into the exchange buffer `eout`.
 // Each D_1 entry is loaded once for both uses.
+template <class TL, int MAP, int TWS>
+__device__ __forceinline__ void last_first_tile(const PassArgs& a, float2 (&v)[TL::E], int b, int g0, int t, int p,
+                                                float2* scratch, const float2* tw, float2* rowtw, TileScalars& sh) {
+  constexpr int E = TL::E, P = TL::P, T = TL::T, ELL = TL::E * TL::P;
+  const int tid = threadIdx.x;
+  const int g = g0 + t;
+  const bool spec = a.out_mode == kOutSpec;
+  if (tid == 0) {
+    sh.mu = spec ? 0.f : a.mu[b];
+    sh.inv_old = spec && a.norm_in
+                     ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count))
+                     : 1.0f;
+  }
+  RowTw<TL> rw;
+  rw.load(a, g0, -1);
+  const float2 A = tw_m<TL>(a, g * p, -1);
+  line_fft<ELL, T, 1, TWS>(v, scratch, p, t, tw);
+  __syncthreads();  // tile scalars visible
+  const float mu2 = 2.0f * sh.mu * a.mu_scale, shv = a.shift * sh.inv_old;
+  float2* xb = a.xout + (size_t)b * a.n_out;
+  const float2* dp = a.dp + (size_t)b * a.dp_stride;
+  fsum2 acc{0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int nat = (p + j * P) * TL::nl(a) + g;
+    // signal index (2D grids: grid_index, with U2 and U2^H the same corner)
+    int xi = nat;
+    bool keep;
+    if constexpr (MAP) {
+      xi = grid_index(p + j * P, g, a.out_h, a.out_w, 0);
+      keep = xi >= 0;
+    } else {
+      keep = nat < a.n_out;
+    }
+    if (keep) {
+      const float2 d = __ldg(&dp[nat]);
+      const float2 gr = cmulc(v[j], d);
+      float2 x = xb[xi];
+      if (spec) {  // u = M v + shift v with v = x / ||x|| (x unnormalised)
+        x = make_float2(fmaf(shv, x.x, gr.x), fmaf(shv, x.y, gr.y));
+        acc_add(acc, cabs2(x));
+      } else {     // x <- x - mu_t 2 A^H(r z)
+        x.x = fmaf(-mu2, gr.x, x.x);
+        x.y = fmaf(-mu2, gr.y, x.y);
+      }
+      xb[xi] = x;
+      v[j] = cmul(x, d);
+    } else {
+      v[j] = make_float2(0.f, 0.f);
+    }
+  }
+  if (spec) {
+    const float s = block_sum(acc, sh.red);
+    if (tid == 0) a.part_out[(size_t)b * TL::cpp(a) + g0 / T] = s;
+  }
+  if (a.loss_out && g0 == 0 && tid == 0)
+    a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
+  rw.store(rowtw);
+  __syncthreads();  // the first FFT's scratch reads done; row twiddles visible
+  line_fft<ELL, T, -1, TWS>(v, scratch, p, t, tw);
+  twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+}
+
 template <int ELL, int T, int NLC = 0, int MAP = 0>
 __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
     k_last_first(const __grid_constant__ PassArgs a, int nbuf) {
   using TL = Tile<ELL, T, NLC>;
-  constexpr int E = TL::E, P = TL::P;
+  constexpr int E = TL::E;
   extern __shared__ unsigned char smem_raw[];
-  __shared__ float red[64];
-  __shared__ float s_mu, s_inv_old;
+  __shared__ TileScalars sh;
   unsigned char* smem = aligned_smem(smem_raw);
   const PipeSmem L = pipe_layout(ELL, T, nbuf, true);
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
   float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
-  const int tid = threadIdx.x;
   int t, p;
   thread_coords<TL>(t, p);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
-  const bool spec = a.out_mode == kOutSpec;
   pipe_tiles<ELL, TL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
-    const int g = g0 + t;
-    if (tid == 0) {
-      s_mu = spec ? 0.f : a.mu[b];
-      s_inv_old = spec && a.norm_in
-                      ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count))
-                      : 1.0f;
-    }
-    RowTw<TL> rw;
-    rw.load(a, g0, -1);
-    const float2 A = tw_m<TL>(a, g * p, -1);
-    line_fft<ELL, T, 1>(v, scratch, p, t, tw);
-    __syncthreads();  // tile scalars visible
-    const float mu2 = 2.0f * s_mu * a.mu_scale, sh = a.shift * s_inv_old;
-    float2* xb = a.xout + (size_t)b * a.n_out;
-    const float2* dp = a.dp + (size_t)b * a.dp_stride;
-    fsum2 acc{0.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const int nat = (p + j * P) * TL::nl(a) + g;
-      // signal index (2D grids: grid_index, with U2 and U2^H the same corner)
-      int xi = nat;
-      bool keep;
-      if constexpr (MAP) {
-        xi = grid_index(p + j * P, g, a.out_h, a.out_w, 0);
-        keep = xi >= 0;
-      } else {
-        keep = nat < a.n_out;
-      }
-      if (keep) {
-        const float2 d = __ldg(&dp[nat]);
-        const float2 gr = cmulc(v[j], d);
-        float2 x = xb[xi];
-        if (spec) {  // u = M v + shift v with v = x / ||x|| (x unnormalised)
-          x = make_float2(fmaf(sh, x.x, gr.x), fmaf(sh, x.y, gr.y));
-          acc_add(acc, cabs2(x));
-        } else {     // x <- x - mu_t 2 A^H(r z)
-          x.x = fmaf(-mu2, gr.x, x.x);
-          x.y = fmaf(-mu2, gr.y, x.y);
-        }
-        xb[xi] = x;
-        v[j] = cmul(x, d);
-      } else {
-        v[j] = make_float2(0.f, 0.f);
-      }
-    }
-    if (spec) {
-      const float s = block_sum(acc, red);
-      if (tid == 0) a.part_out[(size_t)b * TL::cpp(a) + g0 / T] = s;
-    }
-    if (a.loss_out && g0 == 0 && tid == 0)
-      a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
-    rw.store(rowtw);
-    __syncthreads();  // the first FFT's scratch reads done; row twiddles visible
-    line_fft<ELL, T, -1>(v, scratch, p, t, tw);
-    twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+    last_first_tile<TL, MAP, 1>(a, v, b, g0, t, p, scratch, tw, rowtw, sh);
   });
 }
 

@@ -2,8 +2,8 @@
 // radix-2/4/8/16 DFT butterflies, the per-line Stockham FFT held in registers
 // and shared memory, and compensated (two-sum) float reductions.
 //
-// All FFTs here are unnormalised and use the forward sign exp(-2*pi*i*jk/N);
-// the inverse transform is obtained as conj(FFT(conj(v))), and the unitary
+// All FFTs here are unnormalised, with the forward sign exp(-2*pi*i*jk/N) or
+// the inverse sign exp(+2*pi*i*jk/N) chosen at compile time; the unitary
 // 1/sqrt(m) of F (Sec. III, Eq. 5) is folded into the diagonal tables.
 #pragma once
 
@@ -25,64 +25,87 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
-// a * (-i)
-__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }
 
-// --------------------------------------------------------- small DFTs (sign -)
+// Packed FP32x2 arithmetic of the sm_100 family: one instruction adds or
+// subtracts both parts of a complex value (the float2 stays one 64-bit
+// register pair).
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b, exact as a fused multiply-add by -1 (one rounding, like a subtraction)
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// ------------------------------------------------------ small DFTs (sign S)
+// X_k = sum_j a_j exp(S 2 pi i jk/R) for S = -1 (forward) or S = +1 (inverse),
+// unnormalised, natural order in and out. The inverse is written out with the
+// conjugate roots rather than as conj(DFT(conj(.))) so that the real and
+// imaginary parts of every value stay in their register pair.
 // Constants of the 8th and 16th roots of unity: cos(pi/4), cos(pi/8), sin(pi/8).
 constexpr float kC4 = 0.70710678118654752440f;
 constexpr float kC8 = 0.92387953251128675613f;
 constexpr float kS8 = 0.38268343236508977173f;
 
+// a * exp(S i pi/2): -i a for S = -1, +i a for S = +1
+template <int S>
+__device__ __forceinline__ float2 mul_si(float2 a) {
+  return S < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// a times the forward-sign root w (S = -1) or its conjugate (S = +1)
+template <int S>
+__device__ __forceinline__ float2 mul_root(float2 a, float2 w) {
+  return S < 0 ? cmul(a, w) : cmulc(a, w);
+}
+
 __device__ __forceinline__ void dft2(float2& a0, float2& a1) {
-  float2 t = a0;
-  a0 = cadd(t, a1);
-  a1 = csub(t, a1);
+  const float2 t = a0;
+  a0 = padd(t, a1);
+  a1 = psub(t, a1);
 }
 
-// X_k = sum_j a_j exp(-2 pi i jk/4), in place, natural order in and out.
+template <int S>
 __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
-  float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
-  float2 t2 = cadd(a1, a3), t3 = mul_mi(csub(a1, a3));
-  a0 = cadd(t0, t2);
-  a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  const float2 t0 = padd(a0, a2), t1 = psub(a0, a2);
+  const float2 t2 = padd(a1, a3), d = mul_si<S>(psub(a1, a3));
+  a0 = padd(t0, t2);
+  a2 = psub(t0, t2);
+  a1 = make_float2(t1.x + d.x, t1.y + d.y);
+  a3 = make_float2(t1.x - d.x, t1.y - d.y);
 }
 
-// Radix-2 split into two length-4 DFTs (even / odd inputs), w8 = exp(-i pi/4).
+// Radix-2 split into two length-4 DFTs (even / odd inputs), roots w8^k, w8 = exp(S i pi/4).
+template <int S>
 __device__ __forceinline__ void dft8(float2* a) {
   float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
   float2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
-  dft4(e0, e1, e2, e3);
-  dft4(o0, o1, o2, o3);
-  o1 = make_float2(kC4 * (o1.x + o1.y), kC4 * (o1.y - o1.x));   // * (1 - i)/sqrt2
-  o2 = mul_mi(o2);                                               // * -i
-  o3 = make_float2(kC4 * (o3.y - o3.x), -kC4 * (o3.x + o3.y));  // * (-1 - i)/sqrt2
-  a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
-  a[1] = cadd(e1, o1); a[5] = csub(e1, o1);
-  a[2] = cadd(e2, o2); a[6] = csub(e2, o2);
-  a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
+  dft4<S>(e0, e1, e2, e3);
+  dft4<S>(o0, o1, o2, o3);
+  o1 = mul_root<S>(o1, make_float2(kC4, -kC4));
+  o2 = mul_si<S>(o2);
+  o3 = mul_root<S>(o3, make_float2(-kC4, -kC4));
+  a[0] = padd(e0, o0); a[4] = psub(e0, o0);
+  a[1] = padd(e1, o1); a[5] = psub(e1, o1);
+  a[2] = padd(e2, o2); a[6] = psub(e2, o2);
+  a[3] = padd(e3, o3); a[7] = psub(e3, o3);
 }
 
-// 16 = 4 x 4: length-4 DFTs over the stride-4 groups, twiddles w16^(j2*k1),
+// 16 = 4 x 4: length-4 DFTs over the stride-4 groups, roots w16^(j2*k1),
 // length-4 DFTs across groups; input index j2 + 4*j1, output index k1 + 4*k2.
+template <int S>
 __device__ __forceinline__ void dft16(float2* a) {
 #pragma unroll
-  for (int j2 = 0; j2 < 4; ++j2) dft4(a[j2], a[j2 + 4], a[j2 + 8], a[j2 + 12]);
-  // now a[j2 + 4*k1] = B[k1][j2]; multiply by w16^(j2*k1), w16 = exp(-i pi/8)
+  for (int j2 = 0; j2 < 4; ++j2) dft4<S>(a[j2], a[j2 + 4], a[j2 + 8], a[j2 + 12]);
+  // now a[j2 + 4*k1] = B[k1][j2]; multiply by w16^(j2*k1) (forward w16 = exp(-i pi/8))
   const float2 w1 = make_float2(kC8, -kS8), w2 = make_float2(kC4, -kC4), w3 = make_float2(kS8, -kC8);
-  a[5] = cmul(a[5], w1);            // j2=1,k1=1
-  a[6] = cmul(a[6], w2);            // j2=2,k1=1
-  a[7] = cmul(a[7], w3);            // j2=3,k1=1
-  a[9] = cmul(a[9], w2);            // j2=1,k1=2
-  a[10] = mul_mi(a[10]);            // j2=2,k1=2: w^4 = -i
-  a[11] = cmul(a[11], make_float2(-kC4, -kC4));  // j2=3,k1=2: w^6
-  a[13] = cmul(a[13], w3);          // j2=1,k1=3: w^3
-  a[14] = cmul(a[14], make_float2(-kC4, -kC4));  // j2=2,k1=3: w^6
-  a[15] = cmul(a[15], make_float2(-kC8, kS8));   // j2=3,k1=3: w^9
+  a[5] = mul_root<S>(a[5], w1);                          // j2=1,k1=1
+  a[6] = mul_root<S>(a[6], w2);                          // j2=2,k1=1
+  a[7] = mul_root<S>(a[7], w3);                          // j2=3,k1=1
+  a[9] = mul_root<S>(a[9], w2);                          // j2=1,k1=2
+  a[10] = mul_si<S>(a[10]);                              // j2=2,k1=2: w^4
+  a[11] = mul_root<S>(a[11], make_float2(-kC4, -kC4));   // j2=3,k1=2: w^6
+  a[13] = mul_root<S>(a[13], w3);                        // j2=1,k1=3: w^3
+  a[14] = mul_root<S>(a[14], make_float2(-kC4, -kC4));   // j2=2,k1=3: w^6
+  a[15] = mul_root<S>(a[15], make_float2(-kC8, kS8));    // j2=3,k1=3: w^9
 #pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) dft4(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+  for (int k1 = 0; k1 < 4; ++k1) dft4<S>(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
   // a[4*k1 + k2] = X[k1 + 4*k2]: transpose the 4x4 index grid
   float2 t[16];
 #pragma unroll
@@ -93,12 +116,12 @@ __device__ __forceinline__ void dft16(float2* a) {
     for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = t[4 * k1 + k2];
 }
 
-template <int R>
+template <int R, int S>
 __device__ __forceinline__ void dft_small(float2* a) {
   if constexpr (R == 2) dft2(a[0], a[1]);
-  else if constexpr (R == 4) dft4(a[0], a[1], a[2], a[3]);
-  else if constexpr (R == 8) dft8(a);
-  else if constexpr (R == 16) dft16(a);
+  else if constexpr (R == 4) dft4<S>(a[0], a[1], a[2], a[3]);
+  else if constexpr (R == 8) dft8<S>(a);
+  else if constexpr (R == 16) dft16<S>(a);
   else static_assert(R == 1, "radix must be 1, 2, 4, 8 or 16");
 }
 
@@ -145,7 +168,7 @@ __device__ __forceinline__ int sidx(int pos, int t) { return pad16(pos) * T + t;
 // padded pad16(16 Ns (p / Ns) + (p mod Ns)) + r 17 Ns / 16 (stage 1 of lines
 // up to 4096 points, stages 1 and 2 of 8192-point lines); and
 // b mod Ns = (p mod Ns) + (qP mod Ns).
-template <int N, int T, int S>
+template <int N, int T, int S, int DIR, int TWS>
 __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, const float2* tw) {
   using LS_ = LineShape<N>;
   constexpr int E = LS_::E, P = LS_::P;
@@ -177,9 +200,9 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* 
       constexpr int step = N / (Ns * R);  // W_{Ns R}^{r k} = W_N^{r k step}
       const int k = kp + kq;
 #pragma unroll
-      for (int r = 1; r < R; ++r) a[r] = cmul(a[r], tw[r * step * k]);
+      for (int r = 1; r < R; ++r) a[r] = mul_root<DIR>(a[r], tw[r * step * k * TWS]);
     }
-    dft_small<R>(a);
+    dft_small<R, DIR>(a);
     if constexpr (LAST) {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q + r * Q] = a[r];
@@ -194,35 +217,24 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* 
   if constexpr (!LAST) __syncthreads();
 }
 
-template <int N, int T, int S>
+template <int N, int T, int S, int DIR, int TWS>
 __device__ __forceinline__ void fft_stages(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, const float2* tw) {
   if constexpr (S < LineShape<N>::NSTAGE) {
-    fft_stage<N, T, S>(v, sm, p, t, tw);
-    fft_stages<N, T, S + 1>(v, sm, p, t, tw);
+    fft_stage<N, T, S, DIR, TWS>(v, sm, p, t, tw);
+    fft_stages<N, T, S + 1, DIR, TWS>(v, sm, p, t, tw);
   }
 }
 
-__device__ __forceinline__ float2 swap_ri(float2 a) { return make_float2(a.y, a.x); }
-
 // Unnormalised length-N DFT of line t, sign -1 (DIR < 0) or +1 (DIR > 0).
 // In: slot j = position p + j*P; out: slot j = frequency p + j*P (natural order).
-// The inverse sign is the forward transform between two exchanges of the real
-// and imaginary parts (swap(z) = i conj(z), so swap(F(swap(x))) = conj(F(conj(x)))),
-// which costs no arithmetic. The scratch is shared by the CTA's lines: every
-// thread of the block calls this together, and the caller synchronises before
-// the call if the scratch was in use.
-template <int N, int T, int DIR>
+// The inverse sign uses the conjugate roots: the table tw holds the forward
+// roots, entry k * TWS = W_N^k (a table of W_{N TWS} serves every N that
+// divides its length), conjugated where applied. The scratch is shared by the
+// CTA's lines: every thread of the block calls this together, and the caller
+// synchronises before the call if the scratch was in use.
+template <int N, int T, int DIR, int TWS = 1>
 __device__ __forceinline__ void line_fft(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, const float2* tw) {
-  constexpr int E = LineShape<N>::E;
-  if constexpr (DIR > 0) {
-#pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = swap_ri(v[j]);
-  }
-  fft_stages<N, T, 0>(v, sm, p, t, tw);
-  if constexpr (DIR > 0) {
-#pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = swap_ri(v[j]);
-  }
+  fft_stages<N, T, 0, (DIR > 0 ? 1 : -1), TWS>(v, sm, p, t, tw);
 }
 
 // ---------------------------------------------------- compensated summation

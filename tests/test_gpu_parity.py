@@ -196,9 +196,13 @@ def test_headline_solve_matches_oracle(Plan):
     L = 2, noiseless y, 100 power iterations with the optimal weight
     (lambda = -1), then 500 GD steps at mu0 = 0.15, tau0 = 100. Sampled problems
     of the batch are solved by the FP64 oracle from the same inputs; the final
-    reconstruction errors up to a global phase agree within 1e-4 (the target),
-    and the iterates themselves agree within 1e-4 in norm (5e-4 of the RMS per
-    element) after the spectral start and after the whole solve."""
+    reconstruction errors up to a global phase agree within 1e-4 (the target).
+    The iterates agree within 1e-4 in norm (5e-4 of the RMS per element) after
+    the spectral start, and within 1e-3 (5e-3) after the 500 GD steps: GD from
+    a start far from the signal amplifies rounding-level changes (moving the
+    oracle's own start vector by 6e-8 relative moves its final iterate by up to
+    2.5e-4 on problems of this batch), so the FP32 trajectory is pinned to the
+    FP64 one only to that order."""
     n, m, L, B = 2 ** 14, 2 ** 16, 2, 64
     seed = 20240905
     plan = Plan(n, m, L, seed)
@@ -217,7 +221,7 @@ def test_headline_solve_matches_oracle(Plan):
         x0o = O.spectral_init(y_o[b:b + 1], v0[b:b + 1], fwd, adj, 100, mode="optimal", lam=-1.0)
         assert_close_elementwise(x0g[b:b + 1], x0o, tol_norm=1e-4, tol_elem=5e-4)
         xTo, _ = O.gradient_descent(x0o, y_o[b:b + 1], fwd, adj, 500, mu0=0.15, tau0=100.0)
-        assert_close_elementwise(xg[b:b + 1], xTo, tol_norm=1e-4, tol_elem=5e-4)
+        assert_close_elementwise(xg[b:b + 1], xTo, tol_norm=1e-3, tol_elem=5e-3)
         e_gpu = O.relative_error_global_phase(xg[b:b + 1], x_true[b:b + 1])[0]
         e_or = O.relative_error_global_phase(xTo, x_true[b:b + 1])[0]
         assert abs(e_gpu - e_or) <= 1e-4, (b, e_gpu, e_or)
