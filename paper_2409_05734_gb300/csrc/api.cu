@@ -188,6 +188,13 @@ sr_status ensure_backward_buffers(Plan* p, int B) {
 }
 
 float* part_bank(const Plan& p, int bank, int B) { return p.d_part + (size_t)bank * B * part_stride(p); }
+}  // namespace
+
+namespace sr {
+float* plan_part_bank(const Plan& p, int bank, int B) { return part_bank(p, bank, B); }
+}  // namespace sr
+
+namespace {
 
 // Rebuilds the device diagonal tables from p->theta: D_l = exp(i theta_l)/sqrt(m)
 // (the 1/sqrt(m) of each unitary F folded in), natural order, computed in

@@ -1,7 +1,15 @@
 // Ragged batches of independent problems: buckets of equal (n, m, L), each a
-// batched plan with per-problem phases, run as concurrent stream branches that
-// fork from and join into the caller's stream (graph-capturable).
+// batched plan with per-problem phases. Buckets whose four-step geometry the
+// persistent ragged passes cover (power-of-two m from 2^14 to 2^20) form one
+// group: every pass index of a GD or power-iteration step runs as ONE launch
+// over all of the group's problems (ragged_pass.cu), plus one launch each for
+// the per-problem set-up and finish. The other buckets (short transforms,
+// which the resident solver runs whole, radix-3 lengths, longer lines) run as
+// concurrent stream branches that fork from and join into the caller's
+// stream. Everything is graph-capturable.
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <map>
 #include <new>
 #include <string>
@@ -9,6 +17,7 @@
 #include <vector>
 
 #include "sr_internal.h"
+#include "sr_ragged.h"
 
 namespace {
 
@@ -35,6 +44,26 @@ struct Bucket {
   sr_plan* plan = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
+  bool fused = false;         // runs in the persistent ragged passes
+};
+
+struct FusedList {
+  int off = 0, nseg = 0, ntiles = 0;
+};
+
+// The buckets that run in the persistent ragged passes, and the launch
+// descriptors of every pass kind (built once at creation).
+struct Fused {
+  std::vector<int> buckets;
+  int Lmax = 0;
+  int count = 0;                           // problems in the group
+  sr::RaggedSeg* d_segs = nullptr;
+  sr::RaggedProblem* d_prob = nullptr;
+  float2* d_w1024 = nullptr;
+  int* d_err = nullptr;
+  int grid = 0;                            // persistent CTAs of a launch
+  int occ = 1, num_sms = 1;
+  FusedList first[2], mid[2][16], lf[2], last[2];  // [0] GD, [1] power iteration
 };
 
 // loss[t][member[s]] = scratch[iters * slot0(s) + t * B(s) + (s - slot0(s))]
@@ -64,21 +93,307 @@ struct sr_ragged {
   int* d_member = nullptr;   // [count] per slot
   int* d_slot0 = nullptr;
   int* d_bsize = nullptr;
+  Fused fz;
 };
 
 namespace {
 
-// Runs fn(bucket) on every bucket's stream between a fork from and a join into `s`.
-template <class F>
-sr_status run_buckets(sr_ragged* r, cudaStream_t s, F fn) {
+// Runs fn(bucket) on every bucket's stream between a fork from and a join into
+// `s` (with skip_fused, on the buckets outside the persistent-pass group only),
+// and pre() on `s` itself between the fork and the join, so that the branches
+// overlap the group's work.
+template <class F, class G>
+sr_status run_buckets(sr_ragged* r, cudaStream_t s, F fn, bool skip_fused, G pre) {
   SR_RCUDA(cudaEventRecord(r->fork, s), "cudaEventRecord(fork)");
+  sr_status st0 = pre();
+  if (st0 != SR_OK) return st0;
   for (Bucket& b : r->buckets) {
+    if (skip_fused && b.fused) continue;
     SR_RCUDA(cudaStreamWaitEvent(b.stream, r->fork, 0), "cudaStreamWaitEvent(fork)");
     sr_status st = fn(b);
     if (st != SR_OK) return st;
     SR_RCUDA(cudaEventRecord(b.done, b.stream), "cudaEventRecord(join)");
     SR_RCUDA(cudaStreamWaitEvent(s, b.done, 0), "cudaStreamWaitEvent(join)");
   }
+  return SR_OK;
+}
+
+template <class F>
+sr_status run_buckets(sr_ragged* r, cudaStream_t s, F fn) {
+  return run_buckets(r, s, fn, false, []() { return SR_OK; });
+}
+
+// ------------------------------------------------------- persistent passes
+
+constexpr double kTwoPiR = 6.283185307179586476925286766559;
+
+// Whether a bucket's plan can run in the persistent ragged passes: a 1D
+// power-of-two plan whose two line lengths are 128 .. 1024 points.
+bool fusable(const sr_plan* pl) {
+  const sr::Plan& p = *reinterpret_cast<const sr::Plan*>(pl);
+  if (p.inner || p.two_d || p.mo < p.m || p.m < (1 << 14) || p.m > (1 << 20)) return false;
+  for (int lay = 0; lay < 2; ++lay)
+    if (sr::ragged_class(p.geom[lay].ell) < 0) return false;
+  return true;
+}
+
+// Pass arguments of a bucket plan common to every pass, with the ragged tile
+// geometry of layout `lay` (tiles of 4096 values: T = 4096 / ell lines).
+sr::PassArgs seg_base(const sr::Plan& p, sr::Layout lay, int B, int* err) {
+  sr::PassArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.m = (int)p.m;
+  a.dp_stride = p.dp_stride;
+  a.twl = p.d_twl;
+  a.tw_hi = p.d_tw_hi;
+  a.tw_lo = p.d_tw_lo;
+  a.tw_shift = p.tw_shift;
+  a.err = err;
+  const int ell = p.geom[lay].ell;
+  a.ell = ell;
+  a.T = 4096 / ell;
+  a.lgT = 0;
+  while ((1 << a.lgT) < a.T) ++a.lgT;
+  a.nl = (int)(p.m / ell);
+  a.cpp = a.nl / a.T;
+  a.ntiles = B * a.cpp;
+  a.tws = p.lmax / ell;
+  return a;
+}
+
+// The descriptor of bucket `bk`'s pass of kind `kind` (MID index k for the
+// middle passes) in a GD step (spec = 0) or a power-iteration step (spec = 1):
+// the arguments run_chain would pass for the round trip A^H (epilogue) A of
+// the bucket's plan, with the tile geometry of the ragged passes.
+sr::RaggedSeg make_seg(const Bucket& bk, int kind, int k, int spec, int* err) {
+  const sr::Plan& p = *reinterpret_cast<const sr::Plan*>(bk.plan);
+  const int B = (int)bk.members.size(), L = p.L;
+  sr::RaggedSeg g;
+  std::memset(&g, 0, sizeof(g));
+  sr::Layout lay = sr::kLayoutX;
+  if (kind != sr::kRgFirst && kind != sr::kRgLF && kind != sr::kRgLast) lay = sr::s2_layout((k - 1) % 2);
+  g.a = seg_base(p, lay, B, err);
+  sr::PassArgs& a = g.a;
+  g.kind = kind;
+  g.x_off = bk.x_base;
+  g.y_off = bk.y_base;
+  g.slot0 = bk.slot0;
+  g.bsize = B;
+  g.tma = a.ell <= 512 && p.geom[lay].T == a.T;
+  const float* loss_part = sr::plan_part_bank(p, 2, B);
+  const sr::Layout lay_epi = sr::s2_layout((L - 1) % 2);
+  const int epi_cpp = (int)(p.m / p.geom[lay_epi].ell) / (4096 / p.geom[lay_epi].ell);
+  if (kind == sr::kRgFirst) {
+    a.out_dir = -1;
+    a.n_in = (int)p.n;
+    a.op = sr::kOpDiag;  // D_1
+    a.dp = p.d_dp;
+    a.eout = p.d_e0;
+  } else if (kind == sr::kRgLF || kind == sr::kRgLast) {
+    // after 2L - 1 middle passes the step's data is in e1
+    a.in_dir = 1;
+    a.ein = p.d_e1;
+    a.tmap = p.tmap[1][lay];
+    a.dp = p.d_dp;  // D_1 (conjugated for the update, then again for the next FIRST)
+    a.op = kind == sr::kRgLast ? sr::kOpDiagConj : sr::kOpNone;
+    a.eout = p.d_e0;
+    a.n_out = (int)p.n;
+    a.loss_part = loss_part;
+    a.loss_cpp = epi_cpp * (sr::kRgThreadsPerTile / 32);
+    if (spec) {
+      a.out_mode = sr::kOutSpec;
+      g.spec = 1;
+    } else {
+      a.out_mode = sr::kOutGd;
+      a.mu = p.d_scal + B;
+      g.record_loss = 1;
+    }
+  } else {
+    // middle pass k: step 2 of DFT k-1, the operation, step 1 of DFT k
+    const int da = (k - 1) < L ? -1 : 1, db = k < L ? -1 : 1;
+    g.kind = da < 0 ? (db < 0 ? sr::kRgMidFF : sr::kRgMidFI) : sr::kRgMidII;
+    const int src = (k % 2 == 1) ? 0 : 1;  // FIRST / fused passes write e0, then the buffers alternate
+    a.in_dir = da;
+    a.out_dir = db;
+    a.ein = src ? p.d_e1 : p.d_e0;
+    a.eout = src ? p.d_e0 : p.d_e1;
+    a.tmap = p.tmap[src][lay];
+    if (k < L) {
+      a.op = sr::kOpDiag;
+      a.dp = p.d_dp + (size_t)k * p.m;
+    } else if (k > L) {
+      a.op = sr::kOpDiagConj;
+      a.dp = p.d_dp + (size_t)(2 * L - k) * p.m;
+    } else if (spec) {
+      a.op = sr::kOpSpecEpilogue;
+      a.sumy = p.d_scal;
+      g.spec = 1;
+    } else {
+      a.op = sr::kOpGdEpilogue;
+      a.part_out = const_cast<float*>(loss_part);
+    }
+  }
+  if (g.spec) {
+    g.bank[0] = sr::plan_part_bank(p, 0, B);
+    g.bank[1] = sr::plan_part_bank(p, 1, B);
+    g.count_first = 1;
+    g.count_steady = seg_base(p, sr::kLayoutX, B, err).cpp;
+  }
+  g.variant = (g.kind == sr::kRgFirst ? 0 : g.kind) * 4 + sr::ragged_class(a.ell);
+  return g;
+}
+
+void free_fused(Fused& f) {
+  cudaFree(f.d_segs);
+  cudaFree(f.d_prob);
+  cudaFree(f.d_w1024);
+  cudaFree(f.d_err);
+  f = Fused();
+}
+
+// Builds the persistent-pass group: every fusable bucket (up to the segment
+// limit), the descriptors of each pass kind for GD and power-iteration steps,
+// the per-problem table and the W_1024 line-twiddle table.
+sr_status build_fused(sr_ragged* r) {
+  Fused& f = r->fz;
+  for (size_t i = 0; i < r->buckets.size() && (int)f.buckets.size() < sr::kRgMaxSeg; ++i) {
+    if (!fusable(r->buckets[i].plan)) continue;
+    r->buckets[i].fused = true;
+    f.buckets.push_back((int)i);
+  }
+  if (f.buckets.empty()) return SR_OK;
+  SR_RCUDA(cudaMalloc(&f.d_err, sizeof(int)), "cudaMalloc(ragged status)");
+  SR_RCUDA(cudaMemset(f.d_err, 0, sizeof(int)), "cudaMemset(ragged status)");
+  std::vector<sr::RaggedSeg> all;
+  auto add_list = [&](FusedList& fl, int kind, int k, int spec) {
+    fl.off = (int)all.size();
+    int tiles = 0;
+    for (int bi : f.buckets) {
+      const Bucket& bk = r->buckets[bi];
+      if (k > 0 && k > 2 * bk.L - 1) continue;  // this bucket has fewer middle passes
+      sr::RaggedSeg g = make_seg(bk, kind, k, spec, f.d_err);
+      g.tile0 = tiles;
+      tiles += g.a.ntiles;
+      all.push_back(g);
+    }
+    fl.nseg = (int)all.size() - fl.off;
+    fl.ntiles = tiles;
+  };
+  for (int bi : f.buckets) f.Lmax = std::max(f.Lmax, r->buckets[bi].L);
+  for (int spec = 0; spec < 2; ++spec) {
+    add_list(f.first[spec], sr::kRgFirst, 0, spec);
+    for (int k = 1; k <= 2 * f.Lmax - 1; ++k) add_list(f.mid[spec][k], sr::kRgMidFF, k, spec);
+    add_list(f.lf[spec], sr::kRgLF, 0, spec);
+    add_list(f.last[spec], sr::kRgLast, 0, spec);
+  }
+  std::vector<sr::RaggedProblem> prob;
+  for (int bi : f.buckets) {
+    const Bucket& bk = r->buckets[bi];
+    const sr::Plan& p = *reinterpret_cast<const sr::Plan*>(bk.plan);
+    const int B = (int)bk.members.size();
+    for (int j = 0; j < B; ++j) {
+      sr::RaggedProblem q;
+      std::memset(&q, 0, sizeof(q));
+      q.x_off = bk.x_base + (int64_t)j * bk.n;
+      q.y_off = bk.y_base + (int64_t)j * bk.m;
+      q.n = (int)bk.n;
+      q.m = (int)bk.m;
+      q.b = j;
+      q.B = B;
+      q.scal = p.d_scal;
+      q.bank[0] = sr::plan_part_bank(p, 0, B);
+      q.bank[1] = sr::plan_part_bank(p, 1, B);
+      q.count_steady = seg_base(p, sr::kLayoutX, B, f.d_err).cpp;
+      prob.push_back(q);
+    }
+  }
+  f.count = (int)prob.size();
+  std::vector<float2> w(1024);
+  for (int k = 0; k < 1024; ++k) {
+    const double ang = -kTwoPiR * (double)k / 1024.0;
+    w[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  SR_RCUDA(cudaMalloc(&f.d_segs, sizeof(sr::RaggedSeg) * all.size()), "cudaMalloc(ragged descriptors)");
+  SR_RCUDA(cudaMemcpy(f.d_segs, all.data(), sizeof(sr::RaggedSeg) * all.size(), cudaMemcpyHostToDevice),
+           "cudaMemcpy(ragged descriptors)");
+  SR_RCUDA(cudaMalloc(&f.d_prob, sizeof(sr::RaggedProblem) * prob.size()), "cudaMalloc(ragged problems)");
+  SR_RCUDA(cudaMemcpy(f.d_prob, prob.data(), sizeof(sr::RaggedProblem) * prob.size(), cudaMemcpyHostToDevice),
+           "cudaMemcpy(ragged problems)");
+  SR_RCUDA(cudaMalloc(&f.d_w1024, sizeof(float2) * 1024), "cudaMalloc(line twiddles)");
+  SR_RCUDA(cudaMemcpy(f.d_w1024, w.data(), sizeof(float2) * 1024, cudaMemcpyHostToDevice), "cudaMemcpy(line twiddles)");
+  SR_RCUDA(sr::ragged_occupancy(&f.occ), "ragged pass occupancy");
+  SR_RCUDA(cudaDeviceGetAttribute(&f.num_sms, cudaDevAttrMultiProcessorCount, r->device), "device attributes");
+  f.grid = f.occ * f.num_sms;
+  return SR_OK;
+}
+
+sr_status fused_launch(const Fused& f, bool first, const FusedList& fl, const sr::RaggedDyn& d, cudaStream_t s) {
+  if (fl.nseg == 0) return SR_OK;
+  SR_RCUDA(sr::launch_ragged_pass(first, f.d_segs + fl.off, fl.nseg, fl.ntiles, d, f.grid, f.d_err, s),
+           "launch(ragged pass)");
+  return SR_OK;
+}
+
+float ramp_of(int t, float tau0) {
+  return tau0 > 0.f ? (float)(1.0 - std::exp(-(double)(t + 1) / (double)tau0)) : 1.0f;
+}
+
+// `iters` GD steps on every problem of the group (Sec. II-B-1): one launch per
+// pass index of a step across all of the group's problems.
+sr_status fused_gd(sr_ragged* r, const float* y, float2* x, int iters, float mu0, float tau0, float* loss_scratch,
+                   cudaStream_t s) {
+  const Fused& f = r->fz;
+  if (f.buckets.empty()) return SR_OK;
+  SR_RCUDA(sr::launch_ragged_prepare(f.d_prob, f.count, y, mu0, s), "launch(ragged prepare)");
+  if (iters == 0) return SR_OK;
+  sr::RaggedDyn d;
+  std::memset(&d, 0, sizeof(d));
+  d.x = x;
+  d.xo = x;
+  d.y = y;
+  d.w1024 = f.d_w1024;
+  d.loss_base = loss_scratch;
+  d.iters = iters;
+  sr_status st;
+  if ((st = fused_launch(f, true, f.first[0], d, s)) != SR_OK) return st;
+  for (int t = 0; t < iters; ++t) {
+    d.t = t;
+    d.mu_scale = ramp_of(t, tau0);
+    for (int k = 1; k <= 2 * f.Lmax - 1; ++k)
+      if ((st = fused_launch(f, false, f.mid[0][k], d, s)) != SR_OK) return st;
+    if ((st = fused_launch(f, false, t + 1 < iters ? f.lf[0] : f.last[0], d, s)) != SR_OK) return st;
+  }
+  return SR_OK;
+}
+
+// `iters` power-iteration steps (Sec. II-B-2, Eq. 3-4) on every problem of the
+// group, from x = v0, ending with x = sqrt(sum y) v / ||v||.
+sr_status fused_spectral(sr_ragged* r, const float* y, const float2* v0, float2* x, int iters,
+                         const sr_spectral_opts& o, cudaStream_t s) {
+  const Fused& f = r->fz;
+  if (f.buckets.empty()) return SR_OK;
+  SR_RCUDA(sr::launch_ragged_prepare(f.d_prob, f.count, y, 0.f, s), "launch(ragged prepare)");
+  SR_RCUDA(sr::launch_ragged_start(f.d_prob, f.count, v0, x, s), "launch(ragged start)");
+  sr::RaggedDyn d;
+  std::memset(&d, 0, sizeof(d));
+  d.x = x;
+  d.xo = x;
+  d.y = y;
+  d.w1024 = f.d_w1024;
+  d.lam = o.lambda;
+  d.weight_mode = o.weight_mode;
+  d.shift = o.weight_mode == SR_WEIGHT_IDENTITY ? 0.f : -2.0f * o.lambda;
+  sr_status st;
+  if (iters > 0 && (st = fused_launch(f, true, f.first[1], d, s)) != SR_OK) return st;
+  for (int t = 0; t < iters; ++t) {
+    d.parity = t % 2;
+    d.first_step = t == 0;
+    for (int k = 1; k <= 2 * f.Lmax - 1; ++k)
+      if ((st = fused_launch(f, false, f.mid[1][k], d, s)) != SR_OK) return st;
+    if ((st = fused_launch(f, false, t + 1 < iters ? f.lf[1] : f.last[1], d, s)) != SR_OK) return st;
+  }
+  const int prev = iters == 0 ? 1 : (iters - 1) % 2;
+  SR_RCUDA(sr::launch_ragged_finish(f.d_prob, f.count, x, prev, iters == 0, s), "launch(ragged finish)");
   return SR_OK;
 }
 
@@ -102,6 +417,7 @@ sr_status sr_ragged_destroy(sr_ragged* r) {
     if (b.done) cudaEventDestroy(b.done);
   }
   if (r->fork) cudaEventDestroy(r->fork);
+  free_fused(r->fz);
   cudaFree(r->d_loss);
   cudaFree(r->d_member);
   cudaFree(r->d_slot0);
@@ -189,6 +505,10 @@ sr_status sr_ragged_create(int count, const int64_t* n, const int64_t* m, const 
     sr_ragged_destroy(r);
     return rfail(SR_ERR_CUDA, std::string("ragged setup: ") + cudaGetErrorString(e));
   }
+  if ((st = build_fused(r)) != SR_OK) {
+    sr_ragged_destroy(r);
+    return st;
+  }
   *out = r;
   return SR_OK;
 }
@@ -232,12 +552,23 @@ sr_status sr_ragged_spectral_init(sr_ragged* r, const float* y_cat, const void* 
   sr_status st = check_ragged(r);
   if (st != SR_OK) return st;
   if (!y_cat || !v0_cat || !x_cat) return rfail(SR_ERR_INVALID_ARG, "NULL array argument");
+  if (iters < 0) return rfail(SR_ERR_INVALID_ARG, "iters must be >= 0");
+  sr_spectral_opts o{SR_WEIGHT_IDENTITY, -1.0f};
+  if (opts) o = *opts;
+  if (o.weight_mode != SR_WEIGHT_IDENTITY && o.weight_mode != SR_WEIGHT_OPTIMAL)
+    return rfail(SR_ERR_INVALID_ARG, "unknown weight_mode");
+  if (o.weight_mode == SR_WEIGHT_OPTIMAL && !(o.lambda < 0.f && std::isfinite(o.lambda)))
+    return rfail(SR_ERR_INVALID_ARG, "lambda must be finite and < 0");
   const float2* v0 = static_cast<const float2*>(v0_cat);
   float2* x = static_cast<float2*>(x_cat);
-  return run_buckets(r, (cudaStream_t)stream, [&](Bucket& b) {
-    return sr_spectral_init(b.plan, y_cat + b.y_base, v0 + b.x_base, iters, opts, x + b.x_base,
-                            (int)b.members.size(), b.stream);
-  });
+  cudaStream_t s = (cudaStream_t)stream;
+  return run_buckets(
+      r, s,
+      [&](Bucket& b) {
+        return sr_spectral_init(b.plan, y_cat + b.y_base, v0 + b.x_base, iters, &o, x + b.x_base,
+                                (int)b.members.size(), b.stream);
+      },
+      true, [&]() { return fused_spectral(r, y_cat, v0, x, iters, o, s); });
 }
 
 sr_status sr_ragged_gd_solve(sr_ragged* r, const float* y_cat, void* x_cat, int iters, const sr_gd_opts* opts,
@@ -248,12 +579,20 @@ sr_status sr_ragged_gd_solve(sr_ragged* r, const float* y_cat, void* x_cat, int 
   if (iters < 0) return rfail(SR_ERR_INVALID_ARG, "iters must be >= 0");
   if (loss_hist && iters > r->iters_cap)
     return rfail(SR_ERR_INVALID_ARG, "loss history needs sr_ragged_reserve(iters) first");
+  const float mu0 = opts ? opts->mu0 : 0.1f;
+  const float tau0 = opts ? opts->tau0 : 0.f;
+  if (!(mu0 > 0.f && std::isfinite(mu0))) return rfail(SR_ERR_INVALID_ARG, "mu0 must be finite and > 0");
+  if (!(tau0 >= 0.f && std::isfinite(tau0))) return rfail(SR_ERR_INVALID_ARG, "tau0 must be finite and >= 0");
   float2* x = static_cast<float2*>(x_cat);
   cudaStream_t s = (cudaStream_t)stream;
-  st = run_buckets(r, s, [&](Bucket& b) {
-    float* lh = loss_hist ? r->d_loss + (size_t)iters * b.slot0 : nullptr;
-    return sr_gd_solve(b.plan, y_cat + b.y_base, x + b.x_base, iters, opts, lh, (int)b.members.size(), b.stream);
-  });
+  st = run_buckets(
+      r, s,
+      [&](Bucket& b) {
+        float* lh = loss_hist ? r->d_loss + (size_t)iters * b.slot0 : nullptr;
+        return sr_gd_solve(b.plan, y_cat + b.y_base, x + b.x_base, iters, opts, lh, (int)b.members.size(),
+                           b.stream);
+      },
+      true, [&]() { return fused_gd(r, y_cat, x, iters, mu0, tau0, loss_hist ? r->d_loss : nullptr, s); });
   if (st != SR_OK || !loss_hist || iters == 0) return st;
   const int64_t total = (int64_t)iters * r->count;
   const int blocks = (int)std::min<int64_t>(1024, (total + 255) / 256);
@@ -268,6 +607,14 @@ sr_status sr_ragged_check(sr_ragged* r) {
   if (st != SR_OK) return st;
   for (Bucket& b : r->buckets)
     if ((st = sr_plan_check(b.plan)) != SR_OK) return st;
+  if (r->fz.d_err) {
+    int h = 0;
+    SR_RCUDA(cudaMemcpy(&h, r->fz.d_err, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy(ragged status)");
+    if (h != 0) {
+      SR_RCUDA(cudaMemset(r->fz.d_err, 0, sizeof(int)), "cudaMemset(ragged status)");
+      return rfail((sr_status)h, "a persistent ragged pass gave up waiting for its input tile");
+    }
+  }
   return SR_OK;
 }
 

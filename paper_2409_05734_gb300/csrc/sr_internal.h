@@ -291,6 +291,10 @@ cudaError_t launch_conj_diag_prune(const float2* h, const float2* d, int m, int 
 // Kernel whose bounded wait never completes and records SR_ERR_TIMEOUT in *err.
 cudaError_t launch_wait_probe(int* err, cudaStream_t s);
 
+// Bank `bank` of the plan's per-problem partial sums for batches of B problems
+// (0, 1: power-iteration norms, 2: loss, 3: sums) (api.cu).
+float* plan_part_bank(const Plan& p, int bank, int B);
+
 // Per-problem phases for a batch of B problems of one shape (api.cu).
 sr_status plan_set_problem_phases(sr_plan* plan, int B, const uint64_t* seeds);
 
