@@ -196,6 +196,13 @@ float* plan_part_bank(const Plan& p, int bank, int B) { return part_bank(p, bank
 
 namespace {
 
+// theta wrapped to [-pi, pi).
+double wrap_phase(double t) {
+  double w = std::remainder(t, kTwoPi);
+  if (w >= 0.5 * kTwoPi) w -= kTwoPi;
+  return w;
+}
+
 // Rebuilds the device diagonal tables from p->theta: D_l = exp(i theta_l)/sqrt(m)
 // (the 1/sqrt(m) of each unitary F folded in), natural order, computed in
 // double and rounded to float.
@@ -203,6 +210,7 @@ sr_status upload_diagonals(Plan* p) {
   const int64_t m = p->m;
   const double scale = 1.0 / std::sqrt((double)m);
   std::vector<float2> host((size_t)p->L * m);
+  std::vector<float> ph((size_t)p->L * m);
   for (size_t i = 0; i < host.size(); ++i) {
     // 2D grids: layers 2, 4, ... act on the transposed grid (see grid_index),
     // so their tables are stored transposed: entry (r, c) holds D(c, r)
@@ -211,9 +219,11 @@ sr_status upload_diagonals(Plan* p) {
     if (p->two_d && l % 2 == 1) src = (size_t)(l * m + (k % p->gS) * p->gS + k / p->gS);
     const double t = p->theta[src];
     host[i] = make_float2((float)(std::cos(t) * scale), (float)(std::sin(t) * scale));
+    ph[i] = (float)wrap_phase(t);
   }
   SR_CUDA(cudaMemcpy(p->d_dp, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice),
           "cudaMemcpy(diagonals)");
+  SR_CUDA(cudaMemcpy(p->d_ph, ph.data(), ph.size() * sizeof(float), cudaMemcpyHostToDevice), "cudaMemcpy(phases)");
   return SR_OK;
 }
 
@@ -404,6 +414,10 @@ sr_status run_chain(const Plan& p, const Chain& c, int B, cudaStream_t s) {
     a.tmap = p.tmap[cur_idx][lay];
     a.op = c.mid[k].op;
     a.dp = p.d_dp + (size_t)c.mid[k].d * p.m;
+    if (a.op == sr::kOpDiag || a.op == sr::kOpDiagConj) {
+      a.ph = p.d_ph + (size_t)c.mid[k].d * p.m;
+      a.dscale = (float)(1.0 / std::sqrt((double)p.m));
+    }
     if (a.op == sr::kOpGdEpilogue) {
       a.y = c.y;
       a.part_out = c.loss_part;
@@ -689,21 +703,33 @@ sr_status plan_set_problem_phases(sr_plan* plan, int B, const uint64_t* seeds) {
   const double scale = 1.0 / std::sqrt((double)p.m);
   std::vector<double> th((size_t)lm);
   std::vector<float2> host((size_t)B * lm);
+  std::vector<float> phh((size_t)B * lm);
   for (int b = 0; b < B; ++b) {
     gen_phases(seeds[b], p.L, p.m, th.data());
-    for (int64_t i = 0; i < lm; ++i)
+    for (int64_t i = 0; i < lm; ++i) {
       host[(size_t)b * lm + i] = make_float2((float)(std::cos(th[i]) * scale), (float)(std::sin(th[i]) * scale));
+      phh[(size_t)b * lm + i] = (float)wrap_phase(th[i]);
+    }
   }
   float2* d = nullptr;
+  float* ph = nullptr;
   sr_status st = dalloc(&d, host.size());
   if (st != SR_OK) return st;
+  if ((st = dalloc(&ph, phh.size())) != SR_OK) {
+    cudaFree(d);
+    return st;
+  }
   cudaError_t e = cudaMemcpy(d, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ph, phh.data(), phh.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(d);
+    cudaFree(ph);
     return cuda_fail(e, "cudaMemcpy(problem diagonals)");
   }
   cudaFree(p.d_dp);
+  cudaFree(p.d_ph);
   p.d_dp = d;
+  p.d_ph = ph;
   p.dp_stride = lm;
   p.batch_fixed = B;
   gen_phases(seeds[0], p.L, p.m, p.theta.data());
@@ -792,7 +818,8 @@ sr_status create_plan(int64_t n, int64_t m, int L, uint64_t seed, int gh, int gw
   }
   p->theta.resize((size_t)L * m);
   gen_phases(seed, L, m, p->theta.data());
-  if ((st = dalloc(&p->d_dp, (size_t)L * m)) != SR_OK || (st = upload_diagonals(p)) != SR_OK ||
+  if ((st = dalloc(&p->d_dp, (size_t)L * m)) != SR_OK || (st = dalloc(&p->d_ph, (size_t)L * m)) != SR_OK ||
+      (st = upload_diagonals(p)) != SR_OK ||
       (st = dalloc(&p->d_err, 1)) != SR_OK) {
     sr_plan_destroy(p);
     return st;
@@ -1073,6 +1100,7 @@ sr_status sr_plan_destroy(sr_plan* plan) {
   cudaFree(plan->d_w0);
   cudaFree(plan->d_w1);
   cudaFree(plan->d_theta_f);
+  cudaFree(plan->d_ph);
   cudaFree(plan->d_err);
   cudaFree(plan->d_dp);
   cudaFree(plan->d_twl);
@@ -1119,7 +1147,8 @@ sr_status sr_plan_set_phases_device(sr_plan* plan, const float* theta, void* str
   cudaStream_t s = (cudaStream_t)stream;
   SR_CUDA(cudaMemcpyAsync(plan->d_theta_f, theta, count * sizeof(float), cudaMemcpyDeviceToDevice, s),
           "cudaMemcpyAsync(theta)");
-  SR_CUDA(sr::launch_set_diag(plan->d_theta_f, plan->d_dp, count, (float)(1.0 / std::sqrt((double)plan->m)), s),
+  SR_CUDA(sr::launch_set_diag(plan->d_theta_f, plan->d_dp, plan->d_ph, count,
+                              (float)(1.0 / std::sqrt((double)plan->m)), s),
           "launch(diagonals)");
   plan->host_theta_stale = true;
   return SR_OK;

@@ -59,12 +59,19 @@ __global__ void k_scale_rows(float2* __restrict__ v, int n, const float* __restr
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) vb[i] = cscale(vb[i], f);
 }
 
-// D_l[k] = exp(i theta_l[k]) / sqrt(m) from device phases (float), all layers.
-__global__ void k_set_diag(const float* __restrict__ theta, float2* __restrict__ d, size_t count, float scale) {
+// D_l[k] = exp(i theta_l[k]) / sqrt(m) from device phases (float), all layers,
+// and the phases wrapped to [-pi, pi) for the passes that form exp(i theta).
+__global__ void k_set_diag(const float* __restrict__ theta, float2* __restrict__ d, float* __restrict__ ph,
+                           size_t count, float scale) {
+  constexpr float kTwoPiF = 6.28318530717958647692f;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const float th = theta[i];
     float sn, cs;
-    sincosf(theta[i], &sn, &cs);
+    sincosf(th, &sn, &cs);
     d[i] = make_float2(cs * scale, sn * scale);
+    float w = th - kTwoPiF * rintf(th / kTwoPiF);
+    if (w >= 0.5f * kTwoPiF) w -= kTwoPiF;
+    ph[i] = w;
   }
 }
 
@@ -294,9 +301,9 @@ cudaError_t launch_scale_rows(float2* v, int B, int n, const float* part, int ch
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_diag(const float* theta, float2* d, size_t count, float scale, cudaStream_t s) {
+cudaError_t launch_set_diag(const float* theta, float2* d, float* ph, size_t count, float scale, cudaStream_t s) {
   const int blocks = (int)std::min<size_t>(4096, (count + 255) / 256);
-  k_set_diag<<<blocks, 256, 0, s>>>(theta, d, count, scale);
+  k_set_diag<<<blocks, 256, 0, s>>>(theta, d, ph, count, scale);
   count_launch();
   return cudaGetLastError();
 }

@@ -6,6 +6,7 @@
 // beforehand (sr_plan_create allocates its tables once); this entry point then
 // runs the same pass kernels without touching the plan's workspace, using a
 // fixed scratch area compiled into the library instead of cudaMalloc.
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -148,6 +149,8 @@ sr_status sr_forward_noalloc(const sr_plan* plan_in, const void* x, void* z, int
       a.eout = nxt;
       a.op = sr::kOpDiag;
       a.dp = plan->d_dp + (size_t)k * plan->m;
+      a.ph = plan->d_ph + (size_t)k * plan->m;
+      a.dscale = (float)(1.0 / std::sqrt((double)plan->m));
       e = sr::launch_mid(*plan, lay, a, B, s);
       std::swap(cur, nxt);
     } else {

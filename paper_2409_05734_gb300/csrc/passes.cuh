@@ -465,18 +465,40 @@ __device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], 
   const bool vs = EPI && a.op == kOpSpecEpilogue && a.norm_in;
   if (vs && tid == 0)
     sh.scale = 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count));
+  // Diagonal passes with a phase table: theta_l (4 bytes an entry, half of
+  // D_l) is loaded before the first FFT so that its latency overlaps it, and
+  // exp(i theta) is formed in registers (__sincosf: absolute error below
+  // 4e-7 on [-pi, pi)); D_l's 1/sqrt(m) rides on the four-step twiddle.
+  float th[TL::E];
+  const bool phs = DIAG && a.ph != nullptr && (a.op == kOpDiag || a.op == kOpDiagConj);
+  if (phs) {
+    const float* pb = a.ph + (size_t)b * a.dp_stride;
+#pragma unroll
+    for (int j = 0; j < TL::E; ++j) th[j] = __ldg(&pb[(p + j * TL::P) * TL::nl(a) + g]);
+  }
   // four-step twiddles of the second FFT, loaded early so that their latency
   // overlaps the first FFT
   RowTw<TL> rw;
   rw.load(a, g0, DB);
-  const float2 A = tw_m<TL>(a, g * p, DB);
+  float2 A = tw_m<TL>(a, g * p, DB);
   line_fft<ELL, T, DA, TWS>(v, scratch, p, t, tw);
   fsum2 acc{0.f, 0.f};
   if (vs) {
     __syncthreads();  // sh.scale visible
     od.vscale = sh.scale;
   }
-  apply_op<TL, EPI, DIAG>(v, a, od, b, g, p, acc);
+  if (phs) {
+    const bool cj = a.op == kOpDiagConj;
+#pragma unroll
+    for (int j = 0; j < TL::E; ++j) {
+      float sn, cs;
+      __sincosf(th[j], &sn, &cs);
+      v[j] = cj ? cmulc(v[j], make_float2(cs, sn)) : cmul(v[j], make_float2(cs, sn));
+    }
+    A = cscale(A, a.dscale);
+  } else {
+    apply_op<TL, EPI, DIAG>(v, a, od, b, g, p, acc);
+  }
   if (EPI && a.op == kOpGdEpilogue) {
     if constexpr (TL::THREADS % 32 == 0) {
       // one partial per warp (no CTA barrier): [B][tiles][warps]

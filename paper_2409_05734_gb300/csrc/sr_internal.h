@@ -80,6 +80,12 @@ struct PassArgs {
   int op;
   const float2* dp;        // diagonal D_l (natural order, 1/sqrt(m) folded in)
   int64_t dp_stride;       // complex values between problems' tables (0: one table for the batch)
+  // middle passes: the phases theta_l of the same diagonal (float, in
+  // [-pi, pi), indexed like dp), from which the pass forms exp(i theta) itself
+  // (nullptr: use dp); the 1/sqrt(m) of D_l is then applied as `dscale` with
+  // the pass's four-step twiddles
+  const float* ph;
+  float dscale;
   const float* y;          // measurements [B][m], natural order
   const float* sumy;       // [B]
   float lam;
@@ -147,6 +153,7 @@ struct Plan {
   int tw_shift = 0;
   std::vector<double> theta;     // host copy, [L][m]
   float2* d_dp = nullptr;        // diagonals, [L][m] natural order (per problem: [B][L][m])
+  float* d_ph = nullptr;         // their phases as float in [-pi, pi), same layout
   int64_t dp_stride = 0;         // L * m when every problem of the batch has its own phases
   int batch_fixed = 0;           // with per-problem phases: the only valid batch size
   int tuned_per_sm = 0;          // persistent-grid CTAs per SM chosen by sr_plan_autotune (0: occupancy)
@@ -282,7 +289,8 @@ cudaError_t launch_finish_scalars(const float* part, int chunks, int B, float mu
                                   float* sumy, float* mu, cudaStream_t s);
 cudaError_t launch_scale_rows(float2* v, int B, int n, const float* part, int chunks,
                               const float* sumy, cudaStream_t s);
-cudaError_t launch_set_diag(const float* theta, float2* d, size_t count, float scale, cudaStream_t s);
+// d = exp(i theta) * scale and ph = theta wrapped to [-pi, pi), count entries.
+cudaError_t launch_set_diag(const float* theta, float2* d, float* ph, size_t count, float scale, cudaStream_t s);
 cudaError_t launch_theta_grad(const float2* q, int nq, const float2* d, const float2* h, int m, int B, float* out,
                               cudaStream_t s);
 cudaError_t launch_conj_diag_prune(const float2* h, const float2* d, int m, int n, int B, float2* out,
