@@ -296,24 +296,28 @@ def config_dict(W, world):
 
 
 # ------------------------------------------------------------------ our leg
-def algorithmic_mid_bytes(W):
+def algorithmic_mid_bytes(W, own_phases: bool = False):
     """Compulsory HBM bytes of one middle pass, averaged over the 2L-1 middle
     passes of one iteration: each reads and writes the batch's exchange buffer
-    (8 B per complex element each way); the diagonal passes read one shared
-    D table (8 m B); the epilogue pass reads y (4 B per element)."""
+    (8 B per complex element each way); the diagonal passes read the phases
+    theta_l (4 B per entry: one table for the batch, or one per problem with
+    own_phases); the epilogue pass reads y (4 B per element)."""
     m, B, L = W["m"], W["B"], W["L"]
     n_mid = 2 * L - 1
     diag = n_mid - 1
-    total = n_mid * 16 * m * B + diag * 8 * m + 4 * m * B
+    tables = B if own_phases else 1
+    total = n_mid * 16 * m * B + diag * 4 * m * tables + 4 * m * B
     return total / n_mid
 
 
-def iteration_bytes(W):
-    """Compulsory bytes of one iteration (all 2L+1 passes) for the batch."""
+def iteration_bytes(W, own_phases: bool = False):
+    """Compulsory bytes of one iteration (all 2L+1 passes) for the batch: the
+    first and last passes also read D_1 (8 B per entry)."""
     m, n, B, L = W["m"], W["n"], W["B"], W["L"]
-    first = 8 * n * B + 8 * m + 8 * m * B          # read x, D_1, write exchange
-    mids = algorithmic_mid_bytes(W) * (2 * L - 1)
-    last = 8 * m * B + 8 * m + 16 * n * B           # read exchange, D_1, read+write x
+    tables = B if own_phases else 1
+    first = 8 * n * B + 8 * m * tables + 8 * m * B    # read x, D_1, write exchange
+    mids = algorithmic_mid_bytes(W, own_phases) * (2 * L - 1)
+    last = 8 * m * B + 8 * m * tables + 16 * n * B     # read exchange, D_1, read+write x
     return first + mids + last
 
 
@@ -958,7 +962,9 @@ def ragged_workload(torch, dev, flush, reps: int = 3):
     rg.check()
     ms = statistics.median(times)
     iters = R["spectral_iters"] + R["gd_iters"]
-    nbytes = sum(iteration_bytes(dict(n=int(n[i]), m=int(m[i]), L=int(L[i]), B=1)) for i in range(count))
+    # every problem has its own phases (per-problem tables)
+    nbytes = sum(iteration_bytes(dict(n=int(n[i]), m=int(m[i]), L=int(L[i]), B=1), own_phases=True)
+                 for i in range(count))
     errs = np.array([lib_metrics(x[rg.x_off[i]:rg.x_off[i] + n[i]].view(1, -1),
                                  x_true[rg.x_off[i]:rg.x_off[i] + n[i]].view(1, -1))[1][0] for i in range(count)])
     fin = np.isfinite(errs)

@@ -331,8 +331,16 @@ sr_status sr_ragged_spectral_init(sr_ragged* r, const float* y_cat, const void* 
 sr_status sr_ragged_reserve(sr_ragged* r, int iters);
 sr_status sr_ragged_gd_solve(sr_ragged* r, const float* y_cat, void* x_cat, int iters, const sr_gd_opts* opts,
                              float* loss_hist, void* stream);
-/* As sr_plan_check, over every bucket's plan. */
+/* As sr_plan_check, over every bucket's plan and the queue-driven solve. */
 sr_status sr_ragged_check(sr_ragged* r);
+/* Exercises the failure path of the queue-driven solve (the paper has no
+ * counterpart): runs one solve step whose tiles after the first pass can never
+ * see their inputs complete, so each of their bounded waits gives up after the
+ * library's limit (100 ms of GPU time), records SR_ERR_TIMEOUT and returns.
+ * Synchronises `stream`; the next sr_ragged_check reports SR_ERR_TIMEOUT (and
+ * clears it), and the context stays usable. SR_ERR_UNSUPPORTED when no problem
+ * of the batch runs in the queue-driven solve. Allocates scratch inputs. */
+sr_status sr_ragged_selftest_timeout(sr_ragged* r, void* stream);
 
 /* ---- device status -----------------------------------------------------------
  * sr_plan_check: waits for the device (cudaDeviceSynchronize) and reports the

@@ -77,6 +77,7 @@ SIGNATURES = [
     ("sr_ragged_reserve", C.c_int, [_VP, C.c_int]),
     ("sr_ragged_gd_solve", C.c_int, [_VP, _VP, _VP, C.c_int, C.POINTER(GdOpts), _VP, _VP]),
     ("sr_ragged_check", C.c_int, [_VP]),
+    ("sr_ragged_selftest_timeout", C.c_int, [_VP, _VP]),
     ("sr_kernel_launches", C.c_uint64, []),
     ("sr_plan_set_timing", C.c_int, [_VP, C.c_int]),
     ("sr_plan_get_timing", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),

@@ -1,9 +1,9 @@
 // Ragged batches of independent problems: buckets of equal (n, m, L), each a
 // batched plan with per-problem phases. Buckets whose four-step geometry the
-// persistent ragged passes cover (power-of-two m from 2^14 to 2^20) form one
-// group: every pass index of a GD or power-iteration step runs as ONE launch
-// over all of the group's problems (ragged_pass.cu), plus one launch each for
-// the per-problem set-up and finish. The other buckets (short transforms,
+// queue-driven solve covers (power-of-two m from 2^14 to 2^20) form one group:
+// a whole GD or power-iteration call runs as ONE launch over all of the
+// group's problems (ragged_pass.cu), plus a few launches for the per-problem
+// set-up and finish. The other buckets (short transforms,
 // which the resident solver runs whole, radix-3 lengths, longer lines) run as
 // concurrent stream branches that fork from and join into the caller's
 // stream. Everything is graph-capturable.
@@ -47,23 +47,27 @@ struct Bucket {
   bool fused = false;         // runs in the persistent ragged passes
 };
 
-struct FusedList {
-  int off = 0, nseg = 0, ntiles = 0;
-};
-
 // The buckets that run in the persistent ragged passes, and the launch
 // descriptors of every pass kind (built once at creation).
 struct Fused {
   std::vector<int> buckets;
-  int Lmax = 0;
   int count = 0;                           // problems in the group
-  sr::RaggedSeg* d_segs = nullptr;
   sr::RaggedProblem* d_prob = nullptr;
   float2* d_w1024 = nullptr;
   int* d_err = nullptr;
-  int grid = 0;                            // persistent CTAs of a launch
-  int occ = 1, num_sms = 1;
-  FusedList first[2], mid[2][16], lf[2], last[2];  // [0] GD, [1] power iteration
+  int num_sms = 1;
+  // queue-driven solve: per bucket [FIRST, MID_1 .. MID_{2L-1}, LF, LAST] for
+  // GD ([0]) and the power iteration ([1]), problems in group order, groups of
+  // one L whose passes hold about group_tiles tiles (their data stays in L2)
+  sr::RaggedSeg* d_qsegs[2] = {nullptr, nullptr};
+  int* d_seg_base = nullptr;
+  sr::RgQProblem* d_qprob = nullptr;
+  sr::RgGroup* d_grp = nullptr;
+  int ngrp = 0;
+  int* d_done = nullptr;
+  unsigned long long* d_ticket = nullptr;
+  int qgrid = 0;
+  int group_tiles = 1024;
 };
 
 // loss[t][member[s]] = scratch[iters * slot0(s) + t * B(s) + (s - slot0(s))]
@@ -101,18 +105,24 @@ namespace {
 // Runs fn(bucket) on every bucket's stream between a fork from and a join into
 // `s` (with skip_fused, on the buckets outside the persistent-pass group only),
 // and pre() on `s` itself between the fork and the join, so that the branches
-// overlap the group's work.
+// overlap the group's work. The branches are launched first: their kernels use
+// few CTAs each and run for the whole call, while the group's persistent grid
+// takes its work from a queue, so CTAs of it that find no room start later
+// and still share the work.
 template <class F, class G>
 sr_status run_buckets(sr_ragged* r, cudaStream_t s, F fn, bool skip_fused, G pre) {
   SR_RCUDA(cudaEventRecord(r->fork, s), "cudaEventRecord(fork)");
-  sr_status st0 = pre();
-  if (st0 != SR_OK) return st0;
   for (Bucket& b : r->buckets) {
     if (skip_fused && b.fused) continue;
     SR_RCUDA(cudaStreamWaitEvent(b.stream, r->fork, 0), "cudaStreamWaitEvent(fork)");
     sr_status st = fn(b);
     if (st != SR_OK) return st;
     SR_RCUDA(cudaEventRecord(b.done, b.stream), "cudaEventRecord(join)");
+  }
+  sr_status st0 = pre();
+  if (st0 != SR_OK) return st0;
+  for (Bucket& b : r->buckets) {
+    if (skip_fused && b.fused) continue;
     SR_RCUDA(cudaStreamWaitEvent(s, b.done, 0), "cudaStreamWaitEvent(join)");
   }
   return SR_OK;
@@ -179,7 +189,9 @@ sr::RaggedSeg make_seg(const Bucket& bk, int kind, int k, int spec, int* err) {
   g.y_off = bk.y_base;
   g.slot0 = bk.slot0;
   g.bsize = B;
-  g.tma = a.ell <= 512 && p.geom[lay].T == a.T;
+  // staged by TMA: the passes that read exchange-buffer rows (not FIRST, whose
+  // input is the natural-order signal), with the plan's row tensor map
+  g.tma = kind != sr::kRgFirst && a.ell <= 512 && p.geom[lay].T == a.T;
   const float* loss_part = sr::plan_part_bank(p, 2, B);
   const sr::Layout lay_epi = sr::s2_layout((L - 1) % 2);
   const int epi_cpp = (int)(p.m / p.geom[lay_epi].ell) / (4096 / p.geom[lay_epi].ell);
@@ -218,12 +230,12 @@ sr::RaggedSeg make_seg(const Bucket& bk, int kind, int k, int spec, int* err) {
     a.ein = src ? p.d_e1 : p.d_e0;
     a.eout = src ? p.d_e0 : p.d_e1;
     a.tmap = p.tmap[src][lay];
-    if (k < L) {
-      a.op = sr::kOpDiag;
-      a.dp = p.d_dp + (size_t)k * p.m;
-    } else if (k > L) {
-      a.op = sr::kOpDiagConj;
-      a.dp = p.d_dp + (size_t)(2 * L - k) * p.m;
+    if (k != L) {
+      const int d = k < L ? k : 2 * L - k;
+      a.op = k < L ? sr::kOpDiag : sr::kOpDiagConj;
+      a.dp = p.d_dp + (size_t)d * p.m;
+      a.ph = p.d_ph + (size_t)d * p.m;
+      a.dscale = (float)(1.0 / std::sqrt((double)p.m));
     } else if (spec) {
       a.op = sr::kOpSpecEpilogue;
       a.sumy = p.d_scal;
@@ -236,27 +248,123 @@ sr::RaggedSeg make_seg(const Bucket& bk, int kind, int k, int spec, int* err) {
   if (g.spec) {
     g.bank[0] = sr::plan_part_bank(p, 0, B);
     g.bank[1] = sr::plan_part_bank(p, 1, B);
-    g.count_first = 1;
+    g.count_first = sr::kRgChunks;
     g.count_steady = seg_base(p, sr::kLayoutX, B, err).cpp;
   }
-  g.variant = (g.kind == sr::kRgFirst ? 0 : g.kind) * 4 + sr::ragged_class(a.ell);
+  g.variant = g.kind * 4 + sr::ragged_class(a.ell);
   return g;
 }
 
 void free_fused(Fused& f) {
-  cudaFree(f.d_segs);
+  for (int k = 0; k < 2; ++k) cudaFree(f.d_qsegs[k]);
+  cudaFree(f.d_seg_base);
+  cudaFree(f.d_qprob);
+  cudaFree(f.d_grp);
+  cudaFree(f.d_done);
+  cudaFree(f.d_ticket);
   cudaFree(f.d_prob);
   cudaFree(f.d_w1024);
   cudaFree(f.d_err);
   f = Fused();
 }
 
-// Builds the persistent-pass group: every fusable bucket (up to the segment
-// limit), the descriptors of each pass kind for GD and power-iteration steps,
-// the per-problem table and the W_1024 line-twiddle table.
+// The queue-driven solve's tables: every fused bucket's descriptors in pass
+// order, and the problems in groups of one L of about f.group_tiles tiles per
+// pass (a group's exchange buffers, phases and measurements then fit in L2
+// while its passes run).
+sr_status build_queue(sr_ragged* r) {
+  Fused& f = r->fz;
+  std::vector<sr::RaggedSeg> segs[2];
+  std::vector<int> base(r->buckets.size(), 0);
+  for (int bi : f.buckets) {
+    const Bucket& bk = r->buckets[bi];
+    base[bi] = (int)segs[0].size();
+    for (int spec = 0; spec < 2; ++spec) {
+      segs[spec].push_back(make_seg(bk, sr::kRgFirst, 0, spec, f.d_err));
+      for (int k = 1; k <= 2 * bk.L - 1; ++k) segs[spec].push_back(make_seg(bk, sr::kRgMidFF, k, spec, f.d_err));
+      segs[spec].push_back(make_seg(bk, sr::kRgLF, 0, spec, f.d_err));
+      segs[spec].push_back(make_seg(bk, sr::kRgLast, 0, spec, f.d_err));
+    }
+  }
+  // problems by L (a group has one L), buckets kept together
+  std::vector<int> order(f.buckets.begin(), f.buckets.end());
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return r->buckets[a].L < r->buckets[b].L; });
+  std::vector<sr::RgQProblem> prob;
+  std::vector<sr::RgGroup> grp;
+  for (int bi : order) {
+    const Bucket& bk = r->buckets[bi];
+    const int C = (int)(bk.m / 4096);
+    for (int j = 0; j < (int)bk.members.size(); ++j) {
+      if (grp.empty() || grp.back().L != bk.L || grp.back().ipq + C > f.group_tiles) {
+        if ((int)grp.size() == sr::kRgMaxGroups) return rfail(SR_ERR_UNSUPPORTED, "too many problem groups");
+        sr::RgGroup g;
+        g.p0 = (int)prob.size();
+        g.np = 0;
+        g.L = bk.L;
+        g.ipq = 0;
+        grp.push_back(g);
+      }
+      sr::RgQProblem q;
+      q.bucket = bi;
+      q.b = j;
+      q.C = C;
+      q.off = grp.back().ipq;
+      grp.back().ipq += C;
+      grp.back().np += 1;
+      prob.push_back(q);
+    }
+  }
+  f.ngrp = (int)grp.size();
+  for (int k = 0; k < 2; ++k) {
+    SR_RCUDA(cudaMalloc(&f.d_qsegs[k], sizeof(sr::RaggedSeg) * segs[k].size()), "cudaMalloc(queue descriptors)");
+    SR_RCUDA(cudaMemcpy(f.d_qsegs[k], segs[k].data(), sizeof(sr::RaggedSeg) * segs[k].size(), cudaMemcpyHostToDevice),
+             "cudaMemcpy(queue descriptors)");
+  }
+  SR_RCUDA(cudaMalloc(&f.d_seg_base, sizeof(int) * base.size()), "cudaMalloc(queue tables)");
+  SR_RCUDA(cudaMemcpy(f.d_seg_base, base.data(), sizeof(int) * base.size(), cudaMemcpyHostToDevice),
+           "cudaMemcpy(queue tables)");
+  SR_RCUDA(cudaMalloc(&f.d_qprob, sizeof(sr::RgQProblem) * prob.size()), "cudaMalloc(queue problems)");
+  SR_RCUDA(cudaMemcpy(f.d_qprob, prob.data(), sizeof(sr::RgQProblem) * prob.size(), cudaMemcpyHostToDevice),
+           "cudaMemcpy(queue problems)");
+  SR_RCUDA(cudaMalloc(&f.d_grp, sizeof(sr::RgGroup) * grp.size()), "cudaMalloc(queue groups)");
+  SR_RCUDA(cudaMemcpy(f.d_grp, grp.data(), sizeof(sr::RgGroup) * grp.size(), cudaMemcpyHostToDevice),
+           "cudaMemcpy(queue groups)");
+  SR_RCUDA(cudaMalloc(&f.d_done, sizeof(int) * prob.size()), "cudaMalloc(completion counts)");
+  SR_RCUDA(cudaMalloc(&f.d_ticket, sizeof(unsigned long long)), "cudaMalloc(ticket)");
+  int occ = 1;
+  SR_RCUDA(sr::ragged_solve_occupancy(&occ), "ragged solve occupancy");
+  f.qgrid = occ * f.num_sms;
+  return SR_OK;
+}
+
+// One queue-driven launch running `iters` steps (GD: spec = 0; power
+// iteration: spec = 1) of every problem of the group, after the completion
+// counts and the ticket are cleared.
+sr_status fused_queue(const Fused& f, int spec, int iters, float tau0, const sr::RaggedDyn& d, cudaStream_t s) {
+  SR_RCUDA(cudaMemsetAsync(f.d_done, 0, sizeof(int) * f.count, s), "cudaMemsetAsync(completion counts)");
+  SR_RCUDA(cudaMemsetAsync(f.d_ticket, 0, sizeof(unsigned long long), s), "cudaMemsetAsync(ticket)");
+  sr::RgSolveArgs sa;
+  std::memset(&sa, 0, sizeof(sa));
+  sa.segs = f.d_qsegs[spec];
+  sa.seg_base = f.d_seg_base;
+  sa.prob = f.d_qprob;
+  sa.grp = f.d_grp;
+  sa.ngrp = f.ngrp;
+  sa.T = iters;
+  sa.tau0 = tau0;
+  sa.done = f.d_done;
+  sa.ticket = f.d_ticket;
+  SR_RCUDA(sr::launch_ragged_solve(sa, d, f.qgrid, f.d_err, s), "launch(ragged solve)");
+  return SR_OK;
+}
+
+// Builds the queue-driven group: every fusable bucket, the per-problem table of
+// the set-up and finish kernels, the W_1024 line-twiddle table and the queue's
+// tables (build_queue).
 sr_status build_fused(sr_ragged* r) {
   Fused& f = r->fz;
-  for (size_t i = 0; i < r->buckets.size() && (int)f.buckets.size() < sr::kRgMaxSeg; ++i) {
+  for (size_t i = 0; i < r->buckets.size(); ++i) {
     if (!fusable(r->buckets[i].plan)) continue;
     r->buckets[i].fused = true;
     f.buckets.push_back((int)i);
@@ -264,28 +372,6 @@ sr_status build_fused(sr_ragged* r) {
   if (f.buckets.empty()) return SR_OK;
   SR_RCUDA(cudaMalloc(&f.d_err, sizeof(int)), "cudaMalloc(ragged status)");
   SR_RCUDA(cudaMemset(f.d_err, 0, sizeof(int)), "cudaMemset(ragged status)");
-  std::vector<sr::RaggedSeg> all;
-  auto add_list = [&](FusedList& fl, int kind, int k, int spec) {
-    fl.off = (int)all.size();
-    int tiles = 0;
-    for (int bi : f.buckets) {
-      const Bucket& bk = r->buckets[bi];
-      if (k > 0 && k > 2 * bk.L - 1) continue;  // this bucket has fewer middle passes
-      sr::RaggedSeg g = make_seg(bk, kind, k, spec, f.d_err);
-      g.tile0 = tiles;
-      tiles += g.a.ntiles;
-      all.push_back(g);
-    }
-    fl.nseg = (int)all.size() - fl.off;
-    fl.ntiles = tiles;
-  };
-  for (int bi : f.buckets) f.Lmax = std::max(f.Lmax, r->buckets[bi].L);
-  for (int spec = 0; spec < 2; ++spec) {
-    add_list(f.first[spec], sr::kRgFirst, 0, spec);
-    for (int k = 1; k <= 2 * f.Lmax - 1; ++k) add_list(f.mid[spec][k], sr::kRgMidFF, k, spec);
-    add_list(f.lf[spec], sr::kRgLF, 0, spec);
-    add_list(f.last[spec], sr::kRgLast, 0, spec);
-  }
   std::vector<sr::RaggedProblem> prob;
   for (int bi : f.buckets) {
     const Bucket& bk = r->buckets[bi];
@@ -303,6 +389,7 @@ sr_status build_fused(sr_ragged* r) {
       q.scal = p.d_scal;
       q.bank[0] = sr::plan_part_bank(p, 0, B);
       q.bank[1] = sr::plan_part_bank(p, 1, B);
+      q.sums = sr::plan_part_bank(p, 3, B);
       q.count_steady = seg_base(p, sr::kLayoutX, B, f.d_err).cpp;
       prob.push_back(q);
     }
@@ -313,26 +400,15 @@ sr_status build_fused(sr_ragged* r) {
     const double ang = -kTwoPiR * (double)k / 1024.0;
     w[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
   }
-  SR_RCUDA(cudaMalloc(&f.d_segs, sizeof(sr::RaggedSeg) * all.size()), "cudaMalloc(ragged descriptors)");
-  SR_RCUDA(cudaMemcpy(f.d_segs, all.data(), sizeof(sr::RaggedSeg) * all.size(), cudaMemcpyHostToDevice),
-           "cudaMemcpy(ragged descriptors)");
   SR_RCUDA(cudaMalloc(&f.d_prob, sizeof(sr::RaggedProblem) * prob.size()), "cudaMalloc(ragged problems)");
   SR_RCUDA(cudaMemcpy(f.d_prob, prob.data(), sizeof(sr::RaggedProblem) * prob.size(), cudaMemcpyHostToDevice),
            "cudaMemcpy(ragged problems)");
   SR_RCUDA(cudaMalloc(&f.d_w1024, sizeof(float2) * 1024), "cudaMalloc(line twiddles)");
   SR_RCUDA(cudaMemcpy(f.d_w1024, w.data(), sizeof(float2) * 1024, cudaMemcpyHostToDevice), "cudaMemcpy(line twiddles)");
-  SR_RCUDA(sr::ragged_occupancy(&f.occ), "ragged pass occupancy");
   SR_RCUDA(cudaDeviceGetAttribute(&f.num_sms, cudaDevAttrMultiProcessorCount, r->device), "device attributes");
-  f.grid = f.occ * f.num_sms;
-  return SR_OK;
+  return build_queue(r);
 }
 
-sr_status fused_launch(const Fused& f, bool first, const FusedList& fl, const sr::RaggedDyn& d, cudaStream_t s) {
-  if (fl.nseg == 0) return SR_OK;
-  SR_RCUDA(sr::launch_ragged_pass(first, f.d_segs + fl.off, fl.nseg, fl.ntiles, d, f.grid, f.d_err, s),
-           "launch(ragged pass)");
-  return SR_OK;
-}
 
 float ramp_of(int t, float tau0) {
   return tau0 > 0.f ? (float)(1.0 - std::exp(-(double)(t + 1) / (double)tau0)) : 1.0f;
@@ -354,16 +430,7 @@ sr_status fused_gd(sr_ragged* r, const float* y, float2* x, int iters, float mu0
   d.w1024 = f.d_w1024;
   d.loss_base = loss_scratch;
   d.iters = iters;
-  sr_status st;
-  if ((st = fused_launch(f, true, f.first[0], d, s)) != SR_OK) return st;
-  for (int t = 0; t < iters; ++t) {
-    d.t = t;
-    d.mu_scale = ramp_of(t, tau0);
-    for (int k = 1; k <= 2 * f.Lmax - 1; ++k)
-      if ((st = fused_launch(f, false, f.mid[0][k], d, s)) != SR_OK) return st;
-    if ((st = fused_launch(f, false, t + 1 < iters ? f.lf[0] : f.last[0], d, s)) != SR_OK) return st;
-  }
-  return SR_OK;
+  return fused_queue(f, 0, iters, tau0, d, s);
 }
 
 // `iters` power-iteration steps (Sec. II-B-2, Eq. 3-4) on every problem of the
@@ -384,14 +451,7 @@ sr_status fused_spectral(sr_ragged* r, const float* y, const float2* v0, float2*
   d.weight_mode = o.weight_mode;
   d.shift = o.weight_mode == SR_WEIGHT_IDENTITY ? 0.f : -2.0f * o.lambda;
   sr_status st;
-  if (iters > 0 && (st = fused_launch(f, true, f.first[1], d, s)) != SR_OK) return st;
-  for (int t = 0; t < iters; ++t) {
-    d.parity = t % 2;
-    d.first_step = t == 0;
-    for (int k = 1; k <= 2 * f.Lmax - 1; ++k)
-      if ((st = fused_launch(f, false, f.mid[1][k], d, s)) != SR_OK) return st;
-    if ((st = fused_launch(f, false, t + 1 < iters ? f.lf[1] : f.last[1], d, s)) != SR_OK) return st;
-  }
+  if (iters > 0 && (st = fused_queue(f, 1, iters, 0.f, d, s)) != SR_OK) return st;
   const int prev = iters == 0 ? 1 : (iters - 1) % 2;
   SR_RCUDA(sr::launch_ragged_finish(f.d_prob, f.count, x, prev, iters == 0, s), "launch(ragged finish)");
   return SR_OK;
@@ -599,6 +659,54 @@ sr_status sr_ragged_gd_solve(sr_ragged* r, const float* y_cat, void* x_cat, int 
   k_scatter_loss<<<blocks, 256, 0, s>>>(r->d_loss, r->d_member, r->d_slot0, r->d_bsize, r->count, iters, loss_hist);
   sr::count_launch();
   SR_RCUDA(cudaGetLastError(), "launch(scatter loss)");
+  return SR_OK;
+}
+
+sr_status sr_ragged_selftest_timeout(sr_ragged* r, void* stream) {
+  sr_status st = check_ragged(r);
+  if (st != SR_OK) return st;
+  const Fused& f = r->fz;
+  if (f.buckets.empty()) return rfail(SR_ERR_UNSUPPORTED, "the batch has no problems in the queue-driven solve");
+  cudaStream_t s = (cudaStream_t)stream;
+  // scratch inputs for the FIRST tiles (which need nothing and run normally)
+  float2* x = nullptr;
+  float* y = nullptr;
+  SR_RCUDA(cudaMalloc(&x, sizeof(float2) * (size_t)std::max<int64_t>(1, r->x_total)), "cudaMalloc(selftest x)");
+  cudaError_t e = cudaMalloc(&y, sizeof(float) * (size_t)std::max<int64_t>(1, r->y_total));
+  if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, sizeof(float2) * (size_t)std::max<int64_t>(1, r->x_total), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(y, 0, sizeof(float) * (size_t)std::max<int64_t>(1, r->y_total), s);
+  // every completion count starts far below zero, so no tile after FIRST
+  // ever sees its inputs complete: each such wait gives up after the
+  // library's limit, records SR_ERR_TIMEOUT and its CTA returns
+  if (e == cudaSuccess) e = cudaMemsetAsync(f.d_done, 0x80, sizeof(int) * f.count, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f.d_ticket, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) {
+    sr::RgSolveArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
+    sa.segs = f.d_qsegs[0];
+    sa.seg_base = f.d_seg_base;
+    sa.prob = f.d_qprob;
+    sa.grp = f.d_grp;
+    sa.ngrp = f.ngrp;
+    sa.T = 1;
+    sa.done = f.d_done;
+    sa.ticket = f.d_ticket;
+    sr::RaggedDyn d;
+    std::memset(&d, 0, sizeof(d));
+    d.x = x;
+    d.xo = x;
+    d.y = y;
+    d.w1024 = f.d_w1024;
+    d.iters = 1;
+    e = sr::launch_ragged_solve(sa, d, f.qgrid, f.d_err, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(x);
+  cudaFree(y);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return rfail(SR_ERR_CUDA, std::string("ragged selftest: ") + cudaGetErrorString(e));
+  }
   return SR_OK;
 }
 

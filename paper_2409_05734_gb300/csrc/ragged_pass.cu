@@ -1,26 +1,33 @@
-// Persistent passes over ragged batches: one launch runs the same pass index
-// of a GD or power-iteration step (Sec. II-B) for every problem of a ragged
+// The queue-driven solve over ragged batches: ONE launch runs a whole GD or
+// power-iteration call (Sec. II-B, Eq. 2-4) for every problem of a ragged
 // batch whose four-step geometry it covers, whatever the problem's length.
 //
-// A launch covers segments: buckets of problems of one shape (n, m, L), each
-// with its own batched plan (per-problem phases, exchange buffers, partial
-// sums). A segment's descriptor holds the pass arguments the bucket's plan
-// would launch its own kernel with, its first tile in the launch, and which
-// line length and pass kind it runs; the values that change from call to call
-// or step to step (the caller's concatenated x and y, the step's warm-up
-// factor, the loss-history row, the power iteration's ping-pong banks) come
-// as kernel parameters. Every CTA of the persistent grid takes a contiguous
-// chunk of the launch's tiles, so it mostly stays within one segment; per
-// tile it finds the segment and runs the FIRST / MID / LAST / fused body of
-// passes.cuh for that line length, with the same TMA staging and prefetch of
-// the next tile as the single-plan kernels (lines of up to 512 points; the
-// 4-line tiles of 1024-point lines read their input directly).
+// The problems come from buckets of one shape (n, m, L), each with its own
+// batched plan (per-problem phases, exchange buffers, partial sums). A
+// descriptor per (bucket, pass kind) holds the pass arguments the bucket's plan
+// would launch its own kernel with and which line length and pass kind it
+// runs; the values that change from call to call or step to step (the caller's
+// concatenated x and y, the step's warm-up factor, the loss-history row, the
+// power iteration's ping-pong banks) are filled in on the device.
+//
+// Work items are tiles: (problem, pass, tile), dealt out by an atomic ticket in
+// a fixed order -- group by group (problems of one L whose data fits in L2),
+// pass by pass, problem by problem. A tile of pass q of problem p starts once
+// all tiles of pass q - 1 of p are done (a per-problem completion count, read
+// with acquire semantics). Every dependency points to a lower ticket and a CTA
+// takes a ticket only while it runs, so the lowest unfinished ticket can always
+// proceed: the grid needs no co-residency guarantee. Each wait is bounded; one
+// that gives up records SR_ERR_TIMEOUT and ends its CTA.
 //
 // Every CTA has 256 threads and tiles of 4096 values: lines of 128, 256, 512
-// and 1024 points as 32, 16, 8 and 4 lines per tile. The line twiddles come
-// from one table of W_1024^k in global memory (L1-resident), read with the
-// stride 1024 / ELL, so shared memory holds only the staging buffer, the FFT
-// scratch and the row twiddles.
+// and 1024 points as 32, 16, 8 and 4 lines per tile. A CTA holds two items:
+// the one it runs and the next, whose input it stages by TMA as soon as the
+// current tile's values are in registers and the next tile's inputs are
+// complete (lines of up to 512 points; the 4-line tiles of 1024-point lines
+// read their input directly). The line twiddles come from one table of
+// W_1024^k in global memory (L1-resident), read with the stride 1024 / ELL, so
+// shared memory holds only the staging buffer, the FFT scratch and the row
+// twiddles.
 #include <algorithm>
 
 #include "passes.cuh"
@@ -44,11 +51,6 @@ struct RgSmem {
   static constexpr size_t total = bar + 16;
 };
 
-__device__ __forceinline__ int rg_find(const int* tile0, int nseg, int s, int idx) {
-  while (s + 1 < nseg && idx >= tile0[s + 1]) ++s;
-  return s;
-}
-
 // The pass arguments of segment sg for this launch: its descriptor with the
 // call's and the step's values filled in.
 __device__ __forceinline__ void rg_patch(PassArgs& a, const RaggedSeg& sg, const RaggedDyn& d) {
@@ -70,133 +72,272 @@ __device__ __forceinline__ void rg_patch(PassArgs& a, const RaggedSeg& sg, const
   }
 }
 
-// Copies segment s's descriptor into shared-memory copy `slot` and patches it
-// (warp 0; the caller synchronises before any thread reads it).
-__device__ __forceinline__ void rg_load_args(PassArgs* dst, const RaggedSeg& sg, const RaggedDyn& d) {
+// ------------------------------------------------------- queue-driven solve
+
+// A decoded work item: tile `tile` of pass q of problem p, at step t.
+struct RgItem {
+  int valid;
+  int ready;    // inputs known to be complete (a further tile of the previous item's pass)
+  int p, q, tile, t;
+  int b;        // the problem's index in its bucket
+  int si;       // descriptor
+  int need;     // completed tiles of p before this tile may start (q * C)
+  int variant;
+  int tma;
+  int row;      // first exchange-buffer row of the tile (staged tiles)
+  int ell, C, T;  // line length; tiles per pass of the problem; lines per tile
+  unsigned long long ticket;
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// The pass data a producer wrote with ordinary stores is read by this CTA's
+// TMA loads (the async proxy): order them after the acquire.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ RgItem rg_decode(const RgSolveArgs& sa, const unsigned long long* gstart, unsigned long long tk) {
+  RgItem it;
+  it.valid = 0;
+  if (tk >= gstart[sa.ngrp]) return it;
+  int g = 0;
+  while (tk >= gstart[g + 1]) ++g;
+  const RgGroup G = sa.grp[g];
+  const unsigned long long within = tk - gstart[g];
+  const int q = (int)(within / (unsigned long long)G.ipq);
+  const int r = (int)(within - (unsigned long long)q * G.ipq);
+  int lo = G.p0, hi = G.p0 + G.np - 1;  // the problem whose tiles of this pass hold r
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sa.prob[mid].off <= r) lo = mid;
+    else hi = mid - 1;
+  }
+  const RgQProblem P = sa.prob[lo];
+  it.p = lo;
+  it.q = q;
+  it.tile = r - P.off;
+  // pass sequence of a problem: FIRST; then per step MID_1 .. MID_{2L-1} and
+  // the fused LAST/FIRST (LAST after the final step)
+  int kidx = 0, t = 0;
+  if (q > 0) {
+    const int per = 2 * G.L, qq = q - 1;
+    t = qq / per;
+    const int k = qq - t * per + 1;
+    kidx = k < per ? k : (t + 1 < sa.T ? per : per + 1);
+  }
+  it.t = t;
+  it.b = P.b;
+  it.si = sa.seg_base[P.bucket] + kidx;
+  it.need = q * P.C;
+  const RaggedSeg& sg = sa.segs[it.si];
+  it.variant = sg.variant;
+  it.tma = sg.tma && sg.kind != kRgFirst;
+  it.row = P.b * sg.a.nl + it.tile * sg.a.T;
+  it.ell = sg.a.ell;
+  it.C = P.C;
+  it.T = sg.a.T;
+  it.ticket = tk;
+  it.ready = q == 0;
+  it.valid = 1;
+  return it;
+}
+
+// Thread 0: waits (bounded) until problem p has `need` completed tiles.
+__device__ __forceinline__ bool rg_wait_done(const int* done, int p, int need) {
+  if (need <= 0 || ld_acquire_gpu(done + p) >= need) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    __nanosleep(64);
+    if (ld_acquire_gpu(done + p) >= need) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+struct RgQCtx {
+  const RgSolveArgs* sa;
+  const unsigned long long* gstart;
+  unsigned char* smem;
+  float2* scratch;
+  float2* rowtw;
+  const float2* tw;
+  uint32_t bar, stage;
+  int waits;
+  RgItem* items;     // shared: [2] the current and the next item
+  int* issued;       // shared: [2] whether the item's TMA load is in flight
+  int cur;
+  int* err;
+};
+
+// Thread 0: takes the next ticket and decodes it into items[slot]; the item
+// in the other slot is the one taken before it. Consecutive tickets of one
+// problem's pass are decoded from their predecessor without a table lookup.
+// Called between items, when no tile values are live in registers.
+__device__ __noinline__ void rg_take(RgQCtx& cx, int slot) {
+  const unsigned long long tk = atomicAdd(cx.sa->ticket, 1ull);
+  const RgItem& pv = cx.items[slot ^ 1];
+  RgItem nx;
+  if (pv.valid && tk == pv.ticket + 1 && pv.tile + 1 < pv.C) {
+    nx = pv;
+    nx.ticket = tk;
+    nx.tile += 1;
+    nx.row += pv.T;
+    nx.ready = 1;
+  } else {
+    nx = rg_decode(*cx.sa, cx.gstart, tk);
+  }
+  cx.items[slot] = nx;
+  cx.issued[slot] = 0;
+}
+
+// Thread 0: issues the TMA load of items[slot] when it is a staged tile whose
+// inputs are complete (the caller has freed the staging buffer).
+__device__ __forceinline__ void rg_issue(RgQCtx& cx, int slot) {
+  const RgItem& nx = cx.items[slot];
+  if (!nx.valid || !nx.tma) return;
+  if (!nx.ready && ld_acquire_gpu(cx.sa->done + nx.p) < nx.need) return;
+  fence_proxy_async_global();
+  fence_proxy_async_smem();
+  issue_rows(&cx.sa->segs[nx.si].a.tmap, nx.row, nx.ell, nx.T, nx.T * 128, cx.stage, cx.bar);
+  cx.issued[slot] = 1;
+}
+
+// The pass arguments of an item at step t: its descriptor with the call's
+// pointers, the step's warm-up factor and loss row, and the power
+// iteration's banks filled in.
+__device__ __forceinline__ void rg_load_args_q(PassArgs* dst, const RaggedSeg& sg, const RaggedDyn& d, int t,
+                                               float tau0) {
   if (threadIdx.x >= 32) return;
   const uint4* src = reinterpret_cast<const uint4*>(&sg.a);
   uint4* out = reinterpret_cast<uint4*>(dst);
   for (int i = threadIdx.x; i < (int)(sizeof(PassArgs) / 16); i += 32) out[i] = src[i];
   __syncwarp();
-  if (threadIdx.x == 0) rg_patch(*dst, sg, d);
+  if (threadIdx.x == 0) {
+    RaggedDyn e = d;
+    e.t = t;
+    e.mu_scale = tau0 > 0.f ? 1.0f - expf(-(float)(t + 1) / tau0) : 1.0f;
+    e.parity = t & 1;
+    e.first_step = t == 0;
+    rg_patch(*dst, sg, e);
+  }
   __syncwarp();
 }
 
-// Problem and first line of local tile `local` of a segment with T lines per tile.
-__device__ __forceinline__ void rg_tile_pos(const PassArgs& a, int local, int& b, int& g0) {
-  b = local / a.cpp;
-  g0 = (local - b * a.cpp) * a.T;
-}
-
-struct RgCtx {
-  const RaggedSeg* segs;
-  const int* tile0;  // shared
-  int nseg;
-  int c1;            // end of this CTA's chunk
-  unsigned char* smem;
-  float2* scratch;
-  float2* rowtw;
-  const float2* tw;  // W_1024 table
-  uint32_t bar, stage;
-  int waits;         // staged tiles consumed so far (mbarrier phase)
-};
-
-// Thread 0: issues the TMA loads of tile idx (if it is a staged tile).
-__device__ __forceinline__ void rg_issue(const RgCtx& cx, int idx, int s) {
-  if (idx >= cx.c1) return;
-  s = rg_find(cx.tile0, cx.nseg, s, idx);
-  const RaggedSeg& sg = cx.segs[s];
-  if (!sg.tma) return;
-  int b, g0;
-  rg_tile_pos(sg.a, idx - cx.tile0[s], b, g0);
-  fence_proxy_async_smem();
-  issue_rows(&sg.a.tmap, b * sg.a.nl + g0, sg.a.ell, sg.a.T, sg.a.T * 128, cx.stage, cx.bar);
-}
-
-// A run of tiles [i0, i1) of one segment of a pipelined pass (MID, fused
-// LAST/FIRST, LAST) with lines of ELL points: per tile, its input lines into
-// registers (from the staging buffer, or straight from the exchange buffer for
-// unstaged tiles), the refill of the staging buffer with the next tile of the
-// chunk, then the body. False when a staged load never completed (recorded in
-// a.err).
+// One item of a pipelined pass kind (MID, fused LAST/FIRST, LAST) with lines
+// of ELL points: its input lines into registers (from the staging buffer, or
+// straight from the exchange buffer for unstaged tiles), the refill of the
+// staging buffer with the next item, then the body. False when a wait gave up
+// (recorded in err).
 template <int ELL, int KIND>
-__device__ __noinline__ bool rg_run(RgCtx& cx, const PassArgs& a, int s, int i0, int i1, TileScalars& sh) {
+__device__ __noinline__ bool rg_qtile(RgQCtx& cx, const PassArgs& a, const RgItem& it, TileScalars& sh) {
   constexpr int T = 4096 / ELL;
   using TL = Tile<ELL, T>;
   constexpr int TWS = 1024 / ELL;
-  static_assert(TL::THREADS == kRgThreads, "ragged tiles are 256 threads");
   int t, p;
   thread_coords<TL>(t, p);
-  const int cpp = a.cpp, tile0 = cx.tile0[s];
-  for (int idx = i0; idx < i1; ++idx) {
-    const int local = idx - tile0;
-    const int b = local / cpp, g0 = (local - b * cpp) * T;
-    float2 v[TL::E];
-    if constexpr (TL::TMA) {
-      const bool ok = mbar_wait_bounded(cx.bar, (uint32_t)(cx.waits & 1));
-      ++cx.waits;
-      if (!__syncthreads_and(ok)) {
-        if (threadIdx.x == 0) atomicExch(a.err, (int)SR_ERR_TIMEOUT);
-        return false;
+  const int b = it.b, g0 = it.tile * T;  // tiles of a pass hold T consecutive lines
+  float2 v[TL::E];
+  if constexpr (TL::TMA) {
+    if (cx.issued[cx.cur] == 0) {  // the load waits for the producers of this pass (this CTA holds nothing)
+      bool ok = true;
+      if (threadIdx.x == 0) {
+        ok = rg_wait_done(cx.sa->done, it.p, it.need);
+        if (ok) {
+          fence_proxy_async_global();
+          fence_proxy_async_smem();
+          issue_rows(&cx.sa->segs[it.si].a.tmap, it.row, ELL, T, T * 128, cx.stage, cx.bar);
+        } else {
+          atomicExch(cx.err, (int)SR_ERR_TIMEOUT);
+        }
       }
-      load_staged<TL>(cx.smem + RgSmem::stage, t, p, v);
-      __syncthreads();  // every thread has its slots before the buffer is refilled
-      if (threadIdx.x == 0) rg_issue(cx, idx + 1, s);
-    } else {
-      __syncthreads();  // the previous tile's scratch reads are done
-      if (threadIdx.x == 0) rg_issue(cx, idx + 1, s);
-      const float2* src = a.ein + (size_t)b * a.m + (size_t)(g0 + t) * ELL;
-#pragma unroll
-      for (int j = 0; j < TL::E; ++j) v[j] = src[p + j * TL::P];
+      if (!__syncthreads_and(ok)) return false;
     }
-    if constexpr (KIND == kRgMidFF) mid_tile<TL, -1, -1, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
-    else if constexpr (KIND == kRgMidFI) mid_tile<TL, -1, 1, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
-    else if constexpr (KIND == kRgMidII) mid_tile<TL, 1, 1, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
-    else if constexpr (KIND == kRgLF) last_first_tile<TL, 0, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
-    else last_tile<TL, 1, 0, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, sh);
+    const bool ok = mbar_wait_bounded(cx.bar, (uint32_t)(cx.waits & 1));
+    ++cx.waits;
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) atomicExch(cx.err, (int)SR_ERR_TIMEOUT);
+      return false;
+    }
+    load_staged<TL>(cx.smem + RgSmem::stage, t, p, v);
+    __syncthreads();  // slots in registers (staging free); the item's arguments visible
+    if (threadIdx.x == 0) rg_issue(cx, cx.cur ^ 1);
+  } else {
+    bool ok = true;
+    if (threadIdx.x == 0) {
+      ok = rg_wait_done(cx.sa->done, it.p, it.need);
+      if (!ok) atomicExch(cx.err, (int)SR_ERR_TIMEOUT);
+      else rg_issue(cx, cx.cur ^ 1);
+    }
+    if (!__syncthreads_and(ok)) return false;
+    const float2* src = a.ein + (size_t)b * a.m + (size_t)(g0 + t) * ELL;
+#pragma unroll
+    for (int j = 0; j < TL::E; ++j) v[j] = src[p + j * TL::P];
   }
+  if constexpr (KIND == kRgMidFF) mid_tile<TL, -1, -1, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
+  else if constexpr (KIND == kRgMidFI) mid_tile<TL, -1, 1, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
+  else if constexpr (KIND == kRgMidII) mid_tile<TL, 1, 1, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
+  else if constexpr (KIND == kRgLF) last_first_tile<TL, 0, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
+  else last_tile<TL, 1, 0, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, sh);
   return true;
 }
 
-// A run of FIRST tiles [i0, i1) of one segment (lines of ELL points).
+// One FIRST item (lines of ELL points): natural-order input, no wait.
 template <int ELL>
-__device__ __noinline__ void rg_first_run(const PassArgs& a, int tile0, int i0, int i1, float2* scratch,
-                                          const float2* tw, float2* rowtw, TileScalars& sh) {
+__device__ __noinline__ bool rg_qfirst(RgQCtx& cx, const PassArgs& a, const RgItem& it, TileScalars& sh) {
   constexpr int T = 4096 / ELL;
   using TL = Tile<ELL, T>;
   int t, p;
   thread_coords<TL>(t, p);
-  const int cpp = a.cpp;
-  for (int idx = i0; idx < i1; ++idx) {
-    const int local = idx - tile0;
-    const int b = local / cpp, g0 = (local - b * cpp) * T;
-    first_tile<TL, -1, 0, 1024 / ELL>(a, b, g0, t, p, scratch, tw, rowtw, sh);
-    __syncthreads();  // scratch, row twiddles and shared scalars are reused by the next tile
+  const int b = it.b, g0 = it.tile * T;
+  if (threadIdx.x == 0) rg_issue(cx, cx.cur ^ 1);
+  __syncthreads();  // the item's arguments visible
+  first_tile<TL, -1, 0, 1024 / ELL>(a, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
+  return true;
+}
+
+// Runs one item of line length ELL (any pass kind). Each (length, kind) body
+// is a function of its own: one register allocation per body, not one for the
+// union of all of them.
+template <int ELL>
+__device__ __forceinline__ bool rg_qitem(RgQCtx& cx, const PassArgs& a, const RgItem& it, TileScalars& sh) {
+  switch (it.variant >> 2) {
+    case kRgMidFF: return rg_qtile<ELL, kRgMidFF>(cx, a, it, sh);
+    case kRgMidFI: return rg_qtile<ELL, kRgMidFI>(cx, a, it, sh);
+    case kRgMidII: return rg_qtile<ELL, kRgMidII>(cx, a, it, sh);
+    case kRgLF: return rg_qtile<ELL, kRgLF>(cx, a, it, sh);
+    case kRgLast: return rg_qtile<ELL, kRgLast>(cx, a, it, sh);
+    default: return rg_qfirst<ELL>(cx, a, it, sh);
   }
 }
 
-#define SR_RG_CLASSES(X) X(0, 128) X(1, 256) X(2, 512) X(3, 1024)
-
 __global__ void __launch_bounds__(kRgThreads, 3)
-    k_ragged_pipe(const RaggedSeg* __restrict__ segs, int nseg, int ntiles, const __grid_constant__ RaggedDyn dyn,
-                  int* __restrict__ err) {
+    k_ragged_solve(const __grid_constant__ RgSolveArgs sa, const __grid_constant__ RaggedDyn dyn, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ TileScalars sh;
-  __shared__ int tile0[kRgMaxSeg + 1];
+  __shared__ unsigned long long gstart[kRgMaxGroups + 1];
+  __shared__ RgItem items[2];
+  __shared__ int issued[2];
   unsigned char* smem = aligned_smem(smem_raw);
   const int tid = threadIdx.x;
-  for (int i = tid; i < nseg; i += blockDim.x) tile0[i] = segs[i].tile0;
-  if (tid == 0) tile0[nseg] = ntiles;
+  if (tid == 0) {
+    items[0].valid = items[1].valid = 0;
+    unsigned long long acc = 0;
+    for (int g = 0; g < sa.ngrp; ++g) {
+      gstart[g] = acc;
+      const RgGroup G = sa.grp[g];
+      acc += (unsigned long long)(1 + 2 * G.L * sa.T) * (unsigned long long)G.ipq;
+    }
+    gstart[sa.ngrp] = acc;
+  }
   // an earlier pass gave up (see mbar_wait_bounded): do nothing
   if (__syncthreads_or(tid == 0 && *(volatile int*)err != 0)) return;
-  const int per = (ntiles + gridDim.x - 1) / gridDim.x;
-  const int c0 = blockIdx.x * per, c1 = min(ntiles, c0 + per);
-  if (c0 >= c1) return;
-  RgCtx cx;
-  cx.segs = segs;
-  cx.tile0 = tile0;
-  cx.nseg = nseg;
-  cx.c1 = c1;
+  RgQCtx cx;
+  cx.sa = &sa;
+  cx.gstart = gstart;
   cx.smem = smem;
   cx.scratch = reinterpret_cast<float2*>(smem + RgSmem::scratch);
   cx.rowtw = reinterpret_cast<float2*>(smem + RgSmem::rowtw);
@@ -204,145 +345,152 @@ __global__ void __launch_bounds__(kRgThreads, 3)
   cx.bar = smem_addr(smem + RgSmem::bar);
   cx.stage = smem_addr(smem + RgSmem::stage);
   cx.waits = 0;
+  cx.items = items;
+  cx.issued = issued;
+  cx.cur = 0;
+  cx.err = err;
   PassArgs* args = reinterpret_cast<PassArgs*>(smem + RgSmem::args);
   if (tid == 0) {
     mbar_init(cx.bar, 1);
     mbar_init_fence();
+    rg_take(cx, 0);
+    rg_issue(cx, 0);
+    rg_take(cx, 1);
   }
   __syncthreads();
-  int s = rg_find(tile0, nseg, 0, c0);
-  if (tid == 0) rg_issue(cx, c0, s);
-  int cur = 0;
-  for (int idx = c0; idx < c1;) {
-    s = rg_find(tile0, nseg, s, idx);
-    const int i1 = min(c1, tile0[s + 1]);
-    // The copy written here was last read by the run before the previous one,
-    // which ended before the previous run's first barrier.
-    cur ^= 1;
-    rg_load_args(&args[cur], segs[s], dyn);
-    __syncthreads();
+  int slot = 1, cur_si = -1, cur_t = -1;
+  for (;;) {
+    const RgItem it = items[cx.cur];
+    if (!it.valid) break;
+    if (it.si != cur_si || it.t != cur_t) {
+      // the other copy's last reader finished before the previous item's
+      // closing barrier; the item's first barrier publishes this one
+      slot ^= 1;
+      cur_si = it.si;
+      cur_t = it.t;
+      rg_load_args_q(&args[slot], sa.segs[it.si], dyn, it.t, sa.tau0);
+    }
+    const PassArgs& a = args[slot];
     bool ok = true;
-    switch (segs[s].variant) {
-#define SR_RG_CASE(C, ELL)                                                            \
-  case kRgMidFF * 4 + C: ok = rg_run<ELL, kRgMidFF>(cx, args[cur], s, idx, i1, sh); break; \
-  case kRgMidFI * 4 + C: ok = rg_run<ELL, kRgMidFI>(cx, args[cur], s, idx, i1, sh); break; \
-  case kRgMidII * 4 + C: ok = rg_run<ELL, kRgMidII>(cx, args[cur], s, idx, i1, sh); break; \
-  case kRgLF * 4 + C: ok = rg_run<ELL, kRgLF>(cx, args[cur], s, idx, i1, sh); break;       \
-  case kRgLast * 4 + C: ok = rg_run<ELL, kRgLast>(cx, args[cur], s, idx, i1, sh); break;
-      SR_RG_CLASSES(SR_RG_CASE)
-#undef SR_RG_CASE
-      default: break;
+    switch (it.variant & 3) {
+      case 0: ok = rg_qitem<128>(cx, a, it, sh); break;
+      case 1: ok = rg_qitem<256>(cx, a, it, sh); break;
+      case 2: ok = rg_qitem<512>(cx, a, it, sh); break;
+      default: ok = rg_qitem<1024>(cx, a, it, sh); break;
     }
     if (!ok) return;
-    idx = i1;
-  }
-}
-
-// FIRST passes (the input U x, D_1, step 1 of DFT 0) of every segment.
-__global__ void __launch_bounds__(kRgThreads, 3)
-    k_ragged_first(const RaggedSeg* __restrict__ segs, int nseg, int ntiles, const __grid_constant__ RaggedDyn dyn,
-                   int* __restrict__ err) {
-  extern __shared__ unsigned char smem_raw[];
-  __shared__ TileScalars sh;
-  __shared__ int tile0[kRgMaxSeg + 1];
-  unsigned char* smem = aligned_smem(smem_raw);
-  const int tid = threadIdx.x;
-  for (int i = tid; i < nseg; i += blockDim.x) tile0[i] = segs[i].tile0;
-  if (tid == 0) tile0[nseg] = ntiles;
-  if (__syncthreads_or(tid == 0 && *(volatile int*)err != 0)) return;
-  const int per = (ntiles + gridDim.x - 1) / gridDim.x;
-  const int c0 = blockIdx.x * per, c1 = min(ntiles, c0 + per);
-  float2* scratch = reinterpret_cast<float2*>(smem + RgSmem::scratch);
-  float2* rowtw = reinterpret_cast<float2*>(smem + RgSmem::rowtw);
-  PassArgs* args = reinterpret_cast<PassArgs*>(smem + RgSmem::args);
-  int s = 0, cur = 0;
-  for (int idx = c0; idx < c1;) {
-    s = rg_find(tile0, nseg, s, idx);
-    const int i1 = min(c1, tile0[s + 1]);
-    cur ^= 1;
-    rg_load_args(&args[cur], segs[s], dyn);
-    __syncthreads();
-    switch (segs[s].variant & 3) {
-#define SR_RG_FIRST(C, ELL) \
-  case C: rg_first_run<ELL>(args[cur], tile0[s], idx, i1, scratch, dyn.w1024, rowtw, sh); break;
-      SR_RG_CLASSES(SR_RG_FIRST)
-#undef SR_RG_FIRST
-      default: break;
+    __syncthreads();  // every store of the tile issued; every thread has read the item
+    if (tid == 0) {
+      fence_proxy_async_global();
+      __threadfence();
+      atomicAdd(sa.done + it.p, 1);
+      rg_take(cx, cx.cur);  // the item after the next, into the slot just finished
     }
-    idx = i1;
+    cx.cur ^= 1;
   }
 }
 
 // ------------------------------------------------ per-problem set-up / finish
 
-// Compensated block sum (256 threads); valid in thread 0.
-__device__ __forceinline__ float rg_block_sum(fsum2 acc, float* red) { return block_sum(acc, red); }
+// Chunk c = blockIdx.x of problem blockIdx.y (kRgChunks chunks per problem).
+__device__ __forceinline__ void rg_chunk(int len, int& lo, int& hi) {
+  const int per = (len + kRgChunks - 1) / kRgChunks;
+  lo = min(len, (int)blockIdx.x * per);
+  hi = min(len, lo + per);
+}
 
-__global__ void __launch_bounds__(256) k_ragged_prepare(const RaggedProblem* __restrict__ pr, const float* __restrict__ y,
-                                                        float mu0) {
+__global__ void __launch_bounds__(256) k_ragged_sum_y(const RaggedProblem* __restrict__ pr, const float* __restrict__ y) {
   __shared__ float red[64];
-  const RaggedProblem q = pr[blockIdx.x];
+  const RaggedProblem q = pr[blockIdx.y];
+  int lo, hi;
+  rg_chunk(q.m, lo, hi);
   const float* yb = y + q.y_off;
   fsum2 acc{0.f, 0.f};
-  for (int i = threadIdx.x; i < q.m; i += blockDim.x) acc_add(acc, yb[i]);
-  const float s = rg_block_sum(acc, red);
-  if (threadIdx.x == 0) {
-    q.scal[q.b] = s;
-    if (mu0 > 0.f) q.scal[q.B + q.b] = mu0 * (float)q.m / s;
-  }
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) acc_add(acc, yb[i]);
+  const float s = block_sum(acc, red);
+  if (threadIdx.x == 0) q.sums[(size_t)q.b * kRgChunks + blockIdx.x] = s;
+}
+
+__global__ void k_ragged_finish_y(const RaggedProblem* __restrict__ pr, int count, float mu0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const RaggedProblem q = pr[i];
+  const float s = sum_partials(q.sums + (size_t)q.b * kRgChunks, kRgChunks);
+  q.scal[q.b] = s;
+  if (mu0 > 0.f) q.scal[q.B + q.b] = mu0 * (float)q.m / s;
 }
 
 __global__ void __launch_bounds__(256) k_ragged_start(const RaggedProblem* __restrict__ pr, const float2* __restrict__ v0,
                                                       float2* __restrict__ x) {
   __shared__ float red[64];
-  const RaggedProblem q = pr[blockIdx.x];
+  const RaggedProblem q = pr[blockIdx.y];
+  int lo, hi;
+  rg_chunk(q.n, lo, hi);
   fsum2 acc{0.f, 0.f};
-  for (int i = threadIdx.x; i < q.n; i += blockDim.x) {
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const float2 v = v0[q.x_off + i];
     x[q.x_off + i] = v;
     acc_add(acc, cabs2(v));
   }
-  const float s = rg_block_sum(acc, red);
-  if (threadIdx.x == 0) q.bank[1][q.b] = s;
+  const float s = block_sum(acc, red);
+  if (threadIdx.x == 0) q.bank[1][(size_t)q.b * kRgChunks + blockIdx.x] = s;
 }
 
 __global__ void __launch_bounds__(256) k_ragged_finish(const RaggedProblem* __restrict__ pr, float2* __restrict__ x,
                                                        int prev, int first) {
   __shared__ float s_f;
-  const RaggedProblem q = pr[blockIdx.x];
+  const RaggedProblem q = pr[blockIdx.y];
   if (threadIdx.x == 0) {
-    const int cnt = first ? 1 : q.count_steady;
+    const int cnt = first ? kRgChunks : q.count_steady;
     s_f = sqrtf(q.scal[q.b]) / sqrtf(sum_partials(q.bank[prev] + (size_t)q.b * cnt, cnt));
   }
   __syncthreads();
   const float f = s_f;
-  for (int i = threadIdx.x; i < q.n; i += blockDim.x) x[q.x_off + i] = cscale(x[q.x_off + i], f);
+  int lo, hi;
+  rg_chunk(q.n, lo, hi);
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) x[q.x_off + i] = cscale(x[q.x_off + i], f);
 }
 
 }  // namespace
 
 cudaError_t launch_ragged_prepare(const RaggedProblem* pr, int count, const float* y, float mu0, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_ragged_prepare<<<count, 256, 0, s>>>(pr, y, mu0);
+  k_ragged_sum_y<<<dim3(kRgChunks, count), 256, 0, s>>>(pr, y);
+  count_launch();
+  k_ragged_finish_y<<<(count + 127) / 128, 128, 0, s>>>(pr, count, mu0);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_ragged_start(const RaggedProblem* pr, int count, const float2* v0, float2* x, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_ragged_start<<<count, 256, 0, s>>>(pr, v0, x);
+  k_ragged_start<<<dim3(kRgChunks, count), 256, 0, s>>>(pr, v0, x);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_ragged_finish(const RaggedProblem* pr, int count, float2* x, int prev, int first, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_ragged_finish<<<count, 256, 0, s>>>(pr, x, prev, first);
+  k_ragged_finish<<<dim3(kRgChunks, count), 256, 0, s>>>(pr, x, prev, first);
   count_launch();
   return cudaGetLastError();
 }
 
 size_t ragged_smem_bytes() { return RgSmem::total + 1024; }
+
+cudaError_t ragged_solve_occupancy(int* per_sm) {
+  const size_t smem = ragged_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(k_ragged_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_ragged_solve, kRgThreads, smem);
+  if (e == cudaSuccess) *per_sm = std::max(1, *per_sm);
+  return e;
+}
+
+cudaError_t launch_ragged_solve(const RgSolveArgs& sa, const RaggedDyn& d, int grid, int* err, cudaStream_t s) {
+  k_ragged_solve<<<std::max(1, grid), kRgThreads, ragged_smem_bytes(), s>>>(sa, d, err);
+  count_launch();
+  return cudaGetLastError();
+}
 
 int ragged_class(int ell) {
   switch (ell) {
@@ -352,27 +500,6 @@ int ragged_class(int ell) {
     case 1024: return 3;
     default: return -1;
   }
-}
-
-cudaError_t ragged_occupancy(int* per_sm) {
-  const size_t smem = ragged_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(k_ragged_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ragged_first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_ragged_pipe, kRgThreads, smem);
-  if (e == cudaSuccess) *per_sm = std::max(1, *per_sm);
-  return e;
-}
-
-cudaError_t launch_ragged_pass(bool first, const RaggedSeg* segs, int nseg, int ntiles, const RaggedDyn& d, int grid,
-                               int* err, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
-  grid = std::max(1, std::min(grid, ntiles));
-  const size_t smem = ragged_smem_bytes();
-  if (first) k_ragged_first<<<grid, kRgThreads, smem, s>>>(segs, nseg, ntiles, d, err);
-  else k_ragged_pipe<<<grid, kRgThreads, smem, s>>>(segs, nseg, ntiles, d, err);
-  count_launch();
-  return cudaGetLastError();
 }
 
 }  // namespace sr

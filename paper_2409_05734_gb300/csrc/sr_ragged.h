@@ -17,7 +17,6 @@ enum RaggedKind {
   kRgFirst = 5   // FIRST of the first step (k_ragged_first)
 };
 
-constexpr int kRgMaxSeg = 128;  // segments per launch
 constexpr int kRgThreadsPerTile = 256;  // threads of a ragged-pass CTA
 
 // One segment (bucket) of a ragged launch. `a` holds the bucket plan's pass
@@ -27,7 +26,6 @@ struct RaggedSeg {
   PassArgs a;
   int variant;        // kind * 4 + line-length class
   int kind;
-  int tile0;          // first tile of the segment in the launch
   int tma;            // the input lines are staged by TMA
   int spec;           // power-iteration step (norm banks in use)
   int record_loss;    // GD: the step's loss goes to the loss history
@@ -61,11 +59,6 @@ struct RaggedDyn {
 // passes do not cover.
 int ragged_class(int ell);
 size_t ragged_smem_bytes();
-cudaError_t ragged_occupancy(int* per_sm);
-// One persistent launch over `ntiles` tiles of the segments (device array).
-cudaError_t launch_ragged_pass(bool first, const RaggedSeg* segs, int nseg, int ntiles, const RaggedDyn& d, int grid,
-                               int* err, cudaStream_t s);
-
 // One problem of the ragged group, for the per-problem set-up and finish kernels.
 struct RaggedProblem {
   int64_t x_off, y_off;  // offsets in the concatenated x and y (values)
@@ -73,13 +66,53 @@ struct RaggedProblem {
   int b, B;              // index in its bucket and the bucket's size
   float* scal;           // the bucket plan's scalars: sum(y) at [b], the GD step at [B + b]
   float* bank[2];        // the bucket plan's norm-partial banks (power iteration)
+  float* sums;           // the bucket plan's bank of sum partials
   int count_steady;      // norm partials per problem written by a power-iteration step
 };
-// sum(y) and the GD step mu0 m / sum(y) (mu0 > 0) of every problem.
+// ----------------------------------------------------- queue-driven solve
+// One launch runs a whole GD or power-iteration call over every problem of
+// the group: work items (problem, pass, tile) are handed out by an atomic
+// ticket in a fixed order; a tile of pass q of problem p starts once all
+// tiles of pass q - 1 of p are done (a per-problem completion count).
+constexpr int kRgMaxGroups = 64;
+
+struct RgQProblem {
+  int bucket;  // index of the problem's bucket (its descriptors start at seg_base[bucket])
+  int b;       // index in its bucket
+  int C;       // tiles per pass (m / 4096)
+  int off;     // first tile of this problem in its group's pass
+};
+
+struct RgGroup {
+  int p0, np;  // problems [p0, p0 + np) of the problem table
+  int L;       // layers (equal within a group)
+  int ipq;     // tiles per pass of the whole group (sum of C)
+};
+
+struct RgSolveArgs {
+  const RaggedSeg* segs;   // per bucket: FIRST, MID_1 .. MID_{2L-1}, fused LAST/FIRST, LAST
+  const int* seg_base;     // first descriptor of each bucket
+  const RgQProblem* prob;
+  const RgGroup* grp;
+  int ngrp;
+  int T;                   // steps of the call (>= 1)
+  float tau0;              // GD step warm-up: mu_t = mu0 (1 - exp(-(t+1)/tau0)) m / sum(y)
+  int* done;               // per problem: completed tiles (zero at launch)
+  unsigned long long* ticket;  // next work item (zero at launch)
+};
+
+// The queue-driven solve (one launch).
+cudaError_t launch_ragged_solve(const RgSolveArgs& sa, const RaggedDyn& d, int grid, int* err, cudaStream_t s);
+cudaError_t ragged_solve_occupancy(int* per_sm);
+
+// The set-up and finish kernels split every problem into kRgChunks chunks.
+constexpr int kRgChunks = 64;
+// sum(y) and the GD step mu0 m / sum(y) (mu0 > 0) of every problem (two launches).
 cudaError_t launch_ragged_prepare(const RaggedProblem* pr, int count, const float* y, float mu0, cudaStream_t s);
-// Power-iteration start: x = v0 and ||v0||^2 into bank[1] (one partial per problem).
+// Power-iteration start: x = v0 and ||v0||^2 as kRgChunks partials into bank[1].
 cudaError_t launch_ragged_start(const RaggedProblem* pr, int count, const float2* v0, float2* x, cudaStream_t s);
-// x = sqrt(sum y) v / ||v|| with ||v||^2 from bank[prev] (`first`: one partial, else count_steady).
+// x = sqrt(sum y) v / ||v|| with ||v||^2 from bank[prev] (`first`: kRgChunks
+// partials, else count_steady).
 cudaError_t launch_ragged_finish(const RaggedProblem* pr, int count, float2* x, int prev, int first, cudaStream_t s);
 
 }  // namespace sr

@@ -72,6 +72,11 @@ class Ragged:
         with torch.cuda.device(self.device):
             _lib.check(self._lib.sr_ragged_check(self._h), "sr_ragged_check")
 
+    def selftest_timeout(self):
+        """Run the queue-driven solve's failure-path probe: the next check() raises SR_ERR_TIMEOUT."""
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_ragged_selftest_timeout(self._h, _stream_handle()), "sr_ragged_selftest_timeout")
+
     def forward(self, x_cat: torch.Tensor) -> torch.Tensor:
         z = torch.empty(self.y_total, dtype=torch.complex64, device=self.device)
         with torch.cuda.device(self.device):

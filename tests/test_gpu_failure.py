@@ -38,3 +38,32 @@ def test_bounded_wait_gives_up_and_reports_timeout(sr):
     zo = O.forward(x, S.phases(3, L, m), m)
     assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 1e-5
     plan.check()
+
+
+def test_ragged_queue_wait_gives_up_and_reports_timeout(sr):
+    """The queue-driven ragged solve waits (bounded) for the tiles of the
+    previous pass of each problem; with completion counts no pass can reach,
+    every such wait gives up, the status reports SR_ERR_TIMEOUT, and the
+    next solve still matches the oracle."""
+    from paper_2409_05734_gb300._lib import SrError
+    shapes = [(3000, 2 ** 14, 2), (5000, 2 ** 15, 1)]
+    seeds = [11, 12]
+    r = sr.Ragged([s[0] for s in shapes], [s[1] for s in shapes], [s[2] for s in shapes], seeds)
+    r.check()
+    r.selftest_timeout()
+    with pytest.raises(SrError) as exc:
+        r.check()
+    assert exc.value.status == 5  # SR_ERR_TIMEOUT
+    r.check()  # the status was cleared
+    xs = [S.signal_gaussian(sd, 1, n)[0] for sd, (n, _, _) in zip(seeds, shapes)]
+    ys = [np.abs(O.forward(x, S.phases(sd, L, m), m)) ** 2 for x, sd, (n, m, L) in zip(xs, seeds, shapes)]
+    v0 = [S.start_vector(sd, 1, n)[0] for sd, (n, _, _) in zip(seeds, shapes)]
+    y_cat = torch.from_numpy(r.pack(ys, "y")).float().cuda()
+    x = r.spectral_init(y_cat, torch.from_numpy(r.pack(v0, "x")).to(torch.complex64).cuda(), 5, weight="optimal")
+    r.check()
+    xg = x.cpu().numpy()
+    for i, (n, m, L) in enumerate(shapes):
+        fwd, adj = O.structured_ops(S.phases(seeds[i], L, m), n, m)
+        ref = O.spectral_init(ys[i][None], v0[i][None], fwd, adj, 5, mode="optimal")[0]
+        got = xg[r.x_off[i]:r.x_off[i] + n]
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-4
