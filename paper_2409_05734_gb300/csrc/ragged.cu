@@ -9,6 +9,7 @@
 // stream. Everything is graph-capturable.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <new>
@@ -60,12 +61,12 @@ struct Fused {
   // GD ([0]) and the power iteration ([1]), problems in group order, groups of
   // one L whose passes hold about group_tiles tiles (their data stays in L2)
   sr::RaggedSeg* d_qsegs[2] = {nullptr, nullptr};
-  int* d_seg_base = nullptr;
-  sr::RgQProblem* d_qprob = nullptr;
+  sr::RgTileRec* d_rec = nullptr;
   sr::RgGroup* d_grp = nullptr;
   int ngrp = 0;
   int* d_done = nullptr;
-  unsigned long long* d_ticket = nullptr;
+  unsigned* d_ticket = nullptr;
+  int max_iters = 0;  // longest call of one launch (tickets < 2^31)
   int qgrid = 0;
   int group_tiles = 1024;
 };
@@ -257,8 +258,7 @@ sr::RaggedSeg make_seg(const Bucket& bk, int kind, int k, int spec, int* err) {
 
 void free_fused(Fused& f) {
   for (int k = 0; k < 2; ++k) cudaFree(f.d_qsegs[k]);
-  cudaFree(f.d_seg_base);
-  cudaFree(f.d_qprob);
+  cudaFree(f.d_rec);
   cudaFree(f.d_grp);
   cudaFree(f.d_done);
   cudaFree(f.d_ticket);
@@ -268,10 +268,18 @@ void free_fused(Fused& f) {
   f = Fused();
 }
 
+// Line-length class and TMA staging of layout `lay` of a bucket's ragged
+// tiles, packed as in RgTileRec::lay.
+int lay_code(const sr::Plan& p, sr::Layout lay) {
+  const int ell = p.geom[lay].ell;
+  const int tma = ell <= 512 && p.geom[lay].T == 4096 / ell;
+  return sr::ragged_class(ell) | (tma << 4);
+}
+
 // The queue-driven solve's tables: every fused bucket's descriptors in pass
 // order, and the problems in groups of one L of about f.group_tiles tiles per
 // pass (a group's exchange buffers, phases and measurements then fit in L2
-// while its passes run).
+// while its passes run), as one record per tile slot of a group's pass.
 sr_status build_queue(sr_ragged* r) {
   Fused& f = r->fz;
   std::vector<sr::RaggedSeg> segs[2];
@@ -286,52 +294,72 @@ sr_status build_queue(sr_ragged* r) {
       segs[spec].push_back(make_seg(bk, sr::kRgLast, 0, spec, f.d_err));
     }
   }
-  // problems by L (a group has one L), buckets kept together
+  // problems by L (a group has one L), buckets kept together; the group size
+  // grows until the groups fit the kernel's table
   std::vector<int> order(f.buckets.begin(), f.buckets.end());
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return r->buckets[a].L < r->buckets[b].L; });
-  std::vector<sr::RgQProblem> prob;
+  std::vector<sr::RgTileRec> rec;
   std::vector<sr::RgGroup> grp;
-  for (int bi : order) {
-    const Bucket& bk = r->buckets[bi];
-    const int C = (int)(bk.m / 4096);
-    for (int j = 0; j < (int)bk.members.size(); ++j) {
-      if (grp.empty() || grp.back().L != bk.L || grp.back().ipq + C > f.group_tiles) {
-        if ((int)grp.size() == sr::kRgMaxGroups) return rfail(SR_ERR_UNSUPPORTED, "too many problem groups");
-        sr::RgGroup g;
-        g.p0 = (int)prob.size();
-        g.np = 0;
-        g.L = bk.L;
-        g.ipq = 0;
-        grp.push_back(g);
+  for (;;) {
+    rec.clear();
+    grp.clear();
+    int gL = -1, p = 0;
+    for (int bi : order) {
+      const Bucket& bk = r->buckets[bi];
+      const sr::Plan& pl = *reinterpret_cast<const sr::Plan*>(bk.plan);
+      const int C = (int)(bk.m / 4096);
+      int lgm = 0;
+      while ((1ll << lgm) < bk.m) ++lgm;
+      const int lay = lay_code(pl, sr::kLayoutX) | (lay_code(pl, sr::kLayoutY) << 8);
+      for (int j = 0; j < (int)bk.members.size(); ++j, ++p) {
+        if (grp.empty() || gL != bk.L || grp.back().ipq + C > f.group_tiles) {
+          sr::RgGroup g;
+          g.ipq = 0;
+          g.rec0 = (int)rec.size();
+          grp.push_back(g);
+          gL = bk.L;
+        }
+        for (int c = 0; c < C; ++c) {
+          sr::RgTileRec q;
+          q.p = p;
+          q.b = j;
+          q.tile = c;
+          q.C = C;
+          q.si0 = base[bi];
+          q.L = bk.L;
+          q.lgm = lgm;
+          q.lay = lay;
+          rec.push_back(q);
+        }
+        grp.back().ipq += C;
       }
-      sr::RgQProblem q;
-      q.bucket = bi;
-      q.b = j;
-      q.C = C;
-      q.off = grp.back().ipq;
-      grp.back().ipq += C;
-      grp.back().np += 1;
-      prob.push_back(q);
     }
+    if ((int)grp.size() <= sr::kRgMaxGroups) break;
+    f.group_tiles *= 2;
   }
+  // tickets of the longest call the tables can deal in one launch (< 2^31)
+  int64_t per_step = 0, first = 0;
+  for (size_t g = 0; g < grp.size(); ++g) {
+    const int L = rec[grp[g].rec0].L;
+    per_step += 2 * L * (int64_t)grp[g].ipq;
+    first += grp[g].ipq;
+  }
+  f.max_iters = (int)std::min<int64_t>(INT32_MAX, ((int64_t)INT32_MAX - first) / std::max<int64_t>(1, per_step));
   f.ngrp = (int)grp.size();
   for (int k = 0; k < 2; ++k) {
     SR_RCUDA(cudaMalloc(&f.d_qsegs[k], sizeof(sr::RaggedSeg) * segs[k].size()), "cudaMalloc(queue descriptors)");
     SR_RCUDA(cudaMemcpy(f.d_qsegs[k], segs[k].data(), sizeof(sr::RaggedSeg) * segs[k].size(), cudaMemcpyHostToDevice),
              "cudaMemcpy(queue descriptors)");
   }
-  SR_RCUDA(cudaMalloc(&f.d_seg_base, sizeof(int) * base.size()), "cudaMalloc(queue tables)");
-  SR_RCUDA(cudaMemcpy(f.d_seg_base, base.data(), sizeof(int) * base.size(), cudaMemcpyHostToDevice),
-           "cudaMemcpy(queue tables)");
-  SR_RCUDA(cudaMalloc(&f.d_qprob, sizeof(sr::RgQProblem) * prob.size()), "cudaMalloc(queue problems)");
-  SR_RCUDA(cudaMemcpy(f.d_qprob, prob.data(), sizeof(sr::RgQProblem) * prob.size(), cudaMemcpyHostToDevice),
-           "cudaMemcpy(queue problems)");
+  SR_RCUDA(cudaMalloc(&f.d_rec, sizeof(sr::RgTileRec) * rec.size()), "cudaMalloc(queue records)");
+  SR_RCUDA(cudaMemcpy(f.d_rec, rec.data(), sizeof(sr::RgTileRec) * rec.size(), cudaMemcpyHostToDevice),
+           "cudaMemcpy(queue records)");
   SR_RCUDA(cudaMalloc(&f.d_grp, sizeof(sr::RgGroup) * grp.size()), "cudaMalloc(queue groups)");
   SR_RCUDA(cudaMemcpy(f.d_grp, grp.data(), sizeof(sr::RgGroup) * grp.size(), cudaMemcpyHostToDevice),
            "cudaMemcpy(queue groups)");
-  SR_RCUDA(cudaMalloc(&f.d_done, sizeof(int) * prob.size()), "cudaMalloc(completion counts)");
-  SR_RCUDA(cudaMalloc(&f.d_ticket, sizeof(unsigned long long)), "cudaMalloc(ticket)");
+  SR_RCUDA(cudaMalloc(&f.d_done, sizeof(int) * f.count), "cudaMalloc(completion counts)");
+  SR_RCUDA(cudaMalloc(&f.d_ticket, sizeof(unsigned)), "cudaMalloc(ticket)");
   int occ = 1;
   SR_RCUDA(sr::ragged_solve_occupancy(&occ), "ragged solve occupancy");
   f.qgrid = occ * f.num_sms;
@@ -342,13 +370,13 @@ sr_status build_queue(sr_ragged* r) {
 // iteration: spec = 1) of every problem of the group, after the completion
 // counts and the ticket are cleared.
 sr_status fused_queue(const Fused& f, int spec, int iters, float tau0, const sr::RaggedDyn& d, cudaStream_t s) {
+  if (iters > f.max_iters) return rfail(SR_ERR_UNSUPPORTED, "too many steps for one call of this ragged batch");
   SR_RCUDA(cudaMemsetAsync(f.d_done, 0, sizeof(int) * f.count, s), "cudaMemsetAsync(completion counts)");
-  SR_RCUDA(cudaMemsetAsync(f.d_ticket, 0, sizeof(unsigned long long), s), "cudaMemsetAsync(ticket)");
+  SR_RCUDA(cudaMemsetAsync(f.d_ticket, 0, sizeof(unsigned), s), "cudaMemsetAsync(ticket)");
   sr::RgSolveArgs sa;
   std::memset(&sa, 0, sizeof(sa));
   sa.segs = f.d_qsegs[spec];
-  sa.seg_base = f.d_seg_base;
-  sa.prob = f.d_qprob;
+  sa.rec = f.d_rec;
   sa.grp = f.d_grp;
   sa.ngrp = f.ngrp;
   sa.T = iters;
@@ -409,13 +437,8 @@ sr_status build_fused(sr_ragged* r) {
   return build_queue(r);
 }
 
-
-float ramp_of(int t, float tau0) {
-  return tau0 > 0.f ? (float)(1.0 - std::exp(-(double)(t + 1) / (double)tau0)) : 1.0f;
-}
-
-// `iters` GD steps on every problem of the group (Sec. II-B-1): one launch per
-// pass index of a step across all of the group's problems.
+// `iters` GD steps on every problem of the group (Sec. II-B-1): one
+// queue-driven launch after the per-problem set-up.
 sr_status fused_gd(sr_ragged* r, const float* y, float2* x, int iters, float mu0, float tau0, float* loss_scratch,
                    cudaStream_t s) {
   const Fused& f = r->fz;
@@ -679,13 +702,12 @@ sr_status sr_ragged_selftest_timeout(sr_ragged* r, void* stream) {
   // ever sees its inputs complete: each such wait gives up after the
   // library's limit, records SR_ERR_TIMEOUT and its CTA returns
   if (e == cudaSuccess) e = cudaMemsetAsync(f.d_done, 0x80, sizeof(int) * f.count, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(f.d_ticket, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f.d_ticket, 0, sizeof(unsigned), s);
   if (e == cudaSuccess) {
     sr::RgSolveArgs sa;
     std::memset(&sa, 0, sizeof(sa));
     sa.segs = f.d_qsegs[0];
-    sa.seg_base = f.d_seg_base;
-    sa.prob = f.d_qprob;
+    sa.rec = f.d_rec;
     sa.grp = f.d_grp;
     sa.ngrp = f.ngrp;
     sa.T = 1;

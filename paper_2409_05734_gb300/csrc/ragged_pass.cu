@@ -40,14 +40,14 @@ constexpr int kRgThreads = 256;
 
 // Byte layout of the dynamic shared memory (relative to a 1024-byte-aligned
 // base): TMA staging (32 KB), FFT scratch (the padded layout of 4096 values),
-// row twiddles (16 x up to 32 lines), two copies of the segment arguments,
-// the barrier.
+// row twiddles (16 x up to 32 lines), the descriptors of the current and the
+// next item, the barrier.
 struct RgSmem {
   static constexpr size_t stage = 0;
   static constexpr size_t scratch = 4096 * 8;
   static constexpr size_t rowtw = scratch + 4096 * 17 / 16 * 8;
   static constexpr size_t args = rowtw + 16 * 32 * 8;
-  static constexpr size_t bar = args + 2 * sizeof(PassArgs);
+  static constexpr size_t bar = args + 2 * sizeof(RaggedSeg);
   static constexpr size_t total = bar + 16;
 };
 
@@ -77,7 +77,7 @@ __device__ __forceinline__ void rg_patch(PassArgs& a, const RaggedSeg& sg, const
 // A decoded work item: tile `tile` of pass q of problem p, at step t.
 struct RgItem {
   int valid;
-  int ready;    // inputs known to be complete (a further tile of the previous item's pass)
+  int ready;    // inputs known to be complete (the first pass needs none)
   int p, q, tile, t;
   int b;        // the problem's index in its bucket
   int si;       // descriptor
@@ -85,8 +85,7 @@ struct RgItem {
   int variant;
   int tma;
   int row;      // first exchange-buffer row of the tile (staged tiles)
-  int ell, C, T;  // line length; tiles per pass of the problem; lines per tile
-  unsigned long long ticket;
+  int ell, T;   // line length; lines per tile
 };
 
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
@@ -101,50 +100,71 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-__device__ RgItem rg_decode(const RgSolveArgs& sa, const unsigned long long* gstart, unsigned long long tk) {
-  RgItem it;
+// 16-byte asynchronous copy global -> shared (cp.async, L2 only).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Shared tables of the queue: the first ticket of every group (and the total
+// after the last), its tiles per pass and its first record.
+struct RgQTables {
+  unsigned gstart[kRgMaxGroups + 1];
+  int ipq[kRgMaxGroups];
+  int rec0[kRgMaxGroups];
+};
+
+// Decodes ticket tk: the group by binary search in shared memory, pass and tile
+// slot by division, then one 32-byte record load; the pass kind, layout, line
+// length and descriptor follow from the record and the pass index.
+__device__ __forceinline__ void rg_decode(RgItem& it, const RgSolveArgs& sa, const RgQTables& tb, unsigned tk) {
   it.valid = 0;
-  if (tk >= gstart[sa.ngrp]) return it;
-  int g = 0;
-  while (tk >= gstart[g + 1]) ++g;
-  const RgGroup G = sa.grp[g];
-  const unsigned long long within = tk - gstart[g];
-  const int q = (int)(within / (unsigned long long)G.ipq);
-  const int r = (int)(within - (unsigned long long)q * G.ipq);
-  int lo = G.p0, hi = G.p0 + G.np - 1;  // the problem whose tiles of this pass hold r
+  if (tk >= tb.gstart[sa.ngrp]) return;
+  int lo = 0, hi = sa.ngrp - 1;  // the group g with gstart[g] <= tk < gstart[g + 1]
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (sa.prob[mid].off <= r) lo = mid;
+    if (tb.gstart[mid] <= tk) lo = mid;
     else hi = mid - 1;
   }
-  const RgQProblem P = sa.prob[lo];
-  it.p = lo;
-  it.q = q;
-  it.tile = r - P.off;
+  const unsigned within = tk - tb.gstart[lo];
+  const int ipq = tb.ipq[lo];
+  const int q = (int)(within / (unsigned)ipq), r = (int)within - q * ipq;
+  const RgTileRec R = sa.rec[tb.rec0[lo] + r];
   // pass sequence of a problem: FIRST; then per step MID_1 .. MID_{2L-1} and
   // the fused LAST/FIRST (LAST after the final step)
+  const int per = 2 * R.L;
   int kidx = 0, t = 0;
   if (q > 0) {
-    const int per = 2 * G.L, qq = q - 1;
-    t = qq / per;
-    const int k = qq - t * per + 1;
+    t = (q - 1) / per;
+    const int k = q - t * per;
     kidx = k < per ? k : (t + 1 < sa.T ? per : per + 1);
   }
+  int kind;
+  if (kidx == 0) kind = kRgFirst;
+  else if (kidx < R.L) kind = kRgMidFF;
+  else if (kidx == R.L) kind = kRgMidFI;
+  else if (kidx < per) kind = kRgMidII;
+  else kind = kidx == per ? kRgLF : kRgLast;
+  // layouts: FIRST, LAST and the fused pass work on layout X; MID k on Y for
+  // odd k, X for even k
+  const int lay_y = (kidx > 0 && kidx < per && (kidx & 1)) ? 1 : 0;
+  const int code = (R.lay >> (8 * lay_y)) & 0xff;
+  const int cls = code & 15;
+  it.p = R.p;
+  it.q = q;
+  it.tile = R.tile;
   it.t = t;
-  it.b = P.b;
-  it.si = sa.seg_base[P.bucket] + kidx;
-  it.need = q * P.C;
-  const RaggedSeg& sg = sa.segs[it.si];
-  it.variant = sg.variant;
-  it.tma = sg.tma && sg.kind != kRgFirst;
-  it.row = P.b * sg.a.nl + it.tile * sg.a.T;
-  it.ell = sg.a.ell;
-  it.C = P.C;
-  it.T = sg.a.T;
-  it.ticket = tk;
+  it.b = R.b;
+  it.si = R.si0 + kidx;
+  it.need = q * R.C;
+  it.variant = kind * 4 + cls;
+  it.tma = kind != kRgFirst && (code >> 4);
+  it.ell = 128 << cls;
+  it.T = 32 >> cls;
+  it.row = R.b * (1 << (R.lgm - 7 - cls)) + R.tile * it.T;
   it.ready = q == 0;
   it.valid = 1;
-  return it;
 }
 
 // Thread 0: waits (bounded) until problem p has `need` completed tiles.
@@ -160,39 +180,18 @@ __device__ __forceinline__ bool rg_wait_done(const int* done, int p, int need) {
 
 struct RgQCtx {
   const RgSolveArgs* sa;
-  const unsigned long long* gstart;
   unsigned char* smem;
   float2* scratch;
   float2* rowtw;
   const float2* tw;
   uint32_t bar, stage;
   int waits;
-  RgItem* items;     // shared: [2] the current and the next item
+  RgItem* items;     // shared: [2] the current and the next item (slot = item count & 1)
   int* issued;       // shared: [2] whether the item's TMA load is in flight
+  RaggedSeg* args;   // shared: [2] the items' descriptors, patched for their step
   int cur;
   int* err;
 };
-
-// Thread 0: takes the next ticket and decodes it into items[slot]; the item
-// in the other slot is the one taken before it. Consecutive tickets of one
-// problem's pass are decoded from their predecessor without a table lookup.
-// Called between items, when no tile values are live in registers.
-__device__ __noinline__ void rg_take(RgQCtx& cx, int slot) {
-  const unsigned long long tk = atomicAdd(cx.sa->ticket, 1ull);
-  const RgItem& pv = cx.items[slot ^ 1];
-  RgItem nx;
-  if (pv.valid && tk == pv.ticket + 1 && pv.tile + 1 < pv.C) {
-    nx = pv;
-    nx.ticket = tk;
-    nx.tile += 1;
-    nx.row += pv.T;
-    nx.ready = 1;
-  } else {
-    nx = rg_decode(*cx.sa, cx.gstart, tk);
-  }
-  cx.items[slot] = nx;
-  cx.issued[slot] = 0;
-}
 
 // Thread 0: issues the TMA load of items[slot] when it is a staged tile whose
 // inputs are complete (the caller has freed the staging buffer).
@@ -206,32 +205,37 @@ __device__ __forceinline__ void rg_issue(RgQCtx& cx, int slot) {
   cx.issued[slot] = 1;
 }
 
-// The pass arguments of an item at step t: its descriptor with the call's
-// pointers, the step's warm-up factor and loss row, and the power
-// iteration's banks filled in.
-__device__ __forceinline__ void rg_load_args_q(PassArgs* dst, const RaggedSeg& sg, const RaggedDyn& d, int t,
-                                               float tau0) {
-  if (threadIdx.x >= 32) return;
-  const uint4* src = reinterpret_cast<const uint4*>(&sg.a);
-  uint4* out = reinterpret_cast<uint4*>(dst);
-  for (int i = threadIdx.x; i < (int)(sizeof(PassArgs) / 16); i += 32) out[i] = src[i];
-  __syncwarp();
-  if (threadIdx.x == 0) {
-    RaggedDyn e = d;
-    e.t = t;
-    e.mu_scale = tau0 > 0.f ? 1.0f - expf(-(float)(t + 1) / tau0) : 1.0f;
-    e.parity = t & 1;
-    e.first_step = t == 0;
-    rg_patch(*dst, sg, e);
+// Warp 0, once the current tile's input is in registers: the next item's TMA
+// load (lane 0) and the asynchronous copy of its descriptor into its argument
+// slot (patched after the current item, see rg_finish_item).
+__device__ __forceinline__ void rg_prep_next(RgQCtx& cx) {
+  const int nxt = cx.cur ^ 1;
+  if (threadIdx.x == 0) rg_issue(cx, nxt);
+  const RgItem& nx = cx.items[nxt];
+  if (nx.valid) {
+    const uint4* src = reinterpret_cast<const uint4*>(&cx.sa->segs[nx.si]);
+    uint4* dst = reinterpret_cast<uint4*>(&cx.args[nxt]);
+    constexpr int kChunks = (int)(sizeof(RaggedSeg) / 16);
+    for (int i = threadIdx.x; i < kChunks; i += 32) cp_async16(dst + i, src + i);
   }
-  __syncwarp();
+  cp_async_commit();
+}
+
+// The descriptor copy sg for step t of the call: the call's pointers, the
+// step's warm-up factor and loss row, the power iteration's banks.
+__device__ __forceinline__ void rg_patch_step(RaggedSeg& sg, const RaggedDyn& d, int t, float tau0) {
+  RaggedDyn e = d;
+  e.t = t;
+  e.mu_scale = tau0 > 0.f ? 1.0f - expf(-(float)(t + 1) / tau0) : 1.0f;
+  e.parity = t & 1;
+  e.first_step = t == 0;
+  rg_patch(sg.a, sg, e);
 }
 
 // One item of a pipelined pass kind (MID, fused LAST/FIRST, LAST) with lines
 // of ELL points: its input lines into registers (from the staging buffer, or
-// straight from the exchange buffer for unstaged tiles), the refill of the
-// staging buffer with the next item, then the body. False when a wait gave up
-// (recorded in err).
+// straight from the exchange buffer for unstaged tiles), the next item's
+// prefetch, then the body. False when a wait gave up (recorded in err).
 template <int ELL, int KIND>
 __device__ __noinline__ bool rg_qtile(RgQCtx& cx, const PassArgs& a, const RgItem& it, TileScalars& sh) {
   constexpr int T = 4096 / ELL;
@@ -263,16 +267,16 @@ __device__ __noinline__ bool rg_qtile(RgQCtx& cx, const PassArgs& a, const RgIte
       return false;
     }
     load_staged<TL>(cx.smem + RgSmem::stage, t, p, v);
-    __syncthreads();  // slots in registers (staging free); the item's arguments visible
-    if (threadIdx.x == 0) rg_issue(cx, cx.cur ^ 1);
+    __syncthreads();  // slots in registers (staging free)
+    if (threadIdx.x < 32) rg_prep_next(cx);
   } else {
     bool ok = true;
     if (threadIdx.x == 0) {
       ok = rg_wait_done(cx.sa->done, it.p, it.need);
       if (!ok) atomicExch(cx.err, (int)SR_ERR_TIMEOUT);
-      else rg_issue(cx, cx.cur ^ 1);
     }
     if (!__syncthreads_and(ok)) return false;
+    if (threadIdx.x < 32) rg_prep_next(cx);
     const float2* src = a.ein + (size_t)b * a.m + (size_t)(g0 + t) * ELL;
 #pragma unroll
     for (int j = 0; j < TL::E; ++j) v[j] = src[p + j * TL::P];
@@ -293,8 +297,8 @@ __device__ __noinline__ bool rg_qfirst(RgQCtx& cx, const PassArgs& a, const RgIt
   int t, p;
   thread_coords<TL>(t, p);
   const int b = it.b, g0 = it.tile * T;
-  if (threadIdx.x == 0) rg_issue(cx, cx.cur ^ 1);
   __syncthreads();  // the item's arguments visible
+  if (threadIdx.x < 32) rg_prep_next(cx);
   first_tile<TL, -1, 0, 1024 / ELL>(a, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
   return true;
 }
@@ -314,30 +318,52 @@ __device__ __forceinline__ bool rg_qitem(RgQCtx& cx, const PassArgs& a, const Rg
   }
 }
 
+// Warp 0 after an item's closing barrier: the item's completion is released
+// (thread 0), the next item's descriptor copy is awaited and patched for its
+// step, the prefetched ticket is decoded into the finished item's slot (the
+// item after the next) and a new ticket is requested, whose value is needed
+// only after the next item.
+__device__ __forceinline__ void rg_finish_item(RgQCtx& cx, const RgSolveArgs& sa, const RaggedDyn& dyn,
+                                               const RgQTables& tb, unsigned& tk_pf) {
+  cp_async_wait_all();
+  __syncwarp();
+  if (threadIdx.x == 0) {
+    const int cur = cx.cur, nxt = cur ^ 1;
+    fence_proxy_async_global();
+    __threadfence();
+    atomicAdd(sa.done + cx.items[cur].p, 1);
+    if (cx.items[nxt].valid) rg_patch_step(cx.args[nxt], dyn, cx.items[nxt].t, sa.tau0);
+    rg_decode(cx.items[cur], sa, tb, tk_pf);
+    cx.issued[cur] = 0;
+    tk_pf = atomicAdd(sa.ticket, 1u);
+  }
+}
+
 __global__ void __launch_bounds__(kRgThreads, 3)
     k_ragged_solve(const __grid_constant__ RgSolveArgs sa, const __grid_constant__ RaggedDyn dyn, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ TileScalars sh;
-  __shared__ unsigned long long gstart[kRgMaxGroups + 1];
+  __shared__ RgQTables tb;
   __shared__ RgItem items[2];
   __shared__ int issued[2];
   unsigned char* smem = aligned_smem(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) {
-    items[0].valid = items[1].valid = 0;
-    unsigned long long acc = 0;
+    unsigned acc = 0;
     for (int g = 0; g < sa.ngrp; ++g) {
-      gstart[g] = acc;
       const RgGroup G = sa.grp[g];
-      acc += (unsigned long long)(1 + 2 * G.L * sa.T) * (unsigned long long)G.ipq;
+      const int L = sa.rec[G.rec0].L;
+      tb.gstart[g] = acc;
+      tb.ipq[g] = G.ipq;
+      tb.rec0[g] = G.rec0;
+      acc += (unsigned)(1 + 2 * L * sa.T) * (unsigned)G.ipq;
     }
-    gstart[sa.ngrp] = acc;
+    tb.gstart[sa.ngrp] = acc;
   }
   // an earlier pass gave up (see mbar_wait_bounded): do nothing
   if (__syncthreads_or(tid == 0 && *(volatile int*)err != 0)) return;
   RgQCtx cx;
   cx.sa = &sa;
-  cx.gstart = gstart;
   cx.smem = smem;
   cx.scratch = reinterpret_cast<float2*>(smem + RgSmem::scratch);
   cx.rowtw = reinterpret_cast<float2*>(smem + RgSmem::rowtw);
@@ -347,30 +373,36 @@ __global__ void __launch_bounds__(kRgThreads, 3)
   cx.waits = 0;
   cx.items = items;
   cx.issued = issued;
+  cx.args = reinterpret_cast<RaggedSeg*>(smem + RgSmem::args);
   cx.cur = 0;
   cx.err = err;
-  PassArgs* args = reinterpret_cast<PassArgs*>(smem + RgSmem::args);
+  // the first two items, the first one's descriptor and TMA load, and a
+  // ticket in flight for the third
+  unsigned tk_pf = 0;
   if (tid == 0) {
     mbar_init(cx.bar, 1);
     mbar_init_fence();
-    rg_take(cx, 0);
-    rg_issue(cx, 0);
-    rg_take(cx, 1);
+    rg_decode(items[0], sa, tb, atomicAdd(sa.ticket, 1u));
+    rg_decode(items[1], sa, tb, atomicAdd(sa.ticket, 1u));
+    issued[0] = issued[1] = 0;
+    tk_pf = atomicAdd(sa.ticket, 1u);
   }
   __syncthreads();
-  int slot = 1, cur_si = -1, cur_t = -1;
-  for (;;) {
-    const RgItem it = items[cx.cur];
-    if (!it.valid) break;
-    if (it.si != cur_si || it.t != cur_t) {
-      // the other copy's last reader finished before the previous item's
-      // closing barrier; the item's first barrier publishes this one
-      slot ^= 1;
-      cur_si = it.si;
-      cur_t = it.t;
-      rg_load_args_q(&args[slot], sa.segs[it.si], dyn, it.t, sa.tau0);
+  if (tid < 32 && items[0].valid) {
+    const uint4* src = reinterpret_cast<const uint4*>(&sa.segs[items[0].si]);
+    uint4* dst = reinterpret_cast<uint4*>(&cx.args[0]);
+    for (int i = tid; i < (int)(sizeof(RaggedSeg) / 16); i += 32) dst[i] = src[i];
+    __syncwarp();
+    if (tid == 0) {
+      rg_patch_step(cx.args[0], dyn, items[0].t, sa.tau0);
+      rg_issue(cx, 0);
     }
-    const PassArgs& a = args[slot];
+  }
+  __syncthreads();
+  for (;;) {
+    const RgItem& it = items[cx.cur];
+    if (!it.valid) break;
+    const PassArgs& a = cx.args[cx.cur].a;
     bool ok = true;
     switch (it.variant & 3) {
       case 0: ok = rg_qitem<128>(cx, a, it, sh); break;
@@ -378,16 +410,15 @@ __global__ void __launch_bounds__(kRgThreads, 3)
       case 2: ok = rg_qitem<512>(cx, a, it, sh); break;
       default: ok = rg_qitem<1024>(cx, a, it, sh); break;
     }
-    if (!ok) return;
-    __syncthreads();  // every store of the tile issued; every thread has read the item
-    if (tid == 0) {
-      fence_proxy_async_global();
-      __threadfence();
-      atomicAdd(sa.done + it.p, 1);
-      rg_take(cx, cx.cur);  // the item after the next, into the slot just finished
+    if (!ok) {
+      if (tid < 32) cp_async_wait_all();  // no copy into shared memory outlives the CTA
+      return;
     }
+    __syncthreads();  // every store of the tile issued; every thread is done with the item
+    if (tid < 32) rg_finish_item(cx, sa, dyn, tb, tk_pf);
     cx.cur ^= 1;
   }
+  if (tid < 32) cp_async_wait_all();
 }
 
 // ------------------------------------------------ per-problem set-up / finish

@@ -76,29 +76,33 @@ struct RaggedProblem {
 // tiles of pass q - 1 of p are done (a per-problem completion count).
 constexpr int kRgMaxGroups = 64;
 
-struct RgQProblem {
-  int bucket;  // index of the problem's bucket (its descriptors start at seg_base[bucket])
-  int b;       // index in its bucket
-  int C;       // tiles per pass (m / 4096)
-  int off;     // first tile of this problem in its group's pass
+// One tile slot of a group's pass: everything a ticket decodes to, in one
+// 32-byte record (one load).
+struct alignas(32) RgTileRec {
+  int p;        // problem index (completion counts)
+  int b;        // index in its bucket
+  int tile;     // tile within the pass
+  int C;        // tiles per pass of the problem (m / 4096)
+  int si0;      // the bucket's first descriptor (FIRST); pass k is si0 + k
+  int L;        // layers
+  int lgm;      // log2 m
+  int lay;      // per layout (X: bits 0-7, Y: bits 8-15): line-length class | staged-by-TMA << 4
 };
 
 struct RgGroup {
-  int p0, np;  // problems [p0, p0 + np) of the problem table
-  int L;       // layers (equal within a group)
-  int ipq;     // tiles per pass of the whole group (sum of C)
+  int ipq;      // tiles per pass of the whole group
+  int rec0;     // the group's first record
 };
 
 struct RgSolveArgs {
   const RaggedSeg* segs;   // per bucket: FIRST, MID_1 .. MID_{2L-1}, fused LAST/FIRST, LAST
-  const int* seg_base;     // first descriptor of each bucket
-  const RgQProblem* prob;
+  const RgTileRec* rec;    // per group: ipq records, problem-major
   const RgGroup* grp;
   int ngrp;
   int T;                   // steps of the call (>= 1)
   float tau0;              // GD step warm-up: mu_t = mu0 (1 - exp(-(t+1)/tau0)) m / sum(y)
   int* done;               // per problem: completed tiles (zero at launch)
-  unsigned long long* ticket;  // next work item (zero at launch)
+  unsigned* ticket;        // next work item (zero at launch); a launch deals < 2^31 tickets
 };
 
 // The queue-driven solve (one launch).
