@@ -43,8 +43,8 @@ FLUSH_BYTES = 512 << 20  # > 129 MB L2: written between timed steps
 # in {2, 4, 8}, L in {1, 2, 3}, own phase seeds, Poisson measurements at a mean
 # of 100 photons per measurement; one autotuned ragged handle, the solve
 # replayed as a CUDA graph with one branch per shape bucket.
-RAGGED = dict(count=256, k_lo=10, k_hi=16, alphas=(2, 4, 8), Ls=(1, 2, 3), photons=100.0, spectral_iters=50,
-              gd_iters=200, mu0=0.1, tau0=50.0, seed=20240905, parity_sp=10, parity_gd=20)
+RAGGED = dict(count=256, k_lo=10, k_hi=16, alphas=(2, 4, 8), Ls=(1, 2, 3), photons=100.0, spectral_iters=100,
+              gd_iters=500, mu0=0.15, tau0=100.0, seed=20240905, parity_sp=10, parity_gd=20)
 # Structured (L = 2) against dense i.i.d. at equal recovery error (Sec. IV): both
 # models solve the same B signals from their own noiseless y with the same
 # spectral initialisation and step rule; each runs the fewest GD iterations (a
@@ -988,7 +988,8 @@ def ragged_workload(torch, dev, flush, reps: int = 3):
     return {"_parity_inputs": parity_inputs,
             "workload": f"{count} problems: n = 2^k, k ~ U{{{R['k_lo']}..{R['k_hi']}}}, alpha ~ U{list(R['alphas'])}, "
                         f"L ~ U{list(R['Ls'])}, own phases; Poisson y at {R['photons']:.0f} photons/measurement; "
-                        f"{R['spectral_iters']} power + {R['gd_iters']} GD iterations; autotuned; CUDA graph",
+                        f"{R['spectral_iters']} power (optimal weight, lambda = -1) + {R['gd_iters']} GD iterations "
+                        f"(mu0 = {R['mu0']}, tau0 = {R['tau0']:.0f}); autotuned; CUDA graph",
             "buckets": rg.buckets, "total_m": int(m.sum()), "ms_per_solve": ms,
             "problem_iters_per_s": count * iters / (ms / 1e3),
             "algorithmic_gbs": nbytes * iters / (ms / 1e3) / 1e9, "gpu_launches_per_solve": int(launches),

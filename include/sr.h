@@ -68,6 +68,8 @@ typedef enum sr_weight_mode {
                              y_hat <= 0; shift -2*lambda (Eq. 4) */
 } sr_weight_mode;
 
+/* Passing NULL for the options selects SR_WEIGHT_OPTIMAL with lambda = -1:
+ * Sec. IV runs its spectral methods with the optimal preprocessing function. */
 typedef struct sr_spectral_opts {
   int weight_mode; /* sr_weight_mode */
   float lambda;    /* lower threshold, < 0, used by SR_WEIGHT_OPTIMAL */
@@ -184,7 +186,7 @@ sr_status sr_loss_grad(sr_plan* plan, const void* x, const float* y, float* loss
  * weight, -2*lambda for the optimal weight): v <- v0/||v0||, then `iters`
  * times u = M v + s v, v = u/||u||; finally x_out = sqrt(sum(y)) * v.
  * y: float[B][m]; v0: c64[B][n] start vectors (random draws are inputs);
- * x_out: c64[B][n]; x_out may equal v0. opts may be NULL (identity weight). */
+ * x_out: c64[B][n]; x_out may equal v0. opts may be NULL (optimal weight, lambda = -1). */
 sr_status sr_spectral_init(sr_plan* plan, const float* y, const void* v0, int iters,
                            const sr_spectral_opts* opts, void* x_out, int B, void* stream);
 

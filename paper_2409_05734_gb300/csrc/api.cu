@@ -865,7 +865,7 @@ struct SpectralRun {
   int done = 0;  // steps run so far
   bool window = false, fuse = false, small = false;
   const float* ye = nullptr;
-  sr_spectral_opts o{SR_WEIGHT_IDENTITY, -1.0f};
+  sr_spectral_opts o{SR_WEIGHT_OPTIMAL, -1.0f};
   Chain c, f, a;
 
   sr_status setup(sr_plan* plan, const float* y, const void* v0, const sr_spectral_opts* opts, void* x_out, int nb,

@@ -712,7 +712,7 @@ sr_status sr_dense_spectral_init(sr_dense* d, const float* y, const void* v0, in
   if (st != SR_OK) return st;
   if (!y || !v0 || !x_out) return dfail(SR_ERR_INVALID_ARG, "NULL array argument");
   if (iters < 0) return dfail(SR_ERR_INVALID_ARG, "iters must be >= 0");
-  sr_spectral_opts o{SR_WEIGHT_IDENTITY, -1.0f};
+  sr_spectral_opts o{SR_WEIGHT_OPTIMAL, -1.0f};
   if (opts) o = *opts;
   if (o.weight_mode != SR_WEIGHT_IDENTITY && o.weight_mode != SR_WEIGHT_OPTIMAL)
     return dfail(SR_ERR_INVALID_ARG, "unknown weight_mode");

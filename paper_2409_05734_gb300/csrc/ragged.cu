@@ -636,7 +636,7 @@ sr_status sr_ragged_spectral_init(sr_ragged* r, const float* y_cat, const void* 
   if (st != SR_OK) return st;
   if (!y_cat || !v0_cat || !x_cat) return rfail(SR_ERR_INVALID_ARG, "NULL array argument");
   if (iters < 0) return rfail(SR_ERR_INVALID_ARG, "iters must be >= 0");
-  sr_spectral_opts o{SR_WEIGHT_IDENTITY, -1.0f};
+  sr_spectral_opts o{SR_WEIGHT_OPTIMAL, -1.0f};
   if (opts) o = *opts;
   if (o.weight_mode != SR_WEIGHT_IDENTITY && o.weight_mode != SR_WEIGHT_OPTIMAL)
     return rfail(SR_ERR_INVALID_ARG, "unknown weight_mode");

@@ -62,7 +62,7 @@ class DenseModel:
                        "sr_dense_adjoint")
         return x
 
-    def spectral_init(self, y: torch.Tensor, v0: torch.Tensor, iters: int, weight: str = "identity",
+    def spectral_init(self, y: torch.Tensor, v0: torch.Tensor, iters: int, weight: str = "optimal",
                       lam: float = -1.0, out: torch.Tensor | None = None) -> torch.Tensor:
         """Power iteration on M = A^H diag(T(y_hat)) A from v0 (Eq. 3-4); returns sqrt(sum y) v."""
         B = v0.shape[0]

@@ -184,7 +184,7 @@ class Plan:
                        "sr_loss_grad")
         return loss, grad
 
-    def spectral_init(self, y: torch.Tensor, v0: torch.Tensor, iters: int, weight: str = "identity",
+    def spectral_init(self, y: torch.Tensor, v0: torch.Tensor, iters: int, weight: str = "optimal",
                       lam: float = -1.0, out: torch.Tensor | None = None) -> torch.Tensor:
         """Power iteration on M = A^H diag(T(y_hat)) A from v0 (Eq. 3-4); returns sqrt(sum y) v."""
         y = self._f32(y, self.m, "y")
@@ -199,7 +199,7 @@ class Plan:
         return x
 
     def spectral_init_early_stop(self, y: torch.Tensor, v0: torch.Tensor, max_iters: int, rel_tol: float,
-                                 check_every: int = 50, weight: str = "identity", lam: float = -1.0,
+                                 check_every: int = 50, weight: str = "optimal", lam: float = -1.0,
                                  out: torch.Tensor | None = None):
         """Power iteration with early stopping: every check_every steps, stop once
         every problem's eigenvalue estimate ||M v + s v|| changed by <= rel_tol

@@ -83,7 +83,7 @@ class Ragged:
             _lib.check(self._lib.sr_ragged_forward(self._h, _p(x_cat), _p(z), _stream_handle()), "sr_ragged_forward")
         return z
 
-    def spectral_init(self, y_cat: torch.Tensor, v0_cat: torch.Tensor, iters: int, weight: str = "identity",
+    def spectral_init(self, y_cat: torch.Tensor, v0_cat: torch.Tensor, iters: int, weight: str = "optimal",
                       lam: float = -1.0, out: torch.Tensor | None = None) -> torch.Tensor:
         mode = {"identity": _lib.SR_WEIGHT_IDENTITY, "optimal": _lib.SR_WEIGHT_OPTIMAL}[weight]
         opts = _lib.SpectralOpts(mode, float(lam))
