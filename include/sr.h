@@ -143,13 +143,29 @@ sr_status sr_plan_info(const sr_plan* plan, int64_t* n, int64_t* m, int* L);
 /* Grows the workspace to hold B problems (synchronous cudaMalloc). */
 sr_status sr_plan_reserve(sr_plan* plan, int B);
 
-/* Autotunes the persistent grid of the middle and last pass kernels for
- * batches of B problems: times a few GD steps (on scratch data) for every
- * count of co-resident CTAs per SM from the kernels' occupancy down to 1 and
- * keeps the fastest for later calls. Synchronises the stream; allocates and
- * frees scratch (not capturable). The paper has no counterpart (a launch
- * parameter of this implementation). */
+/* Autotunes the plan for batches of B problems: the four-step split of the
+ * DFT length (m = m1 m2: the balanced split and its neighbours by a factor of
+ * two, with lines of 16 to 4096 points; 1D plans on the four-step passes
+ * only) and, for each split, the persistent grid of the middle and last pass
+ * kernels (co-resident CTAs per SM from the kernels' occupancy down to 1).
+ * Times a few GD steps per candidate on scratch data and keeps the fastest for
+ * later calls. Results differ between splits only by rounding. Synchronises
+ * the stream; allocates and frees scratch and may rebuild the workspace (not
+ * capturable; call before capturing a graph and before handing the plan's
+ * buffers to anything else). The paper has no counterpart (launch parameters
+ * of this implementation). */
 sr_status sr_plan_autotune(sr_plan* plan, int B, void* stream);
+/* Sets the four-step split m = m1 * m2 of a 1D plan (for a plan with m =
+ * 3 * 2^a, of its inner power-of-two plan): layout X holds m2 lines of m1
+ * points, layout Y m1 lines of m2 points. SR_ERR_UNSUPPORTED (plan unchanged)
+ * when m1 does not divide m or a line length of the split has no pass kernels,
+ * and for 2D plans (their split is the S x S grid). Waits for the device and
+ * rebuilds the workspace (synchronous cudaMalloc). The paper has no
+ * counterpart (it states the DFT, not how it is factored). */
+sr_status sr_plan_set_split(sr_plan* plan, int m1);
+/* Reports the plan's four-step split and the persistent-grid CTAs per SM that
+ * sr_plan_autotune chose (0: the kernels' occupancy). Any output may be NULL. */
+sr_status sr_plan_tuning(const sr_plan* plan, int* m1, int* m2, int* ctas_per_sm);
 
 /* ---- operator applications (Sec. III, Eq. 5) --------------------------------
  * sr_forward: z = A x.    x: c64[B][n] (input), z: c64[B][m] (output).

@@ -66,6 +66,8 @@ SIGNATURES = [
     ("sr_dense_check", C.c_int, [_VP]),
     ("sr_plan_check", C.c_int, [_VP]),
     ("sr_plan_autotune", C.c_int, [_VP, C.c_int, _VP]),
+    ("sr_plan_set_split", C.c_int, [_VP, C.c_int]),
+    ("sr_plan_tuning", C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("sr_plan_selftest_timeout", C.c_int, [_VP, _VP]),
     ("sr_ragged_create", C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int),
                                    C.POINTER(C.c_uint64), C.c_int, C.POINTER(_VP)]),

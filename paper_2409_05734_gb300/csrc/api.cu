@@ -233,9 +233,20 @@ float2 root_of_unity(int64_t j, int64_t N) {
   return make_float2((float)std::cos(a), (float)std::sin(a));
 }
 
-sr_status upload_twiddles(Plan* p) {
+// Line twiddles W_lmax^j, j < lmax (lmax: the longer line of the split).
+sr_status upload_line_twiddles(Plan* p) {
   std::vector<float2> twl(p->lmax);
   for (int j = 0; j < p->lmax; ++j) twl[j] = root_of_unity(j, p->lmax);
+  cudaFree(p->d_twl);
+  p->d_twl = nullptr;
+  sr_status st;
+  if ((st = dalloc(&p->d_twl, twl.size())) != SR_OK) return st;
+  SR_CUDA(cudaMemcpy(p->d_twl, twl.data(), twl.size() * sizeof(float2), cudaMemcpyHostToDevice), "cudaMemcpy");
+  return SR_OK;
+}
+
+// The two-level W_m tables (the split-independent four-step twiddles).
+sr_status upload_twiddles(Plan* p) {
   const int64_t nlo = int64_t(1) << p->tw_shift, nhi = (p->m + nlo - 1) / nlo;
   std::vector<float2> lo(nlo), hi(nhi);
   for (int64_t j = 0; j < nlo; ++j) lo[j] = root_of_unity(j, p->m);
@@ -246,13 +257,43 @@ sr_status upload_twiddles(Plan* p) {
     std::fill(hi.begin(), hi.end(), make_float2(1.f, 0.f));
   }
   sr_status st;
-  if ((st = dalloc(&p->d_twl, twl.size())) != SR_OK || (st = dalloc(&p->d_tw_lo, lo.size())) != SR_OK ||
-      (st = dalloc(&p->d_tw_hi, hi.size())) != SR_OK)
-    return st;
-  SR_CUDA(cudaMemcpy(p->d_twl, twl.data(), twl.size() * sizeof(float2), cudaMemcpyHostToDevice), "cudaMemcpy");
+  if ((st = dalloc(&p->d_tw_lo, lo.size())) != SR_OK || (st = dalloc(&p->d_tw_hi, hi.size())) != SR_OK) return st;
   SR_CUDA(cudaMemcpy(p->d_tw_lo, lo.data(), lo.size() * sizeof(float2), cudaMemcpyHostToDevice), "cudaMemcpy");
   SR_CUDA(cudaMemcpy(p->d_tw_hi, hi.data(), hi.size() * sizeof(float2), cudaMemcpyHostToDevice), "cudaMemcpy");
   return SR_OK;
+}
+
+// Four-step split m = m1 m2 (layout X: m2 lines of m1 points; layout Y: m1
+// lines of m2 points): geometry, pass occupancy and the line-twiddle table.
+// SR_ERR_UNSUPPORTED (plan unchanged) when a line length of the split has no
+// pass kernels. The workspace (its tensor maps and partial-sum banks depend on
+// the split) is released; the next call rebuilds it.
+sr_status set_split(Plan* p, int m1) {
+  if (m1 < 2 || p->m % m1 != 0 || p->m / m1 < 2) return fail(SR_ERR_UNSUPPORTED, "invalid four-step split");
+  const int m2 = (int)(p->m / m1);
+  sr::LineGeom g[2] = {sr::make_geom(p->m, m1), sr::make_geom(p->m, m2)};
+  int mid[2][3], last[2][2], lf[2], first[2];
+  for (int lay = 0; lay < 2; ++lay) {
+    const cudaError_t e = sr::pass_occupancy(g[lay], mid[lay], last[lay], &lf[lay], &first[lay]);
+    if (e == cudaErrorInvalidValue) {
+      cudaGetLastError();
+      return fail(SR_ERR_UNSUPPORTED, "no pass kernels for this four-step split");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "plan geometry");
+  }
+  p->m1 = m1;
+  p->m2 = m2;
+  p->lmax = std::max(m1, m2);
+  for (int lay = 0; lay < 2; ++lay) {
+    p->geom[lay] = g[lay];
+    std::memcpy(p->per_sm_mid[lay], mid[lay], sizeof(mid[lay]));
+    std::memcpy(p->per_sm_last[lay], last[lay], sizeof(last[lay]));
+    p->per_sm_lf[lay] = lf[lay];
+    p->per_sm_first[lay] = first[lay];
+  }
+  p->tuned_per_sm = 0;
+  free_workspace(p);
+  return upload_line_twiddles(p);
 }
 
 // ------------------------------------------------------------ chains of DFTs
@@ -797,21 +838,14 @@ sr_status create_plan(int64_t n, int64_t m, int L, uint64_t seed, int gh, int gw
     }
   } else {
     const int a = ilog2(m);
-    p->m1 = 1 << ((a + 1) / 2);
-    p->m2 = (int)(m / p->m1);
-    p->lmax = p->m1;
     p->tw_shift = (a + 1) / 2;
-    p->geom[sr::kLayoutX] = sr::make_geom(m, p->m1);
-    p->geom[sr::kLayoutY] = sr::make_geom(m, p->m2);
     e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
-    for (int lay = 0; lay < 2 && e == cudaSuccess; ++lay)
-      e = sr::pass_occupancy(p->geom[lay], p->per_sm_mid[lay], p->per_sm_last[lay], &p->per_sm_lf[lay],
-                             &p->per_sm_first[lay]);
     if (e != cudaSuccess) {
       delete p;
-      return cuda_fail(e, "plan geometry");
+      return cuda_fail(e, "cudaDeviceGetAttribute");
     }
-    if ((st = upload_twiddles(p)) != SR_OK) {
+    // the balanced split (the longer line first); sr_plan_autotune may choose another
+    if ((st = set_split(p, 1 << ((a + 1) / 2))) != SR_OK || (st = upload_twiddles(p)) != SR_OK) {
       sr_plan_destroy(p);
       return st;
     }
@@ -1176,24 +1210,47 @@ sr_status sr_plan_info(const sr_plan* plan, int64_t* n, int64_t* m, int* L) {
 
 sr_status sr_plan_reserve(sr_plan* plan, int B) { return check_plan_call(plan, B); }
 
+// Times `reps` GD steps of the plan over B problems of scratch data (after two
+// untimed steps); 0 on success.
+static sr_status time_gd_steps(sr_plan* plan, const float* y, float2* x, int B, cudaStream_t s, cudaEvent_t e0,
+                               cudaEvent_t e1, float* ms) {
+  const sr_gd_opts o{1e-6f, 0.f};
+  sr_status st;
+  if ((st = sr_gd_solve(plan, y, x, 2, &o, nullptr, B, s)) != SR_OK) return st;
+  SR_CUDA(cudaEventRecord(e0, s), "cudaEventRecord");
+  if ((st = sr_gd_solve(plan, y, x, 5, &o, nullptr, B, s)) != SR_OK) return st;
+  SR_CUDA(cudaEventRecord(e1, s), "cudaEventRecord");
+  SR_CUDA(cudaEventSynchronize(e1), "cudaEventSynchronize");
+  SR_CUDA(cudaEventElapsedTime(ms, e0, e1), "cudaEventElapsedTime");
+  return SR_OK;
+}
+
+// Caps every persistent-pass grid of the plan at c CTAs per SM (c <= 0: the
+// kernels' occupancy).
+static void cap_grids(Plan& p, const int (&mid)[2][3], const int (&last)[2][2], const int (&lf)[2], int c) {
+  for (int l = 0; l < 2; ++l) {
+    for (int k = 0; k < 3; ++k) p.per_sm_mid[l][k] = c > 0 ? std::min(c, mid[l][k]) : mid[l][k];
+    for (int k = 0; k < 2; ++k) p.per_sm_last[l][k] = c > 0 ? std::min(c, last[l][k]) : last[l][k];
+    p.per_sm_lf[l] = c > 0 ? std::min(c, lf[l]) : lf[l];
+  }
+  p.tuned_per_sm = c > 0 ? c : 0;
+}
+
 sr_status sr_plan_autotune(sr_plan* plan, int B, void* stream) {
   sr_status st = check_plan_call(plan, B);
   if (st != SR_OK) return st;
   Plan& p = plan->inner ? *plan->inner : *plan;
-  const int Bt = plan->inner ? 3 * B : B;
   cudaStream_t s = (cudaStream_t)stream;
-  // Candidate persistent-grid sizes of the middle and last passes: c CTAs per
-  // SM, capped by each kernel's occupancy. Timed on one GD step chain of the
-  // plan over B problems of scratch data.
-  int occ_mid[2][3], occ_last[2][2], occ_lf[2];
-  std::memcpy(occ_mid, p.per_sm_mid, sizeof(occ_mid));
-  std::memcpy(occ_last, p.per_sm_last, sizeof(occ_last));
-  std::memcpy(occ_lf, p.per_sm_lf, sizeof(occ_lf));
-  int max_occ = 1;
-  for (int l = 0; l < 2; ++l) {
-    for (int k = 0; k < 3; ++k) max_occ = std::max(max_occ, occ_mid[l][k]);
-    for (int k = 0; k < 2; ++k) max_occ = std::max(max_occ, occ_last[l][k]);
-    max_occ = std::max(max_occ, occ_lf[l]);
+  const int cap_outer = plan->B_cap;
+  // Candidate four-step splits (1D plans on the four-step passes): the
+  // balanced one and its neighbours by a factor of two, each line of 16 to
+  // 4096 points with pass kernels for both line lengths.
+  std::vector<int> splits{p.m1};
+  if (!p.two_d && !sr::small_eligible(p)) {
+    for (int m1 : {p.m1 / 2, p.m1 * 2}) {
+      const int64_t m2 = p.m / std::max(1, m1);
+      if (m1 >= 16 && m1 <= 4096 && m2 >= 16 && m2 <= 4096) splits.push_back(m1);
+    }
   }
   float* y = nullptr;
   float2* x = nullptr;
@@ -1207,41 +1264,76 @@ sr_status sr_plan_autotune(sr_plan* plan, int B, void* stream) {
   if (e == cudaSuccess) e = cudaMemsetAsync(x, 0x3F, sizeof(float2) * (size_t)B * plan->n, s);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  // For every split the kernels support, the persistent-grid sizes of the
+  // middle and last passes from the kernels' occupancy down to 1 CTA per SM.
   float best_ms = 0.f;
-  int best_c = max_occ;
-  const sr_gd_opts o{1e-6f, 0.f};
-  for (int c = max_occ; c >= 1 && e == cudaSuccess && st == SR_OK; --c) {
+  int best_split = p.m1, best_c = 0;
+  bool have = false;
+  for (size_t si = 0; si < splits.size() && e == cudaSuccess && st == SR_OK; ++si) {
+    if (splits[si] != p.m1 && set_split(&p, splits[si]) != SR_OK) continue;  // no kernels for this split
+    if (plan->inner) free_workspace(plan);  // the outer plan's banks follow the inner geometry
+    int mid[2][3], last[2][2], lf[2];
+    std::memcpy(mid, p.per_sm_mid, sizeof(mid));
+    std::memcpy(last, p.per_sm_last, sizeof(last));
+    std::memcpy(lf, p.per_sm_lf, sizeof(lf));
+    int max_occ = 1;
     for (int l = 0; l < 2; ++l) {
-      for (int k = 0; k < 3; ++k) p.per_sm_mid[l][k] = std::min(c, occ_mid[l][k]);
-      for (int k = 0; k < 2; ++k) p.per_sm_last[l][k] = std::min(c, occ_last[l][k]);
-      p.per_sm_lf[l] = std::min(c, occ_lf[l]);
+      for (int k = 0; k < 3; ++k) max_occ = std::max(max_occ, mid[l][k]);
+      for (int k = 0; k < 2; ++k) max_occ = std::max(max_occ, last[l][k]);
+      max_occ = std::max(max_occ, lf[l]);
     }
-    if ((st = sr_gd_solve(plan, y, x, 2, &o, nullptr, B, stream)) != SR_OK) break;
-    e = cudaEventRecord(e0, s);
-    if (e == cudaSuccess && (st = sr_gd_solve(plan, y, x, 5, &o, nullptr, B, stream)) != SR_OK) break;
-    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e == cudaSuccess && (c == max_occ || ms < best_ms)) {
-      best_ms = ms;
-      best_c = c;
+    for (int c = max_occ; c >= 1 && st == SR_OK; --c) {
+      cap_grids(p, mid, last, lf, c);
+      float ms = 0.f;
+      if ((st = time_gd_steps(plan, y, x, B, s, e0, e1, &ms)) != SR_OK) break;
+      if (!have || ms < best_ms) {
+        have = true;
+        best_ms = ms;
+        best_split = p.m1;
+        best_c = c;
+      }
     }
   }
-  (void)Bt;
-  for (int l = 0; l < 2; ++l) {
-    for (int k = 0; k < 3; ++k) p.per_sm_mid[l][k] = std::min(best_c, occ_mid[l][k]);
-    for (int k = 0; k < 2; ++k) p.per_sm_last[l][k] = std::min(best_c, occ_last[l][k]);
-    p.per_sm_lf[l] = std::min(best_c, occ_lf[l]);
-  }
-  p.tuned_per_sm = best_c;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamSynchronize(s);
   cudaFree(y);
   cudaFree(x);
+  if (st == SR_OK && e != cudaSuccess) st = cuda_fail(e, "autotune");
+  // the winner (the balanced split if nothing was timed) with its grid size,
+  // and the workspace the plan held before
+  sr_status st2 = set_split(&p, best_split);
+  if (st2 == SR_OK) {
+    int mid[2][3], last[2][2], lf[2];
+    std::memcpy(mid, p.per_sm_mid, sizeof(mid));
+    std::memcpy(last, p.per_sm_last, sizeof(last));
+    std::memcpy(lf, p.per_sm_lf, sizeof(lf));
+    cap_grids(p, mid, last, lf, best_c);
+    if (plan->inner) free_workspace(plan);
+    st2 = check_plan_call(plan, plan->batch_fixed ? B : std::max(B, cap_outer));
+  }
+  return st != SR_OK ? st : st2;
+}
+
+sr_status sr_plan_set_split(sr_plan* plan, int m1) {
+  if (!plan) return fail(SR_ERR_INVALID_ARG, "plan is NULL");
+  sr_status st = check_device(plan);
   if (st != SR_OK) return st;
-  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  if (plan->two_d) return fail(SR_ERR_UNSUPPORTED, "2D plans keep the S x S split");
+  Plan& p = plan->inner ? *plan->inner : *plan;
+  const int cap = plan->B_cap;
+  SR_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  if ((st = set_split(&p, m1)) != SR_OK) return st;
+  if (plan->inner) free_workspace(plan);
+  return cap > 0 ? check_plan_call(plan, plan->batch_fixed ? plan->batch_fixed : cap) : SR_OK;
+}
+
+sr_status sr_plan_tuning(const sr_plan* plan, int* m1, int* m2, int* ctas_per_sm) {
+  if (!plan) return fail(SR_ERR_INVALID_ARG, "plan is NULL");
+  const Plan& p = plan->inner ? *static_cast<const Plan*>(plan->inner) : *static_cast<const Plan*>(plan);
+  if (m1) *m1 = p.m1;
+  if (m2) *m2 = p.m2;
+  if (ctas_per_sm) *ctas_per_sm = p.tuned_per_sm;
   return SR_OK;
 }
 

@@ -120,9 +120,22 @@ class Plan:
             _lib.check(self._lib.sr_plan_selftest_timeout(self._h, _stream_handle()), "sr_plan_selftest_timeout")
 
     def autotune(self, B: int) -> None:
-        """Choose the persistent grid size of the pass kernels for batches of B (timed on the GPU)."""
+        """Choose the four-step split and the persistent grid size of the pass kernels for
+        batches of B (timed on the GPU)."""
         with torch.cuda.device(self.device):
             _lib.check(self._lib.sr_plan_autotune(self._h, int(B), _stream_handle()), "sr_plan_autotune")
+
+    def set_split(self, m1: int) -> None:
+        """Factor the DFT length as m1 * (m / m1) (lines of m1 and m / m1 points)."""
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.sr_plan_set_split(self._h, int(m1)), "sr_plan_set_split")
+
+    @property
+    def tuning(self):
+        """(m1, m2, CTAs per SM) of the four-step passes; CTAs per SM 0 = the kernels' occupancy."""
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _lib.check(self._lib.sr_plan_tuning(self._h, C.byref(a), C.byref(b), C.byref(c)), "sr_plan_tuning")
+        return a.value, b.value, c.value
 
     def reserve(self, B: int) -> None:
         with torch.cuda.device(self.device):

@@ -1,6 +1,7 @@
 """GPU parity of ragged batches (independent problems with their own sizes,
 layer counts and phase seeds) against the FP64 oracle run problem by problem,
-plus graph capture and autotuning, which must not change any result."""
+plus graph capture (bit-identical results) and autotuning (results equal up to
+the rounding of another four-step split)."""
 import numpy as np
 import pytest
 import torch
@@ -94,7 +95,7 @@ def test_ragged_solver_each_problem(sr):
         assert np.max(np.abs(h[:, i] - ho[:, 0]) / ho[:, 0]) <= 1e-3, i
 
 
-def test_ragged_graph_capture_and_autotune_change_nothing(sr):
+def test_ragged_graph_capture_and_autotune_keep_results(sr):
     r, seeds = make(sr)
     ra, _ = make(sr, autotune=True)
     xt, ys, v0 = _problem_data(r, seeds)
@@ -115,7 +116,9 @@ def test_ragged_graph_capture_and_autotune_change_nothing(sr):
     r.check()
     ra.check()
     assert torch.equal(x_eager, x_graph)
-    assert torch.equal(x_eager, x_tuned)
+    # the autotuner may pick another four-step split for a bucket: the same
+    # iterates up to rounding
+    assert (torch.linalg.vector_norm(x_tuned - x_eager) / torch.linalg.vector_norm(x_eager)).item() <= 1e-5
 
 
 def test_ragged_rejects_bad_arguments(sr):
