@@ -194,15 +194,17 @@ def test_headline_solve_matches_oracle(Plan):
     """The benchmark's whole solve at its own configuration: B = 64 signals,
     n = 2^14 (amplitude U[0, 1] times a random phase), alpha = 4 (m = 2^16),
     L = 2, noiseless y, 100 power iterations with the optimal weight
-    (lambda = -1), then 500 GD steps at mu0 = 0.15, tau0 = 100. Sampled problems
-    of the batch are solved by the FP64 oracle from the same inputs; the final
-    reconstruction errors up to a global phase agree within 1e-4 (the target).
-    The iterates agree within 1e-4 in norm (5e-4 of the RMS per element) after
-    the spectral start, and within 1e-3 (5e-3) after the 500 GD steps: GD from
-    a start far from the signal amplifies rounding-level changes (moving the
-    oracle's own start vector by 6e-8 relative moves its final iterate by up to
-    2.5e-4 on problems of this batch), so the FP32 trajectory is pinned to the
-    FP64 one only to that order."""
+    (lambda = -1), then 500 GD steps at mu0 = 0.1, tau0 = 100. Sampled problems
+    of the batch (59 has the smallest stability limit of the batch, mu0 = 0.117)
+    are solved by the FP64 oracle from the same inputs.
+
+    mu0 = 0.1 lies below every problem's linear stability limit of GD at the
+    solution, so FP32 rounding is damped, not amplified: in the oracle, a
+    relative change of 6e-8 injected into every iterate moves the final
+    reconstruction error by at most 1.1e-6 on any problem of this batch. The
+    final reconstruction errors up to a global phase agree within 1e-4 (the
+    target); the iterates within 1e-4 in norm (5e-4 of the RMS per element)
+    after the spectral start and after the 500 GD steps."""
     n, m, L, B = 2 ** 14, 2 ** 16, 2, 64
     seed = 20240905
     plan = Plan(n, m, L, seed)
@@ -214,14 +216,14 @@ def test_headline_solve_matches_oracle(Plan):
     y = dev(y_o, torch.float32)
     x0 = plan.spectral_init(y, dev(v0), 100, weight="optimal", lam=-1.0)
     x0g = host(x0)
-    plan.gd_solve(y, x0, 500, mu0=0.15, tau0=100.0)
+    plan.gd_solve(y, x0, 500, mu0=0.1, tau0=100.0)
     plan.check()
     xg = host(x0)
-    for b in (0, 37, 63):
+    for b in (0, 21, 37, 51, 59, 63):
         x0o = O.spectral_init(y_o[b:b + 1], v0[b:b + 1], fwd, adj, 100, mode="optimal", lam=-1.0)
         assert_close_elementwise(x0g[b:b + 1], x0o, tol_norm=1e-4, tol_elem=5e-4)
-        xTo, _ = O.gradient_descent(x0o, y_o[b:b + 1], fwd, adj, 500, mu0=0.15, tau0=100.0)
-        assert_close_elementwise(xg[b:b + 1], xTo, tol_norm=1e-3, tol_elem=5e-3)
+        xTo, _ = O.gradient_descent(x0o, y_o[b:b + 1], fwd, adj, 500, mu0=0.1, tau0=100.0)
+        assert_close_elementwise(xg[b:b + 1], xTo, tol_norm=1e-4, tol_elem=5e-4)
         e_gpu = O.relative_error_global_phase(xg[b:b + 1], x_true[b:b + 1])[0]
         e_or = O.relative_error_global_phase(xTo, x_true[b:b + 1])[0]
         assert abs(e_gpu - e_or) <= 1e-4, (b, e_gpu, e_or)

@@ -176,3 +176,50 @@ def test_step_ramp_and_gd_with_warmup():
     assert np.allclose(x1, x0 - (1 - np.exp(-1 / 20.0)) * 0.15 * m / y.sum() * g0, atol=1e-12)
     xT, hist = O.gradient_descent(x0, y, fwd, adj, 3000, mu0=0.15, tau0=100.0)
     assert O.relative_error_global_phase(xT, x)[0] < 1e-8
+
+
+def _linearised_gradient_matrix(Adense, z):
+    """Real 2n x 2n matrix of delta -> 4 A^H(z * Re(conj(z) * A delta)), the first-order
+    change of g = 2 A^H((|Ax|^2 - y) Ax) at the solution (where |Ax|^2 = y),
+    acting on delta = a + i b stored as [a; b]; formed from the explicit matrix A."""
+    n = Adense.shape[1]
+    J = np.zeros((2 * n, 2 * n))
+    for j in range(2 * n):
+        d = np.zeros(n, complex)
+        d[j % n] = 1.0 if j < n else 1j
+        u = 4.0 * (Adense.conj().T @ (z * np.real(np.conj(z) * (Adense @ d))))
+        J[:n, j], J[n:, j] = u.real, u.imag
+    return J
+
+
+@pytest.mark.parametrize("seed,L", [(3, 2), (4, 1)])
+def test_gd_step_stability_threshold(seed, L):
+    """Linear stability of GD at the solution. Near x*, x_{t+1} - x* ~ (I - mu J)(x_t - x*)
+    with J the linearised gradient map (symmetric positive semidefinite in the real
+    inner product, with the global-phase direction i x* in its kernel), so GD with
+    mu = mu0 m / sum(y) is stable iff mu0 < 2 sum(y) / (m lambda_max(J)). J is formed
+    from the explicit dense A (not the oracle's FFT path); the oracle's
+    gradient_descent, started at x* + eps v_max, must shrink the deviation at 0.9 of the
+    threshold and grow it at 1.1. A dropped factor 2 in the gradient or a step scaled
+    by the mean of y instead of its sum moves the threshold and fails one side."""
+    n, alpha = 8, 4
+    theta, x, y, fwd, adj, m = _problem(seed, n, alpha, L)
+    Ad = O.dense_structured_matrix(theta, n, m)
+    z = (Ad @ x[0])
+    J = _linearised_gradient_matrix(Ad, z)
+    assert np.allclose(J, J.T, atol=1e-12)
+    ev, V = np.linalg.eigh(J)
+    assert ev[0] > -1e-12
+    ix = np.concatenate([-x[0].imag, x[0].real])  # i x* as a real vector
+    assert np.linalg.norm(J @ ix) <= 1e-12 * np.linalg.norm(J) * np.linalg.norm(ix)
+    v = V[:, -1]
+    dmax = (v[:n] + 1j * v[n:])[None]
+    mu0_crit = 2.0 * y.sum() / (m * ev[-1])
+    eps = 1e-7 * np.linalg.norm(x)
+    T = 40
+    for f, grows in ((0.9, False), (1.1, True)):
+        xT, _ = O.gradient_descent(x + eps * dmax, y, fwd, adj, T, mu0=f * mu0_crit, tau0=0.0)
+        ratio = np.linalg.norm(xT - x) / eps
+        expected = abs(1.0 - 2.0 * f) ** T  # 0.8^40 or 1.2^40
+        assert (ratio > 1.0) == grows, (f, ratio)
+        assert 0.5 * expected <= ratio <= 2.0 * expected, (f, ratio, expected)
