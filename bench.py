@@ -377,7 +377,8 @@ def quantiles(v):
 
 def dense_comparison(torch, dev, flush, reps: int = 3):
     """Solve time of the structured model against the dense i.i.d. model (tcgen05
-    GEMMs, BF16 matrix) at equal median recovery error; see DENSE_CMP."""
+    GEMMs, BF16 matrix, and the same matrix in TF32) at equal median recovery
+    error; see DENSE_CMP."""
     from paper_2409_05734_gb300 import DenseModel, Plan
     import synthetic as S
     C = DENSE_CMP
@@ -387,10 +388,15 @@ def dense_comparison(torch, dev, flush, reps: int = 3):
     rng = np.random.default_rng(C["seed"])
     a = rng.standard_normal((m, n, 2), dtype=np.float32) * np.float32(1.0 / np.sqrt(2.0 * m))
     dense = DenseModel(a.view(np.complex64)[..., 0])
+    dense_tf32 = DenseModel(a.view(np.complex64)[..., 0], format="tf32")
     del a
     plan = Plan(n, m, C["L"], C["seed"])
     plan.reserve(B)
-    models = {"structured": plan, "dense": dense}
+    models = {"structured": plan, "dense": dense, "dense_tf32": dense_tf32}
+    peaks = {}
+    pth = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pth):
+        peaks = json.load(open(pth))
     out = {}
     for name, mod in models.items():
         y = (mod.forward(x_true).abs() ** 2).contiguous()
@@ -423,7 +429,7 @@ def dense_comparison(torch, dev, flush, reps: int = 3):
                     times.append(e0.elapsed_time(e1))
             ms = statistics.median(times)
             rec.update({"solve_ms": ms, "ms_per_iteration": ms / (C["spectral_iters"] + T)})
-        if name == "dense":
+        if name != "structured":
             # roofline of the dense GD iteration (two tcgen05 GEMMs with fused epilogues)
             it = 50
             mod.gd_solve(y, x, it, mu0=C["mu0"], tau0=C["tau0"])
@@ -434,49 +440,61 @@ def dense_comparison(torch, dev, flush, reps: int = 3):
             e1.record()
             torch.cuda.synchronize()
             t_it = e0.elapsed_time(e1) / 1e3 / it
+            tf32 = name == "dense_tf32"
             tflops = 2 * 16 * m * n * B / t_it / 1e12   # executed: real GEMMs K = 2n, N = 2B, high + low
-            gbs = 2 * 4 * m * n / t_it / 1e9             # the BF16 matrix, read once per product
-            peaks = {}
-            pth = os.path.join(ROOT, "MEASURED_PEAKS.json")
-            if os.path.exists(pth):
-                peaks = json.load(open(pth))
+            gbs = 2 * (8 if tf32 else 4) * m * n / t_it / 1e9  # the matrix, read once per product
+            # TF32 dense peak: the measured BF16 peak x the nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)
+            peak = peaks.get("bf16_tflops_sustained")
+            if peak is not None and tf32:
+                peak = peak * 1.1 / 2.25
             rec["gemm_roofline"] = {"ms_per_gd_iteration": t_it * 1e3, "tensor_tflops": tflops,
-                                    "bf16_peak_tflops": peaks.get("bf16_tflops_sustained"),
-                                    "tensor_frac": tflops / peaks["bf16_tflops_sustained"]
-                                    if "bf16_tflops_sustained" in peaks else None,
+                                    "tensor_peak_tflops": peak,
+                                    "tensor_peak_kind": ("measured bf16 sustained x nominal tf32/bf16 (1.1/2.25)"
+                                                         if tf32 else "measured bf16 sustained"),
+                                    "tensor_frac": tflops / peak if peak else None,
                                     "hbm_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"] if "hbm_gbs" in peaks else None}
         out[name] = rec
     dense.close()
-    del dense
-    s, d = out["structured"], out["dense"]
+    dense_tf32.close()
+    del dense, dense_tf32
+    s, d, d32 = out["structured"], out["dense"], out["dense_tf32"]
     speedup = d["solve_ms"] / s["solve_ms"] if "solve_ms" in s and "solve_ms" in d else None
     per_iter = d["ms_per_iteration"] / s["ms_per_iteration"] if speedup else None
+    speedup32 = d32["solve_ms"] / s["solve_ms"] if "solve_ms" in s and "solve_ms" in d32 else None
     # A stronger dense bound: the same two real GEMMs per iteration (BF16 matrix, the
     # vector's high and low parts as 4B columns, FP32 accumulation) timed in cuBLAS
     # (torch.matmul), with every other step of the iteration taken as free.
-    gemm_us = cublas_dense_gemm_us(torch, dev, n, m, B)
-    bound = None
-    if d.get("gd_iters_to_target") is not None and "solve_ms" in s:
-        iters = C["spectral_iters"] + d["gd_iters_to_target"]
-        bound_ms = iters * (gemm_us["forward"] + gemm_us["adjoint"]) / 1e3
-        bound = {"cublas_gemm_us": gemm_us, "dense_solve_ms_lower_bound": bound_ms,
-                 "speedup_at_equal_error": bound_ms / s["solve_ms"]}
+    bounds = {}
+    for fmt, rec in (("bf16", d), ("tf32", d32)):
+        gemm_us = cublas_dense_gemm_us(torch, dev, n, m, B, fmt=fmt)
+        if rec.get("gd_iters_to_target") is not None and "solve_ms" in s:
+            iters = C["spectral_iters"] + rec["gd_iters_to_target"]
+            bound_ms = iters * (gemm_us["forward"] + gemm_us["adjoint"]) / 1e3
+            bounds[fmt] = {"cublas_gemm_us": gemm_us, "dense_solve_ms_lower_bound": bound_ms,
+                           "speedup_at_equal_error": bound_ms / s["solve_ms"]}
     return {"workload": f"n={n}, m={m} (alpha={m // n}), B={B}, structured L={C['L']} vs dense i.i.d. CN(0,1/m) "
-                        f"(BF16 entries); {C['spectral_iters']} power iterations + GD to median relative "
-                        f"error <= {C['target']}", "speedup_at_equal_error": speedup,
-            "speedup_per_iteration": per_iter, "vs_cublas_gemm_bound": bound, **out}
+                        f"(BF16 entries, and the same matrix in TF32); {C['spectral_iters']} power iterations + GD "
+                        f"to median relative error <= {C['target']}",
+            "speedup_at_equal_error_vs_cublas_gemm_bound": bounds.get("bf16", {}).get("speedup_at_equal_error"),
+            "speedup_at_equal_error": speedup, "speedup_at_equal_error_tf32": speedup32,
+            "speedup_per_iteration": per_iter, "vs_cublas_gemm_bound": bounds.get("bf16"),
+            "vs_cublas_gemm_bound_tf32": bounds.get("tf32"), **out}
 
 
-def cublas_dense_gemm_us(torch, dev, n, m, B, reps=20):
+def cublas_dense_gemm_us(torch, dev, n, m, B, reps=20, fmt="bf16"):
     """Device time (us) of the dense model's forward ([m, 2n] x [2n, 4B]) and adjoint
-    ([2n, m] x [m, 4B]) real GEMMs in cuBLAS, BF16 inputs with FP32 accumulation."""
+    ([2n, m] x [m, 4B]) real GEMMs in cuBLAS with FP32 accumulation: BF16 inputs, or
+    FP32 inputs on the TF32 tensor cores (fmt = "tf32")."""
     g = torch.Generator(device=dev).manual_seed(0)
     prev = torch.backends.cuda.matmul.allow_bf16_reduced_precision_reduction
+    prev32 = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_bf16_reduced_precision_reduction = False  # FP32 split-K reductions
+    torch.backends.cuda.matmul.allow_tf32 = True
+    cast = (lambda t: t.bfloat16()) if fmt == "bf16" else (lambda t: t)
     out = {}
     for name, (M, K) in (("forward", (m, 2 * n)), ("adjoint", (2 * n, m))):
-        a = torch.randn(M, K, device=dev, generator=g).bfloat16()
-        b = torch.randn(K, 4 * B, device=dev, generator=g).bfloat16()
+        a = cast(torch.randn(M, K, device=dev, generator=g))
+        b = cast(torch.randn(K, 4 * B, device=dev, generator=g))
         for _ in range(3):
             torch.matmul(a, b)
         torch.cuda.synchronize()
@@ -489,6 +507,7 @@ def cublas_dense_gemm_us(torch, dev, n, m, B, reps=20):
         out[name] = e0.elapsed_time(e1) / reps * 1e3
         del a, b
     torch.backends.cuda.matmul.allow_bf16_reduced_precision_reduction = prev
+    torch.backends.cuda.matmul.allow_tf32 = prev32
     return out
 
 
@@ -1247,6 +1266,7 @@ EXTRA_LEGS = {
     "small": "small_m_workload",
     "layers": "layers_experiment",
     "ragged": "ragged_workload",
+    "dense": "dense_comparison",
 }
 
 

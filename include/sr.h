@@ -296,7 +296,20 @@ sr_status sr_forward_noalloc(const sr_plan* plan, const void* x, void* z, int B,
  * B a multiple of 8 in [8, 128]. The model owns two copies of A (A and its
  * transpose, 2 * 4 * m * n bytes) and a workspace for B problems. */
 typedef struct sr_dense sr_dense;
+/* Operand formats of the dense model (tensor-core input types). */
+enum { SR_DENSE_BF16 = 0, SR_DENSE_TF32 = 1 };
+/* The BF16 model (sr_dense_create_format with SR_DENSE_BF16). */
 sr_status sr_dense_create(int64_t n, int64_t m, const float* a_host, sr_dense** out);
+/* The model with its matrix in `format`:
+ * - SR_DENSE_BF16: A rounded to BF16 (nearest even); tcgen05 kind::f16; the
+ *   vector operand split into BF16 high and low parts (about 2^-16 relative).
+ * - SR_DENSE_TF32: A rounded to TF32 (10 fraction bits, to nearest with ties
+ *   away from zero, as cvt.rna.tf32.f32); tcgen05 kind::tf32 on FP32-sized
+ *   operands (twice the bytes of BF16: 2 * 8 * m * n for A and its transpose);
+ *   the vector operand split into TF32 high and low parts (about 2^-21).
+ * The rounded matrix is the model's A in both cases. Same sizes and calls as
+ * above; SR_ERR_INVALID_ARG for an unknown format. */
+sr_status sr_dense_create_format(int64_t n, int64_t m, const float* a_host, int format, sr_dense** out);
 sr_status sr_dense_destroy(sr_dense* model); /* NULL accepted */
 /* z = A x (x: c64[B][n], z: c64[B][m], device) and x = A^H w (w: c64[B][m]). */
 sr_status sr_dense_forward(sr_dense* model, const void* x, void* z, int B, void* stream);
@@ -319,17 +332,22 @@ sr_status sr_dense_check(sr_dense* model);
  * A batch of `count` problems with their own sizes n_i, m_i, L_i and phase
  * seeds (the paper's recovery experiments solve many independent problems;
  * Sec. IV). The library buckets problems of equal (n, m, L) into one batched
- * plan whose diagonal tables hold each problem's own phases theta(seed_i), and
- * runs the buckets as concurrent branches (one stream each, forked from and
- * joined back into the caller's stream), so a whole ragged GD step is one
- * capturable sequence and a CUDA graph of it has one branch per bucket.
+ * plan whose diagonal tables hold each problem's own phases theta(seed_i).
+ * Buckets with power-of-two m from 2^14 to 2^20 form one queue-driven group: a
+ * whole GD or power-iteration call on all of the group's problems is ONE
+ * persistent launch (plus a few per-problem set-up and finish launches). The
+ * other buckets (short transforms, which the resident solver runs whole,
+ * radix-3 and longer lengths) run as concurrent branches (one stream each,
+ * forked from and joined back into the caller's stream). Every call is one
+ * capturable sequence.
  *
  * Data layout: the library chooses where each problem lives in the
  * concatenated buffers: x_cat (c64, problem i at x_off[i], n_i values) and
  * y_cat (f32 for measurements, or c64 for sr_ragged_forward's output; problem
  * i at y_off[i], m_i values), both from sr_ragged_layout; problems of a
  * bucket are adjacent. Sizes as for sr_plan_create; autotune != 0 runs
- * sr_plan_autotune on every bucket at creation. */
+ * sr_plan_autotune at creation on every bucket outside the queue-driven group
+ * (the group runs on its own tile geometry and grid). */
 typedef struct sr_ragged sr_ragged;
 sr_status sr_ragged_create(int count, const int64_t* n, const int64_t* m, const int* L, const uint64_t* seeds,
                            int autotune, sr_ragged** out);

@@ -58,6 +58,7 @@ SIGNATURES = [
     ("sr_forward_noalloc", C.c_int, [_VP, _VP, _VP, C.c_int, _VP]),
     ("sr_metrics", C.c_int, [_VP, _VP, C.c_int64, C.c_int, _VP, _VP, _VP]),
     ("sr_dense_create", C.c_int, [C.c_int64, C.c_int64, _VP, C.POINTER(_VP)]),
+    ("sr_dense_create_format", C.c_int, [C.c_int64, C.c_int64, _VP, C.c_int, C.POINTER(_VP)]),
     ("sr_dense_destroy", C.c_int, [_VP]),
     ("sr_dense_forward", C.c_int, [_VP, _VP, _VP, C.c_int, _VP]),
     ("sr_dense_adjoint", C.c_int, [_VP, _VP, _VP, C.c_int, _VP]),

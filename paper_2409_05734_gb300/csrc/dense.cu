@@ -1,13 +1,15 @@
 // Dense i.i.d. comparison model (Sec. II-A): z = A x and A^H w for a dense
 // complex A in C^{m x n}, as real GEMMs on the fifth-generation tensor cores.
 //
-// Number formats. A is stored in BF16 and is, by definition, the model's
-// matrix: the caller's entries are rounded to BF16 once when the model is
-// created, so the product involves no further error from A. The vector
-// operand (x, or the residual-weighted w) is split into a BF16 high part and a
-// BF16 low part (v = hi + lo to about 2^-17 relative); each A tile staged in
-// shared memory is multiplied with both parts, accumulating in FP32 in tensor
-// memory, so the split costs no extra HBM traffic.
+// Number formats. A is stored in BF16 (tcgen05 kind::f16) or in TF32
+// (kind::tf32, FP32 containers, twice the bytes) and is, by definition, the
+// model's matrix: the caller's entries are rounded once when the model is
+// created (BF16: to nearest even; TF32: to nearest, ties away from zero), so
+// the product involves no further error from A. The vector operand (x, or the
+// residual-weighted w) is split into a high and a low part of the same format
+// (v = hi + lo to about 2^-17 relative in BF16, 2^-22 in TF32); each A tile
+// staged in shared memory is multiplied with both parts, accumulating in FP32
+// in tensor memory, so the split costs no extra HBM traffic.
 //
 // Complex products as one real GEMM with interleaved layouts:
 //   forward  Z'[i][c] = sum_k Af[i][k] X'[c][k],  Af[i][2j] = Re A_ij, Af[i][2j+1] = Im A_ij,
@@ -19,8 +21,9 @@
 // Both operands of both GEMMs are K-major (A is stored twice, Af and its
 // transpose Aa), so one kernel serves both.
 //
-// Both operands live in HBM pre-tiled: A as tiles of 128 rows x 64 values and
-// the vector operand X'/W' as blocks of 64 columns (high part, then low part),
+// Both operands live in HBM pre-tiled: A as tiles of 128 rows x VPR values
+// (VPR = 64 BF16 or 32 TF32 values: one 128-byte row) and the vector operand
+// X'/W' as blocks of VPR columns (high part, then low part),
 // each stored as the exact 128-byte-swizzled shared-memory image the MMA reads.
 // A stage of the main loop is then two contiguous bulk copies (16 KB of A and
 // 2 x 2B x 128 bytes of the vector operand), with no tensor maps. The kernels
@@ -35,7 +38,8 @@
 //
 // Kernel: one CTA per 128-row tile of the output, 4 warps. Warp 0 lane 0 issues
 // the loads of a multi-stage ring; warp 1 lane 0 issues tcgen05.mma (M = 128,
-// N = 2B, K = 16 per instruction, high and low parts) into TMEM accumulators and
+// N = 2B, K = 16 BF16 or 8 TF32 values per instruction, four per stage, high
+// and low parts) into TMEM accumulators and
 // frees each stage with tcgen05.commit; then all four warps read their 32 TMEM
 // lanes and run the fused epilogue. All waits are bounded by the global timer.
 #include <algorithm>
@@ -54,9 +58,36 @@ namespace sr {
 namespace {
 
 constexpr int kBM = 128;      // output rows per CTA (TMEM lanes)
-constexpr int kBK = 64;       // BF16 values per 128-byte row of a stage
 constexpr int kThreads = 128;
 constexpr int kMaxStages = 6;
+
+// Operand formats: element type, values per 128-byte row (VPR) and per
+// 16-byte swizzle chunk (VPC), reduction length of one MMA instruction (KPM).
+template <int FMT>
+struct Fmt;
+template <>
+struct Fmt<SR_DENSE_BF16> {
+  using El = __nv_bfloat16;
+  static constexpr int VPR = 64, VPC = 8, KPM = 16;
+  __device__ __forceinline__ static void split(float v, El& hi, El& lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+};
+template <>
+struct Fmt<SR_DENSE_TF32> {
+  using El = uint32_t;  // TF32 in an FP32 container (low 13 mantissa bits zero)
+  static constexpr int VPR = 32, VPC = 4, KPM = 8;
+  __device__ __forceinline__ static uint32_t round(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return r;
+  }
+  __device__ __forceinline__ static void split(float v, El& hi, El& lo) {
+    hi = round(v);
+    lo = round(v - __uint_as_float(hi));
+  }
+};
 
 enum DenseMode {
   kDenseStoreZ = 0,  // forward: z = A x
@@ -68,21 +99,21 @@ enum DenseMode {
 };
 
 struct GemmArgs {
-  const __nv_bfloat16* a_tiles;  // A operand, tiled: [M/128][K/64] images of 128 x 64 (16 KB, swizzled)
-  const __nv_bfloat16* b_tiles;  // vector operand, tiled (vtile_index): [K/64][high, low][2B][64]
+  const void* a_tiles;  // A operand, tiled: [M/128][K/VPR] images of 128 x VPR (16 KB, swizzled)
+  const void* b_tiles;  // vector operand, tiled (vtile_index): [K/VPR][high, low][2B][VPR]
   int M, K, B;      // output rows, reduction length, problems (N = 2B)
   int mode;
   int n, m;         // model sizes
   float2* z;                 // kDenseStoreZ: [B][m]
   const float* y;            // kDenseGdFwd: [B][m]
-  __nv_bfloat16* w_out;      // kDenseGdFwd / kDenseSpecFwd: W' [2B][m], tiled
+  void* w_out;               // kDenseGdFwd / kDenseSpecFwd: W' [2B][m], tiled
   float* loss_part;          // kDenseGdFwd writes [tiles][B]; kDenseGdAdj reads
   int loss_tiles;
   float* loss_out;           // kDenseGdAdj: [B] or nullptr
   float2* x;                 // kDenseStoreX / kDenseGdAdj: [B][n]
   const float* mu;           // kDenseGdAdj: [B]
   float mu_scale;
-  __nv_bfloat16* xo_out;     // kDenseGdAdj / kDenseSpecAdj: next X' [2B][2n], tiled
+  void* xo_out;              // kDenseGdAdj / kDenseSpecAdj: next X' [2B][2n], tiled
   // spectral initialisation
   const float* inv_norm;     // [B]: 1/||u|| of the current iterate
   const float* sumy;         // [B]
@@ -100,28 +131,28 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                : "memory");
 }
 
-__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn(v);
-  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-}
-
 // Position of element (c, k) of a [2B][K] vector operand (X' or W') in its
-// tiled form: per block of 64 columns, the high part's shared-memory image (2B
+// tiled form: per block of VPR columns, the high part's shared-memory image (2B
 // rows of 128 bytes, 128-byte swizzle) followed by the low part's; the low
-// part of an element sits 2B * 64 values after its high part. One stage of the
-// GEMM is then one contiguous copy of 2 * 2B * 128 bytes.
+// part of an element sits 2B * VPR values after its high part. One stage of
+// the GEMM is then one contiguous copy of 2 * 2B * 128 bytes.
+template <int FMT>
 __host__ __device__ __forceinline__ size_t vtile_index(int c, int64_t k, int twoB) {
-  return (size_t)(k / 64) * (size_t)(2 * twoB * 64) + (size_t)c * 64 + (size_t)((((k % 64) / 8) ^ (c % 8)) * 8) +
-         (size_t)(k % 8);
+  constexpr int V = Fmt<FMT>::VPR, C = Fmt<FMT>::VPC;
+  return (size_t)(k / V) * (size_t)(2 * twoB * V) + (size_t)c * V + (size_t)((((k % V) / C) ^ (c % 8)) * C) +
+         (size_t)(k % C);
 }
 
-// Splits v into BF16 high and low parts and stores both at (c, k) of a tiled operand.
-__device__ __forceinline__ void store_split(__nv_bfloat16* t, int twoB, int c, int64_t k, float v) {
-  __nv_bfloat16 h, l;
-  split_bf16(v, h, l);
-  const size_t i = vtile_index(c, k, twoB);
-  t[i] = h;
-  t[i + (size_t)twoB * 64] = l;
+// Splits v into high and low parts and stores both at (c, k) of a tiled operand.
+template <int FMT>
+__device__ __forceinline__ void store_split(void* t, int twoB, int c, int64_t k, float v) {
+  using F = Fmt<FMT>;
+  typename F::El h, l;
+  F::split(v, h, l);
+  typename F::El* te = static_cast<typename F::El*>(t);
+  const size_t i = vtile_index<FMT>(c, k, twoB);
+  te[i] = h;
+  te[i + (size_t)twoB * F::VPR] = l;
 }
 
 // Thread-block-cluster helpers (split-K pairs): barrier over both CTAs, the
@@ -146,8 +177,12 @@ __device__ __forceinline__ void pair_store_i(uint32_t addr, int v) {
 // the K range; after both main loops, rank 1 stores its FP32 sums into rank
 // 0's (drained) stage ring through distributed shared memory, and rank 0 adds
 // them and runs the epilogue.
+template <int FMT>
 __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constant__ GemmArgs a, int stages,
                                                               int split) {
+  using F = Fmt<FMT>;
+  using El = typename F::El;
+  constexpr int kBK = F::VPR;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], done_bar;
   __shared__ uint32_t tmem_slot;
@@ -208,15 +243,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
         const uint32_t fb = smem_addr(&full_bar[s]);
         mbar_arrive_expect_tx(fb, stage_bytes);
         const int kx = (kbeg + (kt + kt0) % KT) * kBK;
-        bulk_load(st, a.a_tiles + ((size_t)tile * (a.K / kBK) + (kx / kBK)) * (kBM * kBK), a_bytes, fb);
-        bulk_load(st + a_bytes, a.b_tiles + (size_t)(kx / kBK) * (2 * N * kBK), 2 * b_bytes, fb);
+        bulk_load(st, static_cast<const El*>(a.a_tiles) + ((size_t)tile * (a.K / kBK) + (kx / kBK)) * (kBM * kBK),
+                  a_bytes, fb);
+        bulk_load(st + a_bytes, static_cast<const El*>(a.b_tiles) + (size_t)(kx / kBK) * (2 * N * kBK), 2 * b_bytes,
+                  fb);
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer: 4 K-steps of 16 per stage, high and low parts
-      const uint32_t idesc = idesc_bf16_f32(kBM, N);
+      // MMA issuer: 4 K-steps of KPM values (32 bytes of each row) per stage,
+      // high and low parts
+      const uint32_t idesc = FMT == SR_DENSE_TF32 ? idesc_tf32_f32(kBM, N) : idesc_bf16_f32(kBM, N);
       for (int kt = 0; kt < KT; ++kt) {
         const int s = kt % stages, round = kt / stages;
         if (!mbar_wait_bounded(smem_addr(&full_bar[s]), (uint32_t)(round & 1))) {
@@ -227,10 +265,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
         const uint32_t st = base + (uint32_t)s * stage_bytes;
         const uint32_t dacc = tmem + (uint32_t)(kt % nacc) * acc_cols;
 #pragma unroll
-        for (int kk = 0; kk < kBK / 16; ++kk) {
+        for (int kk = 0; kk < kBK / F::KPM; ++kk) {
           const uint64_t da = sw128_desc(st + kk * 32);
-          tc_mma_bf16(dacc, da, sw128_desc(st + a_bytes + kk * 32), idesc, (kt >= nacc || kk != 0) ? 1u : 0u);
-          tc_mma_bf16(dacc, da, sw128_desc(st + a_bytes + b_bytes + kk * 32), idesc, 1u);
+          const uint64_t dh = sw128_desc(st + a_bytes + kk * 32), dl = sw128_desc(st + a_bytes + b_bytes + kk * 32);
+          if constexpr (FMT == SR_DENSE_TF32) {
+            tc_mma_tf32(dacc, da, dh, idesc, (kt >= nacc || kk != 0) ? 1u : 0u);
+            tc_mma_tf32(dacc, da, dl, idesc, 1u);
+          } else {
+            tc_mma_bf16(dacc, da, dh, idesc, (kt >= nacc || kk != 0) ? 1u : 0u);
+            tc_mma_bf16(dacc, da, dl, idesc, 1u);
+          }
         }
         tc_commit(smem_addr(&empty_bar[s]));
       }
@@ -314,8 +358,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
           if (q >= nb) continue;
           const int b = c0 + q;
           const float r = fmaf(re[q], re[q], im[q] * im[q]) - a.y[(size_t)b * a.m + row];
-          store_split(a.w_out, N, b, row, r * re[q]);
-          store_split(a.w_out, N, a.B + b, row, r * im[q]);
+          store_split<FMT>(a.w_out, N, b, row, r * re[q]);
+          store_split<FMT>(a.w_out, N, a.B + b, row, r * im[q]);
           float s = r * r;
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -336,8 +380,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
           if (a.weight_mode == SR_WEIGHT_IDENTITY) t = yh;
           else t = yh > 0.f ? fmaxf(1.0f - 1.0f / yh, a.lam) : a.lam;
           t *= a.inv_norm[b];
-          store_split(a.w_out, N, b, row, t * re[q]);
-          store_split(a.w_out, N, a.B + b, row, t * im[q]);
+          store_split<FMT>(a.w_out, N, b, row, t * re[q]);
+          store_split<FMT>(a.w_out, N, a.B + b, row, t * im[q]);
         }
       } else {
         // adjoint: rows 2j (Re A^T) and 2j+1 (Im A^T) sit in neighbouring lanes
@@ -368,10 +412,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_gemm(const __grid_constan
             }
             *xp = xv;
             // next forward operand: X'[b] = (Re x, -Im x), X'[B+b] = (Im x, Re x)
-            store_split(a.xo_out, N, b, 2 * j, xv.x);
-            store_split(a.xo_out, N, b, 2 * j + 1, -xv.y);
-            store_split(a.xo_out, N, a.B + b, 2 * j, xv.y);
-            store_split(a.xo_out, N, a.B + b, 2 * j + 1, xv.x);
+            store_split<FMT>(a.xo_out, N, b, 2 * j, xv.x);
+            store_split<FMT>(a.xo_out, N, b, 2 * j + 1, -xv.y);
+            store_split<FMT>(a.xo_out, N, a.B + b, 2 * j, xv.y);
+            store_split<FMT>(a.xo_out, N, a.B + b, 2 * j + 1, xv.x);
           }
         }
         if (a.mode == kDenseSpecAdj) {
@@ -421,28 +465,30 @@ __global__ void k_dense_inv_norm(const float* __restrict__ part, int count, int 
 }
 
 // X' (tiled, high and low) from x: rows b = (Re x, -Im x), rows B+b = (Im x, Re x).
-__global__ void k_dense_prep_x(const float2* __restrict__ x, int n, int B, __nv_bfloat16* __restrict__ xt) {
+template <int FMT>
+__global__ void k_dense_prep_x(const float2* __restrict__ x, int n, int B, void* __restrict__ xt) {
   const size_t total = (size_t)B * n;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(i / n);
     const int64_t j = (int64_t)(i - (size_t)b * n);
     const float2 v = x[i];
-    store_split(xt, 2 * B, b, 2 * j, v.x);
-    store_split(xt, 2 * B, b, 2 * j + 1, -v.y);
-    store_split(xt, 2 * B, B + b, 2 * j, v.y);
-    store_split(xt, 2 * B, B + b, 2 * j + 1, v.x);
+    store_split<FMT>(xt, 2 * B, b, 2 * j, v.x);
+    store_split<FMT>(xt, 2 * B, b, 2 * j + 1, -v.y);
+    store_split<FMT>(xt, 2 * B, B + b, 2 * j, v.y);
+    store_split<FMT>(xt, 2 * B, B + b, 2 * j + 1, v.x);
   }
 }
 
 // W' (tiled, high and low) from a complex vector w: rows b = Re w, rows B+b = Im w.
-__global__ void k_dense_prep_w(const float2* __restrict__ w, int m, int B, __nv_bfloat16* __restrict__ wt) {
+template <int FMT>
+__global__ void k_dense_prep_w(const float2* __restrict__ w, int m, int B, void* __restrict__ wt) {
   const size_t total = (size_t)B * m;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(i / m);
     const int64_t k = (int64_t)(i - (size_t)b * m);
     const float2 v = w[i];
-    store_split(wt, 2 * B, b, k, v.x);
-    store_split(wt, 2 * B, B + b, k, v.y);
+    store_split<FMT>(wt, 2 * B, b, k, v.x);
+    store_split<FMT>(wt, 2 * B, B + b, k, v.y);
   }
 }
 
@@ -457,15 +503,18 @@ namespace {
 
 struct sr_dense {
   int64_t n = 0, m = 0;
+  int fmt = SR_DENSE_BF16;  // operand format (SR_DENSE_BF16 or SR_DENSE_TF32)
+  int vpr = 64;             // values per 128-byte tile row: 64 (BF16) or 32 (TF32)
+  int eb = 2;               // bytes per operand value
   int device = 0;
   int num_sms = 0;
-  __nv_bfloat16* d_af = nullptr;  // Af [m][2n] as tiles [m/128][2n/64][128][64] (swizzled images)
-  __nv_bfloat16* d_aa = nullptr;  // Aa [2n][m] as tiles [2n/128][m/64][128][64]
+  void* d_af = nullptr;  // Af [m][2n] as tiles [m/128][2n/vpr][128][vpr] (swizzled images)
+  void* d_aa = nullptr;  // Aa [2n][m] as tiles [2n/128][m/vpr][128][vpr]
   int* d_err = nullptr;
   // workspace for B problems
   int B_cap = 0;
-  __nv_bfloat16* d_xt = nullptr;  // X' [2B][2n], tiled high + low (2 * 2B * 2n values)
-  __nv_bfloat16* d_wt = nullptr;  // W' [2B][m], tiled high + low
+  void* d_xt = nullptr;  // X' [2B][2n], tiled high + low (2 * 2B * 2n values)
+  void* d_wt = nullptr;  // W' [2B][m], tiled high + low
   float* d_part = nullptr;                          // [m/128][B]
   float* d_npart = nullptr;                         // [max(2n/128, 64)][B]: norm partials
   float* d_scal = nullptr;                          // [3][B]: sum(y), mu, 1/||u||
@@ -500,7 +549,7 @@ sr_status dense_ws(sr_dense* d, int B) {
   dense_free_ws(d);
   const size_t xs = (size_t)2 * B * 2 * d->n, ws = (size_t)2 * B * d->m;
   cudaError_t e;
-  if ((e = cudaMalloc(&d->d_xt, 2 * xs * 2)) != cudaSuccess || (e = cudaMalloc(&d->d_wt, 2 * ws * 2)) != cudaSuccess ||
+  if ((e = cudaMalloc(&d->d_xt, 2 * xs * d->eb)) != cudaSuccess || (e = cudaMalloc(&d->d_wt, 2 * ws * d->eb)) != cudaSuccess ||
       (e = cudaMalloc(&d->d_part, sizeof(float) * (size_t)std::max<int64_t>(d->m / 128, 64) * B)) != cudaSuccess ||
       (e = cudaMalloc(&d->d_npart, sizeof(float) * (size_t)std::max<int64_t>(2 * d->n / 128, 64) * B)) !=
           cudaSuccess ||
@@ -530,9 +579,9 @@ sr_status check_call(sr_dense* d, int B) {
 }
 
 // One GEMM launch: output rows M (multiple of 128), reduction K (multiple of 64).
-sr_status run_gemm(sr_dense* d, sr::GemmArgs& g, const void* a_op, int64_t M, int64_t K, const __nv_bfloat16* bt,
-                   int B, cudaStream_t s) {
-  g.a_tiles = (const __nv_bfloat16*)a_op;
+sr_status run_gemm(sr_dense* d, sr::GemmArgs& g, const void* a_op, int64_t M, int64_t K, const void* bt, int B,
+                   cudaStream_t s) {
+  g.a_tiles = a_op;
   g.b_tiles = bt;
   g.M = (int)M;
   g.K = (int)K;
@@ -542,12 +591,14 @@ sr_status run_gemm(sr_dense* d, sr::GemmArgs& g, const void* a_op, int64_t M, in
   g.err = d->d_err;
   int stages = 2;
   const size_t smem = gemm_smem(B, &stages);
-  SR_DCUDA(cudaFuncSetAttribute(sr::k_dense_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+  const void* kern = d->fmt == SR_DENSE_TF32 ? (const void*)sr::k_dense_gemm<SR_DENSE_TF32>
+                                              : (const void*)sr::k_dense_gemm<SR_DENSE_BF16>;
+  SR_DCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
            "cudaFuncSetAttribute");
   // Split the K range over a pair of CTAs when the tiles alone would leave
   // SMs idle and twice as many CTAs still fit (the adjoint at n << m).
   const int tiles = (int)(M / sr::kBM);
-  const int split = (2 * tiles <= d->num_sms && (K / sr::kBK) % 2 == 0) ? 2 : 1;
+  const int split = (2 * tiles <= d->num_sms && (K / d->vpr) % 2 == 0) ? 2 : 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(tiles * split));
   cfg.blockDim = dim3(sr::kThreads);
@@ -560,28 +611,61 @@ sr_status run_gemm(sr_dense* d, sr::GemmArgs& g, const void* a_op, int64_t M, in
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = split == 2 ? 1 : 0;
-  SR_DCUDA(cudaLaunchKernelEx(&cfg, sr::k_dense_gemm, g, stages, split), "launch(dense gemm)");
+  void* args[] = {(void*)&g, (void*)&stages, (void*)&split};
+  SR_DCUDA(cudaLaunchKernelExC(&cfg, kern, args), "launch(dense gemm)");
   sr::count_launch();
   return SR_OK;
 }
 
-// Position of element (r, k) of a row-major [rows][K] BF16 matrix in its tiled
-// form: tiles of 128 rows x 64 columns, ordered (r / 128, k / 64), each the
-// exact shared-memory image the MMA reads -- rows of 128 bytes whose 16-byte
-// chunks are permuted by the 128-byte swizzle (chunk c of row r at c ^ (r % 8)).
-size_t tiled_index(int64_t r, int64_t k, int64_t K) {
-  const int64_t tile = (r / sr::kBM) * (K / sr::kBK) + k / sr::kBK;
-  const int64_t rr = r % sr::kBM, kk = k % sr::kBK;
-  const int64_t chunk = (kk / 8) ^ (rr % 8);
-  return (size_t)(tile * sr::kBM * sr::kBK + rr * sr::kBK + chunk * 8 + kk % 8);
+// Position of element (r, k) of a row-major [rows][K] matrix in its tiled
+// form: tiles of 128 rows x vpr columns (one 128-byte row: vpr = 64 BF16 or 32
+// TF32 values), ordered (r / 128, k / vpr), each the exact shared-memory image
+// the MMA reads -- rows of 128 bytes whose 16-byte chunks are permuted by the
+// 128-byte swizzle (chunk c of row r at c ^ (r % 8)).
+size_t tiled_index(int64_t r, int64_t k, int64_t K, int vpr) {
+  const int vpc = vpr / 8;  // values per 16-byte chunk
+  const int64_t tile = (r / sr::kBM) * (K / vpr) + k / vpr;
+  const int64_t rr = r % sr::kBM, kk = k % vpr;
+  const int64_t chunk = (kk / vpc) ^ (rr % 8);
+  return (size_t)(tile * sr::kBM * vpr + rr * vpr + chunk * vpc + kk % vpc);
+}
+
+// Rounds to TF32 (10 fraction bits) to nearest, ties away from zero: the
+// rounding of cvt.rna.tf32.f32, written out on the host.
+uint32_t tf32_rna(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (u & 0x007fffffu) ? 0x7fc00000u : u;  // NaN, +-Inf
+  return (u + 0x1000u) & 0xffffe000u;
 }
 
 sr_status prep_x(sr_dense* d, const float2* x, int B, cudaStream_t s) {
   const size_t total = (size_t)B * d->n;
-  sr::k_dense_prep_x<<<(unsigned)std::min<size_t>(4096, (total + 255) / 256), 256, 0, s>>>(x, (int)d->n, B, d->d_xt);
+  const unsigned grid = (unsigned)std::min<size_t>(4096, (total + 255) / 256);
+  if (d->fmt == SR_DENSE_TF32) sr::k_dense_prep_x<SR_DENSE_TF32><<<grid, 256, 0, s>>>(x, (int)d->n, B, d->d_xt);
+  else sr::k_dense_prep_x<SR_DENSE_BF16><<<grid, 256, 0, s>>>(x, (int)d->n, B, d->d_xt);
   sr::count_launch();
   SR_DCUDA(cudaGetLastError(), "launch(dense prep x)");
   return SR_OK;
+}
+
+// Af and Aa of a row-major complex m x n matrix (interleaved re, im), as
+// tiled host images of element type El, with round(.) applied to every entry.
+template <class El, class Round>
+void tile_matrix(const float* a_host, int64_t n, int64_t m, int vpr, Round round, std::vector<El>& af,
+                 std::vector<El>& aa) {
+  const size_t cnt = (size_t)m * n * 2;
+  af.assign(cnt, El());
+  aa.assign(cnt, El());
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      const El re = round(a_host[(i * n + j) * 2]);
+      const El im = round(a_host[(i * n + j) * 2 + 1]);
+      af[tiled_index(i, 2 * j, 2 * n, vpr)] = re;
+      af[tiled_index(i, 2 * j + 1, 2 * n, vpr)] = im;
+      aa[tiled_index(2 * j, i, m, vpr)] = re;
+      aa[tiled_index(2 * j + 1, i, m, vpr)] = im;
+    }
 }
 
 }  // namespace
@@ -589,32 +673,36 @@ sr_status prep_x(sr_dense* d, const float2* x, int B, cudaStream_t s) {
 extern "C" {
 
 sr_status sr_dense_create(int64_t n, int64_t m, const float* a_host, sr_dense** out) {
+  return sr_dense_create_format(n, m, a_host, SR_DENSE_BF16, out);
+}
+
+sr_status sr_dense_create_format(int64_t n, int64_t m, const float* a_host, int format, sr_dense** out) {
   if (!out || !a_host) return dfail(SR_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
+  if (format != SR_DENSE_BF16 && format != SR_DENSE_TF32) return dfail(SR_ERR_INVALID_ARG, "unknown dense format");
   if (n < 64 || m < 128 || n % 64 != 0 || m % 128 != 0 || n > (1 << 20) || m > (1 << 22) || n > m)
     return dfail(SR_ERR_UNSUPPORTED, "dense model: n a multiple of 64, m a multiple of 128, 64 <= n <= m");
   sr_dense* d = new (std::nothrow) sr_dense();
   if (!d) return dfail(SR_ERR_OOM, "host allocation failed");
   d->n = n;
   d->m = m;
+  d->fmt = format;
+  d->vpr = format == SR_DENSE_TF32 ? 32 : 64;
+  d->eb = format == SR_DENSE_TF32 ? 4 : 2;
   cudaError_t e = cudaGetDevice(&d->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d->num_sms, cudaDevAttrMultiProcessorCount, d->device);
-  const size_t cnt = (size_t)m * n * 2;
-  std::vector<__nv_bfloat16> af(cnt), aa(cnt);
-  for (int64_t i = 0; i < m; ++i)
-    for (int64_t j = 0; j < n; ++j) {
-      const __nv_bfloat16 re = __float2bfloat16_rn(a_host[(i * n + j) * 2]);
-      const __nv_bfloat16 im = __float2bfloat16_rn(a_host[(i * n + j) * 2 + 1]);
-      af[tiled_index(i, 2 * j, 2 * n)] = re;
-      af[tiled_index(i, 2 * j + 1, 2 * n)] = im;
-      aa[tiled_index(2 * j, i, m)] = re;
-      aa[tiled_index(2 * j + 1, i, m)] = im;
-    }
-  if (e == cudaSuccess) e = cudaMalloc(&d->d_af, cnt * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&d->d_aa, cnt * 2);
+  const size_t cnt = (size_t)m * n * 2, bytes = cnt * (size_t)d->eb;
+  std::vector<__nv_bfloat16> af16, aa16;
+  std::vector<uint32_t> af32, aa32;
+  if (format == SR_DENSE_TF32) tile_matrix(a_host, n, m, d->vpr, tf32_rna, af32, aa32);
+  else tile_matrix(a_host, n, m, d->vpr, [](float v) { return __float2bfloat16_rn(v); }, af16, aa16);
+  const void* af = format == SR_DENSE_TF32 ? (const void*)af32.data() : (const void*)af16.data();
+  const void* aa = format == SR_DENSE_TF32 ? (const void*)aa32.data() : (const void*)aa16.data();
+  if (e == cudaSuccess) e = cudaMalloc(&d->d_af, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&d->d_aa, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&d->d_err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemcpy(d->d_af, af.data(), cnt * 2, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d->d_aa, aa.data(), cnt * 2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d->d_af, af, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d->d_aa, aa, bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(d->d_err, 0, sizeof(int));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -655,8 +743,11 @@ sr_status sr_dense_adjoint(sr_dense* d, const void* w, void* x, int B, void* str
   if (!x || !w) return dfail(SR_ERR_INVALID_ARG, "NULL array argument");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t total = (size_t)B * d->m;
-  sr::k_dense_prep_w<<<(unsigned)std::min<size_t>(4096, (total + 255) / 256), 256, 0, s>>>(
-      (const float2*)w, (int)d->m, B, d->d_wt);
+  const unsigned grid = (unsigned)std::min<size_t>(4096, (total + 255) / 256);
+  if (d->fmt == SR_DENSE_TF32)
+    sr::k_dense_prep_w<SR_DENSE_TF32><<<grid, 256, 0, s>>>((const float2*)w, (int)d->m, B, d->d_wt);
+  else
+    sr::k_dense_prep_w<SR_DENSE_BF16><<<grid, 256, 0, s>>>((const float2*)w, (int)d->m, B, d->d_wt);
   sr::count_launch();
   SR_DCUDA(cudaGetLastError(), "launch(dense prep w)");
   sr::GemmArgs g;

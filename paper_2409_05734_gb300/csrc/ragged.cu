@@ -571,7 +571,10 @@ sr_status sr_ragged_create(int count, const int64_t* n, const int64_t* m, const 
       sr_ragged_destroy(r);
       return rfail(SR_ERR_CUDA, "stream or event creation failed");
     }
-    if (autotune && (st = sr_plan_autotune(b.plan, B, b.stream)) != SR_OK) {
+    // (buckets of the queue-driven group run on that group's own tile
+    // geometry and grid, so only the others are tuned; tuning must not move a
+    // bucket out of the group by choosing a split the group does not cover)
+    if (autotune && !fusable(b.plan) && (st = sr_plan_autotune(b.plan, B, b.stream)) != SR_OK) {
       sr_ragged_destroy(r);
       return st;
     }

@@ -13,10 +13,18 @@ from . import _lib
 from .plan import _p, _stream_handle
 
 
-class DenseModel:
-    """Dense A in C^{m x n} (the caller's entries rounded once to BF16)."""
+FORMATS = {"bf16": 0, "tf32": 1}
 
-    def __init__(self, A: np.ndarray, device=None):
+
+class DenseModel:
+    """Dense A in C^{m x n}, the caller's entries rounded once to the operand
+    format: "bf16" (to nearest even, tcgen05 kind::f16) or "tf32" (10 fraction
+    bits, to nearest with ties away from zero, tcgen05 kind::tf32)."""
+
+    def __init__(self, A: np.ndarray, device=None, format: str = "bf16"):
+        if format not in FORMATS:
+            raise ValueError(f"format must be one of {sorted(FORMATS)}")
+        self.format = format
         A = np.asarray(A)
         if A.ndim != 2 or not np.iscomplexobj(A):
             raise ValueError("A must be a complex [m, n] array")
@@ -27,8 +35,8 @@ class DenseModel:
         self.device = dev
         h = C.c_void_p()
         with torch.cuda.device(dev):
-            _lib.check(self._lib.sr_dense_create(self.n, self.m, host.ctypes.data_as(C.c_void_p), C.byref(h)),
-                       "sr_dense_create")
+            _lib.check(self._lib.sr_dense_create_format(self.n, self.m, host.ctypes.data_as(C.c_void_p),
+                                                        FORMATS[format], C.byref(h)), "sr_dense_create_format")
         self._h = h
 
     def close(self):

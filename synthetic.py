@@ -180,6 +180,23 @@ def dense_iid_matrix_bf16(seed: int, m: int, n: int) -> np.ndarray:
     return round_to_bf16(A.real) + 1j * round_to_bf16(A.imag)
 
 
+def round_to_tf32(a: np.ndarray) -> np.ndarray:
+    """Rounding of float values to the TF32 grid (11-bit significand: 10
+    fraction bits) to nearest with ties away from zero, returned as float64.
+    Defines a dense matrix whose entries are exactly representable in TF32
+    (the stored form of the TF32 dense comparison model)."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    with np.errstate(over="ignore"):
+        r = (u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)
+    return r.view(np.float32).astype(np.float64)
+
+
+def dense_iid_matrix_tf32(seed: int, m: int, n: int) -> np.ndarray:
+    """CN(0, 1/m) dense matrix with real and imaginary parts on the TF32 grid: [m, n]."""
+    A = dense_iid_matrix(seed, m, n)
+    return round_to_tf32(A.real) + 1j * round_to_tf32(A.imag)
+
+
 def gaussian_noise(seed: int, shape, sigma) -> np.ndarray:
     """Real N(0, sigma^2) noise via Box-Muller (real part of a CN(0, 2) draw)."""
     g = complex_gaussian(seed, shape, STREAM_NOISE, var=2.0)

@@ -85,3 +85,20 @@ def test_round_to_bf16_grid():
     assert np.isclose(r[5], 3.0e-3, rtol=2 ** -8) and (m * 2 ** 8) == np.round(m * 2 ** 8)
     A = S.dense_iid_matrix_bf16(1, 64, 32)
     assert np.array_equal(S.round_to_bf16(A.real), A.real)
+
+
+def test_round_to_tf32_grid():
+    # exactly representable values are kept; others go to the nearest 11-bit significand
+    # (10 fraction bits), ties away from zero
+    vals = np.array([1.0, -2.5, 1.0 + 2 ** -11, 1.0 + 3 * 2 ** -11, -(1.0 + 2 ** -11), 1.0 + 2 ** -12, 3.0e-3])
+    r = S.round_to_tf32(vals)
+    assert r[0] == 1.0 and r[1] == -2.5
+    assert r[2] == 1.0 + 2 ** -10      # halfway between 1 and 1 + 2^-10: away from zero
+    assert r[3] == 1.0 + 2 ** -9       # halfway between 1 + 2^-10 and 1 + 2^-9: away from zero
+    assert r[4] == -(1.0 + 2 ** -10)   # negative ties move away from zero too
+    assert r[5] == 1.0
+    m, e = np.frexp(r[6])
+    assert np.isclose(r[6], 3.0e-3, rtol=2 ** -11) and (m * 2 ** 11) == np.round(m * 2 ** 11)
+    A = S.dense_iid_matrix_tf32(1, 64, 32)
+    assert np.array_equal(S.round_to_tf32(A.imag), A.imag)
+    assert np.max(np.abs(A - S.dense_iid_matrix(1, 64, 32))) <= 2 ** -11 * np.max(np.abs(A))
