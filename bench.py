@@ -578,14 +578,16 @@ def timed_graph(torch, fn, flush, reps=3):
 
 def radix3_workload(torch, dev, flush):
     """The oversampling ratios 1.5, 3 and 6 of the recovery sweep (m = 3 * 2^a):
-    n = 2^16, L = 2, B = 8 noiseless problems, 20 power + 100 GD iterations."""
+    n = 2^16, L = 2, B = 32 noiseless problems (the sweep's trials per cell),
+    20 power + 100 GD iterations."""
     from paper_2409_05734_gb300 import Plan
     import synthetic as S
     out = {}
-    n, L, B, sp, gd = 2 ** 16, 2, 8, 20, 100
+    n, L, B, sp, gd = 2 ** 16, 2, 32, 20, 100
     for alpha, m in ((1.5, 3 * 2 ** 15), (3, 3 * 2 ** 16), (6, 3 * 2 ** 17)):
         plan = Plan(n, m, L, 31)
         plan.reserve(B)
+        plan.autotune(B)
         x_true = torch.from_numpy(S.signal_gaussian(31, B, n)).to(torch.complex64).to(dev)
         y = (plan.forward(x_true).abs() ** 2).contiguous()
         v0 = torch.from_numpy(S.start_vector(31, B, n)).to(torch.complex64).to(dev)
@@ -598,12 +600,13 @@ def radix3_workload(torch, dev, flush):
         ms = timed_graph(torch, solve, flush)
         it = sp + gd
         W = dict(n=n, m=m, L=L, B=B)
-        out[f"alpha={alpha}"] = {"m": m, "ms_per_solve": ms, "problem_iters_per_s": B * it / (ms / 1e3),
+        out[f"alpha={alpha}"] = {"m": m, "split": list(plan.tuning[:2]), "ms_per_solve": ms,
+                                 "problem_iters_per_s": B * it / (ms / 1e3),
                                  "algorithmic_gbs": iteration_bytes(W) * it / (ms / 1e3) / 1e9}
         plan.check()
         del plan
     return {"workload": f"n = 2^16, L = {L}, B = {B}, x ~ CN(0, I), noiseless, {sp} power + {gd} GD iterations; "
-                        "m = 3 * 2^a runs each DFT as a power-of-two DFT of 3B stride-3 subsequences (gathered by its first pass) -> radix-3 combine",
+                        "m = 3 * 2^a runs on the four-step passes with radix-3 lines (192, 384 or 768 points: a radix-3 step inside the line FFT); autotuned split and grid",
             **out}
 
 

@@ -4,6 +4,7 @@
 // orchestration of the pass kernels into the operator applications and solver
 // loops of the paper (Sec. II-B, Sec. III).
 #include <algorithm>
+#include <numeric>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -283,7 +284,9 @@ sr_status set_split(Plan* p, int m1) {
   }
   p->m1 = m1;
   p->m2 = m2;
-  p->lmax = std::max(m1, m2);
+  // one line-twiddle table W_lmax serves both line lengths: lmax = lcm(m1, m2)
+  // (the longer line for powers of two, 3 x the longer power for radix-3 lines)
+  p->lmax = (int)std::lcm((int64_t)m1, (int64_t)m2);
   for (int lay = 0; lay < 2; ++lay) {
     p->geom[lay] = g[lay];
     std::memcpy(p->per_sm_mid[lay], mid[lay], sizeof(mid[lay]));
@@ -814,8 +817,47 @@ sr_status create_plan(int64_t n, int64_t m, int L, uint64_t seed, int gh, int gw
     delete p;
     return cuda_fail(e, "cudaGetDevice");
   }
-  if (is_three_pow2(m)) {
-    // m = 3 mp: the power-of-two DFTs run on an inner plan of length mp
+  // m = 3 * 2^a: lines of 192, 384 or 768 points (a radix-3 step inside the
+  // line FFT) against power-of-two lines of 16 .. 4096 points, the most
+  // balanced split the pass kernels cover
+  std::vector<int> r3_splits;
+  if (is_three_pow2(m) && gS == 0) {
+    std::vector<std::pair<double, int>> c;
+    for (int r : {192, 384, 768}) {
+      if (m % r != 0 || !is_pow2(m / r) || m / r < 16 || m / r > 4096) continue;
+      const int q = (int)(m / r);
+      const double bal = std::fabs(std::log2((double)r / (double)q));
+      c.push_back({bal, r});
+      c.push_back({bal + 1e-3, q});  // the same lines, radix-3 ones in layout Y
+    }
+    std::sort(c.begin(), c.end());
+    for (auto& e2 : c) r3_splits.push_back(e2.second);
+  }
+  bool r3_lines = false;
+  if (!r3_splits.empty()) {
+    const int a = ilog2(m);
+    p->tw_shift = (a + 1) / 2;
+    e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
+    for (int m1 : r3_splits)
+      if (set_split(p, m1) == SR_OK) {
+        r3_lines = true;
+        break;
+      }
+    if (r3_lines && (st = upload_twiddles(p)) != SR_OK) {
+      sr_plan_destroy(p);
+      return st;
+    }
+    if (!r3_lines) sr::set_last_error("");
+  }
+  if (r3_lines) {
+    // (set up above)
+  } else if (is_three_pow2(m)) {
+    // m = 3 mp without a radix-3 line split: the power-of-two DFTs run on an
+    // inner plan of length mp
     p->mp = m / 3;
     p->r3_chunks = (int)std::min<int64_t>(256, std::max<int64_t>(1, p->mp / 1024));
     sr_plan* in = nullptr;

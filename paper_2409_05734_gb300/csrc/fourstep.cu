@@ -159,10 +159,17 @@ LineGeom make_geom(int64_t m, int ell) {
   g.ell = ell;
   g.nl = (int)(m / ell);
   const int E = ell < 16 ? ell : 16;
-  g.P = ell / E;
-  int T = std::max(8, 256 / g.P);
-  T = std::min(T, pass_threads(ell) / g.P);
+  g.P = ell / E;  // threads per line
+  int T;
+  if (ell % 3 == 0) {
+    T = ell == 768 ? 8 : 16;  // the radix-3 tile shapes: 384 threads (192 for lines of 192)
+  } else {
+    T = std::max(8, 256 / g.P);
+    T = std::min(T, pass_threads(ell) / g.P);
+  }
   T = std::min(T, g.nl);
+  while (T & (T - 1)) T &= T - 1;          // a power of two
+  while (T > 1 && g.nl % T != 0) T >>= 1;  // tiles of whole lines (3 * 2^a lines in the other layout)
   while (T > 1 && pipe_layout(ell, T, 1, true).total + 1024 > kSmemBudget) T >>= 1;
   g.T = T;
   g.lgT = 0;

@@ -65,7 +65,8 @@ sr_status sr_forward_noalloc(const sr_plan* plan_in, const void* x, void* z, int
   const sr::Plan* plan = reinterpret_cast<const sr::Plan*>(plan_in);
   if (!plan || !x || !z) return noalloc_fail(SR_ERR_INVALID_ARG, "NULL argument");
   if (B < 1) return noalloc_fail(SR_ERR_INVALID_ARG, "B must be >= 1");
-  if (plan->inner) return noalloc_fail(SR_ERR_UNSUPPORTED, "only power-of-two m is supported");
+  if (plan->inner || (plan->m & (plan->m - 1)) != 0)
+    return noalloc_fail(SR_ERR_UNSUPPORTED, "only power-of-two m is supported");
   if (plan->two_d) return noalloc_fail(SR_ERR_UNSUPPORTED, "2D plans are not supported");
   if (plan->mo < plan->m) return noalloc_fail(SR_ERR_UNSUPPORTED, "m < n is not supported");
   // A plan with per-problem phases holds diagonal tables for exactly

@@ -37,15 +37,31 @@ __host__ __device__ constexpr bool uses_tma(int ell, int T) { return ell >= 16 &
 // NL = m / ELL when it is fixed at compile time (specialised kernels for the
 // most used lengths: every per-slot offset of the natural-order and exchange
 // accesses then folds into an immediate), or 0 to read it from the arguments.
+//
+// Lines of ELL = 3 M points (M a power of two: the radix-3 lengths m = 3 * 2^a)
+// are three interleaved sub-lines of M points with one radix-3 step: thread
+// (t, p, rho) holds 16 points of sub-line rho (P threads per sub-line, 3P per
+// line). Two slot orders exist per thread, for slot j < 16:
+//   block order     position p + rho M + j P            (BSTR = P)
+//   stride-3 order  position 3 (p + j P) + rho          (SSTR = 3 P)
+// A radix-3 line FFT by decimation in time (fft_s3_to_blk) takes its input in
+// stride-3 order and leaves the output in block order; by decimation in
+// frequency (fft_blk_to_s3) the other way round. Power-of-two lines have one
+// order, p + j P, for both (R = 1, rho = 0).
 template <int ELL, int T_, int NLC_ = 0>
 struct Tile {
+  static constexpr bool R3 = (ELL % 3 == 0);
+  static constexpr int R = R3 ? 3 : 1;         // sub-lines per line
+  static constexpr int M = ELL / R;            // points per sub-line (a power of two)
   static constexpr int T = T_;
   static constexpr int NLC = NLC_;
-  static constexpr int E = LineShape<ELL>::E, P = LineShape<ELL>::P;
-  static constexpr int THREADS = T * P;
+  static constexpr int E = LineShape<M>::E, P = LineShape<M>::P;  // P: threads per sub-line
+  static constexpr int PL = R * P;             // threads per line
+  static constexpr int BSTR = P, SSTR = R * P; // slot strides of the block and stride-3 orders
+  static constexpr int THREADS = T * PL;
   static constexpr bool TMA = uses_tma(ELL, T);
   static constexpr int BOX = T * 128;  // bytes of one box: 16 complex values x T rows
-  static constexpr int MIN_CTAS = THREADS <= 256 ? 3 : 1;
+  static constexpr int MIN_CTAS = THREADS <= 256 ? 3 : THREADS <= 384 ? 2 : 1;
   static_assert(THREADS <= 512, "tile too large");
   static_assert(NLC == 0 || NLC % T == 0, "lines per CTA must divide the line count");
   __device__ __forceinline__ static int nl(const PassArgs& a) { return NLC ? NLC : a.nl; }
@@ -57,18 +73,29 @@ struct Tile {
   }
 };
 
-// Thread coordinates (line t, butterfly column p) with their ranges stated to
-// the compiler, which lets it fold the per-slot index arithmetic (padding,
-// swizzle, Stockham positions) into immediate offsets.
+// Thread coordinates (line t, butterfly column p, sub-line rho) with their
+// ranges stated to the compiler, which lets it fold the per-slot index
+// arithmetic (padding, swizzle, Stockham positions) into immediate offsets.
 template <class TL>
-__device__ __forceinline__ void thread_coords(int& t, int& p) {
+__device__ __forceinline__ void thread_coords(int& t, int& p, int& rho) {
   const int tid = threadIdx.x;
   __builtin_assume(tid >= 0 && tid < TL::THREADS);
   t = tid % TL::T;
-  p = tid / TL::T;
+  const int pl = tid / TL::T;
+  __builtin_assume(pl >= 0 && pl < TL::PL);
+  p = TL::R3 ? pl % TL::P : pl;
+  rho = TL::R3 ? pl / TL::P : 0;
   __builtin_assume(t >= 0 && t < TL::T);
   __builtin_assume(p >= 0 && p < TL::P);
+  __builtin_assume(rho >= 0 && rho < TL::R);
 }
+
+// First position of this thread's slots in block order (stride BSTR) and in
+// stride-3 order (stride SSTR); equal for power-of-two lines.
+template <class TL>
+__device__ __forceinline__ int blk0(int p, int rho) { return p + rho * TL::M; }
+template <class TL>
+__device__ __forceinline__ int s30(int p, int rho) { return TL::R * p + rho; }
 
 // ------------------------------------------------------ shared-memory layout
 struct PipeSmem {
@@ -120,9 +147,81 @@ __device__ __forceinline__ void load_line_twiddles(const PassArgs& a, float2* tw
   for (int i = threadIdx.x; i < ELL; i += blockDim.x) tw[i] = __ldg(&a.twl[i * a.tws]);
 }
 
-// The four-step twiddle of (line g, frequency f = p + j*P) is
-// W_m^(g p) * W_m^(g P j); the second factor is tabulated per tile,
-// rowtw[j*T + t] = W_m^((g0 + t) P j). RowTw holds this thread's entries of
+// ------------------------------------------------------------ line FFTs
+
+// W_3^(k mod 3) in the transform's sign (forward exp(-2 pi i / 3); the
+// inverse conjugates), for k = 0 .. 4.
+template <int DIR>
+__device__ __forceinline__ float2 root3(int k) {
+  constexpr float kS3 = 0.86602540378443864676f;  // sqrt(3) / 2
+  const int r = k % 3;
+  const float s = DIR > 0 ? kS3 : -kS3;
+  return r == 0 ? make_float2(1.f, 0.f) : make_float2(-0.5f, r == 1 ? s : -s);
+}
+
+// Unnormalised DFT of the T lines of a tile, input slots in stride-3 order,
+// output slots in block order. Radix-3 lines by decimation in time: with
+// u_r[j] = x[3 j + r] and U_r = DFT_M(u_r) (one sub-line each),
+//   X[k + s M] = sum_r W_ELL^(r k) W_3^(r s) U_r[k],   k < M, s < 3;
+// thread (t, p, rho) forms the outputs s = rho of its k = p + j P, reading the
+// three U_r[k] from the scratch. tw: table of W_ELL (entry i * TWS).
+template <class TL, int DIR, int TWS>
+__device__ __forceinline__ void fft_s3_to_blk(float2 (&v)[TL::E], float2* sm, int p, int rho, int t,
+                                              const float2* tw) {
+  if constexpr (!TL::R3) {
+    line_fft<TL::M, TL::T, DIR, TWS>(v, sm, p, t, tw);
+  } else {
+    constexpr int T = TL::T, T3 = 3 * TL::T, P = TL::P;
+    line_fft<TL::M, T3, DIR, 3 * TWS>(v, sm, p, t + T * rho, tw);
+    __syncthreads();  // the sub-line FFTs' last scratch reads are done
+#pragma unroll
+    for (int j = 0; j < TL::E; ++j) sm[sidx<T3>(p + j * P, t + T * rho)] = v[j];
+    __syncthreads();
+    const float2 c1 = root3<DIR>(rho), c2 = root3<DIR>(2 * rho);
+#pragma unroll
+    for (int j = 0; j < TL::E; ++j) {
+      const int k = p + j * P;
+      const float2 u0 = sm[sidx<T3>(k, t)];
+      const float2 u1 = mul_root<DIR>(sm[sidx<T3>(k, t + T)], tw[k * TWS]);
+      const float2 u2 = mul_root<DIR>(sm[sidx<T3>(k, t + 2 * T)], tw[2 * k * TWS]);
+      v[j] = padd(u0, padd(cmul(u1, c1), cmul(u2, c2)));
+    }
+  }
+}
+
+// Unnormalised DFT of the T lines of a tile, input slots in block order,
+// output slots in stride-3 order. Radix-3 lines by decimation in frequency:
+//   X[3 k + s] = DFT_M(u_s)[k],  u_s[k] = W_ELL^(k s) sum_r W_3^(r s) x[k + r M];
+// thread (t, p, rho) forms u_rho at its k = p + j P from the three block
+// values read from the scratch, then the sub-line FFT. The caller
+// synchronises before the call if the scratch was in use.
+template <class TL, int DIR, int TWS>
+__device__ __forceinline__ void fft_blk_to_s3(float2 (&v)[TL::E], float2* sm, int p, int rho, int t,
+                                              const float2* tw) {
+  if constexpr (TL::R3) {
+    constexpr int T = TL::T, T3 = 3 * TL::T, P = TL::P;
+#pragma unroll
+    for (int j = 0; j < TL::E; ++j) sm[sidx<T3>(p + j * P, t + T * rho)] = v[j];
+    __syncthreads();
+    const float2 c1 = root3<DIR>(rho), c2 = root3<DIR>(2 * rho);
+#pragma unroll
+    for (int j = 0; j < TL::E; ++j) {
+      const int k = p + j * P;
+      const float2 x0 = sm[sidx<T3>(k, t)], x1 = sm[sidx<T3>(k, t + T)], x2 = sm[sidx<T3>(k, t + 2 * T)];
+      const float2 u = padd(x0, padd(cmul(x1, c1), cmul(x2, c2)));
+      v[j] = mul_root<DIR>(u, tw[rho * k * TWS]);
+    }
+    __syncthreads();  // every block value read before the sub-line FFT writes the scratch
+    line_fft<TL::M, T3, DIR, 3 * TWS>(v, sm, p, t + T * rho, tw);
+  } else {
+    line_fft<TL::M, TL::T, DIR, TWS>(v, sm, p, t, tw);
+  }
+}
+
+// The four-step twiddle of (line g, frequency f = f0 + j*SSTR), f0 the
+// thread's first stride-3-order position (p for power-of-two lines), is
+// W_m^(g f0) * W_m^(g SSTR j); the second factor is tabulated per tile,
+// rowtw[j*T + t] = W_m^((g0 + t) SSTR j). RowTw holds this thread's entries of
 // the table between their (early) load and their (late) store to shared memory.
 template <class TL>
 struct RowTw {
@@ -132,7 +231,7 @@ struct RowTw {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       const int i = threadIdx.x + k * TL::THREADS;
-      if (i < TL::E * TL::T) w[k] = tw_m<TL>(a, (g0 + i % TL::T) * TL::P * (i / TL::T), dir);
+      if (i < TL::E * TL::T) w[k] = tw_m<TL>(a, (g0 + i % TL::T) * TL::SSTR * (i / TL::T), dir);
     }
   }
   __device__ __forceinline__ void store(float2* rowtw) const {
@@ -144,17 +243,18 @@ struct RowTw {
   }
 };
 
-// Step-1 outputs of line g times the four-step twiddles (already conjugated
-// for an inverse transform), stored to the exchange buffer at f*NL + g
-// (T consecutive elements per frequency across the warp).
+// Step-1 outputs of line g (slots in stride-3 order from f0) times the
+// four-step twiddles (already conjugated for an inverse transform), stored to
+// the exchange buffer at f*NL + g (T consecutive elements per frequency across
+// the warp).
 template <class TL>
-__device__ __forceinline__ void twiddle_store(float2 (&v)[TL::E], const PassArgs& a, int b, int g, int t, int p,
+__device__ __forceinline__ void twiddle_store(float2 (&v)[TL::E], const PassArgs& a, int b, int g, int t, int f0,
                                               float2 A, const float2* rowtw) {
   float2* eb = a.eout + (size_t)b * TL::m(a) + g;
 #pragma unroll
   for (int j = 0; j < TL::E; ++j) {
     const float2 w = cmul(A, rowtw[j * TL::T + t]);
-    eb[(size_t)(p + j * TL::P) * TL::nl(a)] = cmul(v[j], w);
+    eb[(size_t)(f0 + j * TL::SSTR) * TL::nl(a)] = cmul(v[j], w);
   }
 }
 
@@ -167,26 +267,28 @@ template <class TL>
 struct OpData {
   float y[TL::E];
   float vscale = 1.0f;  // spectral epilogue: 1/||u|| of the current iterate (when applied here)
-  __device__ __forceinline__ void load_y(const PassArgs& a, int op, int b, int g, int p) {
+  // q0: the thread's first block-order position (slot j at q0 + j*BSTR)
+  __device__ __forceinline__ void load_y(const PassArgs& a, int op, int b, int g, int q0) {
     if (op == kOpGdEpilogue || op == kOpSpecEpilogue) {
       const float* yb = a.y + (size_t)b * TL::m(a) + g;
 #pragma unroll
-      for (int j = 0; j < TL::E; ++j) y[j] = __ldg(&yb[(p + j * TL::P) * TL::nl(a)]);
+      for (int j = 0; j < TL::E; ++j) y[j] = __ldg(&yb[(q0 + j * TL::BSTR) * TL::nl(a)]);
     }
   }
 };
 
+// The operation at natural index (q0 + j*BSTR)*NL + g of slot j (block order).
 template <class TL, bool EPI = true, bool DIAG = true>
 __device__ __forceinline__ void apply_op(float2 (&v)[TL::E], const PassArgs& a, const OpData<TL>& od, int b, int g,
-                                         int p, fsum2& acc) {
+                                         int q0, fsum2& acc) {
   if (DIAG && a.op == kOpDiag) {
     const float2* dp = a.dp + (size_t)b * a.dp_stride;
 #pragma unroll
-    for (int j = 0; j < TL::E; ++j) v[j] = cmul(v[j], __ldg(&dp[(p + j * TL::P) * TL::nl(a) + g]));
+    for (int j = 0; j < TL::E; ++j) v[j] = cmul(v[j], __ldg(&dp[(q0 + j * TL::BSTR) * TL::nl(a) + g]));
   } else if (DIAG && a.op == kOpDiagConj) {
     const float2* dp = a.dp + (size_t)b * a.dp_stride;
 #pragma unroll
-    for (int j = 0; j < TL::E; ++j) v[j] = cmulc(v[j], __ldg(&dp[(p + j * TL::P) * TL::nl(a) + g]));
+    for (int j = 0; j < TL::E; ++j) v[j] = cmulc(v[j], __ldg(&dp[(q0 + j * TL::BSTR) * TL::nl(a) + g]));
   } else if (EPI && a.op == kOpGdEpilogue) {
     // z -> r = |z|^2 - y, w = r z (Eq. 2); loss partial sum of r^2
 #pragma unroll
@@ -238,11 +340,20 @@ struct TileScalars {
 // swz128_offset(BOX, t, p + j*P) as a per-thread base plus a per-slot
 // constant: for P >= 16 the slot only moves the box; for P < 16 it adds
 // (j*P) & 15 to the 16-byte chunk index, whose bits are disjoint from p's.
+// Radix-3 lines: slot j is position q = s30 + j*SSTR (stride-3 order), at
+// byte (q / 16) * BOX + t * 128 + ((q % 16) * 8 ^ (t % 8) * 16).
 template <class TL>
-__device__ __forceinline__ void load_staged(const unsigned char* src, int t, int p, float2 (&v)[TL::E]) {
+__device__ __forceinline__ void load_staged(const unsigned char* src, int t, int p, int rho, float2 (&v)[TL::E]) {
   constexpr int E = TL::E, P = TL::P;
   const int t7 = t & 7;
-  if constexpr (P >= 16) {
+  if constexpr (TL::R3) {
+    const int q0 = s30<TL>(p, rho);
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int q = q0 + j * TL::SSTR;
+      v[j] = *reinterpret_cast<const float2*>(src + (q >> 4) * TL::BOX + t * 128 + (((q & 15) << 3) ^ (t7 << 4)));
+    }
+  } else if constexpr (P >= 16) {
     const unsigned char* base = src + (p >> 4) * TL::BOX + t * 128 + (((p & 15) << 3) ^ (t7 << 4));
 #pragma unroll
     for (int j = 0; j < E; ++j) v[j] = *reinterpret_cast<const float2*>(base + j * (P / 16) * TL::BOX);
@@ -261,15 +372,16 @@ __device__ __forceinline__ void load_staged(const unsigned char* src, int t, int
 // four-step twiddles, into the exchange buffer. tw: line twiddles, entry
 // k * TWS = W_ELL^k. The caller synchronises before the next tile.
 template <class TL, int DB, int MAP, int TWS>
-__device__ __forceinline__ void first_tile(const PassArgs& a, int b, int g0, int t, int p, float2* scratch,
+__device__ __forceinline__ void first_tile(const PassArgs& a, int b, int g0, int t, int p, int rho, float2* scratch,
                                            const float2* tw, float2* rowtw, TileScalars& sh) {
-  constexpr int E = TL::E, P = TL::P, T = TL::T, ELL = TL::E * TL::P;
+  constexpr int E = TL::E, P = TL::P, T = TL::T;
+  const int q0 = blk0<TL>(p, rho), f0 = s30<TL>(p, rho);
   const int tid = threadIdx.x;
   const int g = g0 + t;
   RowTw<TL> rw;
   rw.load(a, g0, DB);
   rw.store(rowtw);
-  const float2 A = tw_m<TL>(a, g * p, DB);
+  const float2 A = tw_m<TL>(a, g * f0, DB);
   // Radix-3 lengths (a.r3): inner problem b = 3 bo + r holds the stride-3
   // subsequence r of outer problem bo (element 3 nat + r), and the operation
   // that precedes this DFT is applied at that outer natural index.
@@ -278,17 +390,18 @@ __device__ __forceinline__ void first_tile(const PassArgs& a, int b, int g0, int
     sh.scale = a.norm_in ? 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)bo * a.norm_in_count, a.norm_in_count))
                          : 1.0f;
   // Natural-order input, zero beyond n_in (the padding U): element (line g,
-  // position q) is x[q*NL + g]; the warp reads T consecutive elements.
+  // position q) is x[q*NL + g], slot j at q = q0 + j*P (block order); the
+  // warp reads T consecutive elements.
   const float2* xb = a.xin + (size_t)bo * a.n_in;
   // (2D grids: the signal entry at grid_index, tables at the layout index nat)
   float2 v[E];
   int idx[E];
 #pragma unroll
   for (int j = 0; j < E; ++j) {
-    const int nat = (p + j * P) * TL::nl(a) + g;
+    const int nat = (q0 + j * P) * TL::nl(a) + g;
     if constexpr (MAP) {
       idx[j] = nat;
-      const int xi = grid_index(p + j * P, g, a.in_h, a.in_w, a.in_tr);
+      const int xi = grid_index(q0 + j * P, g, a.in_h, a.in_w, a.in_tr);
       v[j] = xi >= 0 ? xb[xi] : make_float2(0.f, 0.f);
     } else {
       // in_off: the input is the window off .. off+n_in-1 of the length-m
@@ -333,8 +446,8 @@ __device__ __forceinline__ void first_tile(const PassArgs& a, int b, int g0, int
   const float sc = sh.scale;
 #pragma unroll
   for (int j = 0; j < E; ++j) v[j] = cscale(v[j], sc);
-  line_fft<ELL, T, DB, TWS>(v, scratch, p, t, tw);
-  twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+  fft_blk_to_s3<TL, DB, TWS>(v, scratch, p, rho, t, tw);
+  twiddle_store<TL>(v, a, b, g, t, f0, A, rowtw);
 }
 
 template <int ELL, int T, int DB, int MAP = 0>
@@ -348,12 +461,12 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
   float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
-  int t, p;
-  thread_coords<TL>(t, p);
+  int t, p, rho;
+  thread_coords<TL>(t, p, rho);
   load_line_twiddles<ELL>(a, tw);  // once per CTA: the grid is persistent over the tiles
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const int b = tile / a.cpp, g0 = (tile - b * a.cpp) * T;
-    first_tile<TL, DB, MAP, 1>(a, b, g0, t, p, scratch, tw, rowtw, sh);
+    first_tile<TL, DB, MAP, 1>(a, b, g0, t, p, rho, scratch, tw, rowtw, sh);
     __syncthreads();  // scratch, row twiddles and sh.scale are reused by the next tile
   }
 }
@@ -378,14 +491,15 @@ __device__ __forceinline__ void issue_tile(const PassArgs& a, int tile, uint32_t
 
 // Shared pipeline of the persistent MID / LAST passes: for every tile of this
 // CTA, loads the T input lines (rows of the exchange buffer) into registers
-// (slot j = position p + j*P) and calls body(v, b, g0).
+// (slots in stride-3 order: slot j = position s30 + j*SSTR, which is p + j*P
+// for power-of-two lines) and calls body(v, b, g0).
 template <int ELL, class TL, class Body>
 __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned char* smem, const PipeSmem& L,
                                            Body&& body) {
-  constexpr int E = TL::E, P = TL::P, T = TL::T;
+  constexpr int E = TL::E, T = TL::T;
   const int tid = threadIdx.x;
-  int t, p;
-  thread_coords<TL>(t, p);
+  int t, p, rho;
+  thread_coords<TL>(t, p, rho);
   // an earlier pass gave up (see mbar_wait_bounded): do nothing
   if (__syncthreads_or(tid == 0 && *(volatile int*)a.err != 0)) return;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar);
@@ -422,7 +536,7 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
         }
         return;
       }
-      load_staged<TL>(smem + (buf ? L.in1 : L.in0), t, p, v);
+      load_staged<TL>(smem + (buf ? L.in1 : L.in0), t, p, rho, v);
       if (nbuf == 1) {
         __syncthreads();  // every thread has its slots before the buffer is refilled
         if (tid == 0 && next < a.ntiles) {
@@ -431,9 +545,9 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
         }
       }
     } else {
-      const float2* src = a.ein + (size_t)b * TL::m(a) + (size_t)g * ELL;
+      const float2* src = a.ein + (size_t)b * TL::m(a) + (size_t)g * ELL + s30<TL>(p, rho);
 #pragma unroll
-      for (int j = 0; j < E; ++j) v[j] = src[p + j * P];
+      for (int j = 0; j < E; ++j) v[j] = src[j * TL::SSTR];
     }
     body(v, b, g0);
     // Scratch, tables and shared scalars are free for the next tile. With one
@@ -449,9 +563,13 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
 // partials, or the spectral weights), step 1 of the next DFT (direction DB)
 // and the four-step twiddles, into the exchange buffer.
 template <class TL, int DA, int DB, int TWS>
-__device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], int b, int g0, int t, int p,
+__device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], int b, int g0, int t, int p, int rho,
                                          float2* scratch, const float2* tw, float2* rowtw, TileScalars& sh) {
-  constexpr int T = TL::T, ELL = TL::E * TL::P;
+  constexpr int T = TL::T;
+  // the first FFT leaves its output in block order (slot j at frequency
+  // q0 + j*BSTR), where the operation applies; the second writes stride-3
+  // order (f0 + j*SSTR)
+  const int q0 = blk0<TL>(p, rho), f0 = s30<TL>(p, rho);
   // The chains apply an epilogue (GD residual or spectral weights) exactly
   // between a forward and an inverse DFT, and diagonals (or nothing) between
   // two DFTs of one direction, so each direction pair compiles only its own
@@ -461,7 +579,7 @@ __device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], 
   const int tid = threadIdx.x;
   const int g = g0 + t;
   OpData<TL> od;
-  if constexpr (EPI) od.load_y(a, a.op, b, g, p);
+  if constexpr (EPI) od.load_y(a, a.op, b, g, q0);
   const bool vs = EPI && a.op == kOpSpecEpilogue && a.norm_in;
   if (vs && tid == 0)
     sh.scale = 1.0f / sqrtf(sum_partials(a.norm_in + (size_t)b * a.norm_in_count, a.norm_in_count));
@@ -474,14 +592,14 @@ __device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], 
   if (phs) {
     const float* pb = a.ph + (size_t)b * a.dp_stride;
 #pragma unroll
-    for (int j = 0; j < TL::E; ++j) th[j] = __ldg(&pb[(p + j * TL::P) * TL::nl(a) + g]);
+    for (int j = 0; j < TL::E; ++j) th[j] = __ldg(&pb[(q0 + j * TL::BSTR) * TL::nl(a) + g]);
   }
   // four-step twiddles of the second FFT, loaded early so that their latency
   // overlaps the first FFT
   RowTw<TL> rw;
   rw.load(a, g0, DB);
-  float2 A = tw_m<TL>(a, g * p, DB);
-  line_fft<ELL, T, DA, TWS>(v, scratch, p, t, tw);
+  float2 A = tw_m<TL>(a, g * f0, DB);
+  fft_s3_to_blk<TL, DA, TWS>(v, scratch, p, rho, t, tw);
   fsum2 acc{0.f, 0.f};
   if (vs) {
     __syncthreads();  // sh.scale visible
@@ -497,7 +615,7 @@ __device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], 
     }
     A = cscale(A, a.dscale);
   } else {
-    apply_op<TL, EPI, DIAG>(v, a, od, b, g, p, acc);
+    apply_op<TL, EPI, DIAG>(v, a, od, b, g, q0, acc);
   }
   if (EPI && a.op == kOpGdEpilogue) {
     if constexpr (TL::THREADS % 32 == 0) {
@@ -511,8 +629,8 @@ __device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], 
   }
   rw.store(rowtw);
   __syncthreads();  // first FFT's scratch reads done; row twiddles visible
-  line_fft<ELL, T, DB, TWS>(v, scratch, p, t, tw);
-  twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+  fft_blk_to_s3<TL, DB, TWS>(v, scratch, p, rho, t, tw);
+  twiddle_store<TL>(v, a, b, g, t, f0, A, rowtw);
 }
 
 template <int ELL, int T, int DA, int DB, int NLC = 0>
@@ -527,12 +645,12 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
   float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
-  int t, p;
-  thread_coords<TL>(t, p);
+  int t, p, rho;
+  thread_coords<TL>(t, p, rho);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
   pipe_tiles<ELL, TL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
-    mid_tile<TL, DA, DB, 1>(a, v, b, g0, t, p, scratch, tw, rowtw, sh);
+    mid_tile<TL, DA, DB, 1>(a, v, b, g0, t, p, rho, scratch, tw, rowtw, sh);
   });
 }
 
@@ -540,9 +658,10 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 // the kept entries and the natural-order output or solver update (U^H: only
 // entries < n_out are written).
 template <class TL, int DA, int MAP, int TWS>
-__device__ __forceinline__ void last_tile(const PassArgs& a, float2 (&v)[TL::E], int b, int g0, int t, int p,
+__device__ __forceinline__ void last_tile(const PassArgs& a, float2 (&v)[TL::E], int b, int g0, int t, int p, int rho,
                                           float2* scratch, const float2* tw, TileScalars& sh) {
-  constexpr int E = TL::E, P = TL::P, T = TL::T, ELL = TL::E * TL::P;
+  constexpr int E = TL::E, P = TL::P, T = TL::T;
+  const int q0 = blk0<TL>(p, rho);  // the output's block order: slot j at frequency q0 + j*P
   const int tid = threadIdx.x;
   const int g = g0 + t;
   if (tid == 0) {
@@ -551,7 +670,7 @@ __device__ __forceinline__ void last_tile(const PassArgs& a, float2 (&v)[TL::E],
                      : 1.0f;
     sh.mu = a.mu ? a.mu[b] : 0.f;
   }
-  line_fft<ELL, T, DA, TWS>(v, scratch, p, t, tw);
+  fft_s3_to_blk<TL, DA, TWS>(v, scratch, p, rho, t, tw);
   __syncthreads();  // tile scalars visible
   // natural index of (line g, frequency f) is f*NL + g; keep those < n_out
   // (U^H), and apply D_1^H only to the kept entries
@@ -560,12 +679,12 @@ __device__ __forceinline__ void last_tile(const PassArgs& a, float2 (&v)[TL::E],
   fsum2 acc{0.f, 0.f};
 #pragma unroll
   for (int j = 0; j < E; ++j) {
-    const int nat = (p + j * P) * TL::nl(a) + g;
+    const int nat = (q0 + j * P) * TL::nl(a) + g;
     // output index: the prefix n_out (U^H), the window out_off .. out_off+n_out-1
     // (S of the alpha < 1 branch), or grid_index (2D grids); tables stay at nat
     int oi = nat - a.out_off;
     if constexpr (MAP) {
-      oi = grid_index(p + j * P, g, a.out_h, a.out_w, a.out_tr);
+      oi = grid_index(q0 + j * P, g, a.out_h, a.out_w, a.out_tr);
       if (oi < 0) continue;
     } else {
       if ((unsigned)oi >= (unsigned)a.n_out) continue;
@@ -607,12 +726,12 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   const PipeSmem L = pipe_layout(ELL, T, nbuf, true);
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
-  int t, p;
-  thread_coords<TL>(t, p);
+  int t, p, rho;
+  thread_coords<TL>(t, p, rho);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
   pipe_tiles<ELL, TL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
-    last_tile<TL, DA, MAP, 1>(a, v, b, g0, t, p, scratch, tw, sh);
+    last_tile<TL, DA, MAP, 1>(a, v, b, g0, t, p, rho, scratch, tw, sh);
   });
 }
 
@@ -627,8 +746,12 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 // Each D_1 entry is loaded once for both uses.
 template <class TL, int MAP, int TWS>
 __device__ __forceinline__ void last_first_tile(const PassArgs& a, float2 (&v)[TL::E], int b, int g0, int t, int p,
-                                                float2* scratch, const float2* tw, float2* rowtw, TileScalars& sh) {
-  constexpr int E = TL::E, P = TL::P, T = TL::T, ELL = TL::E * TL::P;
+                                                int rho, float2* scratch, const float2* tw, float2* rowtw,
+                                                TileScalars& sh) {
+  constexpr int E = TL::E, P = TL::P, T = TL::T;
+  // the inverse DFT's output and the update in block order (q0 + j*P); the
+  // next forward DFT's step-1 output in stride-3 order (f0 + j*SSTR)
+  const int q0 = blk0<TL>(p, rho), f0 = s30<TL>(p, rho);
   const int tid = threadIdx.x;
   const int g = g0 + t;
   const bool spec = a.out_mode == kOutSpec;
@@ -640,8 +763,8 @@ __device__ __forceinline__ void last_first_tile(const PassArgs& a, float2 (&v)[T
   }
   RowTw<TL> rw;
   rw.load(a, g0, -1);
-  const float2 A = tw_m<TL>(a, g * p, -1);
-  line_fft<ELL, T, 1, TWS>(v, scratch, p, t, tw);
+  const float2 A = tw_m<TL>(a, g * f0, -1);
+  fft_s3_to_blk<TL, 1, TWS>(v, scratch, p, rho, t, tw);
   __syncthreads();  // tile scalars visible
   const float mu2 = 2.0f * sh.mu * a.mu_scale, shv = a.shift * sh.inv_old;
   float2* xb = a.xout + (size_t)b * a.n_out;
@@ -649,12 +772,12 @@ __device__ __forceinline__ void last_first_tile(const PassArgs& a, float2 (&v)[T
   fsum2 acc{0.f, 0.f};
 #pragma unroll
   for (int j = 0; j < E; ++j) {
-    const int nat = (p + j * P) * TL::nl(a) + g;
+    const int nat = (q0 + j * P) * TL::nl(a) + g;
     // signal index (2D grids: grid_index, with U2 and U2^H the same corner)
     int xi = nat;
     bool keep;
     if constexpr (MAP) {
-      xi = grid_index(p + j * P, g, a.out_h, a.out_w, 0);
+      xi = grid_index(q0 + j * P, g, a.out_h, a.out_w, 0);
       keep = xi >= 0;
     } else {
       keep = nat < a.n_out;
@@ -684,8 +807,8 @@ __device__ __forceinline__ void last_first_tile(const PassArgs& a, float2 (&v)[T
     a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
   rw.store(rowtw);
   __syncthreads();  // the first FFT's scratch reads done; row twiddles visible
-  line_fft<ELL, T, -1, TWS>(v, scratch, p, t, tw);
-  twiddle_store<TL>(v, a, b, g, t, p, A, rowtw);
+  fft_blk_to_s3<TL, -1, TWS>(v, scratch, p, rho, t, tw);
+  twiddle_store<TL>(v, a, b, g, t, f0, A, rowtw);
 }
 
 template <int ELL, int T, int NLC = 0, int MAP = 0>
@@ -700,19 +823,22 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   float2* scratch = reinterpret_cast<float2*>(smem + L.scratch);
   float2* tw = reinterpret_cast<float2*>(smem + L.tw);
   float2* rowtw = reinterpret_cast<float2*>(smem + L.rowtw);
-  int t, p;
-  thread_coords<TL>(t, p);
+  int t, p, rho;
+  thread_coords<TL>(t, p, rho);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
   pipe_tiles<ELL, TL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
-    last_first_tile<TL, MAP, 1>(a, v, b, g0, t, p, scratch, tw, rowtw, sh);
+    last_first_tile<TL, MAP, 1>(a, v, b, g0, t, p, rho, scratch, tw, rowtw, sh);
   });
 }
 
 // Every (line length, lines per CTA) pair make_geom produces for m = 4 .. 2^24.
+// The radix-3 lines of m = 3 * 2^a: 192, 384 and 768 points (sub-lines of 64,
+// 128 and 256; 192 or 384 threads per CTA).
 #define SR_TILE_SHAPES(X)                                                                                      \
   X(2, 2) X(2, 4) X(4, 2) X(4, 4) X(4, 8) X(8, 4) X(8, 8) X(8, 16) X(16, 8) X(16, 16) X(16, 32) X(32, 16)    \
-  X(32, 32) X(32, 64) X(64, 32) X(64, 64) X(128, 32) X(256, 16) X(512, 8) X(1024, 8) X(2048, 4) X(4096, 2)
+  X(32, 32) X(32, 64) X(64, 32) X(64, 64) X(128, 32) X(256, 16) X(512, 8) X(1024, 8) X(2048, 4) X(4096, 2)  \
+  X(192, 16) X(384, 16) X(768, 8)
 
 // The (line length, lines per CTA) pairs of square grids m = S * S, S = 2 .. 4096
 // (line length S): the shapes with 2D-grid (MAP = 1) kernels.

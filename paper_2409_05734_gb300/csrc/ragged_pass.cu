@@ -241,8 +241,8 @@ __device__ __noinline__ bool rg_qtile(RgQCtx& cx, const PassArgs& a, const RgIte
   constexpr int T = 4096 / ELL;
   using TL = Tile<ELL, T>;
   constexpr int TWS = 1024 / ELL;
-  int t, p;
-  thread_coords<TL>(t, p);
+  int t, p, rho;
+  thread_coords<TL>(t, p, rho);
   const int b = it.b, g0 = it.tile * T;  // tiles of a pass hold T consecutive lines
   float2 v[TL::E];
   if constexpr (TL::TMA) {
@@ -266,7 +266,7 @@ __device__ __noinline__ bool rg_qtile(RgQCtx& cx, const PassArgs& a, const RgIte
       if (threadIdx.x == 0) atomicExch(cx.err, (int)SR_ERR_TIMEOUT);
       return false;
     }
-    load_staged<TL>(cx.smem + RgSmem::stage, t, p, v);
+    load_staged<TL>(cx.smem + RgSmem::stage, t, p, rho, v);
     __syncthreads();  // slots in registers (staging free)
     if (threadIdx.x < 32) rg_prep_next(cx);
   } else {
@@ -281,11 +281,11 @@ __device__ __noinline__ bool rg_qtile(RgQCtx& cx, const PassArgs& a, const RgIte
 #pragma unroll
     for (int j = 0; j < TL::E; ++j) v[j] = src[p + j * TL::P];
   }
-  if constexpr (KIND == kRgMidFF) mid_tile<TL, -1, -1, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
-  else if constexpr (KIND == kRgMidFI) mid_tile<TL, -1, 1, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
-  else if constexpr (KIND == kRgMidII) mid_tile<TL, 1, 1, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
-  else if constexpr (KIND == kRgLF) last_first_tile<TL, 0, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
-  else last_tile<TL, 1, 0, TWS>(a, v, b, g0, t, p, cx.scratch, cx.tw, sh);
+  if constexpr (KIND == kRgMidFF) mid_tile<TL, -1, -1, TWS>(a, v, b, g0, t, p, rho, cx.scratch, cx.tw, cx.rowtw, sh);
+  else if constexpr (KIND == kRgMidFI) mid_tile<TL, -1, 1, TWS>(a, v, b, g0, t, p, rho, cx.scratch, cx.tw, cx.rowtw, sh);
+  else if constexpr (KIND == kRgMidII) mid_tile<TL, 1, 1, TWS>(a, v, b, g0, t, p, rho, cx.scratch, cx.tw, cx.rowtw, sh);
+  else if constexpr (KIND == kRgLF) last_first_tile<TL, 0, TWS>(a, v, b, g0, t, p, rho, cx.scratch, cx.tw, cx.rowtw, sh);
+  else last_tile<TL, 1, 0, TWS>(a, v, b, g0, t, p, rho, cx.scratch, cx.tw, sh);
   return true;
 }
 
@@ -294,12 +294,12 @@ template <int ELL>
 __device__ __noinline__ bool rg_qfirst(RgQCtx& cx, const PassArgs& a, const RgItem& it, TileScalars& sh) {
   constexpr int T = 4096 / ELL;
   using TL = Tile<ELL, T>;
-  int t, p;
-  thread_coords<TL>(t, p);
+  int t, p, rho;
+  thread_coords<TL>(t, p, rho);
   const int b = it.b, g0 = it.tile * T;
   __syncthreads();  // the item's arguments visible
   if (threadIdx.x < 32) rg_prep_next(cx);
-  first_tile<TL, -1, 0, 1024 / ELL>(a, b, g0, t, p, cx.scratch, cx.tw, cx.rowtw, sh);
+  first_tile<TL, -1, 0, 1024 / ELL>(a, b, g0, t, p, rho, cx.scratch, cx.tw, cx.rowtw, sh);
   return true;
 }
 

@@ -86,11 +86,12 @@ def test_autotune_picks_a_supported_split_and_keeps_results(sr):
     plan.check()
 
 
-def test_split_on_radix3_plan_sets_the_inner_plan(sr):
+def test_split_on_radix3_plan(sr):
     n, m, L, B, seed = 2000, 3 * 2 ** 14, 2, 2, 5
     plan = sr.Plan(n, m, L, seed)
-    plan.set_split(256)   # inner length 2^14 as 256 x 64
-    assert plan.tuning[:2] == (256, 64)
+    assert plan.tuning[:2] == (192, 256)  # the default: radix-3 lines of 192 in layout X
+    plan.set_split(256)   # lines of 256 in layout X, radix-3 lines of 192 in layout Y
+    assert plan.tuning[:2] == (256, 192)
     fwd, adj = O.structured_ops(S.phases(seed, L, m), n, m)
     x = S.signal_gaussian(seed, B, n)
     close(plan.forward(dev(x)).cpu().numpy(), fwd(x))
@@ -119,3 +120,39 @@ def test_unsupported_splits_are_refused(sr):
     assert plan.tuning[:2] == (128, 128)  # unchanged
     with pytest.raises(SrError):
         sr.Plan2D(8, 8, 16, 2, 1).set_split(8)
+
+
+# Radix-3 lengths on the four-step passes: lines of 192, 384 or 768 points (a
+# radix-3 step inside the line FFT) in either layout, several tiles per pass,
+# ragged n, L = 1 .. 3.
+R3_SPLITS = [(3000, 3 * 2 ** 14, 2, 3, m1) for m1 in (192, 256, 384)] + \
+            [(30000, 3 * 2 ** 16, 3, 2, m1) for m1 in (384, 512, 768)] + \
+            [(9000, 3 * 2 ** 13, 1, 2, 192), (2 ** 16, 3 * 2 ** 17, 2, 1, 768)]
+
+
+@pytest.mark.parametrize("n,m,L,B,m1", R3_SPLITS)
+def test_radix3_line_splits_match_oracle(sr, n, m, L, B, m1):
+    seed = 50 + m1 + L
+    plan = sr.Plan(n, m, L, seed)
+    plan.set_split(m1)
+    got_m1, got_m2, _ = plan.tuning
+    assert (got_m1, got_m2) == (m1, m // m1)
+    th = S.phases(seed, L, m)
+    fwd, adj = O.structured_ops(th, n, m)
+    x = S.signal_gaussian(seed, B, n)
+    close(plan.forward(dev(x)).cpu().numpy(), fwd(x))
+    plan.check()
+    w = S.complex_gaussian(seed, (B, m), S.STREAM_NOISE)
+    close(plan.adjoint(dev(w)).cpu().numpy(), adj(w))
+    y = np.abs(fwd(x)) ** 2
+    x0 = x + 0.3 * S.complex_gaussian(seed + 1, (B, n), S.STREAM_NOISE)
+    xg = dev(x0)
+    plan.gd_solve(dev(y, torch.float32), xg, 10, mu0=0.1)
+    plan.check()
+    xo, _ = O.gradient_descent(x0, y, fwd, adj, 10, mu0=0.1)
+    assert rel(xg.cpu().numpy(), xo) <= 1e-4
+    # the power iteration (spectral epilogue between the forward and inverse DFTs)
+    v0 = S.start_vector(seed, B, n)
+    xs = plan.spectral_init(dev(y, torch.float32), dev(v0), 5, weight="optimal", lam=-1.0).cpu().numpy()
+    plan.check()
+    assert rel(xs, O.spectral_init(y, v0, fwd, adj, 5, mode="optimal", lam=-1.0)) <= 1e-4
