@@ -528,6 +528,9 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
         issue_tile<TL, ELL>(a, next, buf ? in0 : in1, buf ? bar0 : bar1);
       }
       const bool ok = mbar_wait_bounded(bar, parity);
+      if (ok) load_staged<TL>(smem + (buf ? L.in1 : L.in0), t, p, rho, v);
+      // one barrier: every thread has its slots before the buffer is refilled,
+      // and every thread learns whether any wait gave up
       if (!__syncthreads_and(ok)) {
         // a load never completed: record it, let a pending prefetch land, stop
         if (tid == 0) {
@@ -536,13 +539,9 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
         }
         return;
       }
-      load_staged<TL>(smem + (buf ? L.in1 : L.in0), t, p, rho, v);
-      if (nbuf == 1) {
-        __syncthreads();  // every thread has its slots before the buffer is refilled
-        if (tid == 0 && next < a.ntiles) {
-          fence_proxy_async_smem();
-          issue_tile<TL, ELL>(a, next, in0, bar0);
-        }
+      if (nbuf == 1 && tid == 0 && next < a.ntiles) {
+        fence_proxy_async_smem();
+        issue_tile<TL, ELL>(a, next, in0, bar0);
       }
     } else {
       const float2* src = a.ein + (size_t)b * TL::m(a) + (size_t)g * ELL + s30<TL>(p, rho);
