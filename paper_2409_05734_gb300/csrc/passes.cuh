@@ -62,6 +62,11 @@ struct Tile {
   static constexpr bool TMA = uses_tma(ELL, T);
   static constexpr int BOX = T * 128;  // bytes of one box: 16 complex values x T rows
   static constexpr int MIN_CTAS = THREADS <= 256 ? 3 : THREADS <= 384 ? 2 : 1;
+  // Staged tiles whose line FFT runs through the scratch (two or more stages,
+  // or a radix-3 step): the staging buffer, free once the tile is in
+  // registers, serves as the first line FFT's scratch, and the next tile's
+  // load is issued after the second FFT's first barrier.
+  static constexpr bool LATE = TMA && (R3 || LineShape<M>::NSTAGE >= 2);
   static_assert(THREADS <= 512, "tile too large");
   static_assert(NLC == 0 || NLC % T == 0, "lines per CTA must divide the line count");
   __device__ __forceinline__ static int nl(const PassArgs& a) { return NLC ? NLC : a.nl; }
@@ -105,11 +110,14 @@ struct PipeSmem {
 __host__ __device__ inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Layout relative to a 1024-byte-aligned base; input tiles (T rows of ell
-// complex values as ell/16 boxes) in `nbuf` swizzled buffers when staged.
+// complex values as ell/16 boxes) in `nbuf` swizzled buffers when staged,
+// each large enough to serve as a line-FFT scratch once its tile is in
+// registers.
 __host__ __device__ inline PipeSmem pipe_layout(int ell, int T, int nbuf, bool stage_input) {
   PipeSmem L;
   const bool tma = stage_input && uses_tma(ell, T);
-  const size_t tile = tma ? (size_t)(ell / 16) * T * 128 : 0;
+  const size_t box_bytes = (size_t)(ell / 16) * T * 128, scr_bytes = (size_t)T * (ell + ell / 16) * 8;
+  const size_t tile = tma ? round_up(box_bytes > scr_bytes ? box_bytes : scr_bytes, 1024) : 0;
   const int E = ell < 16 ? ell : 16;
   L.in0 = 0;
   L.in1 = tile;
@@ -194,15 +202,17 @@ __device__ __forceinline__ void fft_s3_to_blk(float2 (&v)[TL::E], float2* sm, in
 //   X[3 k + s] = DFT_M(u_s)[k],  u_s[k] = W_ELL^(k s) sum_r W_3^(r s) x[k + r M];
 // thread (t, p, rho) forms u_rho at its k = p + j P from the three block
 // values read from the scratch, then the sub-line FFT. The caller
-// synchronises before the call if the scratch was in use.
-template <class TL, int DIR, int TWS>
+// synchronises before the call if the scratch was in use. hook() runs once
+// after the first CTA barrier of the transform (none for single-stage lines).
+template <class TL, int DIR, int TWS, class Hook = NoHook>
 __device__ __forceinline__ void fft_blk_to_s3(float2 (&v)[TL::E], float2* sm, int p, int rho, int t,
-                                              const float2* tw) {
+                                              const float2* tw, const Hook& hook = Hook()) {
   if constexpr (TL::R3) {
     constexpr int T = TL::T, T3 = 3 * TL::T, P = TL::P;
 #pragma unroll
     for (int j = 0; j < TL::E; ++j) sm[sidx<T3>(p + j * P, t + T * rho)] = v[j];
     __syncthreads();
+    hook();
     const float2 c1 = root3<DIR>(rho), c2 = root3<DIR>(2 * rho);
 #pragma unroll
     for (int j = 0; j < TL::E; ++j) {
@@ -214,7 +224,7 @@ __device__ __forceinline__ void fft_blk_to_s3(float2 (&v)[TL::E], float2* sm, in
     __syncthreads();  // every block value read before the sub-line FFT writes the scratch
     line_fft<TL::M, T3, DIR, 3 * TWS>(v, sm, p, t + T * rho, tw);
   } else {
-    line_fft<TL::M, TL::T, DIR, TWS>(v, sm, p, t, tw);
+    line_fft<TL::M, TL::T, DIR, TWS>(v, sm, p, t, tw, hook);
   }
 }
 
@@ -489,27 +499,50 @@ __device__ __forceinline__ void issue_tile(const PassArgs& a, int tile, uint32_t
   issue_rows(&a.tmap, b * TL::nl(a) + g0, ELL, TL::T, TL::BOX, buf, bar);
 }
 
+// The request of the next tile's load (thread 0 acts; nothing when the tile
+// does not exist or the pass issues its loads early).
+template <class TL, int ELL>
+struct NextLoad {
+  const PassArgs* a;
+  int next;
+  uint32_t buf, bar;
+  __device__ __forceinline__ void operator()() const {
+    if constexpr (TL::LATE) {
+      if (threadIdx.x == 0 && next < a->ntiles) {
+        fence_proxy_async_smem();
+        issue_tile<TL, ELL>(*a, next, buf, bar);
+      }
+    }
+  }
+};
+
 // Shared pipeline of the persistent MID / LAST passes: for every tile of this
 // CTA, loads the T input lines (rows of the exchange buffer) into registers
 // (slots in stride-3 order: slot j = position s30 + j*SSTR, which is p + j*P
-// for power-of-two lines) and calls body(v, b, g0).
+// for power-of-two lines) and calls body(v, b, g0, scr1, issue): scr1 is the
+// scratch for the tile's first line FFT and issue() the request of the next
+// tile's load. With TL::LATE, scr1 is the staging buffer itself and the body
+// calls issue() (every thread; thread 0 acts) once every thread is past its
+// last access to scr1; otherwise scr1 is the regular scratch, the next load
+// is already in flight and issue() does nothing. One staging buffer (nbuf = 1).
 template <int ELL, class TL, class Body>
 __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned char* smem, const PipeSmem& L,
-                                           Body&& body) {
+                                           float2* scratch, Body&& body) {
   constexpr int E = TL::E, T = TL::T;
+  (void)nbuf;
   const int tid = threadIdx.x;
   int t, p, rho;
   thread_coords<TL>(t, p, rho);
   // an earlier pass gave up (see mbar_wait_bounded): do nothing
   if (__syncthreads_or(tid == 0 && *(volatile int*)a.err != 0)) return;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar);
-  const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
-  const uint32_t in0 = smem_addr(smem + L.in0), in1 = smem_addr(smem + L.in1);
+  const uint32_t bar0 = smem_addr(&bars[0]);
+  const uint32_t in0 = smem_addr(smem + L.in0);
+  float2* stage_scr = reinterpret_cast<float2*>(smem + L.in0);
   int tile = blockIdx.x;
   if constexpr (TL::TMA) {
     if (tid == 0) {
       mbar_init(bar0, 1);
-      mbar_init(bar1, 1);
       mbar_init_fence();
     }
     __syncthreads();
@@ -519,27 +552,17 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
     const int b = tile / TL::cpp(a), g0 = (tile - b * TL::cpp(a)) * T, g = g0 + t;
     const int next = tile + (int)gridDim.x;
     float2 v[E];
+    const NextLoad<TL, ELL> issue{&a, next, in0, bar0};
     if constexpr (TL::TMA) {
-      const int buf = nbuf == 2 ? (k & 1) : 0;
-      const uint32_t parity = nbuf == 2 ? (uint32_t)((k >> 1) & 1) : (uint32_t)(k & 1);
-      const uint32_t bar = buf ? bar1 : bar0;
-      if (nbuf == 2 && tid == 0 && next < a.ntiles) {
-        fence_proxy_async_smem();
-        issue_tile<TL, ELL>(a, next, buf ? in0 : in1, buf ? bar0 : bar1);
-      }
-      const bool ok = mbar_wait_bounded(bar, parity);
-      if (ok) load_staged<TL>(smem + (buf ? L.in1 : L.in0), t, p, rho, v);
-      // one barrier: every thread has its slots before the buffer is refilled,
+      const bool ok = mbar_wait_bounded(bar0, (uint32_t)(k & 1));
+      if (ok) load_staged<TL>(smem + L.in0, t, p, rho, v);
+      // one barrier: every thread has its slots before the buffer is reused,
       // and every thread learns whether any wait gave up
       if (!__syncthreads_and(ok)) {
-        // a load never completed: record it, let a pending prefetch land, stop
-        if (tid == 0) {
-          atomicExch(a.err, (int)SR_ERR_TIMEOUT);
-          if (nbuf == 2 && next < a.ntiles) mbar_wait_bounded(buf ? bar0 : bar1, (uint32_t)(((k + 1) >> 1) & 1));
-        }
+        if (tid == 0) atomicExch(a.err, (int)SR_ERR_TIMEOUT);  // a load never completed: record it, stop
         return;
       }
-      if (nbuf == 1 && tid == 0 && next < a.ntiles) {
+      if (!TL::LATE && tid == 0 && next < a.ntiles) {
         fence_proxy_async_smem();
         issue_tile<TL, ELL>(a, next, in0, bar0);
       }
@@ -548,22 +571,25 @@ __device__ __forceinline__ void pipe_tiles(const PassArgs& a, int nbuf, unsigned
 #pragma unroll
       for (int j = 0; j < E; ++j) v[j] = src[j * TL::SSTR];
     }
-    body(v, b, g0);
-    // Scratch, tables and shared scalars are free for the next tile. With one
-    // TMA staging buffer the barrier that follows the next tile's register load
-    // already orders this tile's last shared-memory reads before the next
-    // tile's first writes, so no barrier is needed here.
-    if (!(TL::TMA && nbuf == 1)) __syncthreads();
+    body(v, b, g0, TL::LATE ? stage_scr : scratch, issue);
+    // Scratch, tables and shared scalars are free for the next tile. With TMA
+    // staging the barrier that follows the next tile's register load already
+    // orders this tile's last shared-memory reads before the next tile's first
+    // writes, so no barrier is needed here.
+    if (!TL::TMA) __syncthreads();
   }
 }
 
 // One tile of a MID pass: step 2 of the previous DFT (direction DA) on the T
 // lines in v, the fused operation (D_l, D_l^H, the GD residual with loss
 // partials, or the spectral weights), step 1 of the next DFT (direction DB)
-// and the four-step twiddles, into the exchange buffer.
-template <class TL, int DA, int DB, int TWS>
+// and the four-step twiddles, into the exchange buffer. With SPLIT the first
+// FFT runs in scr1 (the staging buffer) and the second in `scratch`, so no
+// barrier separates them; issue() runs after the second FFT's first barrier.
+template <class TL, int DA, int DB, int TWS, bool SPLIT = false, class Hook = NoHook>
 __device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], int b, int g0, int t, int p, int rho,
-                                         float2* scratch, const float2* tw, float2* rowtw, TileScalars& sh) {
+                                         float2* scratch, const float2* tw, float2* rowtw, TileScalars& sh,
+                                         float2* scr1 = nullptr, const Hook& issue = Hook()) {
   constexpr int T = TL::T;
   // the first FFT leaves its output in block order (slot j at frequency
   // q0 + j*BSTR), where the operation applies; the second writes stride-3
@@ -598,7 +624,7 @@ __device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], 
   RowTw<TL> rw;
   rw.load(a, g0, DB);
   float2 A = tw_m<TL>(a, g * f0, DB);
-  fft_s3_to_blk<TL, DA, TWS>(v, scratch, p, rho, t, tw);
+  fft_s3_to_blk<TL, DA, TWS>(v, SPLIT ? scr1 : scratch, p, rho, t, tw);
   fsum2 acc{0.f, 0.f};
   if (vs) {
     __syncthreads();  // sh.scale visible
@@ -627,8 +653,15 @@ __device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], 
     }
   }
   rw.store(rowtw);
-  __syncthreads();  // first FFT's scratch reads done; row twiddles visible
-  fft_blk_to_s3<TL, DB, TWS>(v, scratch, p, rho, t, tw);
+  if constexpr (SPLIT) {
+    // the second FFT's first barrier orders the row twiddles before their use
+    // and every access to scr1 before the next tile's load into it
+    fence_proxy_async_smem();
+    fft_blk_to_s3<TL, DB, TWS>(v, scratch, p, rho, t, tw, issue);
+  } else {
+    __syncthreads();  // first FFT's scratch reads done; row twiddles visible
+    fft_blk_to_s3<TL, DB, TWS>(v, scratch, p, rho, t, tw);
+  }
   twiddle_store<TL>(v, a, b, g, t, f0, A, rowtw);
 }
 
@@ -648,17 +681,18 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   thread_coords<TL>(t, p, rho);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
-  pipe_tiles<ELL, TL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
-    mid_tile<TL, DA, DB, 1>(a, v, b, g0, t, p, rho, scratch, tw, rowtw, sh);
+  pipe_tiles<ELL, TL>(a, nbuf, smem, L, scratch, [&](float2 (&v)[E], int b, int g0, float2* scr1, const NextLoad<TL, ELL>& issue) {
+    mid_tile<TL, DA, DB, 1, TL::LATE>(a, v, b, g0, t, p, rho, scratch, tw, rowtw, sh, scr1, issue);
   });
 }
 
 // One tile of a LAST pass: step 2 of the final DFT (direction DA), D_1^H on
 // the kept entries and the natural-order output or solver update (U^H: only
 // entries < n_out are written).
-template <class TL, int DA, int MAP, int TWS>
+template <class TL, int DA, int MAP, int TWS, bool SPLIT = false, class Hook = NoHook>
 __device__ __forceinline__ void last_tile(const PassArgs& a, float2 (&v)[TL::E], int b, int g0, int t, int p, int rho,
-                                          float2* scratch, const float2* tw, TileScalars& sh) {
+                                          float2* scratch, const float2* tw, TileScalars& sh,
+                                          float2* scr1 = nullptr, const Hook& issue = Hook()) {
   constexpr int E = TL::E, P = TL::P, T = TL::T;
   const int q0 = blk0<TL>(p, rho);  // the output's block order: slot j at frequency q0 + j*P
   const int tid = threadIdx.x;
@@ -669,8 +703,10 @@ __device__ __forceinline__ void last_tile(const PassArgs& a, float2 (&v)[TL::E],
                      : 1.0f;
     sh.mu = a.mu ? a.mu[b] : 0.f;
   }
-  fft_s3_to_blk<TL, DA, TWS>(v, scratch, p, rho, t, tw);
-  __syncthreads();  // tile scalars visible
+  fft_s3_to_blk<TL, DA, TWS>(v, SPLIT ? scr1 : scratch, p, rho, t, tw);
+  if constexpr (SPLIT) fence_proxy_async_smem();
+  __syncthreads();  // tile scalars visible (and, with SPLIT, scr1 free for the next load)
+  if constexpr (SPLIT) issue();
   // natural index of (line g, frequency f) is f*NL + g; keep those < n_out
   // (U^H), and apply D_1^H only to the kept entries
   float2* xb = a.xout + (size_t)b * a.n_out;
@@ -729,8 +765,8 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   thread_coords<TL>(t, p, rho);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
-  pipe_tiles<ELL, TL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
-    last_tile<TL, DA, MAP, 1>(a, v, b, g0, t, p, rho, scratch, tw, sh);
+  pipe_tiles<ELL, TL>(a, nbuf, smem, L, scratch, [&](float2 (&v)[E], int b, int g0, float2* scr1, const NextLoad<TL, ELL>& issue) {
+    last_tile<TL, DA, MAP, 1, TL::LATE>(a, v, b, g0, t, p, rho, scratch, tw, sh, scr1, issue);
   });
 }
 
@@ -743,10 +779,11 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
 // registers, U (zeros beyond n), D_1 and step 1 of the next step's first
 // forward DFT, with the four-step twiddles, into the exchange buffer `eout`.
 // Each D_1 entry is loaded once for both uses.
-template <class TL, int MAP, int TWS>
+template <class TL, int MAP, int TWS, bool SPLIT = false, class Hook = NoHook>
 __device__ __forceinline__ void last_first_tile(const PassArgs& a, float2 (&v)[TL::E], int b, int g0, int t, int p,
                                                 int rho, float2* scratch, const float2* tw, float2* rowtw,
-                                                TileScalars& sh) {
+                                                TileScalars& sh, float2* scr1 = nullptr,
+                                                const Hook& issue = Hook()) {
   constexpr int E = TL::E, P = TL::P, T = TL::T;
   // the inverse DFT's output and the update in block order (q0 + j*P); the
   // next forward DFT's step-1 output in stride-3 order (f0 + j*SSTR)
@@ -763,8 +800,10 @@ __device__ __forceinline__ void last_first_tile(const PassArgs& a, float2 (&v)[T
   RowTw<TL> rw;
   rw.load(a, g0, -1);
   const float2 A = tw_m<TL>(a, g * f0, -1);
-  fft_s3_to_blk<TL, 1, TWS>(v, scratch, p, rho, t, tw);
-  __syncthreads();  // tile scalars visible
+  fft_s3_to_blk<TL, 1, TWS>(v, SPLIT ? scr1 : scratch, p, rho, t, tw);
+  if constexpr (SPLIT) fence_proxy_async_smem();
+  __syncthreads();  // tile scalars visible (and, with SPLIT, scr1 free for the next load)
+  if constexpr (SPLIT) issue();
   const float mu2 = 2.0f * sh.mu * a.mu_scale, shv = a.shift * sh.inv_old;
   float2* xb = a.xout + (size_t)b * a.n_out;
   const float2* dp = a.dp + (size_t)b * a.dp_stride;
@@ -805,7 +844,9 @@ __device__ __forceinline__ void last_first_tile(const PassArgs& a, float2 (&v)[T
   if (a.loss_out && g0 == 0 && tid == 0)
     a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
   rw.store(rowtw);
-  __syncthreads();  // the first FFT's scratch reads done; row twiddles visible
+  // the first FFT's scratch reads done; row twiddles visible (with SPLIT the
+  // first FFT ran in scr1 and the second FFT's first barrier orders the table)
+  if constexpr (!SPLIT) __syncthreads();
   fft_blk_to_s3<TL, -1, TWS>(v, scratch, p, rho, t, tw);
   twiddle_store<TL>(v, a, b, g, t, f0, A, rowtw);
 }
@@ -826,8 +867,9 @@ __global__ void __launch_bounds__(Tile<ELL, T>::THREADS, Tile<ELL, T>::MIN_CTAS)
   thread_coords<TL>(t, p, rho);
   load_line_twiddles<ELL>(a, tw);
   __syncthreads();
-  pipe_tiles<ELL, TL>(a, nbuf, smem, L, [&](float2 (&v)[E], int b, int g0) {
-    last_first_tile<TL, MAP, 1>(a, v, b, g0, t, p, rho, scratch, tw, rowtw, sh);
+  pipe_tiles<ELL, TL>(a, nbuf, smem, L, scratch, [&](float2 (&v)[E], int b, int g0, float2* scr1,
+                                                     const NextLoad<TL, ELL>& issue) {
+    last_first_tile<TL, MAP, 1, TL::LATE>(a, v, b, g0, t, p, rho, scratch, tw, rowtw, sh, scr1, issue);
   });
 }
 

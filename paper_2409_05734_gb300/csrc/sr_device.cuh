@@ -217,11 +217,18 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[LineShape<N>::E], float2* 
   if constexpr (!LAST) __syncthreads();
 }
 
-template <int N, int T, int S, int DIR, int TWS>
-__device__ __forceinline__ void fft_stages(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, const float2* tw) {
+// A callable that does nothing (the default hook of line_fft).
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+template <int N, int T, int S, int DIR, int TWS, class Hook>
+__device__ __forceinline__ void fft_stages(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, const float2* tw,
+                                           const Hook& hook) {
   if constexpr (S < LineShape<N>::NSTAGE) {
     fft_stage<N, T, S, DIR, TWS>(v, sm, p, t, tw);
-    fft_stages<N, T, S + 1, DIR, TWS>(v, sm, p, t, tw);
+    if constexpr (S == 0 && LineShape<N>::NSTAGE >= 2) hook();  // after stage 0's CTA barrier
+    fft_stages<N, T, S + 1, DIR, TWS>(v, sm, p, t, tw, hook);
   }
 }
 
@@ -231,10 +238,13 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[LineShape<N>::E], float2*
 // roots, entry k * TWS = W_N^k (a table of W_{N TWS} serves every N that
 // divides its length), conjugated where applied. The scratch is shared by the
 // CTA's lines: every thread of the block calls this together, and the caller
-// synchronises before the call if the scratch was in use.
-template <int N, int T, int DIR, int TWS = 1>
-__device__ __forceinline__ void line_fft(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, const float2* tw) {
-  fft_stages<N, T, 0, (DIR > 0 ? 1 : -1), TWS>(v, sm, p, t, tw);
+// synchronises before the call if the scratch was in use. For lines of two or
+// more stages, hook() runs once, right after the CTA barrier that ends stage 0
+// (every thread is then past all its earlier shared-memory accesses).
+template <int N, int T, int DIR, int TWS = 1, class Hook = NoHook>
+__device__ __forceinline__ void line_fft(float2 (&v)[LineShape<N>::E], float2* sm, int p, int t, const float2* tw,
+                                         const Hook& hook = Hook()) {
+  fft_stages<N, T, 0, (DIR > 0 ? 1 : -1), TWS>(v, sm, p, t, tw, hook);
 }
 
 // ---------------------------------------------------- compensated summation
