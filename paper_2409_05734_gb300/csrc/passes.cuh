@@ -801,9 +801,9 @@ __device__ __forceinline__ void last_first_tile(const PassArgs& a, float2 (&v)[T
   rw.load(a, g0, -1);
   const float2 A = tw_m<TL>(a, g * f0, -1);
   fft_s3_to_blk<TL, 1, TWS>(v, SPLIT ? scr1 : scratch, p, rho, t, tw);
-  if constexpr (SPLIT) fence_proxy_async_smem();
-  __syncthreads();  // tile scalars visible (and, with SPLIT, scr1 free for the next load)
-  if constexpr (SPLIT) issue();
+  // tile scalars visible: with SPLIT the first FFT's own barriers publish them
+  // (it runs through the scratch), otherwise a barrier here
+  if constexpr (!SPLIT) __syncthreads();
   const float mu2 = 2.0f * sh.mu * a.mu_scale, shv = a.shift * sh.inv_old;
   float2* xb = a.xout + (size_t)b * a.n_out;
   const float2* dp = a.dp + (size_t)b * a.dp_stride;
@@ -844,10 +844,16 @@ __device__ __forceinline__ void last_first_tile(const PassArgs& a, float2 (&v)[T
   if (a.loss_out && g0 == 0 && tid == 0)
     a.loss_out[b] = sum_partials(a.loss_part + (size_t)b * a.loss_cpp, a.loss_cpp);
   rw.store(rowtw);
-  // the first FFT's scratch reads done; row twiddles visible (with SPLIT the
-  // first FFT ran in scr1 and the second FFT's first barrier orders the table)
-  if constexpr (!SPLIT) __syncthreads();
-  fft_blk_to_s3<TL, -1, TWS>(v, scratch, p, rho, t, tw);
+  if constexpr (SPLIT) {
+    // the first FFT ran in scr1; the second FFT's first barrier orders the row
+    // twiddles before their use and every access to scr1 before the next
+    // tile's load into it
+    fence_proxy_async_smem();
+    fft_blk_to_s3<TL, -1, TWS>(v, scratch, p, rho, t, tw, issue);
+  } else {
+    __syncthreads();  // the first FFT's scratch reads done; row twiddles visible
+    fft_blk_to_s3<TL, -1, TWS>(v, scratch, p, rho, t, tw);
+  }
   twiddle_store<TL>(v, a, b, g, t, f0, A, rowtw);
 }
 
