@@ -13,9 +13,10 @@
 // access (x, y, D_l) and every exchange-buffer write is T consecutive elements
 // per warp instruction straight from registers. The exchange rows a MID/LAST
 // pass reads are brought into shared memory by 2D TMA loads with 128-byte
-// swizzle; in the persistent grid the next tile's load is issued as soon as
-// the current tile's slots are in registers, so it overlaps the current
-// tile's FFTs. Kernels are instantiated per tile shape (line length ELL, lines
+// swizzle; in the persistent grid the staging buffer then serves as the
+// scratch of the tile's first line FFT, and the next tile's load is issued
+// after the second FFT's first barrier, so it overlaps the rest of the tile.
+// Kernels are instantiated per tile shape (line length ELL, lines
 // per CTA T) and per transform direction, so that index arithmetic folds and
 // the inverse-transform exchanges resolve at compile time.
 #pragma once
