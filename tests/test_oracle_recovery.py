@@ -223,3 +223,27 @@ def test_gd_step_stability_threshold(seed, L):
         expected = abs(1.0 - 2.0 * f) ** T  # 0.8^40 or 1.2^40
         assert (ratio > 1.0) == grows, (f, ratio)
         assert 0.5 * expected <= ratio <= 2.0 * expected, (f, ratio, expected)
+
+
+def test_gd_warmup_ramp_follows_the_linearised_product():
+    """The warm-up ramp over many steps: near x*, along the top eigenvector v of
+    the linearised gradient map J, GD with mu_t = mu0 ramp_t m / sum(y) scales
+    the deviation by prod_t |1 - mu_t lambda_max|, ramp_t = 1 - exp(-(t+1)/tau0).
+    At mu0 = 0.4 of the stability limit every factor lies in (0, 1); the
+    oracle's GD must follow the product within 5% over 20 steps, which tells it
+    apart from a ramp shifted by one step (a factor 2 off)."""
+    n, alpha, L, seed, tau0, T = 8, 4, 2, 3, 20.0, 20
+    theta, x, y, fwd, adj, m = _problem(seed, n, alpha, L)
+    Ad = O.dense_structured_matrix(theta, n, m)
+    J = _linearised_gradient_matrix(Ad, Ad @ x[0])
+    ev, V = np.linalg.eigh(J)
+    dmax = (V[:n, -1] + 1j * V[n:, -1])[None]
+    mu0 = 0.4 * 2.0 * y.sum() / (m * ev[-1])
+    mu = mu0 * m / y.sum()
+    eps = 1e-7 * np.linalg.norm(x)
+    xT, _ = O.gradient_descent(x + eps * dmax, y, fwd, adj, T, mu0=mu0, tau0=tau0)
+    expected = np.prod([abs(1.0 - mu * (1.0 - np.exp(-(t + 1) / tau0)) * ev[-1]) for t in range(T)])
+    shifted = np.prod([abs(1.0 - mu * (1.0 - np.exp(-(t + 2) / tau0)) * ev[-1]) for t in range(T)])
+    ratio = np.linalg.norm(xT - x) / eps
+    assert abs(ratio / expected - 1.0) <= 0.05, (ratio, expected)
+    assert abs(ratio / shifted - 1.0) > 0.5, (ratio, shifted)
