@@ -173,26 +173,31 @@ __device__ __forceinline__ float2 root3(int k) {
 // u_r[j] = x[3 j + r] and U_r = DFT_M(u_r) (one sub-line each),
 //   X[k + s M] = sum_r W_ELL^(r k) W_3^(r s) U_r[k],   k < M, s < 3;
 // thread (t, p, rho) forms the outputs s = rho of its k = p + j P, reading the
-// three U_r[k] from the scratch. tw: table of W_ELL (entry i * TWS).
-template <class TL, int DIR, int TWS>
+// three U_r[k] from the scratch. tw: table of W_ELL (entry i * TWS). With
+// XSEP the U_r go through a second scratch `xsm` (free on entry), so no
+// barrier separates the sub-line FFTs' last reads from the exchange.
+template <class TL, int DIR, int TWS, bool XSEP = false>
 __device__ __forceinline__ void fft_s3_to_blk(float2 (&v)[TL::E], float2* sm, int p, int rho, int t,
-                                              const float2* tw) {
+                                              const float2* tw, float2* xsm = nullptr) {
   if constexpr (!TL::R3) {
     line_fft<TL::M, TL::T, DIR, TWS>(v, sm, p, t, tw);
   } else {
     constexpr int T = TL::T, T3 = 3 * TL::T, P = TL::P;
     line_fft<TL::M, T3, DIR, 3 * TWS>(v, sm, p, t + T * rho, tw);
-    __syncthreads();  // the sub-line FFTs' last scratch reads are done
+    if constexpr (!XSEP) {
+      __syncthreads();  // the sub-line FFTs' last scratch reads are done
+      xsm = sm;
+    }
 #pragma unroll
-    for (int j = 0; j < TL::E; ++j) sm[sidx<T3>(p + j * P, t + T * rho)] = v[j];
+    for (int j = 0; j < TL::E; ++j) xsm[sidx<T3>(p + j * P, t + T * rho)] = v[j];
     __syncthreads();
     const float2 c1 = root3<DIR>(rho), c2 = root3<DIR>(2 * rho);
 #pragma unroll
     for (int j = 0; j < TL::E; ++j) {
       const int k = p + j * P;
-      const float2 u0 = sm[sidx<T3>(k, t)];
-      const float2 u1 = mul_root<DIR>(sm[sidx<T3>(k, t + T)], tw[k * TWS]);
-      const float2 u2 = mul_root<DIR>(sm[sidx<T3>(k, t + 2 * T)], tw[2 * k * TWS]);
+      const float2 u0 = xsm[sidx<T3>(k, t)];
+      const float2 u1 = mul_root<DIR>(xsm[sidx<T3>(k, t + T)], tw[k * TWS]);
+      const float2 u2 = mul_root<DIR>(xsm[sidx<T3>(k, t + 2 * T)], tw[2 * k * TWS]);
       v[j] = padd(u0, padd(cmul(u1, c1), cmul(u2, c2)));
     }
   }
@@ -204,26 +209,36 @@ __device__ __forceinline__ void fft_s3_to_blk(float2 (&v)[TL::E], float2* sm, in
 // thread (t, p, rho) forms u_rho at its k = p + j P from the three block
 // values read from the scratch, then the sub-line FFT. The caller
 // synchronises before the call if the scratch was in use. hook() runs once
-// after the first CTA barrier of the transform (none for single-stage lines).
-template <class TL, int DIR, int TWS, class Hook = NoHook>
+// after a CTA barrier that every thread reaches after its last access to the
+// scratch it ran in before the call (none for single-stage lines). With XSEP
+// the block values go through a second scratch `xsm` (free on entry), so no
+// barrier separates their reads from the sub-line FFTs; hook() then runs
+// after the sub-line FFTs' first barrier, once every thread has read xsm.
+template <class TL, int DIR, int TWS, bool XSEP = false, class Hook = NoHook>
 __device__ __forceinline__ void fft_blk_to_s3(float2 (&v)[TL::E], float2* sm, int p, int rho, int t,
-                                              const float2* tw, const Hook& hook = Hook()) {
+                                              const float2* tw, const Hook& hook = Hook(), float2* xsm = nullptr) {
   if constexpr (TL::R3) {
     constexpr int T = TL::T, T3 = 3 * TL::T, P = TL::P;
+    if constexpr (!XSEP) xsm = sm;
 #pragma unroll
-    for (int j = 0; j < TL::E; ++j) sm[sidx<T3>(p + j * P, t + T * rho)] = v[j];
+    for (int j = 0; j < TL::E; ++j) xsm[sidx<T3>(p + j * P, t + T * rho)] = v[j];
     __syncthreads();
-    hook();
+    if constexpr (!XSEP) hook();
     const float2 c1 = root3<DIR>(rho), c2 = root3<DIR>(2 * rho);
 #pragma unroll
     for (int j = 0; j < TL::E; ++j) {
       const int k = p + j * P;
-      const float2 x0 = sm[sidx<T3>(k, t)], x1 = sm[sidx<T3>(k, t + T)], x2 = sm[sidx<T3>(k, t + 2 * T)];
+      const float2 x0 = xsm[sidx<T3>(k, t)], x1 = xsm[sidx<T3>(k, t + T)], x2 = xsm[sidx<T3>(k, t + 2 * T)];
       const float2 u = padd(x0, padd(cmul(x1, c1), cmul(x2, c2)));
       v[j] = mul_root<DIR>(u, tw[rho * k * TWS]);
     }
-    __syncthreads();  // every block value read before the sub-line FFT writes the scratch
-    line_fft<TL::M, T3, DIR, 3 * TWS>(v, sm, p, t + T * rho, tw);
+    if constexpr (XSEP) {
+      fence_proxy_async_smem();  // xsm may next be written by a TMA load (issued by hook)
+      line_fft<TL::M, T3, DIR, 3 * TWS>(v, sm, p, t + T * rho, tw, hook);
+    } else {
+      __syncthreads();  // every block value read before the sub-line FFT writes the scratch
+      line_fft<TL::M, T3, DIR, 3 * TWS>(v, sm, p, t + T * rho, tw);
+    }
   } else {
     line_fft<TL::M, TL::T, DIR, TWS>(v, sm, p, t, tw, hook);
   }
@@ -625,7 +640,7 @@ __device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], 
   RowTw<TL> rw;
   rw.load(a, g0, DB);
   float2 A = tw_m<TL>(a, g * f0, DB);
-  fft_s3_to_blk<TL, DA, TWS>(v, SPLIT ? scr1 : scratch, p, rho, t, tw);
+  fft_s3_to_blk<TL, DA, TWS, SPLIT>(v, SPLIT ? scr1 : scratch, p, rho, t, tw, scratch);
   fsum2 acc{0.f, 0.f};
   if (vs) {
     __syncthreads();  // sh.scale visible
@@ -658,7 +673,7 @@ __device__ __forceinline__ void mid_tile(const PassArgs& a, float2 (&v)[TL::E], 
     // the second FFT's first barrier orders the row twiddles before their use
     // and every access to scr1 before the next tile's load into it
     fence_proxy_async_smem();
-    fft_blk_to_s3<TL, DB, TWS>(v, scratch, p, rho, t, tw, issue);
+    fft_blk_to_s3<TL, DB, TWS, SPLIT>(v, scratch, p, rho, t, tw, issue, scr1);
   } else {
     __syncthreads();  // first FFT's scratch reads done; row twiddles visible
     fft_blk_to_s3<TL, DB, TWS>(v, scratch, p, rho, t, tw);
@@ -704,7 +719,7 @@ __device__ __forceinline__ void last_tile(const PassArgs& a, float2 (&v)[TL::E],
                      : 1.0f;
     sh.mu = a.mu ? a.mu[b] : 0.f;
   }
-  fft_s3_to_blk<TL, DA, TWS>(v, SPLIT ? scr1 : scratch, p, rho, t, tw);
+  fft_s3_to_blk<TL, DA, TWS, SPLIT>(v, SPLIT ? scr1 : scratch, p, rho, t, tw, scratch);
   if constexpr (SPLIT) fence_proxy_async_smem();
   __syncthreads();  // tile scalars visible (and, with SPLIT, scr1 free for the next load)
   if constexpr (SPLIT) issue();
@@ -801,7 +816,7 @@ __device__ __forceinline__ void last_first_tile(const PassArgs& a, float2 (&v)[T
   RowTw<TL> rw;
   rw.load(a, g0, -1);
   const float2 A = tw_m<TL>(a, g * f0, -1);
-  fft_s3_to_blk<TL, 1, TWS>(v, SPLIT ? scr1 : scratch, p, rho, t, tw);
+  fft_s3_to_blk<TL, 1, TWS, SPLIT>(v, SPLIT ? scr1 : scratch, p, rho, t, tw, scratch);
   // tile scalars visible: with SPLIT the first FFT's own barriers publish them
   // (it runs through the scratch), otherwise a barrier here
   if constexpr (!SPLIT) __syncthreads();
@@ -850,7 +865,7 @@ __device__ __forceinline__ void last_first_tile(const PassArgs& a, float2 (&v)[T
     // twiddles before their use and every access to scr1 before the next
     // tile's load into it
     fence_proxy_async_smem();
-    fft_blk_to_s3<TL, -1, TWS>(v, scratch, p, rho, t, tw, issue);
+    fft_blk_to_s3<TL, -1, TWS, SPLIT>(v, scratch, p, rho, t, tw, issue, scr1);
   } else {
     __syncthreads();  // the first FFT's scratch reads done; row twiddles visible
     fft_blk_to_s3<TL, -1, TWS>(v, scratch, p, rho, t, tw);

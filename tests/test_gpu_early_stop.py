@@ -112,12 +112,13 @@ def test_power_iteration_early_stop_matches_oracle(Plan, B, n, m, L, seed, tol, 
     assert (torch.linalg.vector_norm(x3 - x2) / torch.linalg.vector_norm(x2)).item() <= 1e-6
 
 
-@pytest.mark.parametrize("kind", ["radix3", "alpha<1", "2d odd L"])
+@pytest.mark.parametrize("kind", ["radix3", "radix3 lines", "alpha<1", "2d odd L"])
 def test_early_stop_calls_on_every_plan_kind(Plan, kind):
     """With a zero tolerance both early-stopping calls run every step and give
     the plain calls' results (chunk boundaries only change the kernel split)."""
     from paper_2409_05734_gb300 import Plan2D
     plan = {"radix3": lambda: Plan(100, 384, 2, 7),
+            "radix3 lines": lambda: Plan(3000, 3 * 2 ** 12, 3, 7),
             "alpha<1": lambda: Plan(512, 300, 2, 7),
             "2d odd L": lambda: Plan2D(12, 10, 16, 3, 7)}[kind]()
     B = 2

@@ -25,11 +25,12 @@ def sr():
 def _plans(sr):
     return [("pow2", sr.Plan(200, 1024, 2, 3)),
             ("radix3", sr.Plan(200, 768, 2, 4)),
+            ("radix3 lines", sr.Plan(2000, 3 * 2 ** 13, 2, 8)),
             ("alpha<1", sr.Plan(1024, 700, 2, 5)),
             ("2d odd L", sr.Plan2D(20, 24, 32, 3, 6))]
 
 
-@pytest.mark.parametrize("kind", ["pow2", "radix3", "alpha<1", "2d odd L"])
+@pytest.mark.parametrize("kind", ["pow2", "radix3", "radix3 lines", "alpha<1", "2d odd L"])
 def test_solver_calls_capture_and_replay(sr, kind):
     plan = dict(_plans(sr))[kind]
     B = 3

@@ -31,7 +31,8 @@ def rel(a, b):
 # benchmark's ragged workload)
 SHAPES = [(64, 256, 2), (64, 256, 2), (64, 256, 2), (100, 512, 1), (100, 512, 1), (30, 96, 3),
           (1024, 4096, 2), (1024, 4096, 2), (500, 1536, 2), (16, 64, 1), (3000, 16384, 3),
-          (20000, 2 ** 17, 2), (20000, 2 ** 17, 2), (2 ** 16, 2 ** 19, 3)]
+          (20000, 2 ** 17, 2), (20000, 2 ** 17, 2), (2 ** 16, 2 ** 19, 3),
+          (5000, 3 * 2 ** 14, 2), (5000, 3 * 2 ** 14, 2)]
 BASE = 20240905
 
 

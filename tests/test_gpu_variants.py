@@ -45,7 +45,7 @@ def test_one_layer_plus_extra_fft(Plan, n, m, B):
     assert rel(xa, want_a) <= 1e-5
 
 
-@pytest.mark.parametrize("n,m,L", [(100, 512, 2), (64, 192, 3), (512, 300, 2)])
+@pytest.mark.parametrize("n,m,L", [(100, 512, 2), (64, 192, 3), (512, 300, 2), (4000, 3 * 2 ** 13, 2)])
 def test_batch_seeds_give_each_problem_its_own_operator(Plan, n, m, L):
     """Problem b of the batch uses the phases of seeds[b] (power-of-two, radix-3
     and alpha < 1 plans); a call with another batch size is refused."""
