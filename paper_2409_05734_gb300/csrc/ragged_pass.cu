@@ -262,12 +262,14 @@ __device__ __noinline__ bool rg_qtile(RgQCtx& cx, const PassArgs& a, const RgIte
     }
     const bool ok = mbar_wait_bounded(cx.bar, (uint32_t)(cx.waits & 1));
     ++cx.waits;
+    // the slots are read whatever the wait's outcome (in bounds either way);
+    // one barrier then frees the staging buffer and tells every thread
+    // whether a wait gave up
+    load_staged<TL>(cx.smem + RgSmem::stage, t, p, rho, v);
     if (!__syncthreads_and(ok)) {
       if (threadIdx.x == 0) atomicExch(cx.err, (int)SR_ERR_TIMEOUT);
       return false;
     }
-    load_staged<TL>(cx.smem + RgSmem::stage, t, p, rho, v);
-    __syncthreads();  // slots in registers (staging free)
     if (threadIdx.x < 32) rg_prep_next(cx);
   } else {
     bool ok = true;
