@@ -229,6 +229,34 @@ def _oracle_ragged_worker(task):
     return oracle_ragged_solve(*task)
 
 
+def oracle_leg_solve(t):
+    """The FP64 oracle's whole solve of problem 0 of a bench leg from the same
+    signal, start vector and phases as the GPU run (the oracle forms its own
+    y): t = (kind, n, m, L, seed, sp, gd, signal), kind "1d" (signal_gaussian)
+    or "2d" (t[1] = h = w image side, t[2] = grid side S, phase images of
+    seed). Returns the final iterate."""
+    import oracle as O
+    import synthetic as S
+    kind, n, m, L, seed, sp, gd, B = t
+    if kind == "2d":
+        h, S_ = n, m
+        fwd, adj = O.structured_ops_2d(S.phases(seed, L, S_ * S_), h, h, S_)
+        x = S.phase_image_ellipses(seed, B, h, h)[:1]
+        v0 = S.start_vector(seed, B, h * h)[:1]
+    else:
+        fwd, adj = O.structured_ops(S.phases(seed, L, m), n, m)
+        x = S.signal_gaussian(seed, B, n)[:1]
+        v0 = S.start_vector(seed, B, n)[:1]
+    y = np.abs(fwd(x)) ** 2
+    x0 = O.spectral_init(y, v0, fwd, adj, sp, mode="optimal", lam=-1.0)
+    xT, _ = O.gradient_descent(x0, y, fwd, adj, gd, mu0=MU0, tau0=TAU0)
+    return xT[0]
+
+
+def _oracle_leg_worker(task):
+    return oracle_leg_solve(task)
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -255,6 +283,9 @@ class OraclePool:
 
     def ragged_solves(self, tasks):
         return self.pool.map(_oracle_ragged_worker, tasks)
+
+    def leg_solves(self, tasks):
+        return self.pool.map(_oracle_leg_worker, tasks)
 
     def solves(self, W, problems, seed):
         """Each problem solved as given and with its start vector perturbed."""
@@ -582,7 +613,7 @@ def radix3_workload(torch, dev, flush):
     20 power + 100 GD iterations."""
     from paper_2409_05734_gb300 import Plan
     import synthetic as S
-    out = {}
+    out, parity = {}, []
     n, L, B, sp, gd = 2 ** 16, 2, 32, 20, 100
     for alpha, m in ((1.5, 3 * 2 ** 15), (3, 3 * 2 ** 16), (6, 3 * 2 ** 17)):
         plan = Plan(n, m, L, 31)
@@ -598,6 +629,8 @@ def radix3_workload(torch, dev, flush):
             plan.gd_solve(y, x, gd, mu0=MU0, tau0=TAU0)
 
         ms = timed_graph(torch, solve, flush)
+        parity.append({"leg": f"alpha={alpha}", "task": ("1d", n, m, L, 31, sp, gd, B),
+                       "x_gpu": x[0].cpu().numpy().astype(np.complex128)})
         it = sp + gd
         W = dict(n=n, m=m, L=L, B=B)
         out[f"alpha={alpha}"] = {"m": m, "split": list(plan.tuning[:2]), "ms_per_solve": ms,
@@ -607,7 +640,7 @@ def radix3_workload(torch, dev, flush):
         del plan
     return {"workload": f"n = 2^16, L = {L}, B = {B}, x ~ CN(0, I), noiseless, {sp} power + {gd} GD iterations; "
                         "m = 3 * 2^a runs on the four-step passes with radix-3 lines (192, 384 or 768 points: a radix-3 step inside the line FFT); autotuned split and grid",
-            **out}
+            **out, "_parity_inputs": parity}
 
 
 def two_d_workload(torch, dev, flush):
@@ -617,7 +650,7 @@ def two_d_workload(torch, dev, flush):
     odd layer count leaves the forward on the transposed grid."""
     from paper_2409_05734_gb300 import Plan2D
     import synthetic as S
-    out = {}
+    out, parity = {}, []
     h = w = 128
     S_, B, sp, gd = 256, 64, 100, 500
     x_np = S.phase_image_ellipses(20240905, B, h, w)
@@ -634,6 +667,8 @@ def two_d_workload(torch, dev, flush):
             plan.gd_solve(y, x, gd, mu0=MU0, tau0=TAU0)
 
         ms = timed_graph(torch, solve, flush)
+        parity.append({"leg": f"L={L}", "task": ("2d", h, S_, L, 20240905, sp, gd, B),
+                       "x_gpu": x[0].cpu().numpy().astype(np.complex128)})
         it = sp + gd
         W = dict(n=h * w, m=S_ * S_, L=L, B=B)
         out[f"L={L}"] = {"ms_per_solve": ms, "problem_iters_per_s": B * it / (ms / 1e3),
@@ -643,7 +678,7 @@ def two_d_workload(torch, dev, flush):
         del plan
     return {"workload": f"B = {B} phantom-like phase images {h} x {w} (Philox ellipses, phase in [-pi/2, pi/2)) "
                         f"in a {S_} x {S_} grid (alpha = 4), 2D unitary DFTs, noiseless, {sp} power (optimal "
-                        f"weights) + {gd} GD iterations, graph-replayed", **out}
+                        f"weights) + {gd} GD iterations, graph-replayed", **out, "_parity_inputs": parity}
 
 
 def forward_time_vs_size(torch, dev, flush, reps: int = 5):
@@ -804,7 +839,7 @@ def small_m_workload(torch, dev, flush):
     iterations, graph-replayed, for m = 256, 1024 and 4096."""
     from paper_2409_05734_gb300 import Plan
     import synthetic as S
-    out = {}
+    out, parity = {}, []
     B, L, sp, gd = 64, 2, 100, 500
     for m in (256, 1024, 4096):
         n = m // 4
@@ -820,12 +855,14 @@ def small_m_workload(torch, dev, flush):
             plan.gd_solve(y, x, gd, mu0=MU0, tau0=TAU0)
 
         ms = timed_graph(torch, solve, flush)
+        parity.append({"leg": f"m={m}", "task": ("1d", n, m, L, 41, sp, gd, B),
+                       "x_gpu": x[0].cpu().numpy().astype(np.complex128)})
         out[f"m={m}"] = {"n": n, "ms_per_solve": ms, "problem_iters_per_s": B * (sp + gd) / (ms / 1e3),
                          "median_rel_err_global_phase": median_rel_err(torch, x, x_true)}
         plan.check()
         del plan
     return {"workload": f"B = {B}, n = m / 4, L = {L}, x ~ CN(0, I), noiseless, {sp} power + {gd} GD iterations, "
-                        "one launch per call (whole solves in one CTA per problem)", **out}
+                        "one launch per call (whole solves in one CTA per problem)", **out, "_parity_inputs": parity}
 
 
 def layers_experiment(torch, dev, flush, sp=1000, B=32):
@@ -1197,6 +1234,9 @@ def run_ours(args):
         line["differentiable_operator"] = autograd_workload(torch, dev, flush)
         line["robustness_sweep_bounded"] = robustness_sweep(torch, dev, flush, SWEEP_BOUNDED, dense=False)
         line["layer_experiment_bounded"] = layers_experiment(torch, dev, flush, sp=300, B=16)
+    # problem 0 of each of these legs is re-solved by the oracle below
+    leg_parity = {k: line[k].pop("_parity_inputs") for k in ("radix3_batch", "two_dimensional", "small_m")
+                  if k in line}
     ragged_parity = None
     if rank == 0 and not args.no_ragged:
         line["ragged_batch"] = ragged_workload(torch, dev, flush)
@@ -1214,6 +1254,15 @@ def run_ours(args):
         sampled = (0, 9, 21, 30, 42, 51, 59, 63)
         res = pool.solves(W, sampled, seed)
         t_par = time.perf_counter() - t0
+        for leg, items in leg_parity.items():
+            xos = pool.leg_solves([q["task"] for q in items])
+            rows = [{"case": q["leg"], "rel_diff_vs_oracle": float(np.linalg.norm(q["x_gpu"] - xo) / np.linalg.norm(xo))}
+                    for q, xo in zip(items, xos)]
+            line[leg]["oracle_parity"] = {
+                "what": "final iterate of problem 0 of the timed solve against the FP64 oracle's solve from the "
+                        "same signal, start vector and phases (the oracle forms its own y); "
+                        "rel_diff = ||x_gpu - x_oracle|| / ||x_oracle||",
+                "cases": rows, "max_rel_diff_vs_oracle": max(r["rel_diff_vs_oracle"] for r in rows)}
         if ragged_parity:
             R = RAGGED
             rres = pool.ragged_solves([(q["n"], q["m"], q["L"], q["seed"], R["parity_sp"], R["parity_gd"], R["mu0"],
