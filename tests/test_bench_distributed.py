@@ -84,3 +84,29 @@ def test_only_legs_resolve_to_workload_functions():
     for name, fn in bench.EXTRA_LEGS.items():
         assert callable(getattr(bench, fn)), name
     assert {"sweep", "layers", "small", "autograd", "radix3", "two_d", "forward_curve"} <= set(bench.EXTRA_LEGS)
+
+
+def test_leg_parity_solver_is_the_oracle_protocol():
+    """The bench's per-leg oracle solve (problem 0 of a leg, 1D and 2D) is the
+    oracle's spectral initialisation plus GD with the bench's step rule on the
+    leg's own signal, start vector and phases."""
+    import numpy as np
+    import bench
+    import oracle as O
+    import synthetic as S
+    n, m, L, seed, sp, gd, B = 16, 64, 2, 5, 3, 4, 2
+    got = bench.oracle_leg_solve(("1d", n, m, L, seed, sp, gd, B))
+    fwd, adj = O.structured_ops(S.phases(seed, L, m), n, m)
+    x = S.signal_gaussian(seed, B, n)[:1]
+    y = np.abs(fwd(x)) ** 2
+    x0 = O.spectral_init(y, S.start_vector(seed, B, n)[:1], fwd, adj, sp, mode="optimal", lam=-1.0)
+    want, _ = O.gradient_descent(x0, y, fwd, adj, gd, mu0=bench.MU0, tau0=bench.TAU0)
+    assert np.array_equal(got, want[0])
+    h, S_ = 4, 8
+    got2 = bench.oracle_leg_solve(("2d", h, S_, 3, seed, sp, gd, B))
+    fwd2, adj2 = O.structured_ops_2d(S.phases(seed, 3, S_ * S_), h, h, S_)
+    x2 = S.phase_image_ellipses(seed, B, h, h)[:1]
+    y2 = np.abs(fwd2(x2)) ** 2
+    x02 = O.spectral_init(y2, S.start_vector(seed, B, h * h)[:1], fwd2, adj2, sp, mode="optimal", lam=-1.0)
+    want2, _ = O.gradient_descent(x02, y2, fwd2, adj2, gd, mu0=bench.MU0, tau0=bench.TAU0)
+    assert np.array_equal(got2, want2[0])
