@@ -30,10 +30,12 @@
  *   free of allocation. Concurrent calls on one plan must not overlap in time
  *   (they share the workspace); use one plan per stream.
  * - Supported sizes: m = 2^a with 4 <= m <= 2^24, or m = 3 * 2^a with
- *   4 <= 2^a <= 2^22 (oversampling ratios such as 1.5, 3 and 6; the DFT of
- *   length m is then one radix-3 step around three power-of-two DFTs, run
- *   through an inner plan that holds a second workspace of 2 * B_cap * m c64);
- *   1 <= n <= m, 1 <= L <= 8, 1 <= B <= 65535 (B <= 21845 when m = 3 * 2^a).
+ *   4 <= 2^a <= 2^22 (oversampling ratios such as 1.5, 3 and 6). For
+ *   3 * 2^12 <= m <= 3 * 2^20 the four-step passes take lines of 192, 384 or
+ *   768 points with a radix-3 step inside the line FFT; other radix-3 lengths
+ *   run one radix-3 step around three power-of-two DFTs on an inner plan that
+ *   holds a second workspace of 2 * B_cap * m c64 (B <= 21845 there);
+ *   1 <= n <= m, 1 <= L <= 8, 1 <= B <= 65535.
  *   Other sizes return SR_ERR_UNSUPPORTED. sr_forward_noalloc takes
  *   power-of-two m only.
  * - Every call returns SR_OK or an error code; sr_last_error() gives a
@@ -155,8 +157,9 @@ sr_status sr_plan_reserve(sr_plan* plan, int B);
  * buffers to anything else). The paper has no counterpart (launch parameters
  * of this implementation). */
 sr_status sr_plan_autotune(sr_plan* plan, int B, void* stream);
-/* Sets the four-step split m = m1 * m2 of a 1D plan (for a plan with m =
- * 3 * 2^a, of its inner power-of-two plan): layout X holds m2 lines of m1
+/* Sets the four-step split m = m1 * m2 of a 1D plan (for a radix-3 length
+ * run on an inner plan, of that plan; one of m1, m2 may be a radix-3 line of
+ * 192, 384 or 768 points): layout X holds m2 lines of m1
  * points, layout Y m1 lines of m2 points. SR_ERR_UNSUPPORTED (plan unchanged)
  * when m1 does not divide m or a line length of the split has no pass kernels,
  * and for 2D plans (their split is the S x S grid). Waits for the device and
