@@ -39,7 +39,8 @@ def _loss_parts(seed, B, m):
     return c, w
 
 
-@pytest.mark.parametrize("n,m,L,B", [(256, 1024, 2, 3), (100, 512, 1, 2), (37, 128, 3, 4), (5000, 2 ** 14, 2, 2)])
+@pytest.mark.parametrize("n,m,L,B", [(256, 1024, 2, 3), (100, 512, 1, 2), (37, 128, 3, 4), (5000, 2 ** 14, 2, 2),
+                                     (3000, 3 * 2 ** 13, 2, 2), (20, 48, 2, 2)])
 def test_backward_matches_oracle(sr, n, m, L, B):
     seed = n + m
     plan = sr.Plan(n, m, L, seed)
