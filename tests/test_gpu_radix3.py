@@ -74,8 +74,9 @@ def test_radix3_forward_adjoint(sr, n, m, L, B):
     assert_close_elementwise(xa, O.adjoint(w, theta, n))
 
 
-def test_radix3_loss_grad(sr):
-    n, m, L, B = 64, 192, 2, 3
+@pytest.mark.parametrize("n,m", [(64, 192), (3000, 3 * 2 ** 13)])  # inner-plan form; radix-3 lines
+def test_radix3_loss_grad(sr, n, m):
+    L, B = 2, 3
     seed = 11
     plan = sr.Plan(n, m, L, seed)
     theta = S.phases(seed, L, m)
@@ -89,9 +90,10 @@ def test_radix3_loss_grad(sr):
     assert_close_elementwise(host(g), g_o)
 
 
+@pytest.mark.parametrize("n,m", [(64, 192), (3000, 3 * 2 ** 13)])
 @pytest.mark.parametrize("weight", ["identity", "optimal"])
-def test_radix3_spectral_init(sr, weight):
-    n, m, L, B, T = 64, 192, 2, 3, 50
+def test_radix3_spectral_init(sr, weight, n, m):
+    L, B, T = 2, 3, 50
     seed = 20240905
     plan = sr.Plan(n, m, L, seed)
     theta = S.phases(seed, L, m)
@@ -105,10 +107,11 @@ def test_radix3_spectral_init(sr, weight):
         assert rel(got[b], ref[b]) <= 1e-4
 
 
-def test_radix3_gradient_descent_alpha_3(sr):
-    """n = 64, alpha = 3 (m = 192), L = 2: 50 power iterations, then 300 GD steps
-    with the warm-up step schedule; loss history and final estimate vs the oracle."""
-    n, m, L = 64, 192, 2
+@pytest.mark.parametrize("n,m", [(64, 192), (4096, 3 * 2 ** 12)])  # inner-plan form; radix-3 lines
+def test_radix3_gradient_descent_alpha_3(sr, n, m):
+    """alpha = 3 (m = 3n), L = 2: 50 power iterations, then 300 GD steps with
+    the warm-up step schedule; loss history and final estimate vs the oracle."""
+    L = 2
     seed = 20240905
     plan = sr.Plan(n, m, L, seed)
     theta = S.phases(seed, L, m)
